@@ -1,0 +1,678 @@
+/*
+ * Plain CPU oracle for the sparse hot path -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  The product path never calls it.  It shares no code,
+ * header, table or constant with the CUDA library.
+ *
+ * Everything here is the plain definition, computed sequentially in IEEE
+ * double (compiled with -ffp-contract=off, so no fused multiply-adds):
+ *
+ *   SpMV      y = alpha*A*x + beta*y  for the formats the paper lists
+ *             (Coo, Csr, Ell, Hybrid; Section 1, contributions list).
+ *             Each row sum runs left to right in storage order.  beta == 0
+ *             overwrites y without reading it (BLAS convention).
+ *   Formats   ELL / COO / HYB as defined by Bell & Garland, "Implementing
+ *             sparse matrix-vector multiplication on throughput-oriented
+ *             processors", SC'09.  ELL is column-major with stride
+ *             round_up(n, 32), padding col = -1, val = +0.0.
+ *   Solvers   CG (Hestenes & Stiefel 1952; Saad, Iterative Methods for Sparse
+ *             Linear Systems, 2nd ed., Alg. 6.18), BiCGSTAB (van der Vorst
+ *             1992; Saad Alg. 7.7), restarted GMRES(m) with modified
+ *             Gram-Schmidt and Givens rotations (Saad & Schultz 1986; Saad
+ *             Alg. 6.9/6.11), and mixed-precision iterative refinement (an
+ *             FP64 outer residual loop around an inner solve whose matrix and
+ *             vectors are stored in FP32; Buttari et al. 2007).
+ *
+ * The paper (Section 1) names these formats and solvers but prints no
+ * algorithm for them, so the textbook definitions above are the reference.
+ * Readings taken where the paper is silent:
+ *   - stopping: ||r_k|| <= tol*||b|| on the recurrence residual, then the true
+ *     residual b - A x is formed; if that misses the tolerance it replaces r
+ *     and the iteration goes on (CG keeps p; BiCGSTAB restarts its
+ *     recurrences); the reported residual is always the true one;
+ *   - b == 0 returns x = 0 after 0 iterations;
+ *   - breakdown on exact zeros only: CG p.q <= 0; BiCGSTAB rhat.r == 0,
+ *     rhat.v == 0, t.t == 0 or omega == 0; GMRES a zero rotation denominator.
+ *     GMRES h_{j+1,j} == 0 is a lucky breakdown (exact solve).
+ *   - hybrid ELL width K = largest k with #{rows: len >= k} >= 4096 and
+ *     3 * #{rows: len >= k} >= n (Bell-Garland heuristic); K = 0 is pure COO.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_OK = 0, OR_NOT_CONVERGED = 4, OR_BREAKDOWN = 5, OR_INVALID = 1 };
+
+static int g_threads = 1;
+
+/* Threads used by the row-parallel SpMV loops (CSR and ELL only; each row is
+ * still summed sequentially so the result does not depend on the count). */
+int or_set_threads(int t) {
+#ifdef _OPENMP
+  g_threads = t > 0 ? t : omp_get_max_threads();
+  return g_threads;
+#else
+  (void)t;
+  g_threads = 1;
+  return 1;
+#endif
+}
+
+int or_has_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+/* ---------------------------------------------------------------- SpMV -- */
+
+void or_spmv_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                 const double *x, double alpha, double beta, double *y) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(g_threads)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * x[col[k]];
+    y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
+  }
+}
+
+/* FP32 values, FP32 x and y, FP32 accumulation: every product and every
+ * partial sum is rounded to float. */
+void or_spmv_csr_f32(int64_t n, const int32_t *rp, const int32_t *col, const float *val,
+                     const float *x, float alpha, float beta, float *y) {
+  for (int64_t i = 0; i < n; ++i) {
+    float s = 0.0f;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      float p = val[k] * x[col[k]];
+      s = s + p;
+    }
+    y[i] = beta == 0.0f ? alpha * s : alpha * s + beta * y[i];
+  }
+}
+
+/* Error-free transformations (Dekker/Knuth TwoSum, FMA-based TwoProduct)
+ * with Neumaier accumulation: a near-exact row sum used to attribute a
+ * parity failure to summation order.  fma() is the correctly rounded C99
+ * function, so p + e == a*b exactly. */
+void or_spmv_csr_exact(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                       const double *x, double alpha, double beta, double *y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0, c = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      double a = val[k], b = x[col[k]];
+      double p = a * b;
+      double e = fma(a, b, -p);
+      double t = s + p;
+      c += (fabs(s) >= fabs(p)) ? (s - t) + p : (p - t) + s;
+      s = t;
+      c += e;
+    }
+    double row = s + c;
+    y[i] = beta == 0.0 ? alpha * row : alpha * row + beta * y[i];
+  }
+}
+
+int64_t or_ell_stride(int64_t n) { return (n + 31) / 32 * 32; }
+
+int32_t or_ell_width(int64_t n, const int32_t *rp) {
+  int32_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t len = rp[i + 1] - rp[i];
+    if (len > k) k = len;
+  }
+  return k;
+}
+
+/* ELL: entry k of row i at k*stride + i; padding col = -1, val = +0.0. */
+void or_csr_to_ell(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   int32_t K, int64_t stride, int32_t *ecol, double *eval) {
+  for (int64_t s = 0; s < (int64_t)K * stride; ++s) {
+    ecol[s] = -1;
+    eval[s] = 0.0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t len = rp[i + 1] - rp[i];
+    for (int32_t k = 0; k < len && k < K; ++k) {
+      ecol[(int64_t)k * stride + i] = col[rp[i] + k];
+      eval[(int64_t)k * stride + i] = val[rp[i] + k];
+    }
+  }
+}
+
+void or_spmv_ell(int64_t n, int32_t K, int64_t stride, const int32_t *ecol, const double *eval,
+                 const double *x, double alpha, double beta, double *y) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int32_t k = 0; k < K; ++k) {
+      int32_t c = ecol[(int64_t)k * stride + i];
+      if (c >= 0) s += eval[(int64_t)k * stride + i] * x[c];
+    }
+    y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
+  }
+}
+
+/* COO: row-major expansion of CSR in storage order. */
+void or_csr_to_coo(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   int32_t *crow, int32_t *ccol, double *cval) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      crow[k] = (int32_t)i;
+      ccol[k] = col[k];
+      cval[k] = val[k];
+    }
+}
+
+/* COO SpMV: per-row sums accumulated in entry order, then scaled.  The
+ * temporary t is the plain definition's per-row accumulator. */
+int or_spmv_coo(int64_t n, int64_t nnz, const int32_t *crow, const int32_t *ccol,
+                const double *cval, const double *x, double alpha, double beta, double *y) {
+  double *t = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!t) return OR_INVALID;
+  for (int64_t k = 0; k < nnz; ++k) t[crow[k]] += cval[k] * x[ccol[k]];
+  for (int64_t i = 0; i < n; ++i) y[i] = beta == 0.0 ? alpha * t[i] : alpha * t[i] + beta * y[i];
+  free(t);
+  return OR_OK;
+}
+
+/* Hybrid width: largest k with count(len >= k) >= max(4096, n/3). */
+int32_t or_hybrid_width(int64_t n, const int32_t *rp) {
+  int32_t maxlen = or_ell_width(n, rp);
+  int64_t *cnt = (int64_t *)calloc((size_t)maxlen + 2, sizeof(int64_t));
+  if (!cnt) return -1;
+  for (int64_t i = 0; i < n; ++i) cnt[rp[i + 1] - rp[i]] += 1;
+  /* turn the histogram into suffix counts: cnt[k] = #{len >= k} */
+  for (int64_t k = maxlen - 1; k >= 0; --k) cnt[k] += cnt[k + 1];
+  int32_t K = 0;
+  for (int32_t k = 0; k <= maxlen; ++k)
+    if (cnt[k] >= 4096 && 3 * cnt[k] >= n) K = k;
+  free(cnt);
+  return K;
+}
+
+/* Number of COO entries in the hybrid tail for width K. */
+int64_t or_hybrid_tail_nnz(int64_t n, const int32_t *rp, int32_t K) {
+  int64_t t = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t len = rp[i + 1] - rp[i];
+    if (len > K) t += len - K;
+  }
+  return t;
+}
+
+/* Hybrid: the first min(len, K) entries of each row go to ELL (width K),
+ * the rest to a row-major COO tail, both in storage order. */
+void or_csr_to_hybrid(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                      int32_t K, int64_t stride, int32_t *ecol, double *eval, int32_t *crow,
+                      int32_t *ccol, double *cval) {
+  or_csr_to_ell(n, rp, col, val, K, stride, ecol, eval);
+  int64_t t = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i] + K; k < rp[i + 1]; ++k) {
+      crow[t] = (int32_t)i;
+      ccol[t] = col[k];
+      cval[t] = val[k];
+      ++t;
+    }
+}
+
+/* Hybrid SpMV: each row adds its ELL entries then its COO entries, i.e. the
+ * CSR storage order. */
+int or_spmv_hybrid(int64_t n, int32_t K, int64_t stride, const int32_t *ecol, const double *eval,
+                   int64_t tail, const int32_t *crow, const int32_t *ccol, const double *cval,
+                   const double *x, double alpha, double beta, double *y) {
+  double *t = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!t) return OR_INVALID;
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t k = 0; k < K; ++k) {
+      int32_t c = ecol[(int64_t)k * stride + i];
+      if (c >= 0) t[i] += eval[(int64_t)k * stride + i] * x[c];
+    }
+  for (int64_t k = 0; k < tail; ++k) t[crow[k]] += cval[k] * x[ccol[k]];
+  for (int64_t i = 0; i < n; ++i) y[i] = beta == 0.0 ? alpha * t[i] : alpha * t[i] + beta * y[i];
+  free(t);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------- solvers -- */
+
+/* A CSR operator: FP64 values, or FP32 values with FP32 accumulation (the
+ * inner operator of mixed-precision refinement). */
+typedef struct {
+  int64_t n;
+  const int32_t *rp, *col;
+  const double *val;
+  const float *val32;
+} or_op;
+
+/* y = A x.  With FP32 values: the FP32 SpMV above on fl32(x), widened. */
+static void op_apply(const or_op *A, const double *x, double *y) {
+  if (A->val32) {
+    float *xs = (float *)malloc(sizeof(float) * (size_t)(A->n + 1));
+    float *ys = (float *)malloc(sizeof(float) * (size_t)(A->n + 1));
+    for (int64_t i = 0; i < A->n; ++i) xs[i] = (float)x[i];
+    or_spmv_csr_f32(A->n, A->rp, A->col, A->val32, xs, 1.0f, 0.0f, ys);
+    for (int64_t i = 0; i < A->n; ++i) y[i] = (double)ys[i];
+    free(xs);
+    free(ys);
+  } else {
+    for (int64_t i = 0; i < A->n; ++i) {
+      double s = 0.0;
+      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) s += A->val[k] * x[A->col[k]];
+      y[i] = s;
+    }
+  }
+}
+
+/* Storage rounding of a vector element: FP32 for the inner solve of the
+ * mixed-precision refinement, identity otherwise. */
+static inline double st(int f32, double v) { return f32 ? (double)(float)v : v; }
+
+static double dot(int64_t n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double nrm2(int64_t n, const double *a) { return sqrt(dot(n, a, a)); }
+
+/* r = b - A x (FP64 storage) */
+static void residual(const or_op *A, const double *b, const double *x, double *r, double *tmp) {
+  op_apply(A, x, tmp);
+  for (int64_t i = 0; i < A->n; ++i) r[i] = b[i] - tmp[i];
+}
+
+typedef struct {
+  int32_t status;
+  int32_t iterations;
+  int32_t outer_iterations;
+  int32_t pad;
+  double rel_residual;
+} or_result;
+
+/* Common solver context: A, the storage rounding flag, whether to verify a
+ * converged recurrence residual against the true residual, and an optional
+ * per-iteration history of ||r||/||b|| (recurrence or Givens estimate). */
+typedef struct {
+  const or_op *A;
+  int f32;
+  int true_check;
+  double *hist;
+  int32_t hist_len;
+} or_ctx;
+
+static void hist_put(const or_ctx *c, int32_t it, double v) {
+  if (c->hist && it >= 1 && it <= c->hist_len) c->hist[it - 1] = v;
+}
+
+/* CG (Saad Alg. 6.18), x holds x0 on entry and the iterate on exit. */
+static or_result cg_core(const or_ctx *c, const double *b, double *x, double tol, int32_t maxit) {
+  const or_op *A = c->A;
+  int64_t n = A->n;
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
+  double *r = calloc((size_t)n + 1, sizeof(double)), *p = calloc((size_t)n + 1, sizeof(double));
+  double *q = calloc((size_t)n + 1, sizeof(double)), *t = calloc((size_t)n + 1, sizeof(double));
+  double nb = nrm2(n, b);
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  residual(A, b, x, r, t);
+  for (int64_t i = 0; i < n; ++i) r[i] = st(c->f32, r[i]);
+  for (int64_t i = 0; i < n; ++i) p[i] = r[i];
+  double rho = dot(n, r, r);
+  int converged = sqrt(rho) <= tol * nb;
+  int32_t it = 0;
+  while (!converged && it < maxit) {
+    op_apply(A, p, q);
+    for (int64_t i = 0; i < n; ++i) q[i] = st(c->f32, q[i]);
+    double pq = dot(n, p, q);
+    if (!(pq > 0.0)) {
+      res.status = OR_BREAKDOWN;
+      break;
+    }
+    double alpha = rho / pq;
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] = st(c->f32, x[i] + alpha * p[i]);
+      r[i] = st(c->f32, r[i] - alpha * q[i]);
+    }
+    double rho_new = dot(n, r, r);
+    ++it;
+    hist_put(c, it, sqrt(rho_new) / nb);
+    if (sqrt(rho_new) <= tol * nb) {
+      if (!c->true_check) {
+        converged = 1;
+        break;
+      }
+      residual(A, b, x, t, q);
+      if (nrm2(n, t) <= tol * nb) {
+        converged = 1;
+        break;
+      }
+      for (int64_t i = 0; i < n; ++i) r[i] = t[i]; /* residual replacement */
+      rho_new = dot(n, r, r);
+    }
+    double beta = rho_new / rho;
+    for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, r[i] + beta * p[i]);
+    rho = rho_new;
+  }
+  res.iterations = it;
+  if (res.status == OR_OK && !converged) res.status = OR_NOT_CONVERGED;
+done:
+  if (nb == 0.0) {
+    res.rel_residual = 0.0;
+  } else {
+    residual(A, b, x, r, t);
+    res.rel_residual = nrm2(n, r) / nb;
+  }
+  free(r);
+  free(p);
+  free(q);
+  free(t);
+  return res;
+}
+
+/* BiCGSTAB (van der Vorst 1992; Saad Alg. 7.7). */
+static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, double tol,
+                               int32_t maxit) {
+  const or_op *A = c->A;
+  int64_t n = A->n;
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
+  size_t sz = (size_t)n + 1;
+  double *r = calloc(sz, 8), *rh = calloc(sz, 8), *p = calloc(sz, 8), *v = calloc(sz, 8);
+  double *s = calloc(sz, 8), *t = calloc(sz, 8), *w = calloc(sz, 8);
+  double nb = nrm2(n, b);
+  int converged = 0;
+  int32_t it = 0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  residual(A, b, x, r, w);
+  for (int64_t i = 0; i < n; ++i) r[i] = rh[i] = st(c->f32, r[i]);
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  converged = nrm2(n, r) <= tol * nb;
+  while (!converged && it < maxit) {
+    double rho_new = dot(n, rh, r);
+    if (rho_new == 0.0) {
+      res.status = OR_BREAKDOWN;
+      break;
+    }
+    double beta = (rho_new / rho) * (alpha / omega);
+    for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, r[i] + beta * (p[i] - omega * v[i]));
+    op_apply(A, p, v);
+    for (int64_t i = 0; i < n; ++i) v[i] = st(c->f32, v[i]);
+    double rv = dot(n, rh, v);
+    if (rv == 0.0) {
+      res.status = OR_BREAKDOWN;
+      break;
+    }
+    alpha = rho_new / rv;
+    for (int64_t i = 0; i < n; ++i) s[i] = st(c->f32, r[i] - alpha * v[i]);
+    ++it;
+    int restart = 0;
+    if (nrm2(n, s) <= tol * nb) {
+      for (int64_t i = 0; i < n; ++i) x[i] = st(c->f32, x[i] + alpha * p[i]);
+      hist_put(c, it, nrm2(n, s) / nb);
+      if (!c->true_check) {
+        converged = 1;
+        break;
+      }
+      residual(A, b, x, w, t);
+      if (nrm2(n, w) <= tol * nb) {
+        converged = 1;
+        break;
+      }
+      restart = 1;
+    } else {
+      op_apply(A, s, t);
+      for (int64_t i = 0; i < n; ++i) t[i] = st(c->f32, t[i]);
+      double tt = dot(n, t, t);
+      if (tt == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+      omega = dot(n, t, s) / tt;
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] = st(c->f32, x[i] + alpha * p[i] + omega * s[i]);
+        r[i] = st(c->f32, s[i] - omega * t[i]);
+      }
+      rho = rho_new;
+      double nr = nrm2(n, r);
+      hist_put(c, it, nr / nb);
+      if (nr <= tol * nb) {
+        if (!c->true_check) {
+          converged = 1;
+          break;
+        }
+        residual(A, b, x, w, t);
+        if (nrm2(n, w) <= tol * nb) {
+          converged = 1;
+          break;
+        }
+        restart = 1;
+      } else if (omega == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+    }
+    if (restart) { /* residual replacement restarts the recurrences */
+      for (int64_t i = 0; i < n; ++i) {
+        r[i] = w[i];
+        p[i] = v[i] = 0.0;
+      }
+      rho = alpha = omega = 1.0;
+    }
+  }
+  res.iterations = it;
+  if (res.status == OR_OK && !converged) res.status = OR_NOT_CONVERGED;
+done:
+  if (nb == 0.0) {
+    res.rel_residual = 0.0;
+  } else {
+    residual(A, b, x, r, w);
+    res.rel_residual = nrm2(n, r) / nb;
+  }
+  free(r);
+  free(rh);
+  free(p);
+  free(v);
+  free(s);
+  free(t);
+  free(w);
+  return res;
+}
+
+/* Restarted GMRES(m) with modified Gram-Schmidt and Givens rotations
+ * (Saad & Schultz 1986; Saad Alg. 6.9 and 6.11).  Iterations count Arnoldi
+ * steps; each cycle starts from the true residual. */
+static or_result gmres_core(const or_ctx *c, const double *b, double *x, double tol,
+                            int32_t maxit, int32_t m) {
+  const or_op *A = c->A;
+  int64_t n = A->n;
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
+  if (m < 1) m = 1;
+  size_t sz = (size_t)n + 1;
+  double *V = calloc(sz * (size_t)(m + 1), 8);
+  double *H = calloc((size_t)(m + 1) * (size_t)m, 8); /* H[i*m + j] = h_{i,j} */
+  double *cs = calloc((size_t)m, 8), *sn = calloc((size_t)m, 8);
+  double *g = calloc((size_t)m + 1, 8), *yv = calloc((size_t)m, 8);
+  double *r = calloc(sz, 8), *w = calloc(sz, 8), *tmp = calloc(sz, 8);
+  double nb = nrm2(n, b);
+  int converged = 0;
+  int32_t it = 0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  for (;;) {
+    residual(A, b, x, r, tmp);
+    for (int64_t i = 0; i < n; ++i) r[i] = st(c->f32, r[i]);
+    double beta = nrm2(n, r);
+    if (beta <= tol * nb) {
+      converged = 1;
+      break;
+    }
+    if (it >= maxit) break;
+    for (int64_t i = 0; i < n; ++i) V[i] = st(c->f32, r[i] / beta);
+    memset(g, 0, sizeof(double) * (size_t)(m + 1));
+    g[0] = beta;
+    int32_t k = 0;
+    int stop = 0;
+    for (int32_t j = 0; j < m && it < maxit; ++j) {
+      double *vj = V + (size_t)j * sz;
+      op_apply(A, vj, w);
+      for (int64_t i = 0; i < n; ++i) w[i] = st(c->f32, w[i]);
+      for (int32_t i = 0; i <= j; ++i) {
+        double *vi = V + (size_t)i * sz;
+        double h = dot(n, w, vi);
+        H[(size_t)i * m + j] = h;
+        for (int64_t e = 0; e < n; ++e) w[e] = st(c->f32, w[e] - h * vi[e]);
+      }
+      double hn = nrm2(n, w);
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int32_t i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      double den = sqrt(a * a + bb * bb);
+      ++it;
+      k = j + 1;
+      if (den == 0.0) {
+        res.status = OR_BREAKDOWN;
+        k = j;
+        stop = 2;
+        break;
+      }
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      hist_put(c, it, fabs(g[j + 1]) / nb);
+      if (hn == 0.0 || fabs(g[j + 1]) <= tol * nb) {
+        stop = 1;
+        break;
+      }
+      double *vn = V + (size_t)(j + 1) * sz;
+      for (int64_t i = 0; i < n; ++i) vn[i] = st(c->f32, w[i] / hn);
+    }
+    /* back substitution H[0:k,0:k] y = g[0:k], then x += V y */
+    for (int32_t i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int32_t l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * yv[l];
+      yv[i] = s / H[(size_t)i * m + i];
+    }
+    for (int64_t e = 0; e < n; ++e) {
+      double s = 0.0;
+      for (int32_t i = 0; i < k; ++i) s += V[(size_t)i * sz + e] * yv[i];
+      x[e] = st(c->f32, x[e] + s);
+    }
+    res.outer_iterations += 1;
+    if (stop == 2) break;
+    if (stop == 1 && !c->true_check) {
+      converged = 1;
+      break;
+    }
+  }
+  res.iterations = it;
+  if (res.status == OR_OK && !converged) res.status = OR_NOT_CONVERGED;
+done:
+  if (nb == 0.0) {
+    res.rel_residual = 0.0;
+  } else {
+    residual(A, b, x, r, tmp);
+    res.rel_residual = nrm2(n, r) / nb;
+  }
+  free(V);
+  free(H);
+  free(cs);
+  free(sn);
+  free(g);
+  free(yv);
+  free(r);
+  free(w);
+  free(tmp);
+  return res;
+}
+
+enum { OR_SOLVER_CG = 0, OR_SOLVER_BICGSTAB = 1, OR_SOLVER_GMRES = 2 };
+
+static or_result run_solver(const or_ctx *c, int solver, const double *b, double *x, double tol,
+                            int32_t maxit, int32_t restart) {
+  if (solver == OR_SOLVER_CG) return cg_core(c, b, x, tol, maxit);
+  if (solver == OR_SOLVER_BICGSTAB) return bicgstab_core(c, b, x, tol, maxit);
+  return gmres_core(c, b, x, tol, maxit, restart);
+}
+
+/* FP64 Krylov solve.  x: x0 on entry, the solution on exit.  hist (optional,
+ * hist_len entries) receives ||r_k||/||b|| per iteration. */
+int or_solve(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+             const double *b, double *x, double tol, int32_t maxit, int32_t restart,
+             double *hist, int32_t hist_len, or_result *out) {
+  or_op A = {n, rp, col, val, NULL};
+  or_ctx c = {&A, 0, 1, hist, hist_len};
+  *out = run_solver(&c, solver, b, x, tol, maxit, restart);
+  return out->status;
+}
+
+/* Mixed-precision iterative refinement: x = x0; repeat { r = b - A64 x in
+ * FP64; stop if ||r|| <= tol ||b||; solve A32 d = r with FP32-stored values
+ * and vectors (FP32 SpMV accumulation, FP64 dots and scalars) to
+ * ||r_inner|| <= inner_tol ||r||; x += d in FP64 }. */
+int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                const float *val32, const double *b, double *x, double tol, int32_t max_outer,
+                double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
+  or_op A64 = {n, rp, col, val, NULL};
+  or_op A32 = {n, rp, col, NULL, val32};
+  or_ctx inner = {&A32, 1, 0, NULL, 0};
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
+  size_t sz = (size_t)n + 1;
+  double *r = calloc(sz, 8), *d = calloc(sz, 8), *tmp = calloc(sz, 8);
+  double nb = nrm2(n, b);
+  int converged = 0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    converged = 1;
+  }
+  while (!converged) {
+    residual(&A64, b, x, r, tmp);
+    double nr = nrm2(n, r);
+    if (nr <= tol * nb) {
+      converged = 1;
+      break;
+    }
+    if (res.outer_iterations >= max_outer) break;
+    for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
+    or_result in = run_solver(&inner, solver, r, d, inner_tol, inner_maxit, restart);
+    res.iterations += in.iterations;
+    res.outer_iterations += 1;
+    for (int64_t i = 0; i < n; ++i) x[i] += d[i];
+  }
+  if (!converged) res.status = OR_NOT_CONVERGED;
+  if (nb == 0.0) {
+    res.rel_residual = 0.0;
+  } else {
+    residual(&A64, b, x, r, tmp);
+    res.rel_residual = nrm2(n, r) / nb;
+  }
+  free(r);
+  free(d);
+  free(tmp);
+  *out = res;
+  return res.status;
+}

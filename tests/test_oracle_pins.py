@@ -1,0 +1,405 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself.
+
+* SpMV (all formats) against a dense brute-force product on integer data
+  (exact in FP64), against closed-form Laplacian eigenpairs, and against
+  exact rational sums (fractions) for the compensated variant.
+* Conversions against an inverse written here (round trip to CSR) and the
+  padding / nnz invariants of the Bell-Garland formats.
+* The hybrid width rule against hand-derived cases (tests/golden).
+* Solvers against dense LU solves (numpy), the exact solution of b = A*1, the
+  n-step termination of CG and full GMRES, GMRES residual monotonicity and the
+  FP32 accuracy floor of a single mixed-precision refinement step.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2006_14290_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U64 = 2.0**-53
+U32 = 2.0**-24
+
+
+def dense(A):
+    D = np.zeros((A.n_rows, A.n_cols))
+    for i in range(A.n_rows):
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            D[i, A.col[k]] += A.val[k]
+    return D
+
+
+# ------------------------------------------------------------------ SpMV --
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (2.0, -3.0), (-1.0, 1.0), (0.0, 2.0)])
+def test_spmv_csr_dense_bruteforce_integer_exact(seed, alpha, beta):
+    rng = np.random.default_rng(seed)
+    A = I.random_csr(37, 29, 0.25, rng, integer_values=True, empty_rows=0.2, sort_cols=False)
+    x = rng.integers(-5, 6, 29).astype(float)
+    y0 = rng.integers(-5, 6, 37).astype(float)
+    y = O.spmv_csr(A, x, alpha, beta, y0)
+    np.testing.assert_array_equal(y, alpha * (dense(A) @ x) + beta * y0)
+
+
+def test_spmv_beta_zero_ignores_nan_in_y():
+    rng = np.random.default_rng(3)
+    A = I.random_csr(20, 20, 0.3, rng, integer_values=True)
+    x = rng.integers(-3, 4, 20).astype(float)
+    y0 = np.full(20, np.nan)
+    y = O.spmv_csr(A, x, 1.5, 0.0, y0)
+    assert np.all(np.isfinite(y))
+    np.testing.assert_array_equal(y, 1.5 * (dense(A) @ x))
+
+
+def test_spmv_nan_in_x_propagates_even_with_alpha_zero():
+    A = I.laplace2d_5pt(4)
+    x = np.ones(16)
+    x[5] = np.nan
+    y = O.spmv_csr(A, x, 0.0, 1.0, np.ones(16))
+    rows_touching = {i for i in range(16) for k in range(A.row_ptr[i], A.row_ptr[i + 1]) if A.col[k] == 5}
+    assert all(np.isnan(y[i]) for i in rows_touching)
+    assert all(y[i] == 1.0 for i in range(16) if i not in rows_touching)
+
+
+def _eig_check(A, v, lam):
+    y = O.spmv_csr(A, v)
+    normA = np.max(np.abs(A.val)) * np.max(np.diff(A.row_ptr))
+    assert np.max(np.abs(y - lam * v)) <= 10 * U64 * normA * np.max(np.abs(v)) * 4
+
+
+@pytest.mark.parametrize("N,p,q", [(6, 1, 1), (7, 2, 5), (9, 8, 3)])
+def test_laplace2d_closed_form_eigenpairs(N, p, q):
+    A = I.laplace2d_5pt(N)
+    i = np.arange(N)
+    sp_ = np.sin(p * math.pi * (i + 1) / (N + 1))
+    sq = np.sin(q * math.pi * (i + 1) / (N + 1))
+    v = (sp_[None, :] * sq[:, None]).reshape(-1)  # idx = i + N*j
+    lam = 4 - 2 * math.cos(p * math.pi / (N + 1)) - 2 * math.cos(q * math.pi / (N + 1))
+    _eig_check(A, v, lam)
+
+
+@pytest.mark.parametrize("N,pqr", [(5, (1, 2, 3)), (6, (6, 1, 2))])
+def test_stencil3d_7pt_closed_form_eigenpairs(N, pqr):
+    A = I.stencil3d_7pt(N)
+    i = np.arange(N)
+    s = [np.sin(m * math.pi * (i + 1) / (N + 1)) for m in pqr]
+    v = np.einsum("k,j,i->kji", s[2], s[1], s[0]).reshape(-1)
+    lam = 6 - 2 * sum(math.cos(m * math.pi / (N + 1)) for m in pqr)
+    _eig_check(A, v, lam)
+
+
+@pytest.mark.parametrize("N,pqr", [(5, (1, 1, 1)), (6, (2, 5, 3))])
+def test_stencil3d_27pt_closed_form_eigenpairs(N, pqr):
+    # A = 27 I - T (x) T (x) T with T = tridiag(1, 1, 1); T's eigenvalues are
+    # 1 + 2 cos(m pi / (N+1)) on the sine vectors.
+    A = I.stencil3d_27pt(N)
+    i = np.arange(N)
+    s = [np.sin(m * math.pi * (i + 1) / (N + 1)) for m in pqr]
+    v = np.einsum("k,j,i->kji", s[2], s[1], s[0]).reshape(-1)
+    lam = 27 - np.prod([1 + 2 * math.cos(m * math.pi / (N + 1)) for m in pqr])
+    _eig_check(A, v, lam)
+
+
+def test_spmv_invariants_rowsums_and_columns():
+    rng = np.random.default_rng(5)
+    A = I.random_csr(40, 33, 0.2, rng, integer_values=True, sort_cols=False)
+    D = dense(A)
+    np.testing.assert_array_equal(O.spmv_csr(A, np.ones(33)), D.sum(axis=1))
+    for j in (0, 7, 32):
+        e = np.zeros(33)
+        e[j] = 1.0
+        np.testing.assert_array_equal(O.spmv_csr(A, e), D[:, j])
+
+
+def test_spmv_exact_matches_rational_sum():
+    rng = np.random.default_rng(7)
+    lengths = [1, 5, 40, 200]
+    A = I.rows_csr(lengths, 50, rng)
+    # plant heavy cancellation: large +/- pairs
+    A.val[5:7] = [1e16, -1e16]
+    x = rng.uniform(-1, 1, 50)
+    y = O.spmv_csr_exact(A, x)
+    for i in range(len(lengths)):
+        exact = sum((Fraction(float(A.val[k])) * Fraction(float(x[A.col[k]]))
+                     for k in range(A.row_ptr[i], A.row_ptr[i + 1])), Fraction(0))
+        assert abs(Fraction(float(y[i])) - exact) <= Fraction(2 * U64) * abs(exact) + Fraction(1e-300)
+
+
+def test_spmv_f32_rounds_in_float_within_bound():
+    rng = np.random.default_rng(11)
+    A = I.rows_csr(rng.integers(1, 300, 200), 500, rng)
+    x = rng.uniform(-1, 1, 500)
+    x32 = x.astype(np.float32)
+    y32 = O.spmv_csr_f32(A, x32)
+    assert y32.dtype == np.float32
+    A32 = I.Csr(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    ex = O.spmv_csr_exact(A32, x32.astype(np.float64))
+    s = O.spmv_abs_scale(A32, x32.astype(np.float64))
+    lens = np.diff(A.row_ptr)
+    err = np.abs(y32.astype(np.float64) - ex)
+    assert np.all(err <= (lens + 2) * U32 * s)
+    # and it is genuinely FP32: far from the FP64 sum on some rows
+    assert np.max(err / np.maximum(s, 1e-300)) > 1e3 * U64
+
+
+# ----------------------------------------------------------- conversions --
+
+def _ell_to_csr(E, n):
+    rows = []
+    for i in range(n):
+        cols, vals = [], []
+        for k in range(E.K):
+            c = E.col[k * E.stride + i]
+            if c >= 0:
+                cols.append(c)
+                vals.append(E.val[k * E.stride + i])
+        rows.append((cols, vals))
+    return rows
+
+
+def _csr_rows(A):
+    return [(list(A.col[A.row_ptr[i]:A.row_ptr[i + 1]]), list(A.val[A.row_ptr[i]:A.row_ptr[i + 1]]))
+            for i in range(A.n_rows)]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_ell_round_trip_and_padding(seed):
+    rng = np.random.default_rng(seed)
+    A = I.random_csr(45, 60, 0.15, rng, empty_rows=0.2, sort_cols=False)
+    E = O.csr_to_ell(A)
+    assert E.stride == 64 and E.K == int(np.diff(A.row_ptr).max())
+    assert _ell_to_csr(E, A.n_rows) == _csr_rows(A)
+    pad = E.col < 0
+    assert pad.sum() == E.K * E.stride - A.nnz
+    assert np.all(E.col[pad] == -1) and np.all(E.val[pad] == 0.0)
+    assert not np.any(np.signbit(E.val[pad]))
+    x = rng.uniform(-1, 1, 60)
+    np.testing.assert_array_equal(O.spmv_ell(E, x, 1.5, -0.5, np.ones(45)),
+                                  O.spmv_csr(A, x, 1.5, -0.5, np.ones(45)))
+
+
+def test_ell_padding_never_reads_x():
+    A = I.rows_csr([1, 3, 0, 2], 4, np.random.default_rng(0))
+    E = O.csr_to_ell(A)
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    used = set(A.col.tolist())
+    for c in range(4):
+        if c not in used:
+            x[c] = np.inf
+    assert np.all(np.isfinite(O.spmv_ell(E, x)))
+
+
+def test_coo_round_trip_and_dense():
+    rng = np.random.default_rng(4)
+    A = I.random_csr(50, 50, 0.1, rng, integer_values=True, empty_rows=0.3, sort_cols=False)
+    M = O.csr_to_coo(A)
+    assert M.nnz == A.nnz
+    assert np.all(np.diff(M.row) >= 0)
+    counts = np.bincount(M.row, minlength=50)
+    np.testing.assert_array_equal(np.concatenate([[0], np.cumsum(counts)]), A.row_ptr)
+    np.testing.assert_array_equal(M.col, A.col)
+    np.testing.assert_array_equal(M.val, A.val)
+    x = rng.integers(-3, 4, 50).astype(float)
+    y0 = rng.integers(-3, 4, 50).astype(float)
+    np.testing.assert_array_equal(O.spmv_coo(M, x, 2.0, 3.0, y0), 2.0 * (dense(A) @ x) + 3.0 * y0)
+
+
+def test_hybrid_width_golden():
+    with open(os.path.join(GOLDEN, "hybrid_width_cases.json")) as f:
+        cases = json.load(f)["cases"]
+    rng = np.random.default_rng(0)
+    for c in cases:
+        lens = np.concatenate([np.full(cnt, int(L)) for L, cnt in c["lengths"].items()])
+        lens = rng.permutation(lens)
+        rp = np.zeros(lens.size + 1, np.int64)
+        np.cumsum(lens, out=rp[1:])
+        A = I.Csr(lens.size, 16, rp.astype(np.int32), np.zeros(int(rp[-1]), np.int32), np.zeros(int(rp[-1])))
+        assert O.hybrid_width(A) == c["K"], c["name"]
+    assert O.hybrid_width(I.laplace2d_5pt(64)) == 3
+
+
+@pytest.mark.parametrize("K", [None, 0, 2, 7])
+def test_hybrid_round_trip(K):
+    rng = np.random.default_rng(9)
+    A = I.rows_csr(rng.integers(0, 12, 70), 70, rng)
+    H = O.csr_to_hybrid(A, K)
+    Kused = O.hybrid_width(A) if K is None else K
+    assert H.ell.K == Kused
+    ell_rows = _ell_to_csr(H.ell, A.n_rows)
+    rows = []
+    for i in range(A.n_rows):
+        sel = H.coo.row == i
+        rows.append((ell_rows[i][0] + list(H.coo.col[sel]), ell_rows[i][1] + list(H.coo.val[sel])))
+    assert rows == _csr_rows(A)
+    assert np.sum(H.ell.col >= 0) + H.coo.nnz == A.nnz
+    assert np.all(np.diff(H.coo.row) >= 0)
+    x = rng.uniform(-1, 1, 70)
+    np.testing.assert_array_equal(O.spmv_hybrid(H, x, 1.0, 2.0, np.ones(70)),
+                                  O.spmv_csr(A, x, 1.0, 2.0, np.ones(70)))
+
+
+def test_workload_counts_golden():
+    with open(os.path.join(GOLDEN, "workload_counts.json")) as f:
+        g = json.load(f)
+    small = {"laplace2d_5pt": (I.laplace2d_5pt, 2), "stencil3d_7pt": (I.stencil3d_7pt, 3),
+             "stencil3d_27pt": (I.stencil3d_27pt, 3)}
+    for c in g["closed_forms"]:
+        fam = c["family"]
+        if fam in small:
+            f, dim = small[fam]
+            for N in (3, 5, 8):
+                A = f(N)
+                nnz = {"laplace2d_5pt": 5 * N * N - 4 * N, "stencil3d_7pt": 7 * N**3 - 6 * N**2,
+                       "stencil3d_27pt": (3 * N - 2) ** 3}[fam]
+                assert A.n_rows == N**dim and A.nnz == nnz
+    A = I.laplace2d_5pt(64)
+    assert (A.n_rows, A.nnz) == (4096, 20224)
+    B = I.convdiff3d_7pt(10, 3.0)
+    assert B.nnz == 7 * 1000 - 600
+    for s in g["seeded"]:
+        if s["family"] == "powerlaw":
+            P = I.powerlaw(s["n"], s["seed"])
+            L = P.row_lengths()
+            assert (P.nnz, int((L == 10000).sum()), int((L > 1024).sum())) == (
+                s["nnz"], s["rows_at_10000"], s["rows_over_1024"])
+        else:
+            sides = I.batch_sides(s["count"], seed=s["seed"])
+            assert int((sides**2).sum()) == s["sum_n"]
+            assert int((5 * sides**2 - 4 * sides).sum()) == s["sum_nnz"]
+
+
+# --------------------------------------------------------------- solvers --
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    B = I.random_csr(n, n, 0.2, rng)
+    D = dense(B)
+    D = D + D.T
+    D += np.diag(np.abs(D).sum(axis=1) + 1.0)
+    return _from_dense(D)
+
+
+def _from_dense(D):
+    n = D.shape[0]
+    rp = [0]
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.flatnonzero(D[i])
+        cols += nz.tolist()
+        vals += D[i, nz].tolist()
+        rp.append(len(cols))
+    return I.Csr(n, n, np.array(rp, np.int32), np.array(cols, np.int32), np.array(vals))
+
+
+@pytest.mark.parametrize("n,seed", [(8, 0), (20, 1), (32, 2)])
+def test_cg_n_step_and_dense_solve(n, seed):
+    A = _spd(n, seed)
+    b = np.random.default_rng(seed + 100).uniform(-1, 1, n)
+    x, r = O.cg(A, b, tol=1e-10, maxit=10 * n)
+    assert r.status == O.STATUS_OK and r.iterations <= n
+    xd = np.linalg.solve(dense(A), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert r.rel_residual <= 1e-10
+
+
+def test_cg_b_equals_A_ones():
+    A = I.laplace2d_5pt(16)
+    b = O.spmv_csr(A, np.ones(A.n_rows))
+    x, r = O.cg(A, b, tol=1e-12, maxit=1000)
+    assert r.status == 0 and np.max(np.abs(x - 1)) < 1e-9
+
+
+def test_cg_breakdown_on_indefinite_and_zero_rhs():
+    A = _from_dense(np.diag([1.0, -1.0]))
+    x, r = O.cg(A, np.array([1.0, 1.0]), tol=1e-12, maxit=10)
+    assert r.status == O.STATUS_BREAKDOWN
+    x, r = O.cg(I.laplace2d_5pt(4), np.zeros(16), x0=np.ones(16))
+    assert r.status == 0 and r.iterations == 0 and np.all(x == 0)
+
+
+def test_cg_reports_not_converged():
+    A = I.laplace2d_5pt(32)
+    b = np.random.default_rng(0).uniform(-1, 1, A.n_rows)
+    x, r = O.cg(A, b, tol=1e-12, maxit=5)
+    assert r.status == O.STATUS_NOT_CONVERGED and r.iterations == 5 and r.rel_residual > 1e-6
+
+
+@pytest.mark.parametrize("N,P", [(3, 10.0), (4, 1.0), (5, 20.0)])
+def test_bicgstab_dense_and_exact_ones(N, P):
+    A = I.convdiff3d_7pt(N, P)
+    b = dense(A) @ np.ones(A.n_rows)
+    x, r = O.bicgstab(A, b, tol=1e-12, maxit=2000)
+    assert r.status == 0 and r.rel_residual <= 1e-12
+    assert np.max(np.abs(x - 1)) < 1e-8
+    b2 = np.random.default_rng(N).uniform(-1, 1, A.n_rows)
+    x2, r2 = O.bicgstab(A, b2, tol=1e-12, maxit=2000)
+    xd = np.linalg.solve(dense(A), b2)
+    assert np.linalg.norm(x2 - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("N,P", [(3, 10.0), (4, 2.0)])
+def test_gmres_full_terminates_in_n_steps_monotone(N, P):
+    A = I.convdiff3d_7pt(N, P)
+    n = A.n_rows
+    b = np.random.default_rng(1).uniform(-1, 1, n)
+    x, r, hist = O.gmres(A, b, tol=1e-11, maxit=4 * n, restart=n, history=True)
+    assert r.status == 0 and r.iterations <= n
+    assert np.all(np.diff(hist) <= 1e-14)
+    xd = np.linalg.solve(dense(A), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_gmres_restarted_matches_dense():
+    A = I.convdiff3d_7pt(5, 10.0)
+    b = dense(A) @ np.ones(A.n_rows)
+    x, r = O.gmres(A, b, tol=1e-12, maxit=3000, restart=10)
+    assert r.status == 0 and r.outer_iterations >= 2 and np.max(np.abs(x - 1)) < 1e-8
+
+
+def test_gmres_nonsymmetric_small_nonsingular():
+    D = np.array([[2.0, 1.0, 0.0], [0.0, 3.0, -1.0], [4.0, 0.0, 1.0]])
+    A = _from_dense(D)
+    b = np.array([1.0, -2.0, 0.5])
+    x, r = O.gmres(A, b, tol=1e-14, maxit=10, restart=3)
+    np.testing.assert_allclose(x, np.linalg.solve(D, b), rtol=1e-12)
+
+
+@pytest.mark.parametrize("solver", [O.CG, O.BICGSTAB, O.GMRES])
+def test_ir_reaches_fp64_tolerance(solver):
+    A = I.laplace2d_5pt(24) if solver == O.CG else I.convdiff3d_7pt(6, 10.0)
+    b = dense(A) @ np.ones(A.n_rows)
+    x, r = O.solve_ir(solver, A, b, tol=1e-12, inner_tol=1e-4, inner_maxit=2000)
+    assert r.status == 0 and r.rel_residual <= 1e-12 and r.outer_iterations >= 2
+    assert np.max(np.abs(x - 1)) < 1e-9
+
+
+def test_ir_single_step_limited_by_fp32_storage():
+    # with an unreachable inner tolerance one refinement step is still capped
+    # near the FP32 unit roundoff: the inner solve really stores in FP32
+    A = I.varcoef2d_5pt(20, np.random.default_rng(3))
+    b = np.random.default_rng(4).uniform(-1, 1, A.n_rows)
+    x, r = O.solve_ir(O.CG, A, b, tol=1e-14, max_outer=1, inner_tol=1e-14, inner_maxit=400)
+    assert r.status == O.STATUS_NOT_CONVERGED
+    assert 1e-9 < r.rel_residual < 1e-4
+    x2, r2 = O.solve_ir(O.CG, A, b, tol=1e-12, max_outer=30, inner_tol=1e-5, inner_maxit=400)
+    assert r2.status == 0 and r2.rel_residual <= 1e-12
+
+
+def test_ir_inner_update_is_fp32_stored():
+    # from x0 = 0 one refinement step sets x = d, and d is stored in FP32
+    A = I.laplace2d_5pt(12)
+    b = np.random.default_rng(8).uniform(-1, 1, A.n_rows)
+    x, r = O.solve_ir(O.CG, A, b, tol=1e-14, max_outer=1, inner_tol=1e-3, inner_maxit=100)
+    assert r.outer_iterations == 1
+    np.testing.assert_array_equal(x.astype(np.float32).astype(np.float64), x)
+    for solver in (O.BICGSTAB, O.GMRES):
+        B = I.convdiff3d_7pt(4, 5.0)
+        bb = np.random.default_rng(9).uniform(-1, 1, B.n_rows)
+        x, r = O.solve_ir(solver, B, bb, tol=1e-14, max_outer=1, inner_tol=1e-3, inner_maxit=100)
+        np.testing.assert_array_equal(x.astype(np.float32).astype(np.float64), x)
