@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the sparse hot path on one node; prints ONE JSON line.
+
+Step = one SpMV y = A x in every format (CSR, ELL, COO, hybrid) and value
+type (FP64, FP32 values+vectors) on the three synthetic matrices of the SpMV
+sweep: 3D 27-point stencil 128^3 (n = 2,097,152, nnz = 55,742,968), the
+power-law matrix n = 10^6 (Zipf(2) row lengths clipped to [1, 10^4]) and the
+banded matrix n = 10^6 (half-bandwidth 64, fill 0.3).  ELL on the power-law
+matrix is rejected by the padding limit and is not part of the step.
+value = algorithmic bytes of all SpMVs / their summed device time (GB/s);
+L2 is flushed (256 MB write) before every SpMV.  Matrices stay resident in
+HBM; `e2e` repeats the step through the same C ABI calls with x copied in
+from pinned host memory and y copied back inside the timed region.
+
+--impl reference times the CPU oracle (plain C, FP64, OpenMP over rows) on
+a bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): every rank runs an independent replica (the SpMV
+sweep has no exchange step); value is the sum over ranks of bytes divided by
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s (% HBM peak) per format; solves/s + p99 latency at 1e-8 residual, mixed vs FP64"
+WORKLOAD = ("SpMV format sweep: CSR/ELL/COO/hybrid x FP64/FP32 (int32 indices) on 27-pt stencil 128^3, "
+            "power-law n=1e6 (Zipf s=2, clip [1,1e4], seed 0), banded n=1e6 (hb 64, fill 0.3, seed 0)")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_matrices():
+    from paper_2006_14290_gb300 import inputs as I
+
+    return [("stencil27_128", I.stencil3d_27pt(128)), ("powerlaw_1m", I.powerlaw(1_000_000, seed=0)),
+            ("banded_1m", I.banded(1_000_000, 64, 0.3, seed=0))]
+
+
+def spmv_bytes(fmt, n_rows, n_cols, nnz, ell_nnz, tail_nnz, sv, sx, sy):
+    """Algorithmic bytes of one y = A x (beta = 0): values + indices once,
+    x once, y written once; padding, x re-reads and misses excluded."""
+    if fmt == "csr":
+        return nnz * (sv + 4) + 4 * (n_rows + 1) + sx * n_cols + sy * n_rows
+    if fmt == "ell":
+        return nnz * (sv + 4) + sx * n_cols + sy * n_rows
+    if fmt == "coo":
+        return nnz * (sv + 8) + sx * n_cols + sy * n_rows
+    return ell_nnz * (sv + 4) + tail_nnz * (sv + 8) + sx * n_cols + sy * n_rows
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+        return int(ids[local_rank])
+    return local_rank
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2006_14290_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record():
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != source_hash():
+        return None
+    return d
+
+
+# --------------------------------------------------------------- reference --
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.lib()
+    cores = O.set_threads(os.cpu_count() or 1)
+    mats = workload_matrices()
+    step_bytes = 0
+    for name, A in mats:
+        step_bytes += spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, 8, 8, 8)
+    xs = {name: np.random.default_rng(0).uniform(-1, 1, A.n_cols) for name, A in mats}
+
+    def one_step():
+        for name, A in mats:
+            O.spmv_csr(A, xs[name])
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    gbs = step_bytes * args.steps / dt / 1e9
+    sample = (f"oracle FP64 CSR SpMV on the three sweep matrices per step ({args.steps} steps after "
+              f"{args.warmup} warm-up), OpenMP over rows on {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "host caches (CPU run)"},
+            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(mats, budget_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample."""
+    import oracle as O
+
+    O.lib()
+    cores = O.set_threads(os.cpu_count() or 1)
+    xs = {name: np.random.default_rng(0).uniform(-1, 1, A.n_cols) for name, A in mats}
+    nbytes = 0
+    reps = 0
+    t0 = time.perf_counter()
+    while reps < 20 and (time.perf_counter() - t0) < budget_s:
+        for name, A in mats:
+            O.spmv_csr(A, xs[name])
+            nbytes += spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, 8, 8, 8)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 CSR SpMV on the three sweep matrices, {reps} passes ({dt:.1f} s), OpenMP over rows"}
+
+
+# ---------------------------------------------------------------- our path --
+
+def run_ours(args):
+    import torch
+
+    rank, world, local_rank = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_2006_14290_gb300 import gko as G
+
+    G.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    mats = workload_matrices()
+
+    cases = []  # dicts: label, handle, x, y, xh, yh, bytes, launches
+    skipped = []
+    for name, A in mats:
+        M64 = G.from_csr(A)
+        plan = M64.plan()
+        base = {"csr": M64}
+        for fmt, conv in (("ell", lambda m: G.gko_matrix_convert_to_ell(m)),
+                          ("coo", G.gko_matrix_convert_to_coo), ("hybrid", lambda m: G.gko_matrix_convert_to_hybrid(m))):
+            try:
+                base[fmt] = conv(M64)
+            except G.GkoError as e:
+                if e.status != G.FORMAT_UNSUITABLE:
+                    raise
+                skipped.append(f"{name}/{fmt}: ELL padding over the limit")
+        x64 = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, A.n_cols)).to(dev)
+        x32 = x64.float()
+        for fmt, M in base.items():
+            inf = M.info()
+            for dt in ("f64", "f32"):
+                H = M if dt == "f64" else G.gko_matrix_convert_values(M, G.F32)
+                sv = 8 if dt == "f64" else 4
+                ell_nnz = inf["nnz"] - inf["coo_nnz"] if fmt == "hybrid" else 0
+                nb = spmv_bytes(fmt, A.n_rows, A.n_cols, A.nnz, ell_nnz, inf["coo_nnz"], sv, sv, sv)
+                launches = {"csr": 1 + (2 if plan["n_long_rows"] > 0 else 0), "ell": 1, "coo": 2, "hybrid": 3}[fmt]
+                x = x64 if dt == "f64" else x32
+                y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
+                cases.append({"label": f"{name}/{fmt}/{dt}", "M": H, "x": x, "y": y, "bytes": nb,
+                              "launches": launches, "xh": x.cpu().pin_memory(),
+                              "yh": torch.empty(A.n_rows, dtype=x.dtype).pin_memory()})
+        del A
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(events=None):
+        for i, c in enumerate(cases):
+            flush.fill_(float(i))
+            if events is not None:
+                events[i][0].record(stream)
+            G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"], stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    def e2e_step():
+        for i, c in enumerate(cases):
+            flush.fill_(float(i))
+            c["x"].copy_(c["xh"], non_blocking=True)
+            G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"], stream=stream)
+            c["yh"].copy_(c["y"], non_blocking=True)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    sampler = ClockSampler(gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in cases]
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    per_case_ms = [sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)) / args.steps
+                   for i in range(len(cases))]
+    kernel_ms = sum(per_case_ms)
+    wall_ms = t_start.elapsed_time(t_end) / args.steps
+    step_bytes = sum(c["bytes"] for c in cases)
+
+    # end to end: host x in, host y out, through the same C ABI call
+    for _ in range(max(args.warmup, 3)):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms_step = e0.elapsed_time(e1) / args.steps
+    flush_ms = 0.0
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(len(cases)):
+        flush.fill_(float(i))
+    f1.record(stream)
+    torch.cuda.synchronize()
+    flush_ms = f0.elapsed_time(f1)
+    e2e_ms = max(e2e_ms_step - flush_ms, 1e-9)
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([kernel_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        kernel_ms, e2e_ms = float(t[0]), float(t[1])
+
+    peak, peak_kind = measured_peaks()
+    dom = int(np.argmax(per_case_ms))
+    dom_case = cases[dom]
+    achieved = dom_case["bytes"] / (per_case_ms[dom] * 1e-3) / 1e9
+    traffic = None
+    tr = traffic_record()
+    if tr and dom_case["label"] in tr.get("per_case_bytes", {}):
+        traffic = tr["per_case_bytes"][dom_case["label"]]
+    value = world * step_bytes / (kernel_ms * 1e-3) / 1e9
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(kernel_ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed before every SpMV (256 MB write, excluded from time)",
+                       "matrices": {n: {"n": int(A.n_rows), "nnz": int(A.nnz)} for n, A in mats},
+                       "skipped": skipped, "frac_of_peak_value": round(value / world / peak, 4),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom_case["label"], "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes": int(dom_case["bytes"])},
+            "per_case": {c["label"]: {"ms": round(per_case_ms[i], 4),
+                                      "GB_s": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9, 1),
+                                      "frac": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9 / peak, 4)}
+                         for i, c in enumerate(cases)},
+            "e2e": {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": int(sum(c["x"].numel() * c["x"].element_size() for c in cases)),
+                    "d2h_bytes_per_step": int(sum(c["y"].numel() * c["y"].element_size() for c in cases))},
+            "wall_ms_per_step_incl_flush": round(wall_ms, 4),
+            "clocks": clocks,
+            "gpu_launches": int(sum(c["launches"] for c in cases) * args.steps),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(mats)
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

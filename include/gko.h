@@ -1,0 +1,187 @@
+/*
+ * gko.h -- C ABI of the GB300-native sparse-solver hot path.
+ *
+ * The paper (Ginkgo's CUDA-to-HIP port, Section 1 contributions list) names
+ * the sparse formats Coo, Csr, Ell and Hybrid and the Krylov solvers CG,
+ * BiCG(STAB) and GMRES built on SpMV; Section 4 times SpMV kernels and
+ * 1,000 CG iterations.  It prints no algorithm for any of them, so each entry
+ * point below cites the section that names the operation and the textbook
+ * definition it computes.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status (GKO_OK = 0, codes below).  No C++
+ *     exception crosses this boundary and nothing aborts.  gko_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - Indices are int32 (nnz < 2^31); sizes are int64.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     stream-ordered.  Calls that report a host-side result (matrix creation,
+ *     conversions, solves, gko_dot) synchronise that stream before returning.
+ *   - Vectors (x, y, b) are caller-owned DEVICE pointers on the current
+ *     device, contiguous, with the dtype given.  Matrix arrays passed to
+ *     gko_matrix_create_csr are copied into library-owned device memory; the
+ *     caller keeps its arrays.
+ *   - A gko_matrix is immutable after creation; one handle may be used by
+ *     several streams at once.  Every call that needs scratch memory takes it
+ *     from a stream-ordered pool, so concurrent calls never share scratch.
+ *   - The hot path runs only in this library's CUDA kernels (sm_103a).  There
+ *     is no CPU fallback: without a usable GPU calls return GKO_CUDA_ERROR.
+ */
+#ifndef GKO_GB300_H
+#define GKO_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GKO_API __attribute__((visibility("default")))
+#else
+#define GKO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ statuses -- */
+#define GKO_OK 0
+#define GKO_INVALID_ARG 1        /* null pointer, bad sizes, malformed CSR      */
+#define GKO_OUT_OF_MEMORY 2      /* device allocation failed                    */
+#define GKO_FORMAT_UNSUITABLE 3  /* ELL padding above the configured limit      */
+#define GKO_NOT_CONVERGED 4      /* iteration cap reached; x holds last iterate */
+#define GKO_BREAKDOWN 5          /* exact-zero pivot in the Krylov recurrence   */
+#define GKO_TIMEOUT 6            /* a bounded device wait gave up               */
+#define GKO_CUDA_ERROR 7         /* a CUDA runtime call failed                  */
+#define GKO_BUDGET_EXCEEDED 8    /* allocation would exceed the memory budget   */
+#define GKO_NOT_SUPPORTED 9      /* dtype/format combination not provided       */
+
+typedef struct gko_matrix_s *gko_matrix;
+
+/* Value types.  GKO_F64 accumulates in FP64; GKO_F32 and GKO_BF16 values
+ * accumulate in FP32 (vectors are FP32 for both). */
+typedef enum { GKO_F64 = 0, GKO_F32 = 1, GKO_BF16 = 2 } gko_dtype;
+
+/* Storage formats (paper, Section 1: Coo, Csr, Ell, Hybrid). */
+typedef enum { GKO_CSR = 0, GKO_ELL = 1, GKO_COO = 2, GKO_HYBRID = 3 } gko_format;
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+GKO_API const char *gko_last_error(void);
+GKO_API const char *gko_status_string(int status);
+
+/* Library version (major*10000 + minor*100 + patch). */
+GKO_API int gko_version(void);
+
+/* Limit on library-owned device memory in bytes (0 = unlimited, the
+ * default).  Matrix storage and solver workspaces count against it; a call
+ * that would exceed it returns GKO_BUDGET_EXCEEDED and allocates nothing.
+ * Bytes currently held are returned through *in_use when it is non-NULL. */
+GKO_API int gko_set_memory_budget(int64_t bytes);
+GKO_API int gko_memory_in_use(int64_t *in_use);
+
+/* ------------------------------------------------------------ matrices -- */
+
+/* Create a CSR matrix (paper, Section 1: Csr) from row_ptr[n_rows+1],
+ * col_idx[nnz] and values[nnz] of type `dtype`.  The arrays are host
+ * pointers when values_on_device == 0, device pointers otherwise.  Column
+ * order within a row is kept as given (unsorted allowed); duplicate (row,
+ * col) entries are kept and summed by SpMV.
+ * Checks (on the device): row_ptr[0] == 0, row_ptr[n_rows] == nnz,
+ * row_ptr non-decreasing, 0 <= col < n_cols; any failure -> GKO_INVALID_ARG.
+ * Also builds the load-balancing plan of the CSR SpMV: the row-length
+ * histogram, the subwarp width for ordinary rows and the nonzero split of
+ * long rows.  Synchronises `stream`.  *out receives the new handle. */
+GKO_API int gko_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, const void *values, gko_dtype dtype,
+                          int values_on_device, void *stream, gko_matrix *out);
+
+/* Column-major ELL (paper, Section 1: Ell; layout of Bell & Garland, SC'09):
+ * width K = longest row, stride = n_rows rounded up to 32, entry k of row i
+ * at k*stride + i, padding col = -1 and value +0.0.  Returns
+ * GKO_FORMAT_UNSUITABLE when K*n_rows > max_fill * nnz (max_fill <= 0 means
+ * the default limit of 8).  Entries keep CSR storage order. */
+GKO_API int gko_matrix_convert_to_ell(gko_matrix csr, double max_fill, void *stream, gko_matrix *out);
+
+/* Row-major COO (paper, Section 1: Coo): the CSR entries in storage order
+ * with an explicit int32 row index each. */
+GKO_API int gko_matrix_convert_to_coo(gko_matrix csr, void *stream, gko_matrix *out);
+
+/* Hybrid ELL + COO (paper, Section 1: Hybrid; Bell & Garland's HYB): the
+ * first min(len_i, K) entries of each row in ELL of width K, the rest in a
+ * row-major COO tail.  ell_width < 0 picks K as the largest k with
+ * #{rows: len >= k} >= max(4096, n_rows/3); K = 0 gives a pure COO tail. */
+GKO_API int gko_matrix_convert_to_hybrid(gko_matrix csr, int32_t ell_width, void *stream, gko_matrix *out);
+
+/* Copy of `m` (any format) with values converted to `to` (round to nearest
+ * even); index arrays are shared with `m`, which must outlive the copy only
+ * as far as the caller's own handle goes (sharing is reference counted). */
+GKO_API int gko_matrix_convert_values(gko_matrix m, gko_dtype to, void *stream, gko_matrix *out);
+
+/* Sizes and layout of a handle.  Any output pointer may be NULL.
+ * ell_width / coo_nnz are 0 where the format has no such part; bytes is the
+ * device memory owned (shared index arrays counted in full). */
+GKO_API int gko_matrix_info(gko_matrix m, gko_format *format, gko_dtype *dtype, int64_t *n_rows,
+                    int64_t *n_cols, int64_t *nnz, int32_t *ell_width, int64_t *ell_stride,
+                    int64_t *coo_nnz, int64_t *bytes);
+
+/* Copy the device arrays of `m` into caller HOST buffers (any may be NULL):
+ *   CSR:    row_ptr[n_rows+1], col[nnz], val[nnz]
+ *   ELL:    ell_col[K*stride], ell_val[K*stride]
+ *   COO:    coo_row[nnz], coo_col[nnz], coo_val[nnz]
+ *   HYBRID: ell_* for the ELL part and coo_* for the tail
+ * Values are written in the handle's dtype.  Synchronises `stream`. */
+GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void *val, int32_t *ell_col,
+                      void *ell_val, int32_t *coo_row, int32_t *coo_col, void *coo_val,
+                      void *stream);
+
+/* CSR load-balancing plan (built at creation): subwarp width S used for
+ * rows of length <= long_threshold, the number of longer rows and of their
+ * fixed-size nonzero chunks, and the row-length histogram in log2 classes
+ * (hist[0]: empty rows; hist[b], b >= 1: lengths in [2^(b-1), 2^b)),
+ * 33 entries.  Any output may be NULL. */
+GKO_API int gko_matrix_plan(gko_matrix csr, int32_t *subwarp, int32_t *rows_per_subwarp,
+                    int32_t *long_threshold, int64_t *n_long_rows, int64_t *n_long_chunks,
+                    int64_t *hist33);
+
+/* Override the CSR plan's subwarp width S (1,2,4,8,16,32) and rows per
+ * subwarp pass R (1,2,4,8); the long-row threshold becomes 32*S.  Used by
+ * the autotuner; rebuilds the long-row split.  Synchronises `stream`. */
+GKO_API int gko_matrix_set_plan(gko_matrix csr, int32_t subwarp, int32_t rows_per_subwarp, void *stream);
+
+GKO_API int gko_matrix_destroy(gko_matrix m);
+
+/* ----------------------------------------------------------------- SpMV -- */
+
+/* y = alpha * A * x + beta * y  (paper, Section 4: the SpMV kernels timed).
+ * alpha, beta: HOST scalars.  x[n_cols], y[n_rows]: device vectors of
+ * `vec_dtype`, which must be GKO_F64 for an F64 matrix and GKO_F32 for F32
+ * and BF16 matrices.  beta == 0 overwrites y without reading it (NaN in y
+ * does not propagate); NaN/Inf in x propagate through every row that
+ * references them, also when alpha == 0.  ELL padding never reads x.
+ * Deterministic: the same inputs give bit-identical y on every call.
+ * x and y must not overlap.  Asynchronous on `stream`. */
+GKO_API int gko_spmv(const double *alpha, gko_matrix A, const void *x, const double *beta, void *y,
+             gko_dtype vec_dtype, void *stream);
+
+/* ---------------------------------------------------------------- BLAS-1 -- */
+
+/* Deterministic FP64 reductions and updates on device vectors of length n
+ * (the vector kernels inside the Krylov solvers).  *result is a HOST double;
+ * these calls synchronise `stream`. */
+GKO_API int gko_dot(int64_t n, const double *x, const double *y, double *result, void *stream);
+GKO_API int gko_nrm2(int64_t n, const double *x, double *result, void *stream);
+/* y = a*x + y; asynchronous. */
+GKO_API int gko_axpy(int64_t n, double a, const double *x, double *y, void *stream);
+/* Fused multi-axpy + norm: y -= sum_j h[j] * V[j*ldv : j*ldv + n] for
+ * j < k, then *result = ||y||_2 (host, synchronises).  h: host array. */
+GKO_API int gko_multi_axpy_norm(int64_t n, int32_t k, const double *h, const double *V, int64_t ldv,
+                        double *y, double *result, void *stream);
+/* Fused multi-dot: h[j] = V[j] . w for j < k (h: host array; synchronises). */
+GKO_API int gko_multi_dot(int64_t n, int32_t k, const double *V, int64_t ldv, const double *w,
+                  double *h, void *stream);
+/* Fused SpMV + dot: y = A x and *result = x . y (FP64, host; synchronises).
+ * A must be square with FP64 values. */
+GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *result, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKO_GB300_H */

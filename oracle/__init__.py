@@ -64,6 +64,10 @@ _SIGS = {
     "or_hybrid_tail_nnz": (_I64, [_I64, _P, _I32]),
     "or_csr_to_hybrid": (None, [_I64, _P, _P, _P, _I32, _I64, _P, _P, _P, _P, _P]),
     "or_spmv_hybrid": (C.c_int, [_I64, _I32, _I64, _P, _P, _I64, _P, _P, _P, _P, _D, _D, _P]),
+    "or_dot": (_D, [_I64, _P, _P]),
+    "or_axpy": (None, [_I64, _D, _P, _P]),
+    "or_multi_dot": (None, [_I64, _I32, _P, _I64, _P, _P]),
+    "or_multi_axpy_norm": (_D, [_I64, _I32, _P, _P, _I64, _P]),
     "or_solve": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _D, _I32, _I32, _P, _I32,
                            C.POINTER(_Result)]),
     "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
@@ -251,6 +255,37 @@ def spmv_hybrid(H: Hybrid, x, alpha=1.0, beta=0.0, y=None):
                               alpha, beta, _p(out))
     assert rc == 0
     return out
+
+
+def dot(x, y) -> float:
+    """Sequential FP64 dot product."""
+    x, y = _f64(x), _f64(y)
+    return float(lib().or_dot(x.size, _p(x), _p(y)))
+
+
+def axpy(a, x, y):
+    x = _f64(x)
+    out = np.array(y, dtype=np.float64, copy=True)
+    lib().or_axpy(x.size, a, _p(x), _p(out))
+    return out
+
+
+def multi_dot(V, w):
+    """h_j = V[j] . w for each row of the 2-D array V."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    w = _f64(w)
+    h = np.empty(V.shape[0])
+    lib().or_multi_dot(w.size, V.shape[0], _p(V), V.shape[1], _p(w), _p(h))
+    return h
+
+
+def multi_axpy_norm(V, h, y):
+    """Returns (y - sum_j h_j V[j], its 2-norm)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    h = _f64(h)
+    out = np.array(y, dtype=np.float64, copy=True)
+    nrm = lib().or_multi_axpy_norm(out.size, h.size, _p(h), _p(V), V.shape[1], _p(out))
+    return out, float(nrm)
 
 
 def solve(solver: int, A, b, x0=None, tol=1e-10, maxit=1000, restart=30, history=False):

@@ -245,6 +245,32 @@ int or_spmv_hybrid(int64_t n, int32_t K, int64_t stride, const int32_t *ecol, co
   return OR_OK;
 }
 
+/* -------------------------------------------------------------- BLAS-1 -- */
+
+/* Sequential FP64 definitions of the vector operations inside the Krylov
+ * solvers: dot = sum_i x_i y_i (left to right); axpy y_i = a x_i + y_i;
+ * multi-dot h_j = V_j . w; multi-axpy + norm y -= sum_j h_j V_j (j in
+ * order for each i), then ||y||_2. */
+double or_dot(int64_t n, const double *x, const double *y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+void or_axpy(int64_t n, double a, const double *x, double *y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = a * x[i] + y[i];
+}
+
+void or_multi_dot(int64_t n, int32_t k, const double *V, int64_t ldv, const double *w, double *h) {
+  for (int32_t j = 0; j < k; ++j) h[j] = or_dot(n, V + (int64_t)j * ldv, w);
+}
+
+double or_multi_axpy_norm(int64_t n, int32_t k, const double *h, const double *V, int64_t ldv, double *y) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < k; ++j) y[i] = y[i] - h[j] * V[(int64_t)j * ldv + i];
+  return sqrt(or_dot(n, y, y));
+}
+
 /* ------------------------------------------------------------- solvers -- */
 
 /* A CSR operator: FP64 values, or FP32 values with FP32 accumulation (the

@@ -1,0 +1,188 @@
+// Internal declarations shared by the translation units of the CUDA library.
+// Nothing here is part of the C ABI (include/gko.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "gko.h"
+
+namespace gko {
+
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------- errors ----
+
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define GKO_TRY_CUDA(call)                                   \
+  do {                                                       \
+    cudaError_t gko_e_ = (call);                             \
+    if (gko_e_ != cudaSuccess) return ::gko::cuda_fail(gko_e_, #call); \
+  } while (0)
+
+#define GKO_TRY(expr)              \
+  do {                             \
+    int gko_s_ = (expr);           \
+    if (gko_s_ != GKO_OK) return gko_s_; \
+  } while (0)
+
+// ------------------------------------------------------------- memory ----
+
+// A device allocation owned by the library.  Counted against the memory
+// budget; freed when the last reference goes.
+struct DeviceBuffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ~DeviceBuffer();
+};
+using Buf = std::shared_ptr<DeviceBuffer>;
+
+int alloc(size_t bytes, Buf* out);  // cudaMalloc with budget accounting
+template <typename T>
+inline T* ptr(const Buf& b) {
+  return b ? static_cast<T*>(b->ptr) : nullptr;
+}
+
+// Stream-ordered scratch from the library's own memory pool.  Freed (back to
+// the pool, stream-ordered) when the object goes out of scope.
+class Scratch {
+ public:
+  Scratch() = default;
+  ~Scratch();
+  int get(size_t bytes, cudaStream_t s);
+  void* data() const { return p_; }
+  template <typename T>
+  T* as(size_t byte_offset = 0) const {
+    return reinterpret_cast<T*>(static_cast<char*>(p_) + byte_offset);
+  }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+
+ private:
+  void* p_ = nullptr;
+  size_t bytes_ = 0;
+  cudaStream_t s_ = nullptr;
+};
+
+int budget_reserve(size_t bytes);
+void budget_release(size_t bytes);
+
+int sm_count();
+size_t dtype_size(gko_dtype t);
+
+// ------------------------------------------------------------- matrix ----
+
+constexpr int kHistBins = 33;
+constexpr int32_t kLongChunk = 1024;  // nonzeros per chunk of a long CSR row
+
+// Load-balancing plan of the CSR SpMV, built from the row-length histogram.
+struct CsrPlan {
+  int32_t S = 32;           // subwarp width for ordinary rows
+  int32_t R = 4;            // rows per subwarp pass
+  int32_t long_thr = 1024;  // rows longer than this use the nonzero split
+  int32_t max_len = 0;
+  int64_t hist[kHistBins] = {0};
+  int64_t hist_nnz[kHistBins] = {0};
+  int64_t n_long = 0, n_chunks = 0;
+  Buf long_rows;       // int32[n_long]     row index of each long row
+  Buf long_chunk_ptr;  // int32[n_long+1]   first chunk of each long row
+  Buf chunk_row;       // int32[n_chunks]   row index of each chunk
+  Buf chunk_start;     // int32[n_chunks]   first nonzero of each chunk
+};
+
+}  // namespace gko
+
+struct gko_matrix_s {
+  gko_format fmt = GKO_CSR;
+  gko_dtype dtype = GKO_F64;
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  int device = 0;
+  // CSR
+  gko::Buf row_ptr, col, val;
+  gko::CsrPlan plan;
+  // ELL (also the ELL part of HYBRID)
+  int32_t K = 0;
+  int64_t stride = 0;
+  gko::Buf ell_col, ell_val;
+  // COO (also the tail of HYBRID)
+  int64_t coo_nnz = 0;
+  gko::Buf coo_row, coo_col, coo_val;
+  // cached low-precision copies used by mixed-precision solves
+  std::mutex mu;
+  std::map<int, gko_matrix> lowp;
+  ~gko_matrix_s();
+};
+
+namespace gko {
+
+// --------------------------------------------------------- device utils ----
+
+template <typename V>
+struct AccOf {
+  using type = float;
+};
+template <>
+struct AccOf<double> {
+  using type = double;
+};
+template <typename V>
+using acc_t = typename AccOf<V>::type;
+
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__device__ __forceinline__ T from_acc(double v);
+template <>
+__device__ __forceinline__ double from_acc<double>(double v) { return v; }
+template <typename T>
+__device__ __forceinline__ T from_accf(float v);
+template <>
+__device__ __forceinline__ float from_accf<float>(float v) { return v; }
+
+__device__ __forceinline__ double madd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Streaming loads of matrix data (read once: evict-first) and cached loads
+// of the gathered vector (kept resident in L2).
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+template <typename T>
+__device__ __forceinline__ T ld_vec(const T* p) {
+  return __ldg(p);
+}
+
+// Subwarp of `S` contiguous lanes (paper, Section 3.3): Rank = tid % S,
+// LaneOffset = floor((tid % 32) / S) * S, Mask = (~0 >> (32 - S)) << LaneOffset.
+template <int S>
+__device__ __forceinline__ unsigned subwarp_mask() {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned offset = (lane / S) * S;
+  return (0xffffffffu >> (32 - S)) << offset;
+}
+
+// Butterfly sum over a subwarp: log2(S) xor-shuffle steps (paper, Section 3.3
+// reduce listing); every lane of the subwarp ends with the total.
+template <int S, typename T>
+__device__ __forceinline__ T subwarp_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int m = S / 2; m > 0; m >>= 1) v += __shfl_xor_sync(mask, v, m, S);
+  return v;
+}
+
+inline unsigned ceil_div_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace gko

@@ -1,0 +1,675 @@
+// Kernel templates behind spmv_run_{f64,f32,bf16}.  Included by exactly one
+// translation unit per value type.
+#pragma once
+
+#include <algorithm>
+#include <climits>
+
+#include "reduce.cuh"
+#include "spmv.cuh"
+
+namespace gko {
+
+// ------------------------------------------------------------------- CSR --
+
+template <typename VT, typename XT>
+struct CsrArgs {
+  int64_t n;
+  const int32_t* rp;
+  const int32_t* col;
+  const VT* val;
+  const XT* x;
+  XT* y;
+  acc_t<VT> alpha, beta;
+  int32_t long_thr;
+};
+
+// Subwarp-per-row CSR: a subwarp of S lanes owns R consecutive rows per pass;
+// lane `rank` reads entries rank, rank+S, ... of each row, loads of all R rows
+// are issued before the gathers, then a log2(S)-step butterfly sums each row.
+// Rows longer than long_thr are skipped (the nonzero split handles them).
+template <int S, int R, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(256) csr_subwarp_kernel(CsrArgs<VT, XT> a, DotSpec d, int expected,
+                                                          const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  const unsigned mask = subwarp_mask<S>();
+  const int rank = threadIdx.x & (S - 1);
+  const int64_t sub = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / S;
+  const int64_t nsub = ((int64_t)gridDim.x * blockDim.x) / S;
+  double dwy = 0.0, dyy = 0.0;
+  for (int64_t row0 = sub * R; row0 < a.n; row0 += nsub * R) {
+    int32_t beg[R], end[R];
+    unsigned long_bits = 0;
+    int32_t lmax = 0;
+    int32_t p0 = __ldg(a.rp + row0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i1 = row0 + r + 1;
+      const int32_t p1 = i1 <= a.n ? __ldg(a.rp + i1) : p0;
+      beg[r] = p0;
+      if (p1 - p0 > a.long_thr) {
+        end[r] = p0;
+        long_bits |= 1u << r;
+      } else {
+        end[r] = p1;
+        lmax = max(lmax, p1 - p0);
+      }
+      p0 = p1;
+    }
+    AT sum[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sum[r] = AT(0);
+    for (int off = rank; off < lmax; off += S) {
+      int32_t c[R];
+      VT v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int32_t k = beg[r] + off;
+        const bool ok = k < end[r];
+        c[r] = ok ? ld_stream(a.col + k) : -1;
+        v[r] = ok ? ld_stream(a.val + k) : VT(0);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (c[r] >= 0) sum[r] = madd(to_acc(v[r]), to_acc(ld_vec(a.x + c[r])), sum[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) sum[r] = subwarp_sum<S>(sum[r], mask);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = row0 + r;
+      if ((r & (S - 1)) == rank && i < a.n && !((long_bits >> r) & 1u)) {
+        AT v = a.alpha * sum[r];
+        if (a.beta != AT(0)) v = madd(a.beta, to_acc(a.y[i]), v);
+        a.y[i] = (XT)v;
+        if (DOT) {
+          const double yv = (double)(XT)v;
+          dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
+          dyy += yv * yv;
+        }
+      }
+    }
+  }
+  if (DOT) dot_epilogue2<256>(dwy, dyy, d, blockIdx.x, expected);
+}
+
+// Nonzero split of long rows: one warp per fixed-size chunk of a long row,
+// partial sums to scratch.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256)
+    csr_long_chunk_kernel(int64_t n_chunks, const int32_t* __restrict__ chunk_row,
+                          const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
+                          acc_t<VT>* __restrict__ partial, const int* gate) {
+  using AT = acc_t<VT>;
+  constexpr int U = 4;
+  if (gated(gate)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < n_chunks; c += nw) {
+    const int32_t r = chunk_row[c], k0 = chunk_start[c];
+    const int32_t k1 = min(k0 + kLongChunk, rp[r + 1]);
+    AT s = AT(0);
+    for (int32_t k = k0 + lane; k < k1; k += 32 * U) {
+      int32_t cc[U];
+      VT vv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t kk = k + 32 * u;
+        const bool ok = kk < k1;
+        cc[u] = ok ? ld_stream(col + kk) : -1;
+        vv[u] = ok ? ld_stream(val + kk) : VT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (cc[u] >= 0) s = madd(to_acc(vv[u]), to_acc(ld_vec(x + cc[u])), s);
+    }
+    s = subwarp_sum<32>(s, 0xffffffffu);
+    if (lane == 0) partial[c] = s;
+  }
+}
+
+// Sum each long row's chunk partials in chunk order and finish the row.
+template <typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(256)
+    csr_long_fixup_kernel(int64_t n_long, const int32_t* __restrict__ rows, const int32_t* __restrict__ cptr,
+                          const acc_t<VT>* __restrict__ partial, XT* __restrict__ y, acc_t<VT> alpha,
+                          acc_t<VT> beta, DotSpec d, int slot, int expected, const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  double dwy = 0.0, dyy = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_long; j += (int64_t)gridDim.x * blockDim.x) {
+    AT s = AT(0);
+    for (int32_t c = cptr[j]; c < cptr[j + 1]; ++c) s += partial[c];
+    const int32_t i = rows[j];
+    AT v = alpha * s;
+    if (beta != AT(0)) v = madd(beta, to_acc(y[i]), v);
+    y[i] = (XT)v;
+    if (DOT) {
+      const double yv = (double)(XT)v;
+      dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
+      dyy += yv * yv;
+    }
+  }
+  if (DOT) dot_epilogue2<256>(dwy, dyy, d, slot + blockIdx.x, expected);
+}
+
+// ------------------------------------------------------------------- ELL --
+
+template <typename VT, int RPT>
+struct EllVec;
+template <>
+struct EllVec<double, 2> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+};
+template <>
+struct EllVec<float, 4> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+};
+template <>
+struct EllVec<__nv_bfloat16, 4> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, __nv_bfloat16 (&v)[4]) {
+    const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
+    v[0] = __ushort_as_bfloat16((unsigned short)(t.x & 0xffffu));
+    v[1] = __ushort_as_bfloat16((unsigned short)(t.x >> 16));
+    v[2] = __ushort_as_bfloat16((unsigned short)(t.y & 0xffffu));
+    v[3] = __ushort_as_bfloat16((unsigned short)(t.y >> 16));
+  }
+};
+
+template <int RPT>
+__device__ __forceinline__ void ell_cols(const int32_t* p, int32_t (&c)[RPT]);
+template <>
+__device__ __forceinline__ void ell_cols<2>(const int32_t* p, int32_t (&c)[2]) {
+  const int2 t = __ldcs(reinterpret_cast<const int2*>(p));
+  c[0] = t.x;
+  c[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void ell_cols<4>(const int32_t* p, int32_t (&c)[4]) {
+  const int4 t = __ldcs(reinterpret_cast<const int4*>(p));
+  c[0] = t.x;
+  c[1] = t.y;
+  c[2] = t.z;
+  c[3] = t.w;
+}
+
+template <typename VT, typename XT>
+struct EllArgs {
+  int64_t n;
+  int32_t K;
+  int64_t stride;
+  const int32_t* col;
+  const VT* val;
+  const XT* x;
+  XT* y;
+  acc_t<VT> alpha, beta;
+};
+
+// Column-major ELL: each thread owns RPT consecutive rows and reads slot k of
+// all of them with one 128-bit (or 64-bit) load per array; padding slots
+// (col = -1) never touch x.
+template <int RPT, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, int expected, const int* gate) {
+  using AT = acc_t<VT>;
+  constexpr int U = 4;
+  if (gated(gate)) return;
+  const int64_t groups = (a.n + RPT - 1) / RPT;
+  double dwy = 0.0, dyy = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = g * RPT;
+    AT sum[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) sum[r] = AT(0);
+    for (int32_t k = 0; k < a.K; k += U) {
+      int32_t c[U][RPT];
+      VT v[U][RPT];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (k + u < a.K) {
+          const int64_t off = (int64_t)(k + u) * a.stride + i0;
+          ell_cols<RPT>(a.col + off, c[u]);
+          EllVec<VT, RPT>::load(a.val + off, v[u]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) c[u][r] = -1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+          if (c[u][r] >= 0) sum[r] = madd(to_acc(v[u][r]), to_acc(ld_vec(a.x + c[u][r])), sum[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int64_t i = i0 + r;
+      if (i < a.n) {
+        AT v = a.alpha * sum[r];
+        if (a.beta != AT(0)) v = madd(a.beta, to_acc(a.y[i]), v);
+        a.y[i] = (XT)v;
+        if (DOT) {
+          const double yv = (double)(XT)v;
+          dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
+          dyy += yv * yv;
+        }
+      }
+    }
+  }
+  if (DOT) dot_epilogue2<256>(dwy, dyy, d, blockIdx.x, expected);
+}
+
+// ------------------------------------------------------------------- COO --
+
+template <typename VT, typename XT>
+struct CooArgs {
+  int64_t n_rows, nnz;
+  const int32_t* row;
+  const int32_t* col;
+  const VT* val;
+  const XT* x;
+  XT* y;
+  acc_t<VT> alpha, beta;
+};
+
+template <typename VT>
+struct Load8;
+template <>
+struct Load8<double> {
+  static __device__ __forceinline__ void run(const double* p, double (&v)[8]) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 t = __ldcs(reinterpret_cast<const double2*>(p) + h);
+      v[2 * h] = t.x;
+      v[2 * h + 1] = t.y;
+    }
+  }
+};
+template <>
+struct Load8<float> {
+  static __device__ __forceinline__ void run(const float* p, float (&v)[8]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + h);
+      v[4 * h] = t.x;
+      v[4 * h + 1] = t.y;
+      v[4 * h + 2] = t.z;
+      v[4 * h + 3] = t.w;
+    }
+  }
+};
+template <>
+struct Load8<__nv_bfloat16> {
+  static __device__ __forceinline__ void run(const __nv_bfloat16* p, __nv_bfloat16 (&v)[8]) {
+    const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      v[2 * h] = __ushort_as_bfloat16((unsigned short)(w[h] & 0xffffu));
+      v[2 * h + 1] = __ushort_as_bfloat16((unsigned short)(w[h] >> 16));
+    }
+  }
+};
+__device__ __forceinline__ void load8_i32(const int32_t* p, int32_t (&v)[8]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldcs(reinterpret_cast<const int4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Combine of the segmented-sum scan: `prev` precedes `cur`; a segment end in
+// `cur` cuts off everything before it.
+template <typename AT>
+__device__ __forceinline__ void seg_combine(int fp, AT vp, int& f, AT& v) {
+  if (!f) v = vp + v;
+  f = f | fp;
+}
+
+template <typename XT, typename AT>
+__device__ __forceinline__ void coo_store(XT* y, int32_t r, AT s, AT alpha, AT beta, bool accum) {
+  if (accum) {
+    y[r] = (XT)madd(alpha, s, to_acc(y[r]));
+  } else {
+    AT v = alpha * s;
+    if (beta != AT(0)) v = madd(beta, to_acc(y[r]), v);
+    y[r] = (XT)v;
+  }
+}
+
+template <typename XT, typename AT>
+__device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT beta) {
+  for (int64_t r = r0; r < r1; ++r) y[r] = beta == AT(0) ? XT(0) : (XT)(beta * to_acc(y[r]));
+}
+
+// Tiled segmented reduction over row-sorted COO.  Each 256-thread block owns
+// a tile of 2048 entries; each thread owns 8 consecutive entries (vector
+// loads), reduces them sequentially, and a block-wide segmented scan supplies
+// the running sum that enters from earlier threads.  Rows that start and end
+// inside the tile are written directly; the tile's open first/last segment
+// partials go to carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
+// ACCUM: y[r] += alpha*sum for the rows present (hybrid tail); otherwise
+// rows absent from the COO arrays are scaled by beta here too.
+template <typename VT, typename XT, bool ACCUM>
+__global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
+                                                          const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  __shared__ int32_t s_first[kCooThreads + 1];
+  __shared__ int32_t s_last[kCooThreads];
+  __shared__ AT s_wv[kCooThreads / kWarp];
+  __shared__ int s_wf[kCooThreads / kWarp];
+  __shared__ int32_t s_prev_row;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t tile = blockIdx.x;
+  const int64_t base = tile * kCooTile;
+  const int cnt = (int)min((int64_t)kCooTile, a.nnz - base);
+  const int j0 = t * kCooItems;
+  const int my = max(0, min(kCooItems, cnt - j0));
+
+  int32_t rows[kCooItems];
+  AT prod[kCooItems];
+  if (my == kCooItems) {
+    int32_t cols[kCooItems];
+    VT vals[kCooItems];
+    load8_i32(a.row + base + j0, rows);
+    load8_i32(a.col + base + j0, cols);
+    Load8<VT>::run(a.val + base + j0, vals);
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) prod[u] = to_acc(vals[u]) * to_acc(ld_vec(a.x + cols[u]));
+  } else {
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) {
+      if (u < my) {
+        const int64_t k = base + j0 + u;
+        rows[u] = a.row[k];
+        prod[u] = to_acc(a.val[k]) * to_acc(ld_vec(a.x + a.col[k]));
+      } else {
+        rows[u] = INT_MAX;
+        prod[u] = AT(0);
+      }
+    }
+  }
+  s_first[t] = my > 0 ? rows[0] : INT_MAX;
+  s_last[t] = my > 0 ? rows[my - 1] : INT_MAX;
+  if (t == 0) {
+    s_first[kCooThreads] = (base + cnt < a.nnz) ? a.row[base + cnt] : -1;
+    s_prev_row = base > 0 ? a.row[base - 1] : -1;
+  }
+  __syncthreads();
+  const int32_t next_row = (j0 + kCooItems < cnt) ? s_first[t + 1] : s_first[kCooThreads];
+  const int32_t prev_tile_row = s_prev_row;
+  const bool first_open = base > 0 && prev_tile_row == s_first[0];
+
+  // pass 1: (has a segment end, sum after the last end)
+  int f = 0;
+  AT v = AT(0);
+#pragma unroll
+  for (int u = 0; u < kCooItems; ++u) {
+    if (u < my) {
+      v += prod[u];
+      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;
+      if (rows[u] != nr) {
+        f = 1;
+        v = AT(0);
+      }
+    }
+  }
+  // inclusive warp scan of (f, v)
+#pragma unroll
+  for (int dlt = 1; dlt < 32; dlt <<= 1) {
+    const int fp = __shfl_up_sync(0xffffffffu, f, dlt);
+    const AT vp = __shfl_up_sync(0xffffffffu, v, dlt);
+    if (lane >= dlt) seg_combine(fp, vp, f, v);
+  }
+  if (lane == 31) {
+    s_wf[w] = f;
+    s_wv[w] = v;
+  }
+  int ef = __shfl_up_sync(0xffffffffu, f, 1);
+  AT ev = __shfl_up_sync(0xffffffffu, v, 1);
+  if (lane == 0) {
+    ef = 0;
+    ev = AT(0);
+  }
+  __syncthreads();
+  int pf = 0;
+  AT pv = AT(0);
+  for (int i = 0; i < w; ++i) {
+    int ff = s_wf[i];
+    AT vv = s_wv[i];
+    seg_combine(pf, pv, ff, vv);
+    pf = ff;
+    pv = vv;
+  }
+  seg_combine(pf, pv, ef, ev);  // exclusive prefix of this thread
+
+  // pass 2: finish the segments that end in this thread's entries
+  AT run = ev;
+  bool seen_end = ef != 0;
+#pragma unroll
+  for (int u = 0; u < kCooItems; ++u) {
+    if (u < my) {
+      const int32_t r = rows[u];
+      if (!ACCUM) {
+        const int32_t pr = (u > 0) ? rows[u - 1] : (t > 0 ? s_last[t - 1] : prev_tile_row);
+        if (r != pr) coo_empty_rows(a.y, (int64_t)pr + 1, (int64_t)r, a.beta);
+      }
+      run += prod[u];
+      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;
+      if (r != nr) {
+        if (!seen_end && first_open)
+          carry[2 * tile] = run;
+        else
+          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM);
+        run = AT(0);
+        seen_end = true;
+      }
+    }
+  }
+  if (!ACCUM && my > 0 && base + j0 + my == a.nnz) coo_empty_rows(a.y, (int64_t)rows[my - 1] + 1, a.n_rows, a.beta);
+  if (t == 0) {
+    int tf = 0;
+    AT tv = AT(0);
+    for (int i = 0; i < kCooThreads / kWarp; ++i) {
+      int ff = s_wf[i];
+      AT vv = s_wv[i];
+      seg_combine(tf, tv, ff, vv);
+      tf = ff;
+      tv = vv;
+    }
+    // tv: sum of the tile's last segment; without any end the whole tile
+    if (!tf) carry[2 * tile] = tv;
+    carry[2 * tile + 1] = tv;
+  }
+}
+
+// Complete rows that span tiles: the tile where such a row starts adds its
+// last-segment partial and the first-segment partials of the following
+// tiles, in tile order.
+template <typename VT, typename XT, bool ACCUM>
+__global__ void __launch_bounds__(256)
+    coo_fixup_kernel(int64_t nnz, int64_t tiles, const int32_t* __restrict__ row, const acc_t<VT>* __restrict__ carry,
+                     XT* __restrict__ y, acc_t<VT> alpha, acc_t<VT> beta, const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t * kCooTile;
+    const int64_t e = min(b + kCooTile, nnz);  // one past the tile
+    if (e >= nnz || row[e - 1] != row[e]) continue;  // last segment closed
+    const bool first_open = b > 0 && row[b - 1] == row[b];
+    if (first_open && row[b] == row[e - 1]) continue;  // middle of a longer row
+    const int32_t r = row[e - 1];
+    AT s = carry[2 * t + 1];
+    for (int64_t u = t + 1; u < tiles; ++u) {
+      const int64_t bu = u * kCooTile, eu = min(bu + kCooTile, nnz);
+      s += carry[2 * u];
+      const bool open = eu < nnz && row[eu - 1] == row[eu];
+      if (!(open && row[bu] == row[eu - 1])) break;
+    }
+    coo_store(y, r, s, alpha, beta, ACCUM);
+  }
+}
+
+template <typename XT, typename AT>
+__global__ void scale_kernel(int64_t n, XT* __restrict__ y, AT beta, const int* gate) {
+  if (gated(gate)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = beta == AT(0) ? XT(0) : (XT)(beta * to_acc(y[i]));
+}
+
+// -------------------------------------------------------------- dispatch --
+
+template <typename K>
+int resident_blocks(K kernel, int threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb;
+}
+
+template <typename VT, typename XT>
+struct SpmvImpl {
+  using AT = acc_t<VT>;
+
+  template <int S, int R, bool DOT>
+  static int csr_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
+                        const DotSpec& d, int extra, const int* gate) {
+    auto kern = csr_subwarp_kernel<S, R, VT, XT, DOT>;
+    static int per_sm = resident_blocks(kern, 256);
+    const int64_t rows_per_block = (int64_t)R * (256 / S);
+    int64_t g = (A->n_rows + rows_per_block - 1) / rows_per_block;
+    int64_t cap = (int64_t)per_sm * sm_count();
+    if (DOT && cap > kDotSlots - 1) cap = kDotSlots - 1;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    CsrArgs<VT, XT> a{A->n_rows, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val), x, y,
+                      alpha, beta, A->plan.long_thr};
+    kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g + extra, gate);
+    return (int)g;
+  }
+
+  template <bool DOT>
+  static int csr_dispatch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
+                          const DotSpec& d, int extra, const int* gate) {
+    const int S = A->plan.S, R = A->plan.R;
+#define GKO_CSR_CASE(SS, RR) \
+  if (S == SS && R == RR) return csr_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+#define GKO_CSR_ROW(SS) GKO_CSR_CASE(SS, 1) GKO_CSR_CASE(SS, 2) GKO_CSR_CASE(SS, 4) GKO_CSR_CASE(SS, 8)
+    GKO_CSR_ROW(1) GKO_CSR_ROW(2) GKO_CSR_ROW(4) GKO_CSR_ROW(8) GKO_CSR_ROW(16) GKO_CSR_ROW(32)
+#undef GKO_CSR_ROW
+#undef GKO_CSR_CASE
+    return -1;
+  }
+
+  static int csr(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s, void* scratch,
+                 const DotSpec* dot, const int* gate) {
+    const bool has_long = A->plan.n_long > 0;
+    DotSpec d = dot ? *dot : DotSpec{};
+    const int extra = has_long ? 1 : 0;
+    int g = dot ? csr_dispatch<true>(A, x, y, alpha, beta, s, d, extra, gate)
+                : csr_dispatch<false>(A, x, y, alpha, beta, s, d, extra, gate);
+    if (g < 0) return fail(GKO_INVALID_ARG, "unsupported CSR plan");
+    if (has_long) {
+      AT* partial = static_cast<AT*>(scratch);
+      auto kc = csr_long_chunk_kernel<VT, XT>;
+      static int per_sm = resident_blocks(kc, 256);
+      int64_t blocks = (A->plan.n_chunks + 7) / 8;
+      const int64_t cap = (int64_t)per_sm * sm_count();
+      if (blocks > cap) blocks = cap;
+      if (blocks < 1) blocks = 1;
+      kc<<<(unsigned)blocks, 256, 0, s>>>(A->plan.n_chunks, ptr<int32_t>(A->plan.chunk_row),
+                                          ptr<int32_t>(A->plan.chunk_start), ptr<int32_t>(A->row_ptr),
+                                          ptr<int32_t>(A->col), ptr<VT>(A->val), x, partial, gate);
+      if (dot)
+        csr_long_fixup_kernel<VT, XT, true><<<1, 256, 0, s>>>(A->plan.n_long, ptr<int32_t>(A->plan.long_rows),
+            ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha, beta, d, g, g + 1, gate);
+      else
+        csr_long_fixup_kernel<VT, XT, false><<<1, 256, 0, s>>>(A->plan.n_long, ptr<int32_t>(A->plan.long_rows),
+            ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha, beta, d, 0, 0, gate);
+    }
+    GKO_TRY_CUDA(cudaGetLastError());
+    return GKO_OK;
+  }
+
+  static constexpr int ell_rpt() { return sizeof(VT) == 8 ? 2 : 4; }
+
+  template <bool DOT>
+  static int ell_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
+                        const DotSpec& d, const int* gate) {
+    constexpr int RPT = ell_rpt();
+    auto kern = ell_kernel<RPT, VT, XT, DOT>;
+    static int per_sm = resident_blocks(kern, 256);
+    const int64_t groups = (A->n_rows + RPT - 1) / RPT;
+    int64_t g = (groups + 255) / 256;
+    int64_t cap = (int64_t)per_sm * sm_count();
+    if (DOT && cap > kDotSlots) cap = kDotSlots;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    EllArgs<VT, XT> a{A->n_rows, A->K, A->stride, ptr<int32_t>(A->ell_col), ptr<VT>(A->ell_val), x, y, alpha, beta};
+    kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g, gate);
+    GKO_TRY_CUDA(cudaGetLastError());
+    return GKO_OK;
+  }
+
+  static int coo_part(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s, void* scratch,
+                      bool accum, const int* gate) {
+    const int64_t nnz = A->coo_nnz;
+    if (nnz == 0) {
+      if (!accum) {
+        scale_kernel<XT, AT><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((A->n_rows + 255) / 256, 4096)),
+                               256, 0, s>>>(A->n_rows, y, beta, gate);
+        GKO_TRY_CUDA(cudaGetLastError());
+      }
+      return GKO_OK;
+    }
+    const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
+    AT* carry = static_cast<AT*>(scratch);
+    CooArgs<VT, XT> a{A->n_rows, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col), ptr<VT>(A->coo_val),
+                      x, y, alpha, beta};
+    const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
+    if (accum) {
+      coo_kernel<VT, XT, true><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+      coo_fixup_kernel<VT, XT, true><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
+    } else {
+      coo_kernel<VT, XT, false><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+      coo_fixup_kernel<VT, XT, false><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
+    }
+    GKO_TRY_CUDA(cudaGetLastError());
+    return GKO_OK;
+  }
+
+  static int run(const gko_matrix_s* A, const XT* x, XT* y, double alpha_d, double beta_d, cudaStream_t s,
+                 void* scratch, const DotSpec* dot, const int* gate) {
+    const AT alpha = (AT)alpha_d, beta = (AT)beta_d;
+    DotSpec d = dot ? *dot : DotSpec{};
+    switch (A->fmt) {
+      case GKO_CSR:
+        return csr(A, x, y, alpha, beta, s, scratch, dot, gate);
+      case GKO_ELL:
+        return dot ? ell_launch<true>(A, x, y, alpha, beta, s, d, gate)
+                   : ell_launch<false>(A, x, y, alpha, beta, s, d, gate);
+      case GKO_COO:
+        return coo_part(A, x, y, alpha, beta, s, scratch, false, gate);
+      case GKO_HYBRID:
+        GKO_TRY(ell_launch<false>(A, x, y, alpha, beta, s, d, gate));
+        return coo_part(A, x, y, alpha, beta, s, scratch, true, gate);
+    }
+    return fail(GKO_INVALID_ARG, "unknown format");
+  }
+};
+
+}  // namespace gko

@@ -1,0 +1,350 @@
+"""Thin Python binding of the C ABI in ``include/gko.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libgko_gb300.so``.  Functions keep the C names.  Device vectors
+are ``torch`` CUDA tensors (PyTorch provides device memory and streams);
+host arrays are numpy arrays.  A non-OK status raises :class:`GkoError`.
+There is no CPU fallback: without the built library or a GPU, :func:`load`
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgko_gb300.so")
+
+OK, INVALID_ARG, OUT_OF_MEMORY, FORMAT_UNSUITABLE, NOT_CONVERGED, BREAKDOWN, TIMEOUT, CUDA_ERROR, \
+    BUDGET_EXCEEDED, NOT_SUPPORTED = range(10)
+F64, F32, BF16 = 0, 1, 2
+CSR, ELL, COO, HYBRID = 0, 1, 2, 3
+PRECISION_F64, PRECISION_MIXED_F32, PRECISION_MIXED_BF16 = 0, 1, 2
+
+_lib = None
+_P = C.c_void_p
+_I32 = C.c_int32
+_I64 = C.c_int64
+_D = C.c_double
+_PI64 = C.POINTER(C.c_int64)
+_PI32 = C.POINTER(C.c_int32)
+
+
+class GkoError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("precision", C.c_int32), ("inner_tol", C.c_double),
+                ("max_outer", C.c_int32), ("inner_maxit", C.c_int32), ("check_every", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class SolveResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer_iterations", C.c_int32),
+                ("reserved", C.c_int32), ("rel_residual", C.c_double)]
+
+    def __repr__(self):
+        return (f"SolveResult(status={self.status}, iterations={self.iterations}, "
+                f"outer_iterations={self.outer_iterations}, rel_residual={self.rel_residual:.3e})")
+
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "gko_last_error": (C.c_char_p, []),
+    "gko_status_string": (C.c_char_p, [C.c_int]),
+    "gko_version": (C.c_int, []),
+    "gko_set_memory_budget": (C.c_int, [_I64]),
+    "gko_memory_in_use": (C.c_int, [_PI64]),
+    "gko_matrix_create_csr": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "gko_matrix_convert_to_ell": (C.c_int, [_P, _D, _P, C.POINTER(_P)]),
+    "gko_matrix_convert_to_coo": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "gko_matrix_convert_to_hybrid": (C.c_int, [_P, _I32, _P, C.POINTER(_P)]),
+    "gko_matrix_convert_values": (C.c_int, [_P, C.c_int, _P, C.POINTER(_P)]),
+    "gko_matrix_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _PI64, _PI64, _PI64, _PI32,
+                                  _PI64, _PI64, _PI64]),
+    "gko_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gko_matrix_plan": (C.c_int, [_P, _PI32, _PI32, _PI32, _PI64, _PI64, _PI64]),
+    "gko_matrix_set_plan": (C.c_int, [_P, _I32, _I32, _P]),
+    "gko_matrix_destroy": (C.c_int, [_P]),
+    "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
+    "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
+    "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
+    "gko_axpy": (C.c_int, [_I64, _D, _P, _P, _P]),
+    "gko_multi_axpy_norm": (C.c_int, [_I64, _I32, _P, _P, _I64, _P, C.POINTER(_D), _P]),
+    "gko_multi_dot": (C.c_int, [_I64, _I32, _P, _I64, _P, _P, _P]),
+    "gko_spmv_dot": (C.c_int, [_P, _P, _P, C.POINTER(_D), _P]),
+}
+OPTIONAL = {
+    "gko_solve_cg": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "gko_solve_bicgstab": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "gko_solve_gmres": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (no fallback: raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    for name, (ret, args) in {**SIGNATURES, **OPTIONAL}.items():
+        f = getattr(L, name, None)
+        if f is None:
+            if name in SIGNATURES:
+                raise RuntimeError(f"{path} does not export {name}")
+            continue
+        f.restype = ret
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def lib():
+    return _lib if _lib is not None else load()
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        msg = lib().gko_last_error().decode(errors="replace")
+        raise GkoError(status, where, msg or lib().gko_status_string(status).decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (contiguous)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+_NP_DTYPE = {F64: np.float64, F32: np.float32}
+
+
+# ------------------------------------------------------------------ matrices
+
+class Matrix:
+    """Owning wrapper of a gko_matrix handle."""
+
+    def __init__(self, handle: C.c_void_p):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.gko_matrix_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    @property
+    def _as_param_(self):
+        return self.handle
+
+    def info(self):
+        fmt, dt = C.c_int(), C.c_int()
+        n, m, nnz, stride, coo, nbytes = (C.c_int64() for _ in range(6))
+        K = C.c_int32()
+        _check(lib().gko_matrix_info(self.handle, C.byref(fmt), C.byref(dt), C.byref(n), C.byref(m), C.byref(nnz),
+                                     C.byref(K), C.byref(stride), C.byref(coo), C.byref(nbytes)), "info")
+        return dict(format=fmt.value, dtype=dt.value, n_rows=n.value, n_cols=m.value, nnz=nnz.value,
+                    ell_width=K.value, ell_stride=stride.value, coo_nnz=coo.value, bytes=nbytes.value)
+
+    def plan(self):
+        S, R, thr = C.c_int32(), C.c_int32(), C.c_int32()
+        nl, nc = C.c_int64(), C.c_int64()
+        hist = (C.c_int64 * 33)()
+        _check(lib().gko_matrix_plan(self.handle, C.byref(S), C.byref(R), C.byref(thr), C.byref(nl), C.byref(nc),
+                                     hist), "plan")
+        return dict(subwarp=S.value, rows_per_subwarp=R.value, long_threshold=thr.value, n_long_rows=nl.value,
+                    n_long_chunks=nc.value, hist=list(hist))
+
+    def set_plan(self, subwarp: int, rows_per_subwarp: int, stream=None):
+        _check(lib().gko_matrix_set_plan(self.handle, subwarp, rows_per_subwarp, _stream(stream)), "set_plan")
+
+    def export(self, stream=None):
+        """Host copies of the device arrays (dict of numpy arrays)."""
+        inf = self.info()
+        vdt = {F64: np.float64, F32: np.float32, BF16: np.uint16}[inf["dtype"]]
+        out = {}
+        args = [None] * 8
+        if inf["format"] == CSR:
+            out["row_ptr"] = np.empty(inf["n_rows"] + 1, np.int32)
+            out["col"] = np.empty(inf["nnz"], np.int32)
+            out["val"] = np.empty(inf["nnz"], vdt)
+            args[0:3] = [out["row_ptr"], out["col"], out["val"]]
+        if inf["format"] in (ELL, HYBRID):
+            slots = inf["ell_width"] * inf["ell_stride"]
+            out["ell_col"] = np.empty(slots, np.int32)
+            out["ell_val"] = np.empty(slots, vdt)
+            args[3:5] = [out["ell_col"], out["ell_val"]]
+        if inf["format"] in (COO, HYBRID):
+            out["coo_row"] = np.empty(inf["coo_nnz"], np.int32)
+            out["coo_col"] = np.empty(inf["coo_nnz"], np.int32)
+            out["coo_val"] = np.empty(inf["coo_nnz"], vdt)
+            args[5:8] = [out["coo_row"], out["coo_col"], out["coo_val"]]
+        _check(lib().gko_matrix_export(self.handle, *[_hptr(a) for a in args], _stream(stream)), "export")
+        out.update(inf)
+        return out
+
+
+def gko_matrix_create_csr(n_rows, n_cols, row_ptr, col, values, dtype=F64, stream=None) -> Matrix:
+    """Create from host numpy arrays or device torch tensors."""
+    h = C.c_void_p()
+    on_dev = not isinstance(row_ptr, np.ndarray)
+    if on_dev:
+        nnz = int(col.numel())
+        ptrs = (_dptr(row_ptr), _dptr(col), _dptr(values))
+    else:
+        row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+        col = np.ascontiguousarray(col, np.int32)
+        values = np.ascontiguousarray(values)
+        nnz = int(col.size)
+        ptrs = (_hptr(row_ptr), _hptr(col), _hptr(values))
+    _check(lib().gko_matrix_create_csr(n_rows, n_cols, nnz, *ptrs, dtype, 1 if on_dev else 0, _stream(stream),
+                                       C.byref(h)), "gko_matrix_create_csr")
+    return Matrix(h)
+
+
+def from_csr(A, dtype=F64, stream=None) -> Matrix:
+    """Create from an object with n_rows, n_cols, row_ptr, col, val (host)."""
+    vals = np.ascontiguousarray(A.val, dtype=_NP_DTYPE.get(dtype, np.float64))
+    if dtype == BF16:
+        raise ValueError("create F64/F32 and convert with gko_matrix_convert_values for BF16")
+    return gko_matrix_create_csr(A.n_rows, A.n_cols, A.row_ptr, A.col, vals, dtype, stream)
+
+
+def _convert(fn, where, *args, stream=None) -> Matrix:
+    h = C.c_void_p()
+    _check(fn(*args, _stream(stream), C.byref(h)), where)
+    return Matrix(h)
+
+
+def gko_matrix_convert_to_ell(A: Matrix, max_fill: float = 0.0, stream=None) -> Matrix:
+    return _convert(lib().gko_matrix_convert_to_ell, "convert_to_ell", A.handle, max_fill, stream=stream)
+
+
+def gko_matrix_convert_to_coo(A: Matrix, stream=None) -> Matrix:
+    return _convert(lib().gko_matrix_convert_to_coo, "convert_to_coo", A.handle, stream=stream)
+
+
+def gko_matrix_convert_to_hybrid(A: Matrix, ell_width: int = -1, stream=None) -> Matrix:
+    return _convert(lib().gko_matrix_convert_to_hybrid, "convert_to_hybrid", A.handle, ell_width, stream=stream)
+
+
+def gko_matrix_convert_values(A: Matrix, to: int, stream=None) -> Matrix:
+    return _convert(lib().gko_matrix_convert_values, "convert_values", A.handle, to, stream=stream)
+
+
+# ---------------------------------------------------------------------- SpMV
+
+def gko_spmv(alpha: float, A: Matrix, x, beta: float, y, vec_dtype=None, stream=None):
+    """y = alpha*A*x + beta*y on device tensors (asynchronous)."""
+    import torch
+    if vec_dtype is None:
+        vec_dtype = F64 if y.dtype == torch.float64 else F32
+    a, b = C.c_double(alpha), C.c_double(beta)
+    _check(lib().gko_spmv(C.byref(a), A.handle, _dptr(x), C.byref(b), _dptr(y), vec_dtype, _stream(stream)),
+           "gko_spmv")
+    return y
+
+
+def gko_dot(x, y, stream=None) -> float:
+    r = C.c_double()
+    _check(lib().gko_dot(x.numel(), _dptr(x), _dptr(y), C.byref(r), _stream(stream)), "gko_dot")
+    return r.value
+
+
+def gko_nrm2(x, stream=None) -> float:
+    r = C.c_double()
+    _check(lib().gko_nrm2(x.numel(), _dptr(x), C.byref(r), _stream(stream)), "gko_nrm2")
+    return r.value
+
+
+def gko_axpy(a: float, x, y, stream=None):
+    _check(lib().gko_axpy(x.numel(), a, _dptr(x), _dptr(y), _stream(stream)), "gko_axpy")
+    return y
+
+
+def gko_multi_dot(V, w, k: int, stream=None) -> np.ndarray:
+    """h[j] = V[j] . w for the first k rows of the 2-D tensor V."""
+    h = np.empty(k, np.float64)
+    _check(lib().gko_multi_dot(w.numel(), k, _dptr(V), V.stride(0), _dptr(w), _hptr(h), _stream(stream)),
+           "gko_multi_dot")
+    return h
+
+
+def gko_multi_axpy_norm(V, h: np.ndarray, y, stream=None) -> float:
+    """y -= sum_j h[j] V[j]; returns ||y||."""
+    h = np.ascontiguousarray(h, np.float64)
+    r = C.c_double()
+    _check(lib().gko_multi_axpy_norm(y.numel(), h.size, _hptr(h), _dptr(V), V.stride(0), _dptr(y), C.byref(r),
+                                     _stream(stream)), "gko_multi_axpy_norm")
+    return r.value
+
+
+def gko_spmv_dot(A: Matrix, x, y, stream=None) -> float:
+    r = C.c_double()
+    _check(lib().gko_spmv_dot(A.handle, _dptr(x), _dptr(y), C.byref(r), _stream(stream)), "gko_spmv_dot")
+    return r.value
+
+
+# ------------------------------------------------------------------- solvers
+
+def _solve(name, A: Matrix, b, x, rel_tol, max_iters, opts=None, stream=None, raise_on_fail=False):
+    fn = getattr(lib(), name, None)
+    if fn is None:
+        raise RuntimeError(f"{name} not available in {LIB_PATH}")
+    res = SolveResult()
+    st = fn(A.handle, _dptr(b), _dptr(x), rel_tol, max_iters, C.byref(opts) if opts is not None else None,
+            C.byref(res), _stream(stream))
+    if st not in (OK, NOT_CONVERGED, BREAKDOWN) or raise_on_fail:
+        _check(st, name)
+    return res
+
+
+def gko_solve_cg(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=None):
+    return _solve("gko_solve_cg", A, b, x, rel_tol, max_iters, opts, stream)
+
+
+def gko_solve_bicgstab(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=None):
+    return _solve("gko_solve_bicgstab", A, b, x, rel_tol, max_iters, opts, stream)
+
+
+def gko_solve_gmres(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=None):
+    return _solve("gko_solve_gmres", A, b, x, rel_tol, max_iters, opts, stream)
+
+
+def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0):
+    return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, 0)
+
+
+def set_memory_budget(nbytes: int):
+    _check(lib().gko_set_memory_budget(int(nbytes)), "set_memory_budget")
+
+
+def memory_in_use() -> int:
+    v = C.c_int64()
+    _check(lib().gko_memory_in_use(C.byref(v)), "memory_in_use")
+    return v.value

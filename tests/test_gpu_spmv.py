@@ -1,0 +1,259 @@
+"""GPU parity of SpMV (CSR/ELL/COO/hybrid x FP64/FP32/BF16), the format
+conversions and the CSR plan against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import bf16_round, check_spmv_f32, check_spmv_f64, dev, host, rows_subset
+from paper_2006_14290_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FORMATS = ["csr", "ell", "coo", "hybrid"]
+
+
+def small_cases():
+    rng = np.random.default_rng(2024)
+    yield "laplace2d_64", I.laplace2d_5pt(64)
+    yield "stencil27_12", I.stencil3d_27pt(12)
+    yield "stencil7_17", I.stencil3d_7pt(17)
+    yield "convdiff_9", I.convdiff3d_7pt(9, 10.0)
+    yield "random_empty_unsorted", I.random_csr(3001, 2500, 0.004, rng, empty_rows=0.3, sort_cols=False)
+    yield "dup_cols", I.rows_csr(rng.integers(0, 40, 777), 50, rng)
+    yield "long_rows", I.rows_csr([3, 5000, 0, 2, 40000, 1, 1025, 1024, 7] + [2] * 3000, 60000, rng)
+    yield "powerlaw_20k", I.powerlaw(20000, seed=1)
+    yield "banded_5k", I.banded(5000, 16, 0.3, seed=2)
+    yield "n1", I.rows_csr([3], 5, rng)
+
+
+CASES = list(small_cases())
+
+
+def make(G, A, fmt, dtype):
+    vals = A.val if dtype == G.F64 else A.val.astype(np.float32)
+    M = G.from_csr(A, G.F64 if dtype in (G.F64, G.BF16) else G.F32)
+    if dtype == G.BF16:
+        M = G.gko_matrix_convert_values(M, G.BF16)
+    if fmt == "ell":
+        M = G.gko_matrix_convert_to_ell(M, max_fill=1e9)
+    elif fmt == "coo":
+        M = G.gko_matrix_convert_to_coo(M)
+    elif fmt == "hybrid":
+        M = G.gko_matrix_convert_to_hybrid(M, -1)
+    return M
+
+
+def values_for(G, A, dtype):
+    if dtype == G.F64:
+        return A.val
+    if dtype == G.F32:
+        return A.val.astype(np.float32).astype(np.float64)
+    return bf16_round(A.val)
+
+
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+def test_spmv_parity(gko, name, A, fmt, dt):
+    G = gko
+    dtype = {"f64": G.F64, "f32": G.F32, "bf16": G.BF16}[dt]
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    M = make(G, A, fmt, dtype)
+    for alpha, beta in [(1.0, 0.0), (-0.75, 1.5)]:
+        if dtype == G.F64:
+            yd = dev(y0)
+            G.gko_spmv(alpha, M, dev(x), beta, yd)
+            check_spmv_f64(host(yd), A, x, alpha, beta, y0)
+        else:
+            x32 = x.astype(np.float32)
+            yd = dev(y0, np.float32)
+            G.gko_spmv(alpha, M, dev(x32), beta, yd)
+            check_spmv_f32(host(yd), A, x32.astype(np.float64), alpha, beta, y0.astype(np.float32).astype(np.float64),
+                           values_for(G, A, dtype))
+
+
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_conversions_bit_exact(gko, name, A):
+    G = gko
+    M = G.from_csr(A)
+    ex = M.export()
+    np.testing.assert_array_equal(ex["row_ptr"], A.row_ptr)
+    np.testing.assert_array_equal(ex["col"], A.col)
+    assert ex["val"].tobytes() == A.val.tobytes()
+
+    E = G.gko_matrix_convert_to_ell(M, max_fill=1e9).export()
+    Eo = O.csr_to_ell(A)
+    assert (E["ell_width"], E["ell_stride"]) == (Eo.K, Eo.stride)
+    np.testing.assert_array_equal(E["ell_col"], Eo.col)
+    assert E["ell_val"].tobytes() == Eo.val.tobytes()
+
+    C = G.gko_matrix_convert_to_coo(M).export()
+    Co = O.csr_to_coo(A)
+    np.testing.assert_array_equal(C["coo_row"], Co.row)
+    np.testing.assert_array_equal(C["coo_col"], Co.col)
+    assert C["coo_val"].tobytes() == Co.val.tobytes()
+
+    for K in (-1, 0, 2, 5):
+        H = G.gko_matrix_convert_to_hybrid(M, K).export()
+        Ho = O.csr_to_hybrid(A, K)
+        assert H["ell_width"] == Ho.ell.K
+        np.testing.assert_array_equal(H["ell_col"], Ho.ell.col)
+        assert H["ell_val"].tobytes() == Ho.ell.val.tobytes()
+        np.testing.assert_array_equal(H["coo_row"], Ho.coo.row)
+        np.testing.assert_array_equal(H["coo_col"], Ho.coo.col)
+        assert H["coo_val"].tobytes() == Ho.coo.val.tobytes()
+
+
+def test_value_conversions_round_to_nearest(gko):
+    G = gko
+    A = I.powerlaw(3000, seed=5)
+    M = G.from_csr(A)
+    v32 = G.gko_matrix_convert_values(M, G.F32).export()["val"]
+    assert v32.tobytes() == A.val.astype(np.float32).tobytes()
+    vb = G.gko_matrix_convert_values(M, G.BF16).export()["val"]
+    ref = bf16_round(A.val).astype(np.float32).view(np.uint32) >> 16
+    np.testing.assert_array_equal(vb.astype(np.uint32), ref)
+
+
+def test_plan_histogram_and_split(gko):
+    G = gko
+    for A in (I.powerlaw(20000, seed=1), I.laplace2d_5pt(64), I.rows_csr([0, 1, 2, 3, 4, 2000, 70000], 10, np.random.default_rng(0))):
+        p = G.from_csr(A).plan()
+        L = A.row_lengths()
+        cls = np.where(L == 0, 0, np.floor(np.log2(np.maximum(L, 1))).astype(int) + 1)
+        np.testing.assert_array_equal(p["hist"], np.bincount(cls, minlength=33))
+        short = L[L < 1024]
+        mean = short.mean() if short.size else 1.0
+        S = 1
+        while S < 32 and S < mean:
+            S *= 2
+        assert p["subwarp"] == S and p["long_threshold"] == 32 * S
+        longs = L[L > 32 * S]
+        assert p["n_long_rows"] == longs.size
+        assert p["n_long_chunks"] == int(np.sum((longs + 1023) // 1024))
+
+
+@pytest.mark.parametrize("S,R", [(1, 1), (2, 8), (4, 4), (8, 2), (16, 1), (32, 4), (32, 8)])
+def test_every_subwarp_plan_matches_oracle(gko, S, R):
+    G = gko
+    A = I.powerlaw(30000, seed=3)
+    M = G.from_csr(A)
+    M.set_plan(S, R)
+    assert M.plan()["subwarp"] == S
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    yd = dev(y0)
+    G.gko_spmv(2.0, M, dev(x), -1.0, yd)
+    check_spmv_f64(host(yd), A, x, 2.0, -1.0, y0)
+
+
+def test_edge_cases(gko):
+    G = gko
+    # zero rows
+    Z = I.Csr(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    M = G.from_csr(Z)
+    G.gko_spmv(1.0, M, dev(np.ones(5)), 0.0, dev(np.zeros(1)))
+    # no nonzeros: y = beta*y (beta = 0 writes zeros without reading NaN)
+    E = I.Csr(10, 10, np.zeros(11, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    for fmt in FORMATS:
+        M = make(G, E, fmt, G.F64)
+        yd = dev(np.arange(10.0))
+        G.gko_spmv(1.0, M, dev(np.ones(10)), 3.0, yd)
+        np.testing.assert_array_equal(host(yd), 3.0 * np.arange(10.0))
+        yd = dev(np.full(10, np.nan))
+        G.gko_spmv(1.0, M, dev(np.ones(10)), 0.0, yd)
+        np.testing.assert_array_equal(host(yd), np.zeros(10))
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_nan_semantics(gko, fmt):
+    G = gko
+    A = I.laplace2d_5pt(16)
+    M = make(G, A, fmt, G.F64)
+    x = np.ones(256)
+    x[37] = np.nan
+    y0 = np.full(256, np.nan)
+    yd = dev(y0)
+    G.gko_spmv(1.0, M, dev(x), 0.0, yd)
+    check_spmv_f64(host(yd), A, x, 1.0, 0.0, None)
+    yd = dev(np.ones(256))
+    G.gko_spmv(0.0, M, dev(x), 1.0, yd)
+    check_spmv_f64(host(yd), A, x, 0.0, 1.0, np.ones(256))
+
+
+def test_invalid_inputs_rejected(gko):
+    G = gko
+    A = I.laplace2d_5pt(4)
+    bad_col = A.col.copy()
+    bad_col[3] = 16
+    with pytest.raises(G.GkoError) as e:
+        G.gko_matrix_create_csr(16, 16, A.row_ptr, bad_col, A.val)
+    assert e.value.status == G.INVALID_ARG
+    bad_rp = A.row_ptr.copy()
+    bad_rp[5], bad_rp[6] = bad_rp[6], bad_rp[5]
+    with pytest.raises(G.GkoError):
+        G.gko_matrix_create_csr(16, 16, bad_rp, A.col, A.val)
+    with pytest.raises(G.GkoError) as e:
+        G.gko_matrix_convert_to_ell(G.from_csr(I.powerlaw(20000, seed=1)))
+    assert e.value.status == G.FORMAT_UNSUITABLE
+    M = G.from_csr(A)
+    import torch
+    with pytest.raises(G.GkoError):
+        G.gko_spmv(1.0, M, torch.ones(16, device="cuda", dtype=torch.float32), 0.0,
+                   torch.zeros(16, device="cuda", dtype=torch.float32))
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_deterministic(gko, fmt):
+    G = gko
+    A = I.powerlaw(50000, seed=9)
+    M = make(G, A, fmt, G.F64) if fmt != "ell" else make(G, I.banded(20000, 40, 0.5, seed=1), fmt, G.F64)
+    n = M.info()["n_cols"]
+    x = dev(np.random.default_rng(0).uniform(-1, 1, n))
+    outs = []
+    for _ in range(3):
+        yd = dev(np.zeros(M.info()["n_rows"]))
+        G.gko_spmv(1.0, M, x, 0.0, yd)
+        outs.append(host(yd).tobytes())
+    assert outs[0] == outs[1] == outs[2]
+
+
+def _full_size(name):
+    if name == "stencil27_128":
+        return I.stencil3d_27pt(128)
+    if name == "powerlaw_1m":
+        return I.powerlaw(1_000_000, seed=0)
+    return I.banded(1_000_000, 64, 0.3, seed=0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["stencil27_128", "powerlaw_1m", "banded_1m"])
+def test_full_size_sampled(gko, name):
+    """Bench-size matrices in the bench's launch configuration, checked on
+    sampled rows (plus every long row) against the oracle."""
+    G = gko
+    A = _full_size(name)
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-1, 1, A.n_cols)
+    L = A.row_lengths()
+    idx = np.unique(np.concatenate([rng.integers(0, A.n_rows, 4000), [0, A.n_rows - 1],
+                                    np.flatnonzero(L > 256)[:2000]]))
+    sub = rows_subset(A, idx)
+    M64 = G.from_csr(A)
+    formats = [("csr", M64), ("coo", G.gko_matrix_convert_to_coo(M64)), ("hybrid", G.gko_matrix_convert_to_hybrid(M64))]
+    if name != "powerlaw_1m":
+        formats.append(("ell", G.gko_matrix_convert_to_ell(M64)))
+    xd = dev(x)
+    for fmt, M in formats:
+        yd = dev(np.zeros(A.n_rows))
+        G.gko_spmv(1.0, M, xd, 0.0, yd)
+        check_spmv_f64(host(yd)[idx], sub, x, 1.0, 0.0, None)
+        del M
+    M32 = G.from_csr(A, G.F32)
+    x32 = x.astype(np.float32)
+    yd = dev(np.zeros(A.n_rows, np.float32))
+    G.gko_spmv(1.0, M32, dev(x32), 0.0, yd)
+    check_spmv_f32(host(yd)[idx], sub, x32.astype(np.float64), 1.0, 0.0, None, sub.val.astype(np.float32).astype(np.float64))

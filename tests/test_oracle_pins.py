@@ -403,3 +403,27 @@ def test_ir_inner_update_is_fp32_stored():
         bb = np.random.default_rng(9).uniform(-1, 1, B.n_rows)
         x, r = O.solve_ir(solver, B, bb, tol=1e-14, max_outer=1, inner_tol=1e-3, inner_maxit=100)
         np.testing.assert_array_equal(x.astype(np.float32).astype(np.float64), x)
+
+
+# ---------------------------------------------------------------- BLAS-1 --
+
+def test_blas1_exact_on_integers_and_rationals():
+    rng = np.random.default_rng(12)
+    x = rng.integers(-9, 10, 300).astype(float)
+    y = rng.integers(-9, 10, 300).astype(float)
+    assert O.dot(x, y) == float(sum(int(a) * int(b) for a, b in zip(x, y)))
+    np.testing.assert_array_equal(O.axpy(-3.0, x, y), -3.0 * x + y)
+    V = rng.integers(-3, 4, (5, 300)).astype(float)
+    h = O.multi_dot(V, x)
+    np.testing.assert_array_equal(h, [sum(int(a) * int(b) for a, b in zip(v, x)) for v in V])
+    hh = rng.integers(-2, 3, 5).astype(float)
+    out, nrm = O.multi_axpy_norm(V, hh, y)
+    ref = y - hh @ V
+    np.testing.assert_array_equal(out, ref)
+    assert nrm == pytest.approx(math.sqrt(float(sum(int(v) ** 2 for v in ref))), rel=1e-15)
+    # rational check of a non-integer dot
+    xf = rng.uniform(-1, 1, 50)
+    yf = rng.uniform(-1, 1, 50)
+    ex = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(xf, yf))
+    bound = 50 * U64 * float(sum(abs(Fraction(float(a)) * Fraction(float(b))) for a, b in zip(xf, yf)))
+    assert abs(O.dot(xf, yf) - float(ex)) <= bound
