@@ -66,6 +66,11 @@ typedef enum { GKO_CSR = 0, GKO_ELL = 1, GKO_COO = 2, GKO_HYBRID = 3 } gko_forma
 GKO_API const char *gko_last_error(void);
 GKO_API const char *gko_status_string(int status);
 
+/* Synchronise `stream` and report device-side failures recorded since the
+ * last call: GKO_TIMEOUT when a bounded wait inside a kernel gave up (the
+ * kernel then returned without finishing its work).  Clears the record. */
+GKO_API int gko_device_status(void *stream);
+
 /* Library version (major*10000 + minor*100 + patch). */
 GKO_API int gko_version(void);
 
@@ -131,18 +136,23 @@ GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void
                       void *ell_val, int32_t *coo_row, int32_t *coo_col, void *coo_val,
                       void *stream);
 
-/* CSR load-balancing plan (built at creation): subwarp width S used for
- * rows of length <= long_threshold, the number of longer rows and of their
- * fixed-size nonzero chunks, and the row-length histogram in log2 classes
- * (hist[0]: empty rows; hist[b], b >= 1: lengths in [2^(b-1), 2^b)),
- * 33 entries.  Any output may be NULL. */
+/* CSR load-balancing plan (built at creation from the row-length histogram).
+ * rows_per_subwarp == 0 means the row-block kernel: row blocks of the
+ * matrix stream into shared memory by bulk copies and `subwarp` lanes sum
+ * each row (regular matrices: longest row <= 4x the mean).  Otherwise the
+ * subwarp kernel: `subwarp` lanes per row, rows_per_subwarp rows per pass,
+ * and rows longer than long_threshold split into fixed-size nonzero chunks
+ * (n_long_rows rows, n_long_chunks chunks).  hist33: row-length histogram in
+ * log2 classes (hist[0]: empty rows; hist[b], b >= 1: lengths in
+ * [2^(b-1), 2^b)).  Any output may be NULL. */
 GKO_API int gko_matrix_plan(gko_matrix csr, int32_t *subwarp, int32_t *rows_per_subwarp,
                     int32_t *long_threshold, int64_t *n_long_rows, int64_t *n_long_chunks,
                     int64_t *hist33);
 
-/* Override the CSR plan's subwarp width S (1,2,4,8,16,32) and rows per
- * subwarp pass R (1,2,4,8); the long-row threshold becomes 32*S.  Used by
- * the autotuner; rebuilds the long-row split.  Synchronises `stream`. */
+/* Override the CSR plan: subwarp width S (1,2,4,8,16,32) and rows per
+ * subwarp pass R (1,2,4,8; the long-row threshold becomes 32*S), or R = 0 for
+ * the row-block kernel with S in 1,2,4,8 (no long-row split).  Used by the
+ * autotuner; rebuilds the long-row split.  Synchronises `stream`. */
 GKO_API int gko_matrix_set_plan(gko_matrix csr, int32_t subwarp, int32_t rows_per_subwarp, void *stream);
 
 GKO_API int gko_matrix_destroy(gko_matrix m);

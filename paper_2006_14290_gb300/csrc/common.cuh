@@ -78,15 +78,19 @@ int budget_reserve(size_t bytes);
 void budget_release(size_t bytes);
 
 int sm_count();
+int* device_error_word();
 size_t dtype_size(gko_dtype t);
 
 // ------------------------------------------------------------- matrix ----
 
 constexpr int kHistBins = 33;
 constexpr int32_t kLongChunk = 1024;  // nonzeros per chunk of a long CSR row
+constexpr int kRbThreads = 256;      // TMA row-block CSR kernel: threads per block
+constexpr int kRbCap = 4096;         // nonzeros staged per shared-memory stage
 
 // Load-balancing plan of the CSR SpMV, built from the row-length histogram.
 struct CsrPlan {
+  int32_t kind = 0;         // 0: subwarp kernel, 1: TMA row-block kernel
   int32_t S = 32;           // subwarp width for ordinary rows
   int32_t R = 4;            // rows per subwarp pass
   int32_t long_thr = 1024;  // rows longer than this use the nonzero split

@@ -196,22 +196,43 @@ static unsigned grid_for(int64_t work, int threads = 256) {
 
 // ------------------------------------------------------------- plan -----
 
-// Subwarp width from the histogram: the smallest power of two (<= 32) not
-// below the mean length of rows shorter than 1024.
-static int32_t choose_subwarp(const int64_t* hist, const int64_t* hist_nnz) {
+// Plan from the row-length histogram.
+//  * Regular matrices (longest row <= 4x the mean row length, e.g. stencils
+//    and banded matrices) use the TMA row-block kernel with S lanes per row:
+//    S = 1 (one thread per row, no reduction) unless rows average more than
+//    48*S entries.  No row is split.
+//  * Skewed matrices use the subwarp kernel: S = the smallest power of two
+//    (<= 32) not below the mean length of rows shorter than 1024, R = 2 rows
+//    per pass, and rows longer than 32*S go to the nonzero split.
+static void choose_plan(CsrPlan& p, int64_t n) {
+  int64_t nz_all = 0;
+  for (int b = 0; b < kHistBins; ++b) nz_all += p.hist_nnz[b];
+  const double mean_all = n ? (double)nz_all / (double)n : 0.0;
+  if (n > 0 && p.max_len <= 4.0 * mean_all + 1.0) {
+    p.kind = 1;
+    int32_t S = 1;
+    while (S < 8 && mean_all > 48.0 * S) S *= 2;
+    p.S = S;
+    p.R = 0;
+    p.long_thr = INT32_MAX;
+    return;
+  }
   int64_t rows = 0, nz = 0;
   for (int b = 0; b <= 10; ++b) {
-    rows += hist[b];
-    nz += hist_nnz[b];
+    rows += p.hist[b];
+    nz += p.hist_nnz[b];
   }
   const double mean = rows ? (double)nz / (double)rows : 1.0;
   int32_t S = 1;
   while (S < 32 && (double)S < mean) S *= 2;
-  return S;
+  p.kind = 0;
+  p.S = S;
+  p.R = 2;
+  p.long_thr = 32 * S;
 }
 
 static bool valid_S(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32; }
-static bool valid_R(int r) { return r == 1 || r == 2 || r == 4 || r == 8; }
+static bool valid_R(int r) { return r == 0 || r == 1 || r == 2 || r == 4 || r == 8; }
 
 static int build_long_split(gko_matrix m, cudaStream_t s) {
   CsrPlan& p = m->plan;
@@ -267,9 +288,7 @@ static int build_plan(gko_matrix m, cudaStream_t s) {
     p.hist_nnz[b] = (int64_t)hh[kHistBins + b];
   }
   p.max_len = mx;
-  p.S = choose_subwarp(p.hist, p.hist_nnz);
-  p.R = 4;
-  p.long_thr = 32 * p.S;
+  choose_plan(p, n);
   return build_long_split(m, s);
 }
 
@@ -385,14 +404,17 @@ int gko_matrix_plan(gko_matrix m, int32_t* S, int32_t* R, int32_t* thr, int64_t*
 
 int gko_matrix_set_plan(gko_matrix m, int32_t S, int32_t R, void* stream) {
   if (!m || m->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "plan needs a CSR handle");
-  if (!valid_S(S) || !valid_R(R)) return fail(GKO_INVALID_ARG, "subwarp must be 1..32 (power of 2), R 1,2,4,8");
+  if (!valid_S(S) || !valid_R(R) || (R == 0 && S > 8))
+    return fail(GKO_INVALID_ARG, "subwarp must be 1..32 (power of 2), R 1,2,4,8; R 0 (row-block) needs S <= 8");
   std::lock_guard<std::mutex> lk(m->mu);
+  m->plan.kind = R == 0 ? 1 : 0;
   m->plan.S = S;
   m->plan.R = R;
-  m->plan.long_thr = 32 * S;
+  m->plan.long_thr = R == 0 ? INT32_MAX : 32 * S;
   GKO_TRY(build_long_split(m, (cudaStream_t)stream));
   for (auto& kv : m->lowp) {  // low-precision copies share the pattern
     if (kv.second->fmt == GKO_CSR) {
+      kv.second->plan.kind = m->plan.kind;
       kv.second->plan.S = S;
       kv.second->plan.R = R;
       kv.second->plan.long_thr = m->plan.long_thr;
@@ -532,6 +554,7 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   m->device = src->device;
   m->row_ptr = src->row_ptr;
   m->col = src->col;
+  m->plan.kind = src->plan.kind;
   m->plan.S = src->plan.S;
   m->plan.R = src->plan.R;
   m->plan.long_thr = src->plan.long_thr;

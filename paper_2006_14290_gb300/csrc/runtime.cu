@@ -52,7 +52,10 @@ DeviceBuffer::~DeviceBuffer() {
 }
 
 int alloc(size_t bytes, Buf* out) {
-  if (bytes < 256) bytes = 256;  // every buffer is a valid, 256-byte aligned pointer
+  // every buffer is a valid, 256-byte aligned pointer with at least 128 bytes
+  // of slack past the requested end, so bulk copies of a tail rounded up to
+  // 16-byte granules stay inside the allocation
+  bytes = (bytes + 128 + 255) / 256 * 256;
   GKO_TRY(budget_reserve(bytes));
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
@@ -118,6 +121,24 @@ Scratch::~Scratch() {
   }
 }
 
+// Device error word: kernels OR in (1 << status) when a bounded wait gives up.
+__device__ int g_device_error;
+
+int* device_error_word() {
+  static int* cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cached[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cached[dev] = static_cast<int*>(p);
+  }
+  return cached[dev];
+}
+
 int sm_count() {
   static int cached[64] = {0};
   int dev = 0;
@@ -162,6 +183,22 @@ const char* gko_status_string(int s) {
 }
 
 int gko_version(void) { return 100; }
+
+int gko_device_status(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int* w = gko::device_error_word();
+  if (!w) return gko::fail(GKO_CUDA_ERROR, "device error word unavailable");
+  int v = 0;
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  GKO_TRY_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    const int zero = 0;
+    GKO_TRY_CUDA(cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    if (v & (1 << GKO_TIMEOUT)) return gko::fail(GKO_TIMEOUT, "a bounded device wait timed out");
+    return gko::fail(GKO_CUDA_ERROR, "device error word set");
+  }
+  return GKO_OK;
+}
 
 int gko_set_memory_budget(int64_t bytes) {
   if (bytes < 0) return gko::fail(GKO_INVALID_ARG, "negative budget");

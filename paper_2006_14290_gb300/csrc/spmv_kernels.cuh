@@ -1,5 +1,12 @@
 // Kernel templates behind spmv_run_{f64,f32,bf16}.  Included by exactly one
 // translation unit per value type.
+//
+// GB300 note: FP64 arithmetic runs at about 2 FMA per clock per SM, so an
+// FP64 SpMV at HBM speed can afford roughly one fully populated FMA warp
+// instruction per 32 nonzeros.  The kernels below therefore keep every lane
+// of an FP64 FMA busy (thread-per-row over staged data, or one FMA per
+// entry in the segmented COO pass) and avoid shuffle reductions per row
+// wherever the row-length histogram allows.
 #pragma once
 
 #include <algorithm>
@@ -7,8 +14,29 @@
 
 #include "reduce.cuh"
 #include "spmv.cuh"
+#include "tma.cuh"
 
 namespace gko {
+
+// Row result: y = alpha*s + beta*y, or y = s when alpha == 1 and beta == 0
+// (no extra FP64 instruction on the common path).
+template <typename XT, typename AT>
+__device__ __forceinline__ AT finish_row(XT* y, int64_t i, AT s, AT alpha, AT beta, bool plain) {
+  if (plain) return s;
+  AT v = alpha * s;
+  if (beta != AT(0)) v = madd(beta, to_acc(y[i]), v);
+  return v;
+}
+
+__device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+template <typename XT>
+__device__ __forceinline__ void dot_accum(const DotSpec& d, int64_t i, XT v, double& wy, double& yy) {
+  const double yv = (double)v;
+  wy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
+  yy += yv * yv;
+}
 
 // ------------------------------------------------------------------- CSR --
 
@@ -22,12 +50,14 @@ struct CsrArgs {
   XT* y;
   acc_t<VT> alpha, beta;
   int32_t long_thr;
+  bool plain;
 };
 
-// Subwarp-per-row CSR: a subwarp of S lanes owns R consecutive rows per pass;
-// lane `rank` reads entries rank, rank+S, ... of each row, loads of all R rows
-// are issued before the gathers, then a log2(S)-step butterfly sums each row.
-// Rows longer than long_thr are skipped (the nonzero split handles them).
+// Subwarp-per-row CSR (irregular matrices): a subwarp of S lanes owns R
+// consecutive rows per pass; lane `rank` reads entries rank, rank+S, ... of
+// each row, loads of all R rows are issued before the gathers, then a
+// log2(S)-step butterfly sums each row.  Rows longer than long_thr are
+// skipped (the nonzero split handles them).
 template <int S, int R, typename VT, typename XT, bool DOT>
 __global__ void __launch_bounds__(256) csr_subwarp_kernel(CsrArgs<VT, XT> a, DotSpec d, int expected,
                                                           const int* gate) {
@@ -80,18 +110,155 @@ __global__ void __launch_bounds__(256) csr_subwarp_kernel(CsrArgs<VT, XT> a, Dot
     for (int r = 0; r < R; ++r) {
       const int64_t i = row0 + r;
       if ((r & (S - 1)) == rank && i < a.n && !((long_bits >> r) & 1u)) {
-        AT v = a.alpha * sum[r];
-        if (a.beta != AT(0)) v = madd(a.beta, to_acc(a.y[i]), v);
-        a.y[i] = (XT)v;
-        if (DOT) {
-          const double yv = (double)(XT)v;
-          dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
-          dyy += yv * yv;
-        }
+        const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
+        a.y[i] = v;
+        if (DOT) dot_accum(d, i, v, dwy, dyy);
       }
     }
   }
   if (DOT) dot_epilogue2<256>(dwy, dyy, d, blockIdx.x, expected);
+}
+
+// TMA row-block CSR (regular matrices).  A block owns row blocks of
+// RB = 256/S consecutive rows (round robin over a persistent grid).  The
+// nonzeros of a row block, [row_ptr[b*RB], row_ptr[(b+1)*RB]) widened to
+// 8-entry granules, stream into shared memory by bulk copies in stages of
+// kRbCap entries, double buffered: thread 0 issues the copy of stage q+2
+// while all threads consume stage q.  Each row is summed by S lanes reading
+// the staged entries (S = 1: one thread per row, no reduction at all), so
+// global loads are fully coalesced and every FMA lane is busy.
+template <typename VT>
+constexpr size_t rb_smem_bytes() {
+  return 128 + 2 * (size_t)kRbCap * (sizeof(int32_t) + sizeof(VT));
+}
+
+template <int S, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, DotSpec d, int expected,
+                                                                   const int* gate, int* err) {
+  using AT = acc_t<VT>;
+  constexpr int RB = kRbThreads / S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
+  VT* sval = reinterpret_cast<VT*>(smem + 128 + 2 * (size_t)kRbCap * sizeof(int32_t));
+  if (gated(gate)) return;
+  const int64_t nrb = (a.n + RB - 1) / RB;
+  if ((int64_t)blockIdx.x >= nrb) return;
+  const int tid = threadIdx.x;
+  const int rank = tid & (S - 1);
+  const int lrow = tid / S;
+  const unsigned mask = subwarp_mask<S>();
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  // chunk cursor over this block's row blocks
+  struct Cur {
+    int64_t b, kb, ke;
+    int j, nch;
+  };
+  auto open = [&](Cur& c) {
+    const int32_t k0 = __ldg(a.rp + c.b * RB);
+    const int32_t k1 = __ldg(a.rp + min((c.b + 1) * RB, a.n));
+    c.kb = (int64_t)(k0 & ~7);
+    c.ke = ((int64_t)k1 + 7) & ~7ll;
+    c.nch = (int)imax64(1, (c.ke - c.kb + kRbCap - 1) / kRbCap);
+    c.j = 0;
+  };
+  auto advance = [&](Cur& c) -> bool {
+    if (++c.j < c.nch) return true;
+    c.b += gridDim.x;
+    if (c.b >= nrb) return false;
+    open(c);
+    return true;
+  };
+  auto issue = [&](const Cur& c, int stage) {
+    const int64_t cs = c.kb + (int64_t)c.j * kRbCap;
+    const int64_t len = imin64(kRbCap, c.ke - cs);
+    if (len <= 0) {
+      mbar_arrive(&bar[stage]);
+    } else {
+      const unsigned bc = (unsigned)(len * sizeof(int32_t)), bv = (unsigned)(len * sizeof(VT));
+      mbar_arrive_expect_tx(&bar[stage], bc + bv);
+      bulk_g2s(scol + (size_t)stage * kRbCap, a.col + cs, bc, &bar[stage]);
+      bulk_g2s(sval + (size_t)stage * kRbCap, a.val + cs, bv, &bar[stage]);
+    }
+  };
+
+  Cur c;
+  c.b = blockIdx.x;
+  open(c);
+  Cur p = c;
+  bool p_ok = true;
+  if (tid == 0) {
+    issue(p, 0);
+    p_ok = advance(p);
+    if (p_ok) {
+      issue(p, 1);
+      p_ok = advance(p);
+    }
+  }
+  auto row_bounds = [&](int64_t b, int32_t& rs, int32_t& re) {
+    const int64_t i = b * RB + lrow;
+    rs = re = 0;
+    if (i < a.n) {
+      rs = __ldg(a.rp + i);
+      re = __ldg(a.rp + i + 1);
+    }
+  };
+  int32_t rs, re;
+  row_bounds(c.b, rs, re);
+  AT sum = AT(0);
+  double dwy = 0.0, dyy = 0.0;
+  bool timed_out = false;
+  for (unsigned q = 0;; ++q) {
+    const int stage = q & 1;
+    const bool ok = mbar_wait(&bar[stage], (q >> 1) & 1u, err);
+    if (__syncthreads_or(!ok)) {
+      if (!ok) mbar_wait(&bar[stage], (q >> 1) & 1u, err);  // let our own copy land before leaving
+      timed_out = true;
+      break;
+    }
+    const int32_t* sc = scol + (size_t)stage * kRbCap;
+    const VT* sv = sval + (size_t)stage * kRbCap;
+    const int64_t cs = c.kb + (int64_t)c.j * kRbCap;
+    const int lo = (int)(imax64(rs, cs) - cs);
+    const int hi = (int)(imin64(re, cs + kRbCap) - cs);
+    int k = lo + rank;
+    for (; k + 3 * S < hi; k += 4 * S) {
+      const int32_t c0 = sc[k], c1 = sc[k + S], c2 = sc[k + 2 * S], c3 = sc[k + 3 * S];
+      const VT v0 = sv[k], v1 = sv[k + S], v2 = sv[k + 2 * S], v3 = sv[k + 3 * S];
+      const XT x0 = ld_vec(a.x + c0), x1 = ld_vec(a.x + c1), x2 = ld_vec(a.x + c2), x3 = ld_vec(a.x + c3);
+      sum = madd(to_acc(v0), to_acc(x0), sum);
+      sum = madd(to_acc(v1), to_acc(x1), sum);
+      sum = madd(to_acc(v2), to_acc(x2), sum);
+      sum = madd(to_acc(v3), to_acc(x3), sum);
+    }
+    for (; k < hi; k += S) sum = madd(to_acc(sv[k]), to_acc(ld_vec(a.x + sc[k])), sum);
+    __syncthreads();  // stage consumed by everyone
+    if (tid == 0 && p_ok) {
+      issue(p, stage);
+      p_ok = advance(p);
+    }
+    const bool last = c.j + 1 >= c.nch;
+    if (last) {
+      if (S > 1) sum = subwarp_sum<S>(sum, mask);
+      const int64_t i = c.b * RB + lrow;
+      if (rank == 0 && i < a.n) {
+        const XT v = (XT)finish_row(a.y, i, sum, a.alpha, a.beta, a.plain);
+        a.y[i] = v;
+        if (DOT) dot_accum(d, i, v, dwy, dyy);
+      }
+      sum = AT(0);
+    }
+    if (!advance(c)) break;
+    if (last) row_bounds(c.b, rs, re);
+  }
+  if (DOT && !timed_out) dot_epilogue2<kRbThreads>(dwy, dyy, d, blockIdx.x, expected);
 }
 
 // Nonzero split of long rows: one warp per fixed-size chunk of a long row,
@@ -136,7 +303,7 @@ template <typename VT, typename XT, bool DOT>
 __global__ void __launch_bounds__(256)
     csr_long_fixup_kernel(int64_t n_long, const int32_t* __restrict__ rows, const int32_t* __restrict__ cptr,
                           const acc_t<VT>* __restrict__ partial, XT* __restrict__ y, acc_t<VT> alpha,
-                          acc_t<VT> beta, DotSpec d, int slot, int expected, const int* gate) {
+                          acc_t<VT> beta, bool plain, DotSpec d, int slot, int expected, const int* gate) {
   using AT = acc_t<VT>;
   if (gated(gate)) return;
   double dwy = 0.0, dyy = 0.0;
@@ -144,14 +311,9 @@ __global__ void __launch_bounds__(256)
     AT s = AT(0);
     for (int32_t c = cptr[j]; c < cptr[j + 1]; ++c) s += partial[c];
     const int32_t i = rows[j];
-    AT v = alpha * s;
-    if (beta != AT(0)) v = madd(beta, to_acc(y[i]), v);
-    y[i] = (XT)v;
-    if (DOT) {
-      const double yv = (double)(XT)v;
-      dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
-      dyy += yv * yv;
-    }
+    const XT v = (XT)finish_row(y, i, s, alpha, beta, plain);
+    y[i] = v;
+    if (DOT) dot_accum(d, i, v, dwy, dyy);
   }
   if (DOT) dot_epilogue2<256>(dwy, dyy, d, slot + blockIdx.x, expected);
 }
@@ -216,6 +378,7 @@ struct EllArgs {
   const XT* x;
   XT* y;
   acc_t<VT> alpha, beta;
+  bool plain;
 };
 
 // Column-major ELL: each thread owns RPT consecutive rows and reads slot k of
@@ -257,14 +420,9 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
     for (int r = 0; r < RPT; ++r) {
       const int64_t i = i0 + r;
       if (i < a.n) {
-        AT v = a.alpha * sum[r];
-        if (a.beta != AT(0)) v = madd(a.beta, to_acc(a.y[i]), v);
-        a.y[i] = (XT)v;
-        if (DOT) {
-          const double yv = (double)(XT)v;
-          dwy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
-          dyy += yv * yv;
-        }
+        const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
+        a.y[i] = v;
+        if (DOT) dot_accum(d, i, v, dwy, dyy);
       }
     }
   }
@@ -288,7 +446,7 @@ template <typename VT>
 struct Load8;
 template <>
 struct Load8<double> {
-  static __device__ __forceinline__ void run(const double* p, double (&v)[8]) {
+  static __device__ __forceinline__ void run(const double* p, double* v) {
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const double2 t = __ldcs(reinterpret_cast<const double2*>(p) + h);
@@ -299,7 +457,7 @@ struct Load8<double> {
 };
 template <>
 struct Load8<float> {
-  static __device__ __forceinline__ void run(const float* p, float (&v)[8]) {
+  static __device__ __forceinline__ void run(const float* p, float* v) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + h);
@@ -312,7 +470,7 @@ struct Load8<float> {
 };
 template <>
 struct Load8<__nv_bfloat16> {
-  static __device__ __forceinline__ void run(const __nv_bfloat16* p, __nv_bfloat16 (&v)[8]) {
+  static __device__ __forceinline__ void run(const __nv_bfloat16* p, __nv_bfloat16* v) {
     const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
     const unsigned w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
@@ -322,7 +480,7 @@ struct Load8<__nv_bfloat16> {
     }
   }
 };
-__device__ __forceinline__ void load8_i32(const int32_t* p, int32_t (&v)[8]) {
+__device__ __forceinline__ void load8_i32(const int32_t* p, int32_t* v) {
   const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
   const int4 b = __ldcs(reinterpret_cast<const int4*>(p) + 1);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -354,50 +512,56 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
 }
 
 // Tiled segmented reduction over row-sorted COO.  Each 256-thread block owns
-// a tile of 2048 entries; each thread owns 8 consecutive entries (vector
-// loads), reduces them sequentially, and a block-wide segmented scan supplies
-// the running sum that enters from earlier threads.  Rows that start and end
-// inside the tile are written directly; the tile's open first/last segment
-// partials go to carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
-// ACCUM: y[r] += alpha*sum for the rows present (hybrid tail); otherwise
-// rows absent from the COO arrays are scaled by beta here too.
+// a tile of 256*kCooItems entries; each thread owns kCooItems consecutive
+// entries (vector loads) and folds them with one FMA per entry, finishing
+// the rows that start and end inside its entries on the spot.  A block-wide
+// segmented scan of (has a row end, trailing sum) supplies the running sum
+// that enters the thread's first row from earlier threads.  The tile's open
+// first/last segment partials go to carry[2*tile] / carry[2*tile+1] for
+// coo_fixup_kernel.  ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows
+// absent from the COO arrays are scaled by beta here too.
 template <typename VT, typename XT, bool ACCUM>
 __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
                                                           const int* gate) {
   using AT = acc_t<VT>;
-  if (gated(gate)) return;
+  constexpr int IPT = kCooItems;
   __shared__ int32_t s_first[kCooThreads + 1];
   __shared__ int32_t s_last[kCooThreads];
   __shared__ AT s_wv[kCooThreads / kWarp];
   __shared__ int s_wf[kCooThreads / kWarp];
+  __shared__ AT s_pv[kCooThreads / kWarp + 1];
+  __shared__ int s_pf[kCooThreads / kWarp + 1];
   __shared__ int32_t s_prev_row;
+  if (gated(gate)) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t tile = blockIdx.x;
   const int64_t base = tile * kCooTile;
   const int cnt = (int)min((int64_t)kCooTile, a.nnz - base);
-  const int j0 = t * kCooItems;
-  const int my = max(0, min(kCooItems, cnt - j0));
+  const int j0 = t * IPT;
+  const int my = max(0, min(IPT, cnt - j0));
 
-  int32_t rows[kCooItems];
-  AT prod[kCooItems];
-  if (my == kCooItems) {
-    int32_t cols[kCooItems];
-    VT vals[kCooItems];
-    load8_i32(a.row + base + j0, rows);
-    load8_i32(a.col + base + j0, cols);
-    Load8<VT>::run(a.val + base + j0, vals);
+  int32_t rows[IPT];
+  int32_t cols[IPT];
+  VT vals[IPT];
+  if (my == IPT) {
 #pragma unroll
-    for (int u = 0; u < kCooItems; ++u) prod[u] = to_acc(vals[u]) * to_acc(ld_vec(a.x + cols[u]));
+    for (int h = 0; h < IPT; h += 8) {
+      load8_i32(a.row + base + j0 + h, rows + h);
+      load8_i32(a.col + base + j0 + h, cols + h);
+      Load8<VT>::run(a.val + base + j0 + h, vals + h);
+    }
   } else {
 #pragma unroll
-    for (int u = 0; u < kCooItems; ++u) {
+    for (int u = 0; u < IPT; ++u) {
       if (u < my) {
         const int64_t k = base + j0 + u;
         rows[u] = a.row[k];
-        prod[u] = to_acc(a.val[k]) * to_acc(ld_vec(a.x + a.col[k]));
+        cols[u] = a.col[k];
+        vals[u] = a.val[k];
       } else {
         rows[u] = INT_MAX;
-        prod[u] = AT(0);
+        cols[u] = 0;
+        vals[u] = VT(0);
       }
     }
   }
@@ -408,25 +572,41 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
     s_prev_row = base > 0 ? a.row[base - 1] : -1;
   }
   __syncthreads();
-  const int32_t next_row = (j0 + kCooItems < cnt) ? s_first[t + 1] : s_first[kCooThreads];
+  const int32_t next_row = (j0 + IPT < cnt) ? s_first[t + 1] : s_first[kCooThreads];
   const int32_t prev_tile_row = s_prev_row;
   const bool first_open = base > 0 && prev_tile_row == s_first[0];
 
-  // pass 1: (has a segment end, sum after the last end)
-  int f = 0;
-  AT v = AT(0);
+  // one pass: FMA per entry; rows that start and end here are finished now
+  AT run = AT(0), first_sum = AT(0);
+  int32_t first_row = -1;
+  int nends = 0;
 #pragma unroll
-  for (int u = 0; u < kCooItems; ++u) {
+  for (int u = 0; u < IPT; ++u) {
     if (u < my) {
-      v += prod[u];
+      const int32_t r = rows[u];
+      if (!ACCUM) {
+        const int32_t pr = (u > 0) ? rows[u - 1] : (t > 0 ? s_last[t - 1] : prev_tile_row);
+        if (r != pr) coo_empty_rows(a.y, (int64_t)pr + 1, (int64_t)r, a.beta);
+      }
+      run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
       const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;
-      if (rows[u] != nr) {
-        f = 1;
-        v = AT(0);
+      if (r != nr) {
+        if (nends == 0) {
+          first_sum = run;
+          first_row = r;
+        } else {
+          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM);
+        }
+        ++nends;
+        run = AT(0);
       }
     }
   }
-  // inclusive warp scan of (f, v)
+  if (!ACCUM && my > 0 && base + j0 + my == a.nnz) coo_empty_rows(a.y, (int64_t)rows[my - 1] + 1, a.n_rows, a.beta);
+
+  // segmented scan of (has an end, trailing sum) over the block
+  int f = nends > 0;
+  AT v = run;
 #pragma unroll
   for (int dlt = 1; dlt < 32; dlt <<= 1) {
     const int fp = __shfl_up_sync(0xffffffffu, f, dlt);
@@ -444,51 +624,34 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
     ev = AT(0);
   }
   __syncthreads();
-  int pf = 0;
-  AT pv = AT(0);
-  for (int i = 0; i < w; ++i) {
-    int ff = s_wf[i];
-    AT vv = s_wv[i];
-    seg_combine(pf, pv, ff, vv);
-    pf = ff;
-    pv = vv;
-  }
-  seg_combine(pf, pv, ef, ev);  // exclusive prefix of this thread
-
-  // pass 2: finish the segments that end in this thread's entries
-  AT run = ev;
-  bool seen_end = ef != 0;
-#pragma unroll
-  for (int u = 0; u < kCooItems; ++u) {
-    if (u < my) {
-      const int32_t r = rows[u];
-      if (!ACCUM) {
-        const int32_t pr = (u > 0) ? rows[u - 1] : (t > 0 ? s_last[t - 1] : prev_tile_row);
-        if (r != pr) coo_empty_rows(a.y, (int64_t)pr + 1, (int64_t)r, a.beta);
-      }
-      run += prod[u];
-      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;
-      if (r != nr) {
-        if (!seen_end && first_open)
-          carry[2 * tile] = run;
-        else
-          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM);
-        run = AT(0);
-        seen_end = true;
-      }
-    }
-  }
-  if (!ACCUM && my > 0 && base + j0 + my == a.nnz) coo_empty_rows(a.y, (int64_t)rows[my - 1] + 1, a.n_rows, a.beta);
-  if (t == 0) {
-    int tf = 0;
-    AT tv = AT(0);
+  if (t == 0) {  // exclusive prefixes of the warp aggregates, and the tile total
+    int pf = 0;
+    AT pv = AT(0);
     for (int i = 0; i < kCooThreads / kWarp; ++i) {
+      s_pf[i] = pf;
+      s_pv[i] = pv;
       int ff = s_wf[i];
       AT vv = s_wv[i];
-      seg_combine(tf, tv, ff, vv);
-      tf = ff;
-      tv = vv;
+      seg_combine(pf, pv, ff, vv);
+      pf = ff;
+      pv = vv;
     }
+    s_pf[kCooThreads / kWarp] = pf;
+    s_pv[kCooThreads / kWarp] = pv;
+  }
+  __syncthreads();
+  seg_combine(s_pf[w], s_pv[w], ef, ev);  // exclusive prefix of this thread
+
+  if (nends > 0) {
+    const AT total = ev + first_sum;
+    if (!ef && first_open)
+      carry[2 * tile] = total;  // the tile's first row began in an earlier tile
+    else
+      coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM);
+  }
+  if (t == 0) {
+    const int tf = s_pf[kCooThreads / kWarp];
+    const AT tv = s_pv[kCooThreads / kWarp];
     // tv: sum of the tile's last segment; without any end the whole tile
     if (!tf) carry[2 * tile] = tv;
     carry[2 * tile + 1] = tv;
@@ -532,9 +695,9 @@ __global__ void scale_kernel(int64_t n, XT* __restrict__ y, AT beta, const int* 
 // -------------------------------------------------------------- dispatch --
 
 template <typename K>
-int resident_blocks(K kernel, int threads) {
+int resident_blocks(K kernel, int threads, size_t smem = 0) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) {
     cudaGetLastError();
     nb = 1;
   }
@@ -545,6 +708,11 @@ template <typename VT, typename XT>
 struct SpmvImpl {
   using AT = acc_t<VT>;
 
+  static CsrArgs<VT, XT> csr_args(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta) {
+    return CsrArgs<VT, XT>{A->n_rows, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val), x, y,
+                           alpha, beta, A->plan.long_thr, alpha == AT(1) && beta == AT(0)};
+  }
+
   template <int S, int R, bool DOT>
   static int csr_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                         const DotSpec& d, int extra, const int* gate) {
@@ -553,12 +721,30 @@ struct SpmvImpl {
     const int64_t rows_per_block = (int64_t)R * (256 / S);
     int64_t g = (A->n_rows + rows_per_block - 1) / rows_per_block;
     int64_t cap = (int64_t)per_sm * sm_count();
-    if (DOT && cap > kDotSlots - 1) cap = kDotSlots - 1;
+    if (DOT && cap > kDotSlots - extra) cap = kDotSlots - extra;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    CsrArgs<VT, XT> a{A->n_rows, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val), x, y,
-                      alpha, beta, A->plan.long_thr};
-    kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g + extra, gate);
+    kern<<<(unsigned)g, 256, 0, s>>>(csr_args(A, x, y, alpha, beta), d, (int)g + extra, gate);
+    return (int)g;
+  }
+
+  template <int S, bool DOT>
+  static int rowblock_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
+                             const DotSpec& d, int extra, const int* gate) {
+    auto kern = csr_rowblock_kernel<S, VT, XT, DOT>;
+    constexpr size_t smem = rb_smem_bytes<VT>();
+    static int per_sm = [&] {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return resident_blocks(kern, kRbThreads, smem);
+    }();
+    constexpr int RB = kRbThreads / S;
+    int64_t g = (A->n_rows + RB - 1) / RB;
+    int64_t cap = (int64_t)per_sm * sm_count();
+    if (DOT && cap > kDotSlots - extra) cap = kDotSlots - extra;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    kern<<<(unsigned)g, kRbThreads, smem, s>>>(csr_args(A, x, y, alpha, beta), d, (int)g + extra, gate,
+                                                device_error_word());
     return (int)g;
   }
 
@@ -566,6 +752,13 @@ struct SpmvImpl {
   static int csr_dispatch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                           const DotSpec& d, int extra, const int* gate) {
     const int S = A->plan.S, R = A->plan.R;
+    if (A->plan.kind == 1) {
+      if (S == 1) return rowblock_launch<1, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+      if (S == 2) return rowblock_launch<2, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+      if (S == 4) return rowblock_launch<4, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+      if (S == 8) return rowblock_launch<8, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+      return -1;
+    }
 #define GKO_CSR_CASE(SS, RR) \
   if (S == SS && R == RR) return csr_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
 #define GKO_CSR_ROW(SS) GKO_CSR_CASE(SS, 1) GKO_CSR_CASE(SS, 2) GKO_CSR_CASE(SS, 4) GKO_CSR_CASE(SS, 8)
@@ -579,7 +772,9 @@ struct SpmvImpl {
                  const DotSpec* dot, const int* gate) {
     const bool has_long = A->plan.n_long > 0;
     DotSpec d = dot ? *dot : DotSpec{};
-    const int extra = has_long ? 1 : 0;
+    const int64_t fix_blocks =
+        has_long ? std::max<int64_t>(1, std::min<int64_t>((A->plan.n_long + 255) / 256, 256)) : 0;
+    const int extra = (int)fix_blocks;
     int g = dot ? csr_dispatch<true>(A, x, y, alpha, beta, s, d, extra, gate)
                 : csr_dispatch<false>(A, x, y, alpha, beta, s, d, extra, gate);
     if (g < 0) return fail(GKO_INVALID_ARG, "unsupported CSR plan");
@@ -594,12 +789,15 @@ struct SpmvImpl {
       kc<<<(unsigned)blocks, 256, 0, s>>>(A->plan.n_chunks, ptr<int32_t>(A->plan.chunk_row),
                                           ptr<int32_t>(A->plan.chunk_start), ptr<int32_t>(A->row_ptr),
                                           ptr<int32_t>(A->col), ptr<VT>(A->val), x, partial, gate);
+      const bool plain = alpha == AT(1) && beta == AT(0);
       if (dot)
-        csr_long_fixup_kernel<VT, XT, true><<<1, 256, 0, s>>>(A->plan.n_long, ptr<int32_t>(A->plan.long_rows),
-            ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha, beta, d, g, g + 1, gate);
+        csr_long_fixup_kernel<VT, XT, true><<<(unsigned)fix_blocks, 256, 0, s>>>(
+            A->plan.n_long, ptr<int32_t>(A->plan.long_rows), ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha,
+            beta, plain, d, g, g + extra, gate);
       else
-        csr_long_fixup_kernel<VT, XT, false><<<1, 256, 0, s>>>(A->plan.n_long, ptr<int32_t>(A->plan.long_rows),
-            ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha, beta, d, 0, 0, gate);
+        csr_long_fixup_kernel<VT, XT, false><<<(unsigned)fix_blocks, 256, 0, s>>>(
+            A->plan.n_long, ptr<int32_t>(A->plan.long_rows), ptr<int32_t>(A->plan.long_chunk_ptr), partial, y, alpha,
+            beta, plain, d, 0, 0, gate);
     }
     GKO_TRY_CUDA(cudaGetLastError());
     return GKO_OK;
@@ -619,7 +817,8 @@ struct SpmvImpl {
     if (DOT && cap > kDotSlots) cap = kDotSlots;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    EllArgs<VT, XT> a{A->n_rows, A->K, A->stride, ptr<int32_t>(A->ell_col), ptr<VT>(A->ell_val), x, y, alpha, beta};
+    EllArgs<VT, XT> a{A->n_rows, A->K, A->stride, ptr<int32_t>(A->ell_col), ptr<VT>(A->ell_val), x, y, alpha, beta,
+                      alpha == AT(1) && beta == AT(0)};
     kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g, gate);
     GKO_TRY_CUDA(cudaGetLastError());
     return GKO_OK;

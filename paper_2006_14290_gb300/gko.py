@@ -59,6 +59,7 @@ SIGNATURES = {
     "gko_last_error": (C.c_char_p, []),
     "gko_status_string": (C.c_char_p, [C.c_int]),
     "gko_version": (C.c_int, []),
+    "gko_device_status": (C.c_int, [_P]),
     "gko_set_memory_budget": (C.c_int, [_I64]),
     "gko_memory_in_use": (C.c_int, [_PI64]),
     "gko_matrix_create_csr": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(_P)]),
@@ -338,6 +339,11 @@ def gko_solve_gmres(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=N
 
 def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0):
     return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, 0)
+
+
+def gko_device_status(stream=None):
+    """Raise if a kernel recorded a device-side failure (bounded wait timeout)."""
+    _check(lib().gko_device_status(_stream(stream)), "gko_device_status")
 
 
 def set_memory_budget(nbytes: int):
