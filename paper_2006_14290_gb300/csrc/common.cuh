@@ -85,14 +85,14 @@ size_t dtype_size(gko_dtype t);
 
 constexpr int kHistBins = 33;
 constexpr int32_t kLongChunk = 1024;  // nonzeros per chunk of a long CSR row
-constexpr int kRbThreads = 256;      // TMA row-block CSR kernel: threads per block
-constexpr int kRbCap = 4096;         // nonzeros staged per shared-memory stage
+constexpr int kRbThreads = 128;      // TMA row-block CSR kernel: threads per block
 
 // Load-balancing plan of the CSR SpMV, built from the row-length histogram.
 struct CsrPlan {
   int32_t kind = 0;         // 0: subwarp kernel, 1: TMA row-block kernel
   int32_t S = 32;           // subwarp width for ordinary rows
-  int32_t R = 4;            // rows per subwarp pass
+  int32_t R = 4;            // rows per subwarp pass (row-block: rows per subwarp)
+  int32_t cap = 2048;       // row-block kernel: nonzeros per shared-memory stage
   int32_t long_thr = 1024;  // rows longer than this use the nonzero split
   int32_t max_len = 0;
   int64_t hist[kHistBins] = {0};

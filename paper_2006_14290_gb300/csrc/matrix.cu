@@ -197,10 +197,14 @@ static unsigned grid_for(int64_t work, int threads = 256) {
 // ------------------------------------------------------------- plan -----
 
 // Plan from the row-length histogram.
-//  * Regular matrices (longest row <= 4x the mean row length, e.g. stencils
-//    and banded matrices) use the TMA row-block kernel with S lanes per row:
-//    S = 1 (one thread per row, no reduction) unless rows average more than
-//    48*S entries.  No row is split.
+//  * Regular matrices (longest row <= 4x the mean row length m, e.g. stencils
+//    and banded matrices) use the TMA row-block kernel.  With 128 threads per
+//    block and stages of cap = 1024 entries (small stages keep many blocks
+//    resident), S (lanes per row) is the smallest power of two with
+//    (128/S)*m <= 0.9*cap (S = 1: one thread per row, no reduction), and R
+//    (interleaved rows per subwarp) the largest power of two <= 4 with
+//    (128/S)*R*m <= cap, so one row block fills about a stage.
+//    No row is split.
 //  * Skewed matrices use the subwarp kernel: S = the smallest power of two
 //    (<= 32) not below the mean length of rows shorter than 1024, R = 2 rows
 //    per pass, and rows longer than 32*S go to the nonzero split.
@@ -210,10 +214,13 @@ static void choose_plan(CsrPlan& p, int64_t n) {
   const double mean_all = n ? (double)nz_all / (double)n : 0.0;
   if (n > 0 && p.max_len <= 4.0 * mean_all + 1.0) {
     p.kind = 1;
+    p.cap = 1024;
     int32_t S = 1;
-    while (S < 8 && mean_all > 48.0 * S) S *= 2;
+    while (S < 8 && (double)(kRbThreads / S) * mean_all > 0.9 * p.cap) S *= 2;
+    int32_t R = 1;
+    while (R < 4 && (double)(kRbThreads / S) * (2 * R) * mean_all <= p.cap) R *= 2;
     p.S = S;
-    p.R = 0;
+    p.R = R;
     p.long_thr = INT32_MAX;
     return;
   }
@@ -232,7 +239,7 @@ static void choose_plan(CsrPlan& p, int64_t n) {
 }
 
 static bool valid_S(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32; }
-static bool valid_R(int r) { return r == 0 || r == 1 || r == 2 || r == 4 || r == 8; }
+static bool valid_R(int r) { return r == 1 || r == 2 || r == 4; }
 
 static int build_long_split(gko_matrix m, cudaStream_t s) {
   CsrPlan& p = m->plan;
@@ -389,11 +396,13 @@ int gko_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int
   return GKO_OK;
 }
 
-int gko_matrix_plan(gko_matrix m, int32_t* S, int32_t* R, int32_t* thr, int64_t* n_long, int64_t* n_chunks,
-                    int64_t* hist33) {
+int gko_matrix_plan(gko_matrix m, int32_t* kernel, int32_t* S, int32_t* R, int32_t* cap, int32_t* thr,
+                    int64_t* n_long, int64_t* n_chunks, int64_t* hist33) {
   if (!m || m->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "plan needs a CSR handle");
+  if (kernel) *kernel = m->plan.kind;
   if (S) *S = m->plan.S;
   if (R) *R = m->plan.R;
+  if (cap) *cap = m->plan.cap;
   if (thr) *thr = m->plan.long_thr;
   if (n_long) *n_long = m->plan.n_long;
   if (n_chunks) *n_chunks = m->plan.n_chunks;
@@ -402,28 +411,34 @@ int gko_matrix_plan(gko_matrix m, int32_t* S, int32_t* R, int32_t* thr, int64_t*
   return GKO_OK;
 }
 
-int gko_matrix_set_plan(gko_matrix m, int32_t S, int32_t R, void* stream) {
+int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int32_t cap, void* stream) {
   if (!m || m->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "plan needs a CSR handle");
-  if (!valid_S(S) || !valid_R(R) || (R == 0 && S > 8))
-    return fail(GKO_INVALID_ARG, "subwarp must be 1..32 (power of 2), R 1,2,4,8; R 0 (row-block) needs S <= 8");
+  const bool rb = kernel == 1;
+  if ((kernel != 0 && kernel != 1) || !valid_S(S) || !valid_R(R) || (rb && S > 8) ||
+      (rb && (cap < 512 || cap > 8192 || (cap & (cap - 1)))))
+    return fail(GKO_INVALID_ARG,
+                "kernel 0 (subwarp: S 1..32, R 1,2,4) or 1 (row-block: S 1..8, R 1,2,4, cap 512..8192, powers of 2)");
   std::lock_guard<std::mutex> lk(m->mu);
-  m->plan.kind = R == 0 ? 1 : 0;
+  m->plan.kind = kernel;
   m->plan.S = S;
   m->plan.R = R;
-  m->plan.long_thr = R == 0 ? INT32_MAX : 32 * S;
+  if (rb) m->plan.cap = cap;
+  m->plan.long_thr = rb ? INT32_MAX : 32 * S;
   GKO_TRY(build_long_split(m, (cudaStream_t)stream));
   for (auto& kv : m->lowp) {  // low-precision copies share the pattern
     if (kv.second->fmt == GKO_CSR) {
-      kv.second->plan.kind = m->plan.kind;
-      kv.second->plan.S = S;
-      kv.second->plan.R = R;
-      kv.second->plan.long_thr = m->plan.long_thr;
-      kv.second->plan.n_long = m->plan.n_long;
-      kv.second->plan.n_chunks = m->plan.n_chunks;
-      kv.second->plan.long_rows = m->plan.long_rows;
-      kv.second->plan.long_chunk_ptr = m->plan.long_chunk_ptr;
-      kv.second->plan.chunk_row = m->plan.chunk_row;
-      kv.second->plan.chunk_start = m->plan.chunk_start;
+      CsrPlan& q = kv.second->plan;
+      q.kind = m->plan.kind;
+      q.S = S;
+      q.R = R;
+      q.cap = m->plan.cap;
+      q.long_thr = m->plan.long_thr;
+      q.n_long = m->plan.n_long;
+      q.n_chunks = m->plan.n_chunks;
+      q.long_rows = m->plan.long_rows;
+      q.long_chunk_ptr = m->plan.long_chunk_ptr;
+      q.chunk_row = m->plan.chunk_row;
+      q.chunk_start = m->plan.chunk_start;
     }
   }
   return GKO_OK;
@@ -557,6 +572,7 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   m->plan.kind = src->plan.kind;
   m->plan.S = src->plan.S;
   m->plan.R = src->plan.R;
+  m->plan.cap = src->plan.cap;
   m->plan.long_thr = src->plan.long_thr;
   m->plan.max_len = src->plan.max_len;
   for (int b = 0; b < kHistBins; ++b) {

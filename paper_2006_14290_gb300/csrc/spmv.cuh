@@ -41,7 +41,7 @@ int spmv_run_bf16(const gko_matrix_s* A, const float* x, float* y, double alpha,
                   void* scratch, const DotSpec* dot, const int* gate);
 
 constexpr int kCooThreads = 256;
-constexpr int kCooItems = 16;
+constexpr int kCooItems = 8;
 constexpr int kCooTile = kCooThreads * kCooItems;
 
 }  // namespace gko

@@ -119,34 +119,37 @@ __global__ void __launch_bounds__(256) csr_subwarp_kernel(CsrArgs<VT, XT> a, Dot
   if (DOT) dot_epilogue2<256>(dwy, dyy, d, blockIdx.x, expected);
 }
 
-// TMA row-block CSR (regular matrices).  A block owns row blocks of
-// RB = 256/S consecutive rows (round robin over a persistent grid).  The
+// TMA row-block CSR (regular matrices).  A 128-thread block owns row blocks
+// of RB = (128/S)*R consecutive rows (round robin over a persistent grid):
+// subwarp g (S lanes) sums rows g, g + 128/S, ..., R rows interleaved.  The
 // nonzeros of a row block, [row_ptr[b*RB], row_ptr[(b+1)*RB]) widened to
 // 8-entry granules, stream into shared memory by bulk copies in stages of
-// kRbCap entries, double buffered: thread 0 issues the copy of stage q+2
-// while all threads consume stage q.  Each row is summed by S lanes reading
-// the staged entries (S = 1: one thread per row, no reduction at all), so
-// global loads are fully coalesced and every FMA lane is busy.
+// `cap` entries, double buffered: thread 0 issues the copy of stage q+2 while
+// all threads consume stage q.  The plan sizes RB so that a typical row
+// block fits one stage, so every thread has work in every stage.  Global
+// loads are bulk and coalesced, and with S = 1 a row needs no reduction, so
+// every FP64 FMA lane is busy.
 template <typename VT>
-constexpr size_t rb_smem_bytes() {
-  return 128 + 2 * (size_t)kRbCap * (sizeof(int32_t) + sizeof(VT));
+inline size_t rb_smem_bytes(int cap) {
+  return 128 + 2 * (size_t)cap * (sizeof(int32_t) + sizeof(VT));
 }
 
-template <int S, typename VT, typename XT, bool DOT>
-__global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, DotSpec d, int expected,
-                                                                   const int* gate, int* err) {
+template <int S, int R, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
+                                                                   int expected, const int* gate, int* err) {
   using AT = acc_t<VT>;
-  constexpr int RB = kRbThreads / S;
+  constexpr int G = kRbThreads / S;  // subwarps per block
+  constexpr int RB = G * R;          // rows per row block
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
-  VT* sval = reinterpret_cast<VT*>(smem + 128 + 2 * (size_t)kRbCap * sizeof(int32_t));
+  VT* sval = reinterpret_cast<VT*>(smem + 128 + 2 * (size_t)cap * sizeof(int32_t));
   if (gated(gate)) return;
   const int64_t nrb = (a.n + RB - 1) / RB;
   if ((int64_t)blockIdx.x >= nrb) return;
   const int tid = threadIdx.x;
   const int rank = tid & (S - 1);
-  const int lrow = tid / S;
+  const int sg = tid / S;
   const unsigned mask = subwarp_mask<S>();
 
   if (tid == 0) {
@@ -156,7 +159,6 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
   }
   __syncthreads();
 
-  // chunk cursor over this block's row blocks
   struct Cur {
     int64_t b, kb, ke;
     int j, nch;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
     const int32_t k1 = __ldg(a.rp + min((c.b + 1) * RB, a.n));
     c.kb = (int64_t)(k0 & ~7);
     c.ke = ((int64_t)k1 + 7) & ~7ll;
-    c.nch = (int)imax64(1, (c.ke - c.kb + kRbCap - 1) / kRbCap);
+    c.nch = (int)imax64(1, (c.ke - c.kb + cap - 1) / cap);
     c.j = 0;
   };
   auto advance = [&](Cur& c) -> bool {
@@ -177,15 +179,15 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
     return true;
   };
   auto issue = [&](const Cur& c, int stage) {
-    const int64_t cs = c.kb + (int64_t)c.j * kRbCap;
-    const int64_t len = imin64(kRbCap, c.ke - cs);
+    const int64_t cs = c.kb + (int64_t)c.j * cap;
+    const int64_t len = imin64(cap, c.ke - cs);
     if (len <= 0) {
       mbar_arrive(&bar[stage]);
     } else {
       const unsigned bc = (unsigned)(len * sizeof(int32_t)), bv = (unsigned)(len * sizeof(VT));
       mbar_arrive_expect_tx(&bar[stage], bc + bv);
-      bulk_g2s(scol + (size_t)stage * kRbCap, a.col + cs, bc, &bar[stage]);
-      bulk_g2s(sval + (size_t)stage * kRbCap, a.val + cs, bv, &bar[stage]);
+      bulk_g2s(scol + (size_t)stage * cap, a.col + cs, bc, &bar[stage]);
+      bulk_g2s(sval + (size_t)stage * cap, a.val + cs, bv, &bar[stage]);
     }
   };
 
@@ -202,17 +204,22 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
       p_ok = advance(p);
     }
   }
-  auto row_bounds = [&](int64_t b, int32_t& rs, int32_t& re) {
-    const int64_t i = b * RB + lrow;
-    rs = re = 0;
-    if (i < a.n) {
-      rs = __ldg(a.rp + i);
-      re = __ldg(a.rp + i + 1);
+  int32_t rs[R], re[R];
+  auto row_bounds = [&](int64_t b) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = b * RB + sg + (int64_t)r * G;
+      rs[r] = re[r] = 0;
+      if (i < a.n) {
+        rs[r] = __ldg(a.rp + i);
+        re[r] = __ldg(a.rp + i + 1);
+      }
     }
   };
-  int32_t rs, re;
-  row_bounds(c.b, rs, re);
-  AT sum = AT(0);
+  row_bounds(c.b);
+  AT sum[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) sum[r] = AT(0);
   double dwy = 0.0, dyy = 0.0;
   bool timed_out = false;
   for (unsigned q = 0;; ++q) {
@@ -223,22 +230,27 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
       timed_out = true;
       break;
     }
-    const int32_t* sc = scol + (size_t)stage * kRbCap;
-    const VT* sv = sval + (size_t)stage * kRbCap;
-    const int64_t cs = c.kb + (int64_t)c.j * kRbCap;
-    const int lo = (int)(imax64(rs, cs) - cs);
-    const int hi = (int)(imin64(re, cs + kRbCap) - cs);
-    int k = lo + rank;
-    for (; k + 3 * S < hi; k += 4 * S) {
-      const int32_t c0 = sc[k], c1 = sc[k + S], c2 = sc[k + 2 * S], c3 = sc[k + 3 * S];
-      const VT v0 = sv[k], v1 = sv[k + S], v2 = sv[k + 2 * S], v3 = sv[k + 3 * S];
-      const XT x0 = ld_vec(a.x + c0), x1 = ld_vec(a.x + c1), x2 = ld_vec(a.x + c2), x3 = ld_vec(a.x + c3);
-      sum = madd(to_acc(v0), to_acc(x0), sum);
-      sum = madd(to_acc(v1), to_acc(x1), sum);
-      sum = madd(to_acc(v2), to_acc(x2), sum);
-      sum = madd(to_acc(v3), to_acc(x3), sum);
+    const int32_t* sc = scol + (size_t)stage * cap;
+    const VT* sv = sval + (size_t)stage * cap;
+    const int64_t cs = c.kb + (int64_t)c.j * cap;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int lo = (int)(imax64(rs[r], cs) - cs);
+      const int hi = (int)(imin64(re[r], cs + cap) - cs);
+      AT acc = sum[r];
+      int k = lo + rank;
+      for (; k + 3 * S < hi; k += 4 * S) {
+        const int32_t c0 = sc[k], c1 = sc[k + S], c2 = sc[k + 2 * S], c3 = sc[k + 3 * S];
+        const VT v0 = sv[k], v1 = sv[k + S], v2 = sv[k + 2 * S], v3 = sv[k + 3 * S];
+        const XT x0 = ld_vec(a.x + c0), x1 = ld_vec(a.x + c1), x2 = ld_vec(a.x + c2), x3 = ld_vec(a.x + c3);
+        acc = madd(to_acc(v0), to_acc(x0), acc);
+        acc = madd(to_acc(v1), to_acc(x1), acc);
+        acc = madd(to_acc(v2), to_acc(x2), acc);
+        acc = madd(to_acc(v3), to_acc(x3), acc);
+      }
+      for (; k < hi; k += S) acc = madd(to_acc(sv[k]), to_acc(ld_vec(a.x + sc[k])), acc);
+      sum[r] = acc;
     }
-    for (; k < hi; k += S) sum = madd(to_acc(sv[k]), to_acc(ld_vec(a.x + sc[k])), sum);
     __syncthreads();  // stage consumed by everyone
     if (tid == 0 && p_ok) {
       issue(p, stage);
@@ -246,17 +258,20 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
     }
     const bool last = c.j + 1 >= c.nch;
     if (last) {
-      if (S > 1) sum = subwarp_sum<S>(sum, mask);
-      const int64_t i = c.b * RB + lrow;
-      if (rank == 0 && i < a.n) {
-        const XT v = (XT)finish_row(a.y, i, sum, a.alpha, a.beta, a.plain);
-        a.y[i] = v;
-        if (DOT) dot_accum(d, i, v, dwy, dyy);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (S > 1) sum[r] = subwarp_sum<S>(sum[r], mask);
+        const int64_t i = c.b * RB + sg + (int64_t)r * G;
+        if (rank == 0 && i < a.n) {
+          const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
+          a.y[i] = v;
+          if (DOT) dot_accum(d, i, v, dwy, dyy);
+        }
+        sum[r] = AT(0);
       }
-      sum = AT(0);
     }
     if (!advance(c)) break;
-    if (last) row_bounds(c.b, rs, re);
+    if (last) row_bounds(c.b);
   }
   if (DOT && !timed_out) dot_epilogue2<kRbThreads>(dwy, dyy, d, blockIdx.x, expected);
 }
@@ -498,7 +513,9 @@ __device__ __forceinline__ void seg_combine(int fp, AT vp, int& f, AT& v) {
 template <typename XT, typename AT>
 __device__ __forceinline__ void coo_store(XT* y, int32_t r, AT s, AT alpha, AT beta, bool accum) {
   if (accum) {
-    y[r] = (XT)madd(alpha, s, to_acc(y[r]));
+    y[r] = (XT)(alpha == AT(1) ? s + to_acc(y[r]) : madd(alpha, s, to_acc(y[r])));
+  } else if (alpha == AT(1) && beta == AT(0)) {
+    y[r] = (XT)s;
   } else {
     AT v = alpha * s;
     if (beta != AT(0)) v = madd(beta, to_acc(y[r]), v);
@@ -728,22 +745,26 @@ struct SpmvImpl {
     return (int)g;
   }
 
-  template <int S, bool DOT>
+  template <int S, int R, bool DOT>
   static int rowblock_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                              const DotSpec& d, int extra, const int* gate) {
-    auto kern = csr_rowblock_kernel<S, VT, XT, DOT>;
-    constexpr size_t smem = rb_smem_bytes<VT>();
-    static int per_sm = [&] {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      return resident_blocks(kern, kRbThreads, smem);
-    }();
-    constexpr int RB = kRbThreads / S;
+    auto kern = csr_rowblock_kernel<S, R, VT, XT, DOT>;
+    const int cap = A->plan.cap;
+    const size_t smem = rb_smem_bytes<VT>(cap);
+    static int per_sm_cache[8] = {0};  // by log2(cap / 512)
+    int slot = 0;
+    while ((512 << slot) < cap && slot < 7) ++slot;
+    if (!per_sm_cache[slot]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb_smem_bytes<VT>(8192));
+      per_sm_cache[slot] = resident_blocks(kern, kRbThreads, smem);
+    }
+    constexpr int RB = (kRbThreads / S) * R;
     int64_t g = (A->n_rows + RB - 1) / RB;
-    int64_t cap = (int64_t)per_sm * sm_count();
-    if (DOT && cap > kDotSlots - extra) cap = kDotSlots - extra;
-    if (g > cap) g = cap;
+    int64_t cap_g = (int64_t)per_sm_cache[slot] * sm_count();
+    if (DOT && cap_g > kDotSlots - extra) cap_g = kDotSlots - extra;
+    if (g > cap_g) g = cap_g;
     if (g < 1) g = 1;
-    kern<<<(unsigned)g, kRbThreads, smem, s>>>(csr_args(A, x, y, alpha, beta), d, (int)g + extra, gate,
+    kern<<<(unsigned)g, kRbThreads, smem, s>>>(csr_args(A, x, y, alpha, beta), cap, d, (int)g + extra, gate,
                                                 device_error_word());
     return (int)g;
   }
@@ -753,15 +774,17 @@ struct SpmvImpl {
                           const DotSpec& d, int extra, const int* gate) {
     const int S = A->plan.S, R = A->plan.R;
     if (A->plan.kind == 1) {
-      if (S == 1) return rowblock_launch<1, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
-      if (S == 2) return rowblock_launch<2, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
-      if (S == 4) return rowblock_launch<4, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
-      if (S == 8) return rowblock_launch<8, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+#define GKO_RB_CASE(SS, RR) \
+  if (S == SS && R == RR) return rowblock_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
+#define GKO_RB_ROW(SS) GKO_RB_CASE(SS, 1) GKO_RB_CASE(SS, 2) GKO_RB_CASE(SS, 4)
+      GKO_RB_ROW(1) GKO_RB_ROW(2) GKO_RB_ROW(4) GKO_RB_ROW(8)
+#undef GKO_RB_ROW
+#undef GKO_RB_CASE
       return -1;
     }
 #define GKO_CSR_CASE(SS, RR) \
   if (S == SS && R == RR) return csr_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
-#define GKO_CSR_ROW(SS) GKO_CSR_CASE(SS, 1) GKO_CSR_CASE(SS, 2) GKO_CSR_CASE(SS, 4) GKO_CSR_CASE(SS, 8)
+#define GKO_CSR_ROW(SS) GKO_CSR_CASE(SS, 1) GKO_CSR_CASE(SS, 2) GKO_CSR_CASE(SS, 4)
     GKO_CSR_ROW(1) GKO_CSR_ROW(2) GKO_CSR_ROW(4) GKO_CSR_ROW(8) GKO_CSR_ROW(16) GKO_CSR_ROW(32)
 #undef GKO_CSR_ROW
 #undef GKO_CSR_CASE

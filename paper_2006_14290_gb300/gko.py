@@ -70,8 +70,8 @@ SIGNATURES = {
     "gko_matrix_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _PI64, _PI64, _PI64, _PI32,
                                   _PI64, _PI64, _PI64]),
     "gko_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gko_matrix_plan": (C.c_int, [_P, _PI32, _PI32, _PI32, _PI64, _PI64, _PI64]),
-    "gko_matrix_set_plan": (C.c_int, [_P, _I32, _I32, _P]),
+    "gko_matrix_plan": (C.c_int, [_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI64, _PI64, _PI64]),
+    "gko_matrix_set_plan": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P]),
     "gko_matrix_destroy": (C.c_int, [_P]),
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
@@ -173,16 +173,17 @@ class Matrix:
                     ell_width=K.value, ell_stride=stride.value, coo_nnz=coo.value, bytes=nbytes.value)
 
     def plan(self):
-        S, R, thr = C.c_int32(), C.c_int32(), C.c_int32()
+        K, S, R, cap, thr = (C.c_int32() for _ in range(5))
         nl, nc = C.c_int64(), C.c_int64()
         hist = (C.c_int64 * 33)()
-        _check(lib().gko_matrix_plan(self.handle, C.byref(S), C.byref(R), C.byref(thr), C.byref(nl), C.byref(nc),
-                                     hist), "plan")
-        return dict(subwarp=S.value, rows_per_subwarp=R.value, long_threshold=thr.value, n_long_rows=nl.value,
-                    n_long_chunks=nc.value, hist=list(hist))
+        _check(lib().gko_matrix_plan(self.handle, C.byref(K), C.byref(S), C.byref(R), C.byref(cap), C.byref(thr),
+                                     C.byref(nl), C.byref(nc), hist), "plan")
+        return dict(kernel=K.value, subwarp=S.value, rows_per_subwarp=R.value, stage_cap=cap.value,
+                    long_threshold=thr.value, n_long_rows=nl.value, n_long_chunks=nc.value, hist=list(hist))
 
-    def set_plan(self, subwarp: int, rows_per_subwarp: int, stream=None):
-        _check(lib().gko_matrix_set_plan(self.handle, subwarp, rows_per_subwarp, _stream(stream)), "set_plan")
+    def set_plan(self, kernel: int, subwarp: int, rows_per_subwarp: int, stage_cap: int = 2048, stream=None):
+        _check(lib().gko_matrix_set_plan(self.handle, kernel, subwarp, rows_per_subwarp, stage_cap,
+                                         _stream(stream)), "set_plan")
 
     def export(self, stream=None):
         """Host copies of the device arrays (dict of numpy arrays)."""

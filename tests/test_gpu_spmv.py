@@ -125,33 +125,43 @@ def test_plan_histogram_and_split(gko):
         cls = np.where(L == 0, 0, np.floor(np.log2(np.maximum(L, 1))).astype(int) + 1)
         np.testing.assert_array_equal(p["hist"], np.bincount(cls, minlength=33))
         if L.max() <= 4 * L.mean() + 1:  # regular: row-block kernel, nothing split
+            m = L.mean()
             S = 1
-            while S < 8 and L.mean() > 48 * S:
+            while S < 8 and (128 // S) * m > 0.9 * 1024:
                 S *= 2
-            assert (p["subwarp"], p["rows_per_subwarp"], p["n_long_rows"]) == (S, 0, 0)
+            R = 1
+            while R < 4 and (128 // S) * 2 * R * m <= 1024:
+                R *= 2
+            assert (p["kernel"], p["subwarp"], p["rows_per_subwarp"], p["stage_cap"], p["n_long_rows"]) == \
+                (1, S, R, 1024, 0)
             continue
         short = L[L < 1024]
         mean = short.mean() if short.size else 1.0
         S = 1
         while S < 32 and S < mean:
             S *= 2
-        assert p["subwarp"] == S and p["long_threshold"] == 32 * S and p["rows_per_subwarp"] == 2
+        assert p["kernel"] == 0 and p["subwarp"] == S and p["long_threshold"] == 32 * S and p["rows_per_subwarp"] == 2
         longs = L[L > 32 * S]
         assert p["n_long_rows"] == longs.size
         assert p["n_long_chunks"] == int(np.sum((longs + 1023) // 1024))
 
 
-@pytest.mark.parametrize("S,R", [(1, 1), (2, 8), (4, 4), (8, 2), (16, 1), (32, 4), (32, 8),
-                                 (1, 0), (2, 0), (4, 0), (8, 0)])
+PLANS = ([(0, S, R, 2048) for S in (1, 2, 4, 8, 16, 32) for R in (1, 2, 4)]
+         + [(1, S, R, cap) for S in (1, 2, 4, 8) for R in (1, 2, 4) for cap in (512, 2048)]
+         + [(1, 1, 4, 8192), (1, 2, 1, 1024)])
+
+
+@pytest.mark.parametrize("kernel,S,R,cap", PLANS)
 @pytest.mark.parametrize("mat", ["powerlaw", "banded"])
-def test_every_plan_matches_oracle(gko, S, R, mat):
-    """Every subwarp plan, and the row-block kernel (R = 0) with 1-8 lanes per
-    row, including a matrix whose row blocks need several shared-memory stages."""
+def test_every_plan_matches_oracle(gko, kernel, S, R, cap, mat):
+    """Every subwarp plan and every row-block plan (lanes per row, interleaved
+    rows, stage capacity), including row blocks that need many stages."""
     G = gko
     A = I.powerlaw(30000, seed=3) if mat == "powerlaw" else I.banded(40000, 200, 0.7, seed=5)
     M = G.from_csr(A)
-    M.set_plan(S, R)
-    assert M.plan()["subwarp"] == S
+    M.set_plan(kernel, S, R, cap)
+    p = M.plan()
+    assert (p["kernel"], p["subwarp"], p["rows_per_subwarp"]) == (kernel, S, R)
     rng = np.random.default_rng(1)
     x = rng.uniform(-1, 1, A.n_cols)
     y0 = rng.uniform(-1, 1, A.n_rows)
