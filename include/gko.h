@@ -173,6 +173,22 @@ GKO_API int gko_matrix_destroy(gko_matrix m);
 GKO_API int gko_spmv(const double *alpha, gko_matrix A, const void *x, const double *beta, void *y,
              gko_dtype vec_dtype, void *stream);
 
+/* y = alpha * A * x + beta * y for an F64 COO handle, allocating nothing.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory at the time they multiply (their memory is owned by
+ * another allocator, or an allocation's possible implicit synchronisation is
+ * not acceptable in their loop).  Same kernels and results as gko_spmv on the
+ * handle, but the per-tile carries live in a fixed 1 MiB device array inside
+ * the library (held on every GPU that loads the library until exit) instead
+ * of pool scratch.  At most 134,217,728 COO entries; larger handles are
+ * rejected with GKO_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current).
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, or other threads) race and give wrong results; serialise them.
+ * Asynchronous on `stream`. */
+GKO_API int gko_spmv_coo_noalloc(const double *alpha, gko_matrix A, const double *x, const double *beta,
+                                 double *y, void *stream);
+
 /* ---------------------------------------------------------------- BLAS-1 -- */
 
 /* Deterministic FP64 reductions and updates on device vectors of length n

@@ -74,6 +74,7 @@ SIGNATURES = {
     "gko_matrix_set_plan": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P]),
     "gko_matrix_destroy": (C.c_int, [_P]),
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
+    "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
     "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
     "gko_axpy": (C.c_int, [_I64, _D, _P, _P, _P]),
@@ -269,6 +270,14 @@ def gko_spmv(alpha: float, A: Matrix, x, beta: float, y, vec_dtype=None, stream=
     a, b = C.c_double(alpha), C.c_double(beta)
     _check(lib().gko_spmv(C.byref(a), A.handle, _dptr(x), C.byref(b), _dptr(y), vec_dtype, _stream(stream)),
            "gko_spmv")
+    return y
+
+
+def gko_spmv_coo_noalloc(alpha: float, A: Matrix, x, beta: float, y, stream=None):
+    """y = alpha*A*x + beta*y for an F64 COO handle without any allocation."""
+    a, b = C.c_double(alpha), C.c_double(beta)
+    _check(lib().gko_spmv_coo_noalloc(C.byref(a), A.handle, _dptr(x), C.byref(b), _dptr(y), _stream(stream)),
+           "gko_spmv_coo_noalloc")
     return y
 
 
