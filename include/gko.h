@@ -209,6 +209,64 @@ GKO_API int gko_multi_dot(int64_t n, int32_t k, const double *V, int64_t ldv, co
  * A must be square with FP64 values. */
 GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *result, void *stream);
 
+/* --------------------------------------------------------------- solvers -- */
+
+#define GKO_PRECISION_F64 0        /* all FP64                                   */
+#define GKO_PRECISION_MIXED_F32 1  /* FP32 inner solve + FP64 refinement         */
+#define GKO_PRECISION_MIXED_BF16 2 /* BF16-valued inner SpMV + FP64 refinement   */
+
+typedef struct {
+  int32_t restart;      /* GMRES restart length m (<= 0: 30)                     */
+  int32_t precision;    /* GKO_PRECISION_*                                       */
+  double inner_tol;     /* mixed: inner relative tolerance (<= 0: 1e-4)          */
+  int32_t max_outer;    /* mixed: refinement steps (<= 0: 30)                    */
+  int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters) */
+  int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */
+  int32_t reserved;
+} gko_solve_opts;
+
+typedef struct {
+  int32_t status;           /* GKO_OK, GKO_NOT_CONVERGED or GKO_BREAKDOWN          */
+  int32_t iterations;       /* Krylov iterations (inner ones for mixed precision) */
+  int32_t outer_iterations; /* GMRES restart cycles / refinement steps            */
+  int32_t reserved;
+  double rel_residual;      /* true ||b - A x||_2 / ||b||_2, computed in FP64      */
+} gko_solve_result;
+
+/* Solve A x = b with unpreconditioned Krylov methods (paper, Section 1:
+ * CG, BiCG(STAB), GMRES; Section 4: CG timed on GPUs).
+ *   A: square FP64 matrix of any format (for mixed precision an FP32 or
+ *      BF16 copy is made once and cached on the handle);
+ *   b[n], x[n]: device FP64 vectors; x holds x0 on entry, the solution on
+ *      exit (also on NOT_CONVERGED / BREAKDOWN: the last iterate);
+ *   stop when ||r_k|| <= rel_tol * ||b|| for the recurrence residual, then
+ *      verify with the true residual b - A x; if the true residual misses,
+ *      it replaces r and iteration goes on until max_iters;
+ *   b == 0 gives x = 0 after 0 iterations.
+ * CG: Hestenes-Stiefel (Saad Alg. 6.18); breakdown when p.Ap <= 0.
+ * BiCGSTAB: van der Vorst 1992 (Saad Alg. 7.7); breakdown on exact zeros
+ *      of rhat.r, rhat.v, t.t or omega.
+ * GMRES(m): Saad-Schultz restarted GMRES with classical Gram-Schmidt applied
+ *      twice (CGS2) and Givens rotations on the device; iterations count
+ *      Arnoldi steps, outer_iterations restart cycles; each cycle starts
+ *      from the true residual.
+ * Mixed precision (opts->precision): x stays FP64; each refinement step
+ *      forms r = b - A x in FP64, solves A d = r with the same method on an
+ *      FP32 (or BF16-valued) copy of A with FP32 vectors, FP64 dots and FP64
+ *      scalars to ||r_inner|| <= inner_tol ||r||, and adds d in FP64, until
+ *      ||b - A x|| <= rel_tol ||b|| or max_outer steps.
+ * All scalars and convergence checks stay on the device; the host polls a
+ * status word every few iterations.  *res is written before returning
+ * (synchronises `stream`); opts may be NULL.  Returns res->status (GKO_OK,
+ * GKO_NOT_CONVERGED, GKO_BREAKDOWN) or an error. */
+GKO_API int gko_solve_cg(gko_matrix A, const double *b, double *x, double rel_tol, int32_t max_iters,
+                 const gko_solve_opts *opts, gko_solve_result *res, void *stream);
+GKO_API int gko_solve_bicgstab(gko_matrix A, const double *b, double *x, double rel_tol,
+                       int32_t max_iters, const gko_solve_opts *opts, gko_solve_result *res,
+                       void *stream);
+GKO_API int gko_solve_gmres(gko_matrix A, const double *b, double *x, double rel_tol, int32_t max_iters,
+                    const gko_solve_opts *opts, gko_solve_result *res, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

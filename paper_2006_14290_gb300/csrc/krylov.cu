@@ -1,0 +1,990 @@
+// Krylov solvers on the device: CG, BiCGSTAB and restarted GMRES (the solver
+// family the paper's Section 1 lists and Section 4 times), and
+// mixed-precision iterative refinement around them.
+//
+// Design: every vector kernel that ends in a reduction finishes with the
+// "last block" pattern of reduce.cuh, and that block's thread 0 runs the
+// scalar step of the method (alpha, beta, omega, convergence and breakdown
+// tests, iteration count) on the device state `Ctl`.  Every kernel of an
+// iteration is gated by Ctl::done, so the host enqueues batches of iterations
+// and only polls the state every few iterations; iterations enqueued after
+// convergence cost one empty launch each.  Dots and norms accumulate in FP64;
+// vectors are stored as T (double, or float for the inner solve of mixed
+// precision) with every update computed in FP64 and rounded once on store.
+#include <math.h>
+
+#include <algorithm>
+
+#include "blas1.cuh"
+#include "reduce.cuh"
+#include "spmv.cuh"
+
+namespace gko {
+
+enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kNotConverged = 3, kCheck = 4 };
+
+// Device-resident solver state.  The first three ints are gate words: an
+// SpMV gated on &done runs unless done|zero; gated on &phase it also stops
+// when `phase` is set (BiCGSTAB half step converged / GMRES cycle ended).
+struct Ctl {
+  int phase;
+  int done;
+  int zero;
+  int status;
+  int iter;
+  int maxit;
+  int replace;
+  int check_true;
+  int cycles;
+  int k;  // GMRES: columns of the finished cycle
+  int pad[2];
+  double nb, tol_abs;
+  double rho, rho_new, alpha, beta, omega;
+  double red[4];  // fused SpMV dots: red[0] = w.y, red[1] = y.y
+  double rr;
+};
+
+__device__ __forceinline__ double wd(double v) { return v; }
+__device__ __forceinline__ double wd(float v) { return (double)v; }
+
+template <int NV, typename Op>
+__device__ __forceinline__ void reduce_op(double (&v)[NV], RedWs ws, Op op) {
+  grid_reduce<256, NV>(v, ws.partials, ws.counter, blockIdx.x, gridDim.x, op);
+}
+
+#define GKO_GRID_LOOP(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// --------------------------------------------------------------- shared --
+
+// r = b - q (q = A x0, or zero when q == nullptr); copies of r into c1/c2
+// (optional), zeroes z1/z2 (optional).  Reduces ||b||^2, ||r||^2.
+struct InitOp {
+  Ctl* c;
+  double rel_tol;
+  int kind;  // 0 CG, 1 BiCGSTAB, 2 GMRES (GMRES runs its own restart step)
+  __device__ void operator()(const double (&t)[2]) const {
+    c->nb = sqrt(t[0]);
+    c->tol_abs = rel_tol * c->nb;
+    c->rr = t[1];
+    c->iter = 0;
+    c->cycles = 0;
+    c->phase = 0;
+    c->replace = 0;
+    if (t[0] == 0.0) {  // b == 0: x = 0 after 0 iterations
+      c->status = kConverged;
+      c->done = 1;
+      return;
+    }
+    if (sqrt(t[1]) <= c->tol_abs) {
+      c->status = kConverged;
+      c->done = 1;
+      return;
+    }
+    c->status = kRun;
+    c->done = 0;
+    if (kind == 0) {
+      c->rho = t[1];
+    } else if (kind == 1) {
+      c->rho = c->alpha = c->omega = 1.0;
+      c->rho_new = t[1];  // rhat = r
+      c->beta = t[1];
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) init_residual_kernel(int64_t n, const double* __restrict__ b,
+                                                            const T* __restrict__ q, T* __restrict__ r, T* c1, T* c2,
+                                                            T* z1, T* z2, RedWs ws, InitOp op) {
+  double acc[2] = {0.0, 0.0};
+  GKO_GRID_LOOP(i, n) {
+    const double bi = b[i];
+    const T ri = (T)(q ? bi - wd(q[i]) : bi);
+    r[i] = ri;
+    if (c1) c1[i] = ri;
+    if (c2) c2[i] = ri;
+    if (z1) z1[i] = T(0);
+    if (z2) z2[i] = T(0);
+    acc[0] += bi * bi;
+    acc[1] += wd(ri) * wd(ri);
+  }
+  reduce_op<2>(acc, ws, op);
+}
+
+// t = b - q stored into q; ||t||^2 decides: converged, or replace r by t.
+struct TrueResOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const {
+    if (sqrt(t[0]) <= c->tol_abs) {
+      c->status = kConverged;
+      c->done = 1;
+    } else {
+      c->status = kRun;
+      c->done = 0;
+      c->replace = 1;
+      c->rho_new = t[0];
+      c->phase = 0;
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) true_res_kernel(int64_t n, const double* __restrict__ b, T* __restrict__ q,
+                                                       RedWs ws, TrueResOp op) {
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const T t = (T)(b[i] - wd(q[i]));
+    q[i] = t;
+    acc[0] += wd(t) * wd(t);
+  }
+  reduce_op<1>(acc, ws, op);
+}
+
+// red[0] = w.y, red[1] = y.y (formats whose SpMV cannot fuse the dot).
+struct Store2 {
+  double* out;
+  __device__ void operator()(const double (&t)[2]) const {
+    out[0] = t[0];
+    out[1] = t[1];
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) dot2_kernel(int64_t n, const T* __restrict__ w, const T* __restrict__ y,
+                                                   RedWs ws, double* out, const int* gate) {
+  if (gated(gate)) return;
+  double acc[2] = {0.0, 0.0};
+  GKO_GRID_LOOP(i, n) {
+    const double yi = wd(y[i]);
+    acc[0] += wd(w[i]) * yi;
+    acc[1] += yi * yi;
+  }
+  reduce_op<2>(acc, ws, Store2{out});
+}
+
+// ------------------------------------------------------------------- CG --
+
+struct CgUpdateOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const {
+    const double pq = c->red[0];
+    if (!(pq > 0.0)) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    const double rho_new = t[0];
+    c->iter += 1;
+    c->rho_new = rho_new;
+    if (sqrt(rho_new) <= c->tol_abs) {
+      c->status = c->check_true ? kCheck : kConverged;
+      c->done = 1;
+      return;
+    }
+    if (c->iter >= c->maxit) {
+      c->status = kNotConverged;
+      c->done = 1;
+      return;
+    }
+    c->beta = rho_new / c->rho;
+    c->rho = rho_new;
+  }
+};
+
+// alpha = rho / (p.q); x += alpha p; r -= alpha q; reduces r.r
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
+                                                        const T* __restrict__ p, const T* __restrict__ q, Ctl* c,
+                                                        RedWs ws) {
+  if (gated(&c->done)) return;
+  const double pq = c->red[0];
+  const bool ok = pq > 0.0;
+  const double alpha = ok ? c->rho / pq : 0.0;
+  double acc[1] = {0.0};
+  if (ok) {
+    GKO_GRID_LOOP(i, n) {
+      x[i] = (T)__fma_rn(alpha, wd(p[i]), wd(x[i]));
+      const T ri = (T)__fma_rn(-alpha, wd(q[i]), wd(r[i]));
+      r[i] = ri;
+      acc[0] += wd(ri) * wd(ri);
+    }
+  }
+  reduce_op<1>(acc, ws, CgUpdateOp{c});
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c) {
+  if (gated(&c->done)) return;
+  const double beta = c->beta;
+  GKO_GRID_LOOP(i, n) p[i] = (T)__fma_rn(beta, wd(p[i]), wd(r[i]));
+}
+
+// after a failed true-residual check: r = t, beta = rho_new/rho, p = r + beta p
+struct CgReplaceOp {
+  Ctl* c;
+  __device__ void operator()(const double (&)[1]) const {
+    c->replace = 0;
+    c->rho = c->rho_new;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
+                                                         const T* __restrict__ t, Ctl* c, RedWs ws) {
+  if (!*(volatile int*)&c->replace) return;
+  const double beta = c->rho_new / c->rho;
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const T ri = t[i];
+    r[i] = ri;
+    p[i] = (T)__fma_rn(beta, wd(p[i]), wd(ri));
+  }
+  reduce_op<1>(acc, ws, CgReplaceOp{c});
+}
+
+// ------------------------------------------------------------- BiCGSTAB --
+
+// p = r + beta (p - omega v)
+template <typename T>
+__global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
+                                                     const T* __restrict__ v, Ctl* c) {
+  if (gated(&c->done)) return;
+  const double beta = c->beta, omega = c->omega;
+  GKO_GRID_LOOP(i, n) p[i] = (T)__fma_rn(beta, __fma_rn(-omega, wd(v[i]), wd(p[i])), wd(r[i]));
+}
+
+struct BicgSOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const {
+    const double rv = c->red[0];
+    if (rv == 0.0) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    c->alpha = c->rho_new / rv;
+    c->iter += 1;
+    if (sqrt(t[0]) <= c->tol_abs) c->phase = 1;  // finish with x += alpha p
+  }
+};
+
+// alpha = rho_new / (rhat.v); s = r - alpha v; reduces s.s
+template <typename T>
+__global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ v,
+                                                     T* __restrict__ s, Ctl* c, RedWs ws) {
+  if (gated(&c->done)) return;
+  const double rv = c->red[0];
+  const double alpha = rv != 0.0 ? c->rho_new / rv : 0.0;
+  double acc[1] = {0.0};
+  if (rv != 0.0) {
+    GKO_GRID_LOOP(i, n) {
+      const T si = (T)__fma_rn(-alpha, wd(v[i]), wd(r[i]));
+      s[i] = si;
+      acc[0] += wd(si) * wd(si);
+    }
+  }
+  reduce_op<1>(acc, ws, BicgSOp{c});
+}
+
+struct BicgXOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[2]) const {
+    if (c->phase) {  // half step: ||s|| small, x += alpha p was done
+      c->phase = 0;
+      c->status = c->check_true ? kCheck : kConverged;
+      c->done = 1;
+      return;
+    }
+    const double tt = c->red[1];
+    if (tt == 0.0) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    const double omega = c->red[0] / tt;
+    c->omega = omega;
+    c->rho = c->rho_new;
+    c->rho_new = t[1];
+    if (sqrt(t[0]) <= c->tol_abs) {
+      c->status = c->check_true ? kCheck : kConverged;
+      c->done = 1;
+      return;
+    }
+    if (omega == 0.0 || (c->iter < c->maxit && c->rho_new == 0.0)) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    if (c->iter >= c->maxit) {
+      c->status = kNotConverged;
+      c->done = 1;
+      return;
+    }
+    c->beta = (c->rho_new / c->rho) * (c->alpha / omega);
+  }
+};
+
+// omega = t.s / t.t; x += alpha p + omega s; r = s - omega t; reduces r.r and
+// rhat.r.  In the half step only x += alpha p.
+template <typename T>
+__global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ x, const T* __restrict__ p,
+                                                     const T* __restrict__ s, const T* __restrict__ t,
+                                                     T* __restrict__ r, const T* __restrict__ rh, Ctl* c, RedWs ws) {
+  if (gated(&c->done)) return;
+  const double alpha = c->alpha;
+  double acc[2] = {0.0, 0.0};
+  if (*(volatile int*)&c->phase) {
+    GKO_GRID_LOOP(i, n) x[i] = (T)__fma_rn(alpha, wd(p[i]), wd(x[i]));
+  } else {
+    const double tt = c->red[1];
+    if (tt != 0.0) {
+      const double omega = c->red[0] / tt;
+      GKO_GRID_LOOP(i, n) {
+        const double si = wd(s[i]);
+        x[i] = (T)__fma_rn(omega, si, __fma_rn(alpha, wd(p[i]), wd(x[i])));
+        const T ri = (T)__fma_rn(-omega, wd(t[i]), si);
+        r[i] = ri;
+        acc[0] += wd(ri) * wd(ri);
+        acc[1] += wd(rh[i]) * wd(ri);
+      }
+    }
+  }
+  reduce_op<2>(acc, ws, BicgXOp{c});
+}
+
+// after a failed true-residual check: restart the recurrences from r = t
+struct BicgRestartOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const {
+    c->replace = 0;
+    c->rho = c->alpha = c->omega = 1.0;
+    c->rho_new = t[0];
+    c->beta = t[0];
+    if (c->iter >= c->maxit) {
+      c->status = kNotConverged;
+      c->done = 1;
+    } else if (t[0] == 0.0) {
+      c->status = kBreakdown;
+      c->done = 1;
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) bicg_restart_kernel(int64_t n, T* __restrict__ r, const T* __restrict__ rh,
+                                                           T* __restrict__ p, T* __restrict__ v,
+                                                           const T* __restrict__ t, Ctl* c, RedWs ws) {
+  if (!*(volatile int*)&c->replace) return;
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const T ri = t[i];
+    r[i] = ri;
+    p[i] = T(0);
+    v[i] = T(0);
+    acc[0] += wd(rh[i]) * wd(ri);
+  }
+  reduce_op<1>(acc, ws, BicgRestartOp{c});
+}
+
+// ---------------------------------------------------------------- GMRES --
+
+// Cycle start: v0 = r = b - A x (q = A x), ||r|| -> beta, g = beta e1.
+struct GmStartOp {
+  Ctl* c;
+  double* g;
+  int m;
+  __device__ void operator()(const double (&t)[1]) const {
+    const double beta = sqrt(t[0]);
+    c->rr = t[0];
+    c->phase = 0;
+    c->k = 0;
+    if (beta <= c->tol_abs) {
+      c->status = kConverged;
+      c->done = 1;
+      return;
+    }
+    if (c->iter >= c->maxit) {
+      c->status = kNotConverged;
+      c->done = 1;
+      return;
+    }
+    c->beta = beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) gm_start_kernel(int64_t n, const double* __restrict__ b,
+                                                       const T* __restrict__ q, T* __restrict__ v0, Ctl* c, RedWs ws,
+                                                       GmStartOp op) {
+  if (gated(&c->done)) return;
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const T ri = (T)(q ? b[i] - wd(q[i]) : b[i]);
+    v0[i] = ri;
+    acc[0] += wd(ri) * wd(ri);
+  }
+  reduce_op<1>(acc, ws, op);
+}
+
+// v = v * (1 / *den); den = &beta for v0, &H[(j+1), j] for v_{j+1}
+template <typename T>
+__global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict__ v, const double* den, Ctl* c) {
+  if (gated(&c->phase)) return;
+  const double inv = 1.0 / *den;
+  GKO_GRID_LOOP(i, n) v[i] = (T)(wd(v[i]) * inv);
+}
+
+// gated multi-dot: partial sums of V_j . w for j <= jmax (blockIdx.y = j)
+template <typename T>
+__global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ldv,
+                                                          const T* __restrict__ w, double* __restrict__ partials,
+                                                          Ctl* c) {
+  if (gated(&c->phase)) return;
+  const int j = blockIdx.y;
+  const T* v = V + (int64_t)j * ldv;
+  double acc = 0.0;
+  GKO_GRID_LOOP(i, n) acc += wd(v[i]) * wd(__ldg(w + i));
+  const double sblk = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[(int64_t)j * kMultiSlots + blockIdx.x] = sblk;
+}
+
+__global__ void __launch_bounds__(256) gm_multidot_finish_kernel(int g, const double* __restrict__ partials,
+                                                                 double* __restrict__ h, int accumulate, Ctl* c) {
+  if (gated(&c->phase)) return;
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < g; i += 256) acc += partials[(int64_t)j * kMultiSlots + i];
+  const double t = block_sum<256>(acc);
+  if (threadIdx.x == 0) h[j] = accumulate ? h[j] + t : t;
+}
+
+struct StoreRr {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const { c->rr = t[0]; }
+};
+
+// w -= sum_{j<=jmax} h_j V_j (h: device, the pass's coefficients); with
+// NORM also reduces ||w||^2 into c->rr.
+template <typename T, bool NORM>
+__global__ void __launch_bounds__(256) gm_axpy_kernel(int64_t n, int jcount, const double* __restrict__ h,
+                                                      const T* __restrict__ V, int64_t ldv, T* __restrict__ w, Ctl* c,
+                                                      RedWs ws) {
+  if (gated(&c->phase)) return;
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    double v = wd(w[i]);
+    for (int j = 0; j < jcount; ++j) v = __fma_rn(-__ldg(h + j), wd(V[(int64_t)j * ldv + i]), v);
+    const T o = (T)v;
+    w[i] = o;
+    if (NORM) acc[0] += wd(o) * wd(o);
+  }
+  if (NORM) reduce_op<1>(acc, ws, StoreRr{c});
+}
+
+// Column j of the Hessenberg matrix from the two CGS passes, previous Givens
+// rotations, a new rotation, the residual estimate |g_{j+1}| and the cycle
+// end test.  One thread.
+__global__ void gm_givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
+                                 double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                                 double* __restrict__ g, Ctl* c) {
+  if (gated(&c->phase)) return;
+  double* col = H + (int64_t)j;  // H[i*m + j]
+  for (int i = 0; i <= j; ++i) col[(int64_t)i * m] = h1[i] + h2[i];
+  const double hn = sqrt(c->rr);
+  col[(int64_t)(j + 1) * m] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[(int64_t)i * m], b = col[(int64_t)(i + 1) * m];
+    col[(int64_t)i * m] = cs[i] * a + sn[i] * b;
+    col[(int64_t)(i + 1) * m] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[(int64_t)j * m], b = col[(int64_t)(j + 1) * m];
+  const double den = sqrt(a * a + b * b);
+  c->iter += 1;
+  c->k = j + 1;
+  if (den == 0.0) {
+    c->status = kBreakdown;
+    c->k = j;
+    c->phase = 1;
+    return;
+  }
+  cs[j] = a / den;
+  sn[j] = b / den;
+  col[(int64_t)j * m] = den;
+  col[(int64_t)(j + 1) * m] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  c->rho = hn;  // h_{j+1,j}, the divisor of the next basis vector
+  if (hn == 0.0 || fabs(g[j + 1]) <= c->tol_abs) c->replace = 1;  // estimate says converged
+  if (c->replace || c->iter >= c->maxit || j + 1 == m) c->phase = 1;
+}
+
+// v_{j+1} = w / h_{j+1,j} (skipped once the cycle has ended)
+template <typename T>
+__global__ void __launch_bounds__(256) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
+                                                      Ctl* c) {
+  if (gated(&c->phase)) return;
+  const double inv = 1.0 / c->rho;
+  GKO_GRID_LOOP(i, n) vn[i] = (T)(wd(w[i]) * inv);
+}
+
+// Back substitution H[0:k,0:k] y = g[0:k]; stores -y for the x update.
+__global__ void gm_backsolve_kernel(int m, const double* __restrict__ H, const double* __restrict__ g,
+                                    double* __restrict__ ny, Ctl* c) {
+  if (gated(&c->done)) return;
+  const int k = c->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= H[(int64_t)i * m + l] * (-ny[l]);
+    ny[i] = -(s / H[(int64_t)i * m + i]);
+  }
+  c->cycles += 1;
+}
+
+// x += V y  (= x - sum_j ny_j V_j), then close the cycle: stop on breakdown,
+// otherwise the next cycle recomputes the true residual.
+template <typename T>
+__global__ void __launch_bounds__(256) gm_update_x_kernel(int64_t n, const double* __restrict__ ny,
+                                                          const T* __restrict__ V, int64_t ldv, T* __restrict__ x,
+                                                          Ctl* c) {
+  if (gated(&c->done)) return;
+  const int k = c->k;
+  GKO_GRID_LOOP(i, n) {
+    double v = wd(x[i]);
+    for (int j = 0; j < k; ++j) v = __fma_rn(-__ldg(ny + j), wd(V[(int64_t)j * ldv + i]), v);
+    x[i] = (T)v;
+  }
+}
+
+// End of cycle: stop on breakdown; an inner solve (no true-residual check)
+// also stops when the Givens estimate met the tolerance.  Otherwise the next
+// cycle start recomputes the true residual and decides.
+__global__ void gm_close_kernel(Ctl* c) {
+  if (gated(&c->done)) return;
+  if (c->status == kBreakdown) {
+    c->done = 1;
+  } else if (!c->check_true && c->replace) {
+    c->status = kConverged;
+    c->done = 1;
+  }
+  c->replace = 0;
+  c->phase = 0;
+}
+
+// ------------------------------------------------------- final residual --
+
+struct FinalOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const { c->rr = t[0]; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) final_res_kernel(int64_t n, const double* __restrict__ b,
+                                                        const T* __restrict__ q, RedWs ws, Ctl* c) {
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const double t = b[i] - wd(q[i]);
+    acc[0] += t * t;
+  }
+  reduce_op<1>(acc, ws, FinalOp{c});
+}
+
+template <typename T>
+__global__ void zero_kernel(int64_t n, T* __restrict__ x) {
+  GKO_GRID_LOOP(i, n) x[i] = T(0);
+}
+
+// x64 += d (mixed precision refinement update)
+__global__ void add_f32_kernel(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  GKO_GRID_LOOP(i, n) x[i] += (double)d[i];
+}
+
+// ================================================================ host ====
+
+static int vec_grid(int64_t n) {
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
+  return (int)g;
+}
+
+// Pinned host mirror of Ctl for polling.
+static Ctl* host_ctl() {
+  thread_local Ctl* h = nullptr;
+  if (!h) {
+    if (cudaMallocHost((void**)&h, sizeof(Ctl)) != cudaSuccess) {
+      cudaGetLastError();
+      static thread_local Ctl fallback;
+      h = &fallback;
+    }
+  }
+  return h;
+}
+
+static int read_ctl(const Ctl* d, Ctl* h, cudaStream_t s) {
+  GKO_TRY_CUDA(cudaMemcpyAsync(h, d, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  return GKO_OK;
+}
+
+// Bump allocator over one pool allocation.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) / 256 * 256;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * count + 64;
+    return p;
+  }
+};
+
+struct SolveSpec {
+  int solver;  // 0 CG, 1 BiCGSTAB, 2 GMRES
+  double rel_tol;
+  int maxit;
+  int restart;
+  int check_true;
+  int check_every;
+};
+
+struct SolveOut {
+  int status;
+  int iterations;
+  int cycles;
+};
+
+// One Krylov solve on the device.  A: matrix whose value type matches T
+// (double: F64; float: F32/BF16).  b: FP64 right-hand side; x: T vector,
+// x0 on entry (x_zero: treat x0 as zero without reading it).
+template <typename T>
+static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero, const SolveSpec& sp,
+                       cudaStream_t s, SolveOut* out) {
+  const int64_t n = A->n_rows;
+  const int m = std::max(1, sp.restart);
+  const int nvec = sp.solver == 0 ? 3 : sp.solver == 1 ? 7 : (m + 2);
+  const size_t spmv_sb = spmv_scratch_bytes(A);
+  const size_t bytes = 256 * 16 + sizeof(Ctl) + sizeof(double) * 2 * kDotSlots + 512 +
+                       (size_t)nvec * (sizeof(T) * ((size_t)n + 64) + 320) + spmv_sb + 320 +
+                       sizeof(double) * ((size_t)(m + 1) * m + 6 * (m + 2) + (size_t)(m + 1) * kMultiSlots) + 4096;
+  Scratch mem;
+  GKO_TRY(mem.get(bytes, s));
+  Carve cv{static_cast<char*>(mem.data())};
+  Ctl* c = cv.take<Ctl>(1);
+  unsigned* counter = cv.take<unsigned>(4);
+  double* partials = cv.take<double>(2 * kDotSlots);
+  void* spmv_scratch = spmv_sb ? cv.take<char>(spmv_sb) : nullptr;
+  RedWs ws{partials, counter};
+  GKO_TRY_CUDA(cudaMemsetAsync(counter, 0, 16, s));
+  Ctl init{};
+  init.maxit = sp.maxit;
+  init.check_true = sp.check_true;
+  GKO_TRY_CUDA(cudaMemcpyAsync(c, &init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  Ctl* hc = host_ctl();
+  const int vg = vec_grid(n), rg = reduce_grid(n);
+  const bool fused = spmv_fuses_dot(A);
+  auto spmv = [&](const T* in, T* outv, const T* w, const int* gate) -> int {
+    if (w && fused) {
+      DotSpec d;
+      d.w = w;
+      d.partials = partials;
+      d.counter = counter;
+      d.result = c->red;
+      return spmv_run(A, in, outv, 1.0, 0.0, s, spmv_scratch, &d, gate);
+    }
+    GKO_TRY(spmv_run(A, in, outv, 1.0, 0.0, s, spmv_scratch, nullptr, gate));
+    if (w) {
+      dot2_kernel<T><<<rg, 256, 0, s>>>(n, w, outv, ws, c->red, gate);
+      GKO_TRY_CUDA(cudaGetLastError());
+    }
+    return GKO_OK;
+  };
+  out->iterations = 0;
+  out->cycles = 0;
+
+  if (sp.solver == 0 || sp.solver == 1) {
+    T* r = cv.take<T>(n);
+    T* p = cv.take<T>(n);
+    T* q = cv.take<T>(n);
+    T *rh = nullptr, *v = nullptr, *sv = nullptr, *tv = nullptr;
+    if (sp.solver == 1) {
+      rh = cv.take<T>(n);
+      v = cv.take<T>(n);
+      sv = cv.take<T>(n);
+      tv = cv.take<T>(n);
+    }
+    if (!x_zero) GKO_TRY(spmv(x, q, nullptr, nullptr));
+    if (sp.solver == 0)
+      init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, p, nullptr, nullptr, nullptr, ws,
+                                                 InitOp{c, sp.rel_tol, 0});
+    else
+      init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, rh, nullptr, p, v, ws,
+                                                 InitOp{c, sp.rel_tol, 1});
+    GKO_TRY_CUDA(cudaGetLastError());
+    if (x_zero) zero_kernel<T><<<vg, 256, 0, s>>>(n, x);
+    GKO_TRY(read_ctl(c, hc, s));
+    if (hc->nb == 0.0) zero_kernel<T><<<vg, 256, 0, s>>>(n, x);
+    if (!hc->done && sp.maxit <= 0) {  // no iterations allowed
+      hc->status = kNotConverged;
+      hc->done = 1;
+    }
+    int batch = sp.check_every > 0 ? sp.check_every : 8;
+    while (!hc->done) {
+      for (int it = 0; it < batch; ++it) {
+        if (sp.solver == 0) {
+          GKO_TRY(spmv(p, q, p, &c->done));
+          cg_update_kernel<T><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws);
+          cg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, c);
+        } else {
+          bicg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, v, c);
+          GKO_TRY(spmv(p, v, rh, &c->done));
+          bicg_s_kernel<T><<<rg, 256, 0, s>>>(n, r, v, sv, c, ws);
+          GKO_TRY(spmv(sv, tv, sv, &c->phase));
+          bicg_x_kernel<T><<<rg, 256, 0, s>>>(n, x, p, sv, tv, r, rh, c, ws);
+        }
+        GKO_TRY_CUDA(cudaGetLastError());
+      }
+      GKO_TRY(read_ctl(c, hc, s));
+      if (sp.check_every <= 0) batch = std::min(batch * 2, 64);
+      if (hc->status == kCheck) {  // verify with the true residual
+        GKO_TRY(spmv(x, q, nullptr, nullptr));
+        true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c});
+        if (sp.solver == 0)
+          cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws);
+        else
+          bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
+        GKO_TRY_CUDA(cudaGetLastError());
+        GKO_TRY(read_ctl(c, hc, s));
+      }
+    }
+  } else {
+    const int64_t ld = ((int64_t)n + 63) / 64 * 64;
+    T* V = cv.take<T>((size_t)ld * (m + 1));
+    T* w = cv.take<T>(n);
+    double* H = cv.take<double>((size_t)(m + 1) * m);
+    double* cs = cv.take<double>(m + 1);
+    double* sn = cv.take<double>(m + 1);
+    double* g = cv.take<double>(m + 2);
+    double* h1 = cv.take<double>(m + 2);
+    double* h2 = cv.take<double>(m + 2);
+    double* ny = cv.take<double>(m + 2);
+    double* mpart = cv.take<double>((size_t)(m + 1) * kMultiSlots);
+    // ||b|| and the zero-b case through the common init kernel
+    init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, nullptr, w, nullptr, nullptr, nullptr, nullptr, ws,
+                                               InitOp{c, sp.rel_tol, 2});
+    if (x_zero) zero_kernel<T><<<vg, 256, 0, s>>>(n, x);
+    GKO_TRY_CUDA(cudaGetLastError());
+    GKO_TRY(read_ctl(c, hc, s));
+    if (hc->nb == 0.0) {
+      zero_kernel<T><<<vg, 256, 0, s>>>(n, x);
+    } else {
+      // the initial residual decides afresh in the first cycle start
+      const int zero = 0, run = kRun;
+      GKO_TRY_CUDA(cudaMemcpyAsync(&c->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+      GKO_TRY_CUDA(cudaMemcpyAsync(&c->status, &run, sizeof(int), cudaMemcpyHostToDevice, s));
+      hc->done = 0;
+    }
+    int64_t mg = std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, kMultiSlots));
+    bool first = true;
+    while (!hc->done) {
+      // cycle start: v0 = b - A x
+      if (!(first && x_zero)) GKO_TRY(spmv(x, w, nullptr, &c->done));
+      gm_start_kernel<T><<<rg, 256, 0, s>>>(n, b, (first && x_zero) ? nullptr : w, V, c, ws, GmStartOp{c, g, m});
+      first = false;
+      gm_scale_kernel<T><<<vg, 256, 0, s>>>(n, V, &c->beta, c);
+      for (int j = 0; j < m; ++j) {
+        T* vj = V + (int64_t)j * ld;
+        GKO_TRY(spmv(vj, w, nullptr, &c->phase));
+        for (int pass = 0; pass < 2; ++pass) {
+          double* hp = pass == 0 ? h1 : h2;
+          gm_multidot_kernel<T><<<dim3((unsigned)mg, (unsigned)(j + 1)), 256, 0, s>>>(n, V, ld, w, mpart, c);
+          gm_multidot_finish_kernel<<<j + 1, 256, 0, s>>>((int)mg, mpart, hp, 0, c);
+          if (pass == 0)
+            gm_axpy_kernel<T, false><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws);
+          else
+            gm_axpy_kernel<T, true><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws);
+        }
+        gm_givens_kernel<<<1, 1, 0, s>>>(j, m, h1, h2, H, cs, sn, g, c);
+        if (j + 1 <= m) gm_next_kernel<T><<<vg, 256, 0, s>>>(n, w, V + (int64_t)(j + 1) * ld, c);
+        GKO_TRY_CUDA(cudaGetLastError());
+      }
+      gm_backsolve_kernel<<<1, 1, 0, s>>>(m, H, g, ny, c);
+      gm_update_x_kernel<T><<<vg, 256, 0, s>>>(n, ny, V, ld, x, c);
+      gm_close_kernel<<<1, 1, 0, s>>>(c);
+      GKO_TRY_CUDA(cudaGetLastError());
+      GKO_TRY(read_ctl(c, hc, s));
+    }
+  }
+  out->status = hc->status;
+  out->iterations = hc->iter;
+  out->cycles = hc->cycles;
+  return GKO_OK;
+}
+
+// true relative residual ||b - A x|| / ||b|| in FP64 (A: F64)
+static int true_rel_residual(const gko_matrix_s* A, const double* b, const double* x, double nb, double* out,
+                             cudaStream_t s) {
+  const int64_t n = A->n_rows;
+  if (nb == 0.0) {
+    *out = 0.0;
+    return GKO_OK;
+  }
+  Scratch mem;
+  const size_t sb = spmv_scratch_bytes(A);
+  GKO_TRY(mem.get(sizeof(double) * (n + 2 * kDotSlots) + sizeof(Ctl) + sb + 2048, s));
+  Carve cv{static_cast<char*>(mem.data())};
+  Ctl* c = cv.take<Ctl>(1);
+  unsigned* counter = cv.take<unsigned>(4);
+  double* partials = cv.take<double>(2 * kDotSlots);
+  double* q = cv.take<double>(n);
+  void* ss = sb ? cv.take<char>(sb) : nullptr;
+  GKO_TRY_CUDA(cudaMemsetAsync(counter, 0, 16, s));
+  GKO_TRY(spmv_run(A, x, q, 1.0, 0.0, s, ss, nullptr, nullptr));
+  final_res_kernel<double><<<reduce_grid(n), 256, 0, s>>>(n, b, q, RedWs{partials, counter}, c);
+  GKO_TRY_CUDA(cudaGetLastError());
+  double rr = 0.0;
+  GKO_TRY_CUDA(cudaMemcpyAsync(&rr, &c->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  *out = sqrt(rr) / nb;
+  return GKO_OK;
+}
+
+static int map_status(int st) {
+  switch (st) {
+    case kConverged: return GKO_OK;
+    case kBreakdown: return GKO_BREAKDOWN;
+    default: return GKO_NOT_CONVERGED;
+  }
+}
+
+// Low-precision copy of A cached on the handle for mixed-precision solves.
+static int lowp_copy(gko_matrix A, gko_dtype to, cudaStream_t s, gko_matrix* out) {
+  std::lock_guard<std::mutex> lk(A->mu);
+  auto it = A->lowp.find((int)to);
+  if (it != A->lowp.end()) {
+    *out = it->second;
+    return GKO_OK;
+  }
+  gko_matrix m = nullptr;
+  GKO_TRY(gko_matrix_convert_values(A, to, s, &m));
+  A->lowp[(int)to] = m;
+  *out = m;
+  return GKO_OK;
+}
+
+static int norm2_host(const double* v, int64_t n, double* out, cudaStream_t s) {
+  double d = 0.0;
+  GKO_TRY(gko_dot(n, v, v, &d, s));
+  *out = sqrt(d);
+  return GKO_OK;
+}
+
+// r = b - A x (FP64)
+__global__ void residual64_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ q) {
+  GKO_GRID_LOOP(i, n) q[i] = b[i] - q[i];
+}
+
+static int solve_entry(int solver, gko_matrix A, const double* b, double* x, double rel_tol, int32_t max_iters,
+                       const gko_solve_opts* opts, gko_solve_result* res, void* stream) {
+  if (!A || !res) return fail(GKO_INVALID_ARG, "null matrix or result");
+  res->status = GKO_NOT_CONVERGED;
+  res->iterations = res->outer_iterations = 0;
+  res->rel_residual = 0.0;
+  if (A->n_rows != A->n_cols) return fail(GKO_INVALID_ARG, "solvers need a square matrix");
+  if (A->dtype != GKO_F64) return fail(GKO_INVALID_ARG, "solvers take the FP64 matrix (mixed precision copies it)");
+  if (A->n_rows > 0 && (!b || !x)) return fail(GKO_INVALID_ARG, "null b or x");
+  if (!(rel_tol >= 0.0) || max_iters < 0) return fail(GKO_INVALID_ARG, "bad tolerance or iteration cap");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n_rows;
+  if (n == 0) {
+    res->status = GKO_OK;
+    return GKO_OK;
+  }
+  gko_solve_opts o{};
+  if (opts) o = *opts;
+  SolveSpec sp;
+  sp.solver = solver;
+  sp.rel_tol = rel_tol;
+  sp.maxit = max_iters;
+  sp.restart = o.restart > 0 ? o.restart : 30;
+  sp.check_true = 1;
+  sp.check_every = o.check_every;
+  double nb = 0.0;
+  GKO_TRY(norm2_host(b, n, &nb, s));
+
+  if (o.precision == GKO_PRECISION_F64) {
+    SolveOut so{};
+    GKO_TRY(krylov_core<double>(A, b, x, false, sp, s, &so));
+    res->iterations = so.iterations;
+    res->outer_iterations = so.cycles;
+    GKO_TRY(true_rel_residual(A, b, x, nb, &res->rel_residual, s));
+    res->status = map_status(so.status);
+    return res->status;
+  }
+  if (o.precision != GKO_PRECISION_MIXED_F32 && o.precision != GKO_PRECISION_MIXED_BF16)
+    return fail(GKO_INVALID_ARG, "unknown precision");
+  gko_matrix A32 = nullptr;
+  GKO_TRY(lowp_copy(A, o.precision == GKO_PRECISION_MIXED_F32 ? GKO_F32 : GKO_BF16, s, &A32));
+  // mixed-precision iterative refinement: FP64 residual, FP32-stored inner solve
+  SolveSpec in = sp;
+  in.rel_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+  in.maxit = o.inner_maxit > 0 ? o.inner_maxit : max_iters;
+  in.check_true = 0;
+  const int max_outer = o.max_outer > 0 ? o.max_outer : 30;
+  Scratch mem;
+  const size_t sb = spmv_scratch_bytes(A);
+  GKO_TRY(mem.get(sizeof(double) * n + sizeof(float) * n + sb + 2048, s));
+  Carve cv{static_cast<char*>(mem.data())};
+  double* r = cv.take<double>(n);
+  float* d = cv.take<float>(n);
+  void* ss = sb ? cv.take<char>(sb) : nullptr;
+  const int vg = vec_grid(n);
+  int total_inner = 0, outer = 0;
+  bool converged = nb == 0.0;
+  if (nb == 0.0) zero_kernel<double><<<vg, 256, 0, s>>>(n, x);
+  while (!converged) {
+    GKO_TRY(spmv_run(A, x, r, 1.0, 0.0, s, ss, nullptr, nullptr));
+    residual64_kernel<<<vg, 256, 0, s>>>(n, b, r);
+    GKO_TRY_CUDA(cudaGetLastError());
+    double nr = 0.0;
+    GKO_TRY(norm2_host(r, n, &nr, s));
+    if (nr <= rel_tol * nb) {
+      converged = true;
+      break;
+    }
+    if (outer >= max_outer) break;
+    SolveOut so{};
+    GKO_TRY(krylov_core<float>(A32, r, d, true, in, s, &so));
+    total_inner += so.iterations;
+    outer += 1;
+    add_f32_kernel<<<vg, 256, 0, s>>>(n, x, d);
+    GKO_TRY_CUDA(cudaGetLastError());
+  }
+  res->iterations = total_inner;
+  res->outer_iterations = outer;
+  GKO_TRY(true_rel_residual(A, b, x, nb, &res->rel_residual, s));
+  res->status = converged ? GKO_OK : GKO_NOT_CONVERGED;
+  return res->status;
+}
+
+}  // namespace gko
+
+extern "C" {
+
+int gko_solve_cg(gko_matrix A, const double* b, double* x, double rel_tol, int32_t max_iters,
+                 const gko_solve_opts* opts, gko_solve_result* res, void* stream) {
+  return gko::solve_entry(0, A, b, x, rel_tol, max_iters, opts, res, stream);
+}
+
+int gko_solve_bicgstab(gko_matrix A, const double* b, double* x, double rel_tol, int32_t max_iters,
+                       const gko_solve_opts* opts, gko_solve_result* res, void* stream) {
+  return gko::solve_entry(1, A, b, x, rel_tol, max_iters, opts, res, stream);
+}
+
+int gko_solve_gmres(gko_matrix A, const double* b, double* x, double rel_tol, int32_t max_iters,
+                    const gko_solve_opts* opts, gko_solve_result* res, void* stream) {
+  return gko::solve_entry(2, A, b, x, rel_tol, max_iters, opts, res, stream);
+}
+
+}  // extern "C"

@@ -81,12 +81,11 @@ SIGNATURES = {
     "gko_multi_axpy_norm": (C.c_int, [_I64, _I32, _P, _P, _I64, _P, C.POINTER(_D), _P]),
     "gko_multi_dot": (C.c_int, [_I64, _I32, _P, _I64, _P, _P, _P]),
     "gko_spmv_dot": (C.c_int, [_P, _P, _P, C.POINTER(_D), _P]),
-}
-OPTIONAL = {
     "gko_solve_cg": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "gko_solve_bicgstab": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "gko_solve_gmres": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
 }
+OPTIONAL = {}
 
 
 def load(path: str = LIB_PATH):

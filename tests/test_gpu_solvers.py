@@ -1,0 +1,172 @@
+"""GPU parity of the Krylov solvers (CG, BiCGSTAB, GMRES) and of
+mixed-precision iterative refinement against the CPU oracle, through the C ABI.
+
+Readings used here (the paper states no solver algorithm):
+* solution parity: both sides solve to 1e-12, then ||x_gpu - x_oracle|| <=
+  1e-8 ||x_oracle|| (kappa * 1e-12 << 1e-8 for these systems);
+* the reported residual is the true ||b - A x|| / ||b||, recomputed here with
+  the oracle's SpMV;
+* iteration counts agree within 10% or 2 (GMRES orthogonalises with CGS2 on
+  the GPU and MGS in the oracle, which changes rounding only).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, host
+from paper_2006_14290_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+SOLVERS = {"cg": O.CG, "bicgstab": O.BICGSTAB, "gmres": O.GMRES}
+
+
+def gpu_solve(G, name, M, b, x0=None, tol=1e-10, maxit=5000, **opt):
+    xd = dev(np.zeros(b.size) if x0 is None else x0)
+    fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[name]
+    res = fn(M, dev(b), xd, tol, maxit, G.opts(**opt) if opt else None)
+    return host(xd), res
+
+
+def true_rel_res(A, x, b):
+    return float(np.linalg.norm(b - O.spmv_csr(A, x)) / np.linalg.norm(b))
+
+
+def iters_close(a, b):
+    return abs(a - b) <= max(2, 0.1 * max(a, b))
+
+
+def spd_problem():
+    A = I.varcoef3d_7pt(12, np.random.default_rng(5))
+    b = np.random.default_rng(6).uniform(-1, 1, A.n_rows)
+    return A, b
+
+
+def nonsym_problem(N=10, P=10.0):
+    A = I.convdiff3d_7pt(N, P)
+    b = O.spmv_csr(A, np.ones(A.n_rows))
+    return A, b
+
+
+def test_cg_laplace2d_64_matches_oracle(gko):
+    G = gko
+    A, x, b = I.laplace2d_problem(64)
+    M = G.from_csr(A)
+    xg, res = gpu_solve(G, "cg", M, b, tol=1e-10)
+    xo, ro = O.cg(A, b, tol=1e-10, maxit=5000)
+    assert res.status == G.OK and ro.status == 0
+    assert res.rel_residual <= 1e-10 and true_rel_res(A, xg, b) <= 1.01e-10
+    assert abs(res.rel_residual - true_rel_res(A, xg, b)) <= 1e-13
+    assert iters_close(res.iterations, ro.iterations)
+    xg12, _ = gpu_solve(G, "cg", M, b, tol=1e-12)
+    xo12, _ = O.cg(A, b, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(xg12 - xo12) <= 1e-8 * np.linalg.norm(xo12)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid"])
+@pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
+def test_solvers_all_formats(gko, fmt, name):
+    G = gko
+    A, b = spd_problem() if name == "cg" else nonsym_problem()
+    M = G.from_csr(A)
+    if fmt == "ell":
+        M = G.gko_matrix_convert_to_ell(M)
+    elif fmt == "coo":
+        M = G.gko_matrix_convert_to_coo(M)
+    elif fmt == "hybrid":
+        M = G.gko_matrix_convert_to_hybrid(M, 3)
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=4000)
+    xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=4000)
+    assert res.status == G.OK and ro.status == 0, (res, ro)
+    assert res.rel_residual <= 1e-12
+    assert true_rel_res(A, xg, b) <= 1.01e-12
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    if name != "gmres":
+        assert iters_close(res.iterations, ro.iterations), (res.iterations, ro.iterations)
+    else:
+        assert iters_close(res.iterations, ro.iterations) or abs(res.outer_iterations - ro.outer_iterations) <= 1
+
+
+@pytest.mark.parametrize("restart", [5, 30])
+def test_gmres_restart_lengths(gko, restart):
+    G = gko
+    A, b = nonsym_problem(12, 3.0)
+    M = G.from_csr(A)
+    xg, res = gpu_solve(G, "gmres", M, b, tol=1e-11, maxit=5000, restart=restart)
+    xo, ro = O.gmres(A, b, tol=1e-11, maxit=5000, restart=restart)
+    assert res.status == G.OK and res.rel_residual <= 1e-11
+    assert iters_close(res.iterations, ro.iterations), (res, ro)
+    assert np.max(np.abs(xg - 1.0)) < 1e-7
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
+def test_mixed_precision_refinement(gko, precision, name):
+    G = gko
+    A, b = spd_problem() if name == "cg" else nonsym_problem()
+    M = G.from_csr(A)
+    prec = G.PRECISION_MIXED_F32 if precision == "f32" else G.PRECISION_MIXED_BF16
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=2000, precision=prec, inner_tol=1e-3 if precision == "bf16" else 1e-4)
+    assert res.status == G.OK, res
+    assert res.outer_iterations >= 2
+    assert res.rel_residual <= 1e-12 and true_rel_res(A, xg, b) <= 1.01e-12
+    xo, _ = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=4000)
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    if precision == "f32":
+        xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, inner_maxit=2000)
+        assert ri.status == 0 and abs(res.outer_iterations - ri.outer_iterations) <= 2, (res, ri)
+
+
+def test_edge_cases(gko):
+    G = gko
+    A, b = spd_problem()
+    M = G.from_csr(A)
+    for name in ("cg", "bicgstab", "gmres"):
+        x, res = gpu_solve(G, name, M, np.zeros(A.n_rows), x0=np.ones(A.n_rows))
+        assert res.status == G.OK and res.iterations == 0 and np.all(x == 0)
+        xs, _ = O.cg(A, b, tol=1e-14, maxit=5000)
+        x, res = gpu_solve(G, name, M, b, x0=xs, tol=1e-10)
+        assert res.status == G.OK and res.iterations == 0
+        x, res = gpu_solve(G, name, M, b, maxit=0)
+        assert res.status == G.NOT_CONVERGED and res.iterations == 0
+        x, res = gpu_solve(G, name, M, b, tol=1e-14, maxit=3)
+        assert res.status == G.NOT_CONVERGED and res.iterations == 3 and res.rel_residual > 1e-6
+        assert abs(res.rel_residual - true_rel_res(A, x, b)) <= 1e-12
+    D = I.Csr(2, 2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, -1.0]))
+    x, res = gpu_solve(G, "cg", G.from_csr(D), np.array([1.0, 1.0]))
+    assert res.status == G.BREAKDOWN
+
+
+@pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
+def test_nonzero_x0_and_determinism(gko, name):
+    G = gko
+    A, b = spd_problem() if name == "cg" else nonsym_problem()
+    M = G.from_csr(A)
+    x0 = np.random.default_rng(1).uniform(-1, 1, A.n_rows)
+    x1, r1 = gpu_solve(G, name, M, b, x0=x0, tol=1e-11)
+    x2, r2 = gpu_solve(G, name, M, b, x0=x0, tol=1e-11)
+    assert r1.status == G.OK and x1.tobytes() == x2.tobytes() and r1.iterations == r2.iterations
+    xo, ro = O.solve(SOLVERS[name], A, b, x0=x0, tol=1e-11, maxit=5000)
+    assert iters_close(r1.iterations, ro.iterations) or name == "gmres"
+    assert true_rel_res(A, x1, b) <= 1.01e-11
+
+
+@pytest.mark.slow
+def test_cg_poisson_256_full_size(gko):
+    """The CG workload of the solver benchmark (7-point 256^3, b = A*1), FP64
+    and mixed FP32, checked with the oracle's SpMV."""
+    import torch
+
+    G = gko
+    A = I.stencil3d_7pt(256)
+    M = G.from_csr(A)
+    ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd)
+    b = host(bd)
+    for prec in (G.PRECISION_F64, G.PRECISION_MIXED_F32):
+        xd = torch.zeros_like(ones)
+        res = G.gko_solve_cg(M, bd, xd, 1e-8, 5000, G.opts(precision=prec))
+        assert res.status == G.OK, res
+        x = host(xd)
+        assert true_rel_res(A, x, b) <= 1.01e-8
+        assert abs(res.rel_residual - true_rel_res(A, x, b)) <= 1e-11
