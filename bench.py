@@ -158,6 +158,207 @@ def traffic_record():
     return d
 
 
+# ----------------------------------------------------------------- solvers --
+
+def solver_suite(G, dev, stream):
+    """Krylov solves to 1e-8 relative residual, FP64 vs mixed precision:
+    CG on the 7-point Poisson problem 256^3 (b = A*1) and BiCGSTAB / GMRES(30)
+    on 7-point upwind convection-diffusion 128^3 (cell Peclet 10, b = A*1);
+    plus 1,000 CG iterations of fixed work (the paper's CG experiment)."""
+    import torch
+    from paper_2006_14290_gb300 import inputs as I
+
+    out = {}
+
+    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30):
+        fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
+        if solver == "bicgstab":
+            maxit = 2000
+        opts = G.opts(precision=prec, restart=restart, inner_maxit=2000, max_outer=12)
+        xd = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn(M, bd, xd, tol, maxit, opts, stream=stream)  # warm-up (also builds the low-precision copy)
+        xd.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        res = fn(M, bd, xd, tol, maxit, opts, stream=stream)
+        wall = time.perf_counter() - t0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sv = 8 if prec == G.PRECISION_F64 else (4 if prec == G.PRECISION_MIXED_F32 else 2)
+        vb = 8 if prec == G.PRECISION_F64 else 4
+        per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver]
+        spmvs = {"cg": 1, "bicgstab": 2, "gmres": 1}[solver]
+        it_bytes = spmvs * (nnz * (sv + 4) + 4 * (n + 1) + 2 * vb * n) + per_vec_passes * vb * n
+        out[tag] = {"status": int(res.status), "iterations": int(res.iterations),
+                    "outer_iterations": int(res.outer_iterations), "rel_residual": float(res.rel_residual),
+                    "time_ms": round(ms, 3), "wall_ms": round(wall * 1e3, 3), "solves_per_s": round(1e3 / ms, 3),
+                    "GB_s_per_iteration": round(it_bytes * max(res.iterations, 1) / (ms * 1e-3) / 1e9, 1)}
+        return ms
+
+    A = I.stencil3d_7pt(256)
+    M = G.from_csr(A)
+    n, nnz = A.n_rows, A.nnz
+    del A
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
+    t64 = run("cg_poisson256_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
+    t32 = run("cg_poisson256_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32)
+    run("cg_poisson256_mixed_bf16", "cg", M, bd, n, nnz, G.PRECISION_MIXED_BF16)
+    out["cg_poisson256_mixed_f32_speedup"] = round(t64 / t32, 3)
+    # fixed work: 1,000 iterations (tolerance 0 never stops early)
+    xd = torch.zeros(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = G.gko_solve_cg(M, bd, xd, 0.0, 1000, G.opts(check_every=1000), stream=stream)
+    dt = time.perf_counter() - t0
+    out["cg_poisson256_1000_iterations"] = {"iterations": int(res.iterations), "time_ms": round(dt * 1e3, 3),
+                                            "iterations_per_s": round(res.iterations / dt, 1)}
+    del M, ones, bd, xd
+    A = I.convdiff3d_7pt(128, 10.0)
+    M = G.from_csr(A)
+    n, nnz = A.n_rows, A.nnz
+    del A
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
+    for solver in ("bicgstab", "gmres"):
+        tag = "bicgstab" if solver == "bicgstab" else "gmres30"
+        t64 = run(f"{tag}_convdiff128_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
+        t32 = run(f"{tag}_convdiff128_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
+        out[f"{tag}_convdiff128_mixed_f32_speedup"] = round(t64 / t32, 3)
+    del M, ones, bd
+    # unpreconditioned BiCGSTAB does not converge at cell Peclet 10 on 128^3
+    # (the oracle diverges too); Peclet 1 is the converging companion case
+    A = I.convdiff3d_7pt(128, 1.0)
+    M = G.from_csr(A)
+    del A
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
+    t64 = run("bicgstab_convdiff128_P1_f64", "bicgstab", M, bd, n, nnz, G.PRECISION_F64)
+    t32 = run("bicgstab_convdiff128_P1_mixed_f32", "bicgstab", M, bd, n, nnz, G.PRECISION_MIXED_F32)
+    out["bicgstab_convdiff128_P1_mixed_f32_speedup"] = round(t64 / t32, 3)
+    del M, ones, bd
+    out["batched_cg"] = batched_suite(G, dev, stream)
+    return out
+
+
+def batched_suite(G, dev, stream):
+    """4096 variable-coefficient 2D 5-point systems (sides log-uniform in
+    [8, 64]) solved by batched CG to 1e-10 in one persistent graph-captured
+    launch; FP64 and FP32 storage; warp/block threshold from the autotuner."""
+    import torch
+    from paper_2006_14290_gb300 import inputs as I
+
+    sides = I.batch_sides(4096)
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, int(sd))
+        systems.append(A)
+        bs.append(b)
+    b = torch.from_numpy(np.concatenate(bs)).to(dev)
+    res = {"systems": 4096, "rows": int(sum(S.n_rows for S in systems)), "nnz": int(sum(S.nnz for S in systems))}
+    for storage, tag in ((G.F64, "f64"), (G.F32, "f32_storage")):
+        B = G.Batch(systems, storage=storage)
+        x0 = torch.zeros(B.total_rows, dtype=torch.float64, device=dev)
+        chosen, tune_ms = B.tune(b, x0, 1e-10, 20000, stream=stream)
+        x = torch.zeros_like(x0)
+        B.cg(b, x, 1e-10, 20000, stream=stream)  # capture the graph
+        times = []
+        for _ in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code, it, rr, st = B.cg(b, x, 1e-10, 20000, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        res[tag] = {"status": int(code), "time_ms": round(ms, 3), "systems_per_s": round(4096 / (ms * 1e-3), 1),
+                    "warp_rows_threshold": int(chosen), "tuned_ms": round(float(tune_ms), 3),
+                    "iterations_total": int(it.sum()), "iterations_max": int(it.max()),
+                    "max_rel_residual": float(rr.max())}
+        del B
+    return res
+
+
+# ----------------------------------------------------------------- serving --
+
+def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_bytes=150 << 30):
+    """Poisson arrivals of sparse solves against resident matrices.
+
+    Pool: 8 variable-coefficient 7-point Poisson matrices (CG) and 8 upwind
+    convection-diffusion matrices with cell Peclet ~ U[1, 20] (BiCGSTAB), cube
+    sides rint(n^(1/3)) for n log-uniform in [1e3, 4e6], all from
+    default_rng(0), uploaded before the window.  Requests: 70% CG / 30%
+    BiCGSTAB on a uniformly chosen pool matrix, b = A*1, tolerance 1e-8
+    (iteration caps CG 5000, BiCGSTAB 500), admitted by a 150 GB budget over
+    `slots` concurrent solves.  Each arrival window runs FP64 and mixed FP32.
+    """
+    import torch
+    from paper_2006_14290_gb300 import inputs as I
+
+    rng = np.random.default_rng(0)
+    pool = []
+    for kind in ("cg", "bicgstab"):
+        for _ in range(8):
+            n = float(np.exp(rng.uniform(np.log(1e3), np.log(4e6))))
+            side = max(4, int(np.rint(n ** (1.0 / 3.0))))
+            if kind == "cg":
+                A = I.varcoef3d_7pt(side, rng)
+            else:
+                A = I.convdiff3d_7pt(side, float(rng.uniform(1.0, 20.0)))
+            M = G.from_csr(A)
+            ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+            bd = torch.zeros_like(ones)
+            G.gko_spmv(1.0, M, ones, 0.0, bd)
+            pool.append((kind, M, bd.cpu().numpy(), A.n_rows))
+            del A
+    out = {"pool_rows": [p[3] for p in pool], "slots": slots, "budget_GB": budget_bytes / 2**30}
+    for rate, window in windows:
+        arr = np.random.default_rng(1)
+        times, picks = [], []
+        t = 0.0
+        while True:
+            t += arr.exponential(1.0 / rate)
+            if t > window:
+                break
+            times.append(t)
+            k = 0 if arr.random() < 0.7 else 1
+            picks.append(int(arr.integers(0, 8)) + 8 * k)
+        for prec_name, prec in (("f64", G.PRECISION_F64), ("mixed_f32", G.PRECISION_MIXED_F32)):
+            S = G.Server(slots=slots, budget_bytes=budget_bytes)
+            ids = [S.add_matrix(p[1]) for p in pool]
+            opts = G.opts(precision=prec, inner_maxit=1000)
+            t0 = time.perf_counter()
+            rids = []
+            for at, m in zip(times, picks):
+                now = time.perf_counter() - t0
+                if at > now:
+                    time.sleep(at - now)
+                kind = pool[m][0]
+                rids.append(S.submit(ids[m], 0 if kind == "cg" else 1, pool[m][2], 1e-8,
+                                     5000 if kind == "cg" else 500, opts))
+            results = [S.result(r) for r in rids]
+            wall = time.perf_counter() - t0
+            st = S.stats()
+            S.close()
+            ok = sum(1 for r in results if r[0] == G.OK)
+            cg_ok = sum(1 for r, m in zip(results, picks) if r[0] == G.OK and pool[m][0] == "cg")
+            out[f"rate{int(rate)}_{prec_name}"] = {
+                "requests": len(rids), "window_s": window, "converged": ok,
+                "cg_converged": cg_ok, "cg_requests": sum(1 for m in picks if pool[m][0] == "cg"),
+                "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                "solves_per_s": round(st["solves_per_s"], 2), "drain_s": round(wall, 3),
+                "peak_concurrent": st["peak_active"]}
+    return out
+
+
 # --------------------------------------------------------------- reference --
 
 def run_reference(args):
@@ -373,6 +574,10 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": int(sum(c["launches"] for c in cases) * args.steps),
         }
+        if not args.no_solvers:
+            result["solvers"] = solver_suite(G, dev, stream)
+        if not args.no_serving:
+            result["serving"] = serving_suite(G)
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(mats)
         print(json.dumps(result), flush=True)
@@ -388,6 +593,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -267,6 +267,90 @@ GKO_API int gko_solve_bicgstab(gko_matrix A, const double *b, double *x, double 
 GKO_API int gko_solve_gmres(gko_matrix A, const double *b, double *x, double rel_tol, int32_t max_iters,
                     const gko_solve_opts *opts, gko_solve_result *res, void *stream);
 
+/* ------------------------------------------------------------ batched CG -- */
+
+/* Many independent small SPD systems solved by CG in one persistent launch
+ * (the CG of the paper's Section 1 solver list, per system).  Systems are
+ * concatenated: system i has rows [row_off[i], row_off[i+1]) and nonzeros
+ * [nnz_off[i], nnz_off[i+1]); its local row pointers (n_i + 1 entries, from
+ * 0 to nnz_i) start at row_ptr[row_off[i] + i]; col holds local column
+ * indices (0 <= col < n_i).  All arrays are HOST arrays, copied and checked
+ * at creation (bad input -> GKO_INVALID_ARG); values are F64, or F32 for
+ * FP32 storage (the F32 batch solves the FP32-rounded systems; arithmetic and
+ * vectors stay FP64).  Systems may have up to 8192 rows. */
+typedef struct gko_batch_s *gko_batch;
+GKO_API int gko_batch_create(int32_t count, const int64_t *row_off, const int64_t *nnz_off,
+                             const int32_t *row_ptr, const int32_t *col, const void *values,
+                             gko_dtype storage, void *stream, gko_batch *out);
+
+/* Solve every system: b, x are DEVICE FP64 vectors laid out like the rows
+ * (x: x0 in, solution out).  Per system: stop when ||r_k|| <= rel_tol ||b_i||
+ * and the true residual confirms (else it replaces r), or after max_iters.
+ * Systems with at most the batch's warp-mode threshold rows are solved by one
+ * warp each, larger ones by a 256-thread block; the launch is captured once
+ * into a CUDA graph per (b, x, rel_tol, max_iters, stream) and replayed.
+ * iterations / rel_residuals (true residuals) / statuses: optional HOST
+ * arrays of `count` entries.  Returns GKO_OK when every system converged,
+ * else GKO_BREAKDOWN or GKO_NOT_CONVERGED.  Synchronises `stream`. */
+GKO_API int gko_batch_cg(gko_batch B, const double *b, double *x, double rel_tol, int32_t max_iters,
+                         int32_t *iterations, double *rel_residuals, int32_t *statuses, void *stream);
+
+/* Autotuner: times the whole batch for warp-mode thresholds 0, 64, 100, 144,
+ * 196 and 256 rows (solving from a scratch copy of x0; x0 is not changed)
+ * and keeps the fastest.  *chosen and *best_ms (either may be NULL) report
+ * the choice.  Synchronises `stream`. */
+GKO_API int gko_batch_tune(gko_batch B, const double *b, const double *x0, double rel_tol, int32_t max_iters,
+                           int32_t *chosen, float *best_ms, void *stream);
+
+/* Set the warp-mode threshold directly (rows; 0 = block mode only; capped at
+ * 256). */
+GKO_API int gko_batch_set_threshold(gko_batch B, int32_t warp_rows, void *stream);
+
+GKO_API int gko_batch_info(gko_batch B, int32_t *count, int64_t *total_rows, int64_t *total_nnz,
+                           int32_t *warp_rows, int32_t *n_items);
+GKO_API int gko_batch_destroy(gko_batch B);
+
+/* --------------------------------------------------------------- serving -- */
+
+/* Request loop with continuous batching over resident matrices.  `slots`
+ * worker threads, each with its own CUDA stream on the current device, take
+ * the oldest queued request as soon as a slot is free and its device-memory
+ * estimate (b, x and solver workspace) fits in budget_bytes together with
+ * the resident matrices and the requests already running (budget_bytes = 0:
+ * no limit).  Solves of different requests overlap on the GPU; each result
+ * is the one the same call gives alone (deterministic kernels).  Mixed-
+ * precision requests create the matrix's low-precision copy on first use. */
+typedef struct gko_server_s *gko_server;
+GKO_API int gko_server_create(int32_t slots, int64_t budget_bytes, gko_server *out);
+
+/* Register a resident square F64 matrix (the caller keeps the handle alive
+ * until the server is destroyed).  GKO_BUDGET_EXCEEDED if the resident set
+ * would exceed the budget. */
+GKO_API int gko_server_add_matrix(gko_server S, gko_matrix A, int32_t *matrix_id);
+
+/* Queue a solve of A_matrix_id x = b (b: HOST array of n doubles, copied at
+ * submission; x0 = 0) with solver 0 CG, 1 BiCGSTAB, 2 GMRES.  Returns at
+ * once with *request_id.  GKO_BUDGET_EXCEEDED if the request alone cannot
+ * fit the budget; GKO_INVALID_ARG for an unknown matrix or bad arguments. */
+GKO_API int gko_server_submit(gko_server S, int32_t matrix_id, int32_t solver, const double *b, double rel_tol,
+                              int32_t max_iters, const gko_solve_opts *opts, int64_t *request_id);
+
+/* Result of a request: wait != 0 blocks until it is done.  *done = 0 while
+ * it runs (non-blocking call).  When done: *res, the solution in x (HOST, n
+ * doubles; may be NULL) and the submission-to-result latency in ms (may be
+ * NULL); the request is then forgotten.  Returns the solve's status. */
+GKO_API int gko_server_result(gko_server S, int64_t request_id, int wait, int32_t *done,
+                              gko_solve_result *res, double *x, double *latency_ms);
+
+/* Completed requests, latency percentiles (ms, submission to result) and
+ * completions per second between the first submission and the last
+ * completion; peak number of solves running at once. */
+GKO_API int gko_server_stats(gko_server S, int64_t *completed, double *p50_ms, double *p99_ms,
+                             double *solves_per_s, int32_t *peak_active);
+
+/* Stop the workers (requests still queued are dropped) and free the server. */
+GKO_API int gko_server_destroy(gko_server S);
+
 #ifdef __cplusplus
 }
 #endif

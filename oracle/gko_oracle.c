@@ -659,7 +659,8 @@ int or_solve(int solver, int64_t n, const int32_t *rp, const int32_t *col, const
 /* Mixed-precision iterative refinement: x = x0; repeat { r = b - A64 x in
  * FP64; stop if ||r|| <= tol ||b||; solve A32 d = r with FP32-stored values
  * and vectors (FP32 SpMV accumulation, FP64 dots and scalars) to
- * ||r_inner|| <= inner_tol ||r||; x += d in FP64 }. */
+ * ||r_inner|| <= max(inner_tol, min(0.5, 0.5 tol ||b|| / ||r||)) ||r||;
+ * x += d in FP64 }. */
 int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                 const float *val32, const double *b, double *x, double tol, int32_t max_outer,
                 double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
@@ -684,7 +685,12 @@ int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, co
     }
     if (res.outer_iterations >= max_outer) break;
     for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
-    or_result in = run_solver(&inner, solver, r, d, inner_tol, inner_maxit, restart);
+    /* the inner solve is asked only for the reduction still needed, with a
+     * factor-2 margin: max(inner_tol, min(0.5, 0.5 * tol * ||b|| / ||r||)) */
+    double need = 0.5 * tol * nb / nr;
+    if (need > 0.5) need = 0.5;
+    const double itol = need > inner_tol ? need : inner_tol;
+    or_result in = run_solver(&inner, solver, r, d, itol, inner_maxit, restart);
     res.iterations += in.iterations;
     res.outer_iterations += 1;
     for (int64_t i = 0; i < n; ++i) x[i] += d[i];

@@ -1,0 +1,495 @@
+// Batched CG: many independent small SPD systems solved in one persistent
+// launch (the CG of the paper's Section 1 solver list, applied per system).
+//
+// Layout: the systems' CSR arrays are concatenated (local row pointers, local
+// column indices), with per-system row and nonzero offsets.  At creation the
+// systems are ordered largest first and grouped into work items: "block"
+// items (one system per 256-thread block, vectors r, p, q in shared memory,
+// one thread per row, block reductions) for systems above a size threshold,
+// and "warp" items (eight systems per block, one per warp, warp-shuffle
+// reductions and no block barriers) below it.  Blocks of a persistent grid
+// take items from an atomic queue.  The threshold is the tunable: a built-in
+// autotuner times the batch with each candidate and keeps the fastest.
+// The launch (queue reset + kernel) is captured once into a CUDA graph and
+// replayed.  All loops are bounded by the iteration cap; nothing spins.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace gko {
+
+constexpr int kBatchThreads = 256;
+constexpr int kWarpItemSystems = kBatchThreads / kWarp;  // 8
+constexpr int kWarpMaxRows = 256;                         // warp mode: rows per system
+
+enum : int { kBRun = 0, kBOk = 1, kBBreak = 2, kBNotConv = 3 };
+
+struct BatchArgs {
+  int n_items;
+  const int2* items;        // (kind | first << 1, count): kind 0 block, 1 warp
+  const int32_t* order;     // systems, largest first
+  const int64_t* row_off;   // [count+1]
+  const int64_t* nnz_off;   // [count+1]
+  const int32_t* rp;        // concatenated local row pointers (n_i + 1 each)
+  const int32_t* col;
+  const void* val;
+  const double* b;
+  double* x;
+  double rel_tol;
+  int maxit;
+  int32_t* iters;
+  double* relres;
+  int32_t* status;
+  unsigned* queue;
+};
+
+template <typename VT>
+__device__ __forceinline__ double ldv(const VT* v, int64_t k) {
+  return (double)v[k];
+}
+
+// sum over the block, result in every thread
+__device__ __forceinline__ double block_allsum(double v, double* red) {
+  v = subwarp_sum<32>(v, 0xffffffffu);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kBatchThreads / kWarp; ++i) s += red[i];
+  return s;
+}
+
+// One CG solve by a group of G threads (G = 256: a block; G = 32: a warp).
+// r, p, q: the group's shared-memory vectors.  Follows the single-system
+// solver: recurrence residual test, then the true residual; a failed true
+// check replaces r and continues.
+template <int G, typename VT>
+__device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, double* q, double* red, int lane) {
+  const int64_t r0 = a.row_off[sys];
+  const int n = (int)(a.row_off[sys + 1] - r0);
+  const int32_t* rp = a.rp + r0 + sys;
+  const int64_t k0 = a.nnz_off[sys];
+  const int32_t* col = a.col + k0;
+  const VT* val = static_cast<const VT*>(a.val) + k0;
+  const double* b = a.b + r0;
+  double* x = a.x + r0;
+  auto gsum = [&](double v) -> double {
+    if (G == kWarp) return subwarp_sum<32>(v, 0xffffffffu);
+    return block_allsum(v, red);
+  };
+  auto gsync = [&]() {
+    if (G == kWarp) __syncwarp();
+    else __syncthreads();
+  };
+  auto row_dot = [&](int i, const double* v) -> double {
+    double s = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fma_rn(ldv(val, k), v[col[k]], s);
+    return s;
+  };
+  // r = b - A x0, p = r (x0 staged through q)
+  double bb = 0.0;
+  for (int i = lane; i < n; i += G) {
+    q[i] = x[i];
+    bb += b[i] * b[i];
+  }
+  gsync();
+  double rr = 0.0;
+  for (int i = lane; i < n; i += G) {
+    const double ri = b[i] - row_dot(i, q);
+    r[i] = ri;
+    p[i] = ri;
+    rr += ri * ri;
+  }
+  const double nb = sqrt(gsum(bb));
+  double rho = gsum(rr);
+  const double tol = a.rel_tol * nb;
+  int status = kBRun, it = 0;
+  double res = nb > 0.0 ? sqrt(rho) / nb : 0.0;
+  if (nb == 0.0) {
+    for (int i = lane; i < n; i += G) x[i] = 0.0;
+    status = kBOk;
+  } else if (sqrt(rho) <= tol) {
+    status = kBOk;
+  }
+  gsync();
+  while (status == kBRun && it < a.maxit) {
+    double pq = 0.0;
+    for (int i = lane; i < n; i += G) {
+      const double qi = row_dot(i, p);
+      q[i] = qi;
+      pq += p[i] * qi;
+    }
+    pq = gsum(pq);
+    if (!(pq > 0.0)) {
+      status = kBBreak;
+      break;
+    }
+    const double alpha = rho / pq;
+    double rn = 0.0;
+    for (int i = lane; i < n; i += G) {
+      x[i] = __fma_rn(alpha, p[i], x[i]);
+      const double ri = __fma_rn(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rn += ri * ri;
+    }
+    double rho_new = gsum(rn);
+    ++it;
+    if (sqrt(rho_new) <= tol) {
+      // true residual b - A x (x staged through q)
+      gsync();
+      for (int i = lane; i < n; i += G) q[i] = x[i];
+      gsync();
+      double tt = 0.0;
+      for (int i = lane; i < n; i += G) {
+        const double ti = b[i] - row_dot(i, q);
+        r[i] = ti;
+        tt += ti * ti;
+      }
+      tt = gsum(tt);
+      res = sqrt(tt) / nb;
+      if (sqrt(tt) <= tol) {
+        status = kBOk;
+        break;
+      }
+      rho_new = tt;  // residual replacement
+    }
+    const double beta = rho_new / rho;
+    rho = rho_new;
+    for (int i = lane; i < n; i += G) p[i] = __fma_rn(beta, p[i], r[i]);
+    gsync();
+  }
+  if (status == kBRun) status = kBNotConv;
+  if (status != kBOk) {  // report the true residual of the last iterate
+    gsync();
+    for (int i = lane; i < n; i += G) q[i] = x[i];
+    gsync();
+    double tt = 0.0;
+    for (int i = lane; i < n; i += G) {
+      const double ti = b[i] - row_dot(i, q);
+      tt += ti * ti;
+    }
+    tt = gsum(tt);
+    res = nb > 0.0 ? sqrt(tt) / nb : 0.0;
+  }
+  if (lane == 0) {
+    a.iters[sys] = it;
+    a.relres[sys] = res;
+    a.status[sys] = status;
+  }
+  gsync();
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kBatchThreads) batch_cg_kernel(BatchArgs a, int block_rows) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double red[kBatchThreads / kWarp];
+  __shared__ int item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= a.n_items) return;
+    const int2 it = a.items[item];
+    const int kind = it.x & 1, first = it.x >> 1;
+    if (kind == 0) {
+      double* r = sm;
+      double* p = sm + block_rows;
+      double* q = sm + 2 * block_rows;
+      cg_group<kBatchThreads, VT>(a, a.order[first], r, p, q, red, threadIdx.x);
+    } else {
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      double* base = sm + (size_t)w * 3 * kWarpMaxRows;
+      if (w < it.y) cg_group<kWarp, VT>(a, a.order[first + w], base, base + kWarpMaxRows, base + 2 * kWarpMaxRows,
+                                        red, lane);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace gko
+
+using namespace gko;
+
+struct gko_batch_s {
+  int32_t count = 0;
+  gko_dtype dtype = GKO_F64;
+  int64_t total_rows = 0, total_nnz = 0;
+  int32_t max_rows = 0;
+  Buf row_off, nnz_off, rp, col, val, order, items, iters, relres, status, queue;
+  std::vector<int64_t> h_rows;   // rows per system
+  std::vector<int32_t> h_order;  // largest first
+  int32_t threshold = 0;         // warp mode for systems with <= threshold rows
+  int n_items = 0;
+  int block_rows = 0;
+  // cached graph of (queue reset + kernel)
+  cudaGraphExec_t exec = nullptr;
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  double g_tol = -1;
+  int g_maxit = -1;
+  cudaStream_t g_stream = nullptr;
+  ~gko_batch_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+namespace gko {
+
+static int build_items(gko_batch B, int32_t threshold, cudaStream_t s) {
+  threshold = std::min(threshold, kWarpMaxRows);
+  std::vector<int2> items;
+  int block_rows = 0;
+  size_t i = 0;
+  const size_t n = B->h_order.size();
+  while (i < n && B->h_rows[B->h_order[i]] > threshold) {
+    block_rows = std::max<int>(block_rows, (int)B->h_rows[B->h_order[i]]);
+    items.push_back(make_int2((int)(i << 1) | 0, 1));
+    ++i;
+  }
+  while (i < n) {
+    const int cnt = (int)std::min<size_t>(kWarpItemSystems, n - i);
+    items.push_back(make_int2((int)(i << 1) | 1, cnt));
+    i += cnt;
+  }
+  GKO_TRY(alloc(sizeof(int2) * std::max<size_t>(1, items.size()), &B->items));
+  if (!items.empty())
+    GKO_TRY_CUDA(cudaMemcpyAsync(B->items->ptr, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  B->threshold = threshold;
+  B->n_items = (int)items.size();
+  B->block_rows = block_rows;
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  return GKO_OK;
+}
+
+static size_t batch_smem(const gko_batch_s* B) {
+  const size_t blk = (size_t)3 * B->block_rows * sizeof(double);
+  const size_t wrp = B->threshold > 0 ? (size_t)kWarpItemSystems * 3 * kWarpMaxRows * sizeof(double) : 0;
+  return std::max<size_t>(std::max(blk, wrp), 16);
+}
+
+static int batch_launch(gko_batch B, const double* b, double* x, double tol, int maxit, cudaStream_t s) {
+  BatchArgs a;
+  a.n_items = B->n_items;
+  a.items = ptr<int2>(B->items);
+  a.order = ptr<int32_t>(B->order);
+  a.row_off = ptr<int64_t>(B->row_off);
+  a.nnz_off = ptr<int64_t>(B->nnz_off);
+  a.rp = ptr<int32_t>(B->rp);
+  a.col = ptr<int32_t>(B->col);
+  a.val = B->val->ptr;
+  a.b = b;
+  a.x = x;
+  a.rel_tol = tol;
+  a.maxit = maxit;
+  a.iters = ptr<int32_t>(B->iters);
+  a.relres = ptr<double>(B->relres);
+  a.status = ptr<int32_t>(B->status);
+  a.queue = ptr<unsigned>(B->queue);
+  const size_t smem = batch_smem(B);
+  int per_sm = 1;
+  if (B->dtype == GKO_F64) {
+    GKO_TRY_CUDA(cudaFuncSetAttribute(batch_cg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cg_kernel<double>, kBatchThreads, smem));
+  } else {
+    GKO_TRY_CUDA(cudaFuncSetAttribute(batch_cg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cg_kernel<float>, kBatchThreads, smem));
+  }
+  const int grid = std::max(1, std::min(B->n_items, std::max(1, per_sm) * sm_count()));
+  GKO_TRY_CUDA(cudaMemsetAsync(B->queue->ptr, 0, sizeof(unsigned), s));
+  if (B->dtype == GKO_F64)
+    batch_cg_kernel<double><<<grid, kBatchThreads, smem, s>>>(a, B->block_rows);
+  else
+    batch_cg_kernel<float><<<grid, kBatchThreads, smem, s>>>(a, B->block_rows);
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
+}
+
+// Capture (queue reset + kernel) once per (b, x, tol, maxit, stream) and
+// replay it afterwards.
+static int batch_run(gko_batch B, const double* b, double* x, double tol, int maxit, cudaStream_t s) {
+  const bool same = B->exec && B->g_b == b && B->g_x == x && B->g_tol == tol && B->g_maxit == maxit &&
+                    B->g_stream == s;
+  if (!same) {
+    if (B->exec) {
+      cudaGraphExecDestroy(B->exec);
+      B->exec = nullptr;
+    }
+    cudaStream_t cs;
+    GKO_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    GKO_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int st = batch_launch(B, b, x, tol, maxit, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != GKO_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      B->exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    B->g_b = b;
+    B->g_x = x;
+    B->g_tol = tol;
+    B->g_maxit = maxit;
+    B->g_stream = s;
+  }
+  GKO_TRY_CUDA(cudaGraphLaunch(B->exec, s));
+  return GKO_OK;
+}
+
+}  // namespace gko
+
+extern "C" {
+
+int gko_batch_create(int32_t count, const int64_t* row_off, const int64_t* nnz_off, const int32_t* row_ptr,
+                     const int32_t* col, const void* values, gko_dtype storage, void* stream, gko_batch* out) {
+  if (!out) return fail(GKO_INVALID_ARG, "null out");
+  *out = nullptr;
+  if (count <= 0 || !row_off || !nnz_off || !row_ptr || !col || !values)
+    return fail(GKO_INVALID_ARG, "bad batch arguments");
+  if (storage != GKO_F64 && storage != GKO_F32) return fail(GKO_INVALID_ARG, "batch storage must be F64 or F32");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<gko_batch_s> B(new gko_batch_s());
+  B->count = count;
+  B->dtype = storage;
+  B->total_rows = row_off[count];
+  B->total_nnz = nnz_off[count];
+  if (row_off[0] != 0 || nnz_off[0] != 0 || B->total_nnz >= INT32_MAX)
+    return fail(GKO_INVALID_ARG, "offsets must start at 0 and nnz fit int32");
+  B->h_rows.resize(count);
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t n = row_off[i + 1] - row_off[i], z = nnz_off[i + 1] - nnz_off[i];
+    if (n <= 0 || z < 0) return fail(GKO_INVALID_ARG, "every system needs rows");
+    const int32_t* rp = row_ptr + row_off[i] + i;
+    if (rp[0] != 0 || rp[n] != z) return fail(GKO_INVALID_ARG, "system row pointers must run 0..nnz_i");
+    for (int64_t r = 0; r < n; ++r)
+      if (rp[r] > rp[r + 1]) return fail(GKO_INVALID_ARG, "row pointers must not decrease");
+    for (int64_t k = nnz_off[i]; k < nnz_off[i + 1]; ++k)
+      if (col[k] < 0 || col[k] >= n) return fail(GKO_INVALID_ARG, "column index out of range");
+    B->h_rows[i] = n;
+    B->max_rows = std::max<int32_t>(B->max_rows, (int32_t)n);
+  }
+  if (B->max_rows > 8192) return fail(GKO_NOT_SUPPORTED, "batched systems are limited to 8192 rows");
+  B->h_order.resize(count);
+  std::iota(B->h_order.begin(), B->h_order.end(), 0);
+  std::stable_sort(B->h_order.begin(), B->h_order.end(),
+                   [&](int32_t a, int32_t b) { return B->h_rows[a] > B->h_rows[b]; });
+  const int64_t nrp = B->total_rows + count;
+  const size_t vs = dtype_size(storage);
+  GKO_TRY(alloc(sizeof(int64_t) * (count + 1), &B->row_off));
+  GKO_TRY(alloc(sizeof(int64_t) * (count + 1), &B->nnz_off));
+  GKO_TRY(alloc(sizeof(int32_t) * nrp, &B->rp));
+  GKO_TRY(alloc(sizeof(int32_t) * B->total_nnz, &B->col));
+  GKO_TRY(alloc(vs * B->total_nnz, &B->val));
+  GKO_TRY(alloc(sizeof(int32_t) * count, &B->order));
+  GKO_TRY(alloc(sizeof(int32_t) * count, &B->iters));
+  GKO_TRY(alloc(sizeof(double) * count, &B->relres));
+  GKO_TRY(alloc(sizeof(int32_t) * count, &B->status));
+  GKO_TRY(alloc(sizeof(unsigned), &B->queue));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->row_off->ptr, row_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->nnz_off->ptr, nnz_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->rp->ptr, row_ptr, sizeof(int32_t) * nrp, cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->col->ptr, col, sizeof(int32_t) * B->total_nnz, cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->val->ptr, values, vs * B->total_nnz, cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->order->ptr, B->h_order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+  GKO_TRY(build_items(B.get(), 144, s));
+  *out = B.release();
+  return GKO_OK;
+}
+
+int gko_batch_set_threshold(gko_batch B, int32_t warp_rows, void* stream) {
+  if (!B || warp_rows < 0) return fail(GKO_INVALID_ARG, "bad batch threshold");
+  return build_items(B, warp_rows, (cudaStream_t)stream);
+}
+
+int gko_batch_info(gko_batch B, int32_t* count, int64_t* total_rows, int64_t* total_nnz, int32_t* warp_rows,
+                   int32_t* n_items) {
+  if (!B) return fail(GKO_INVALID_ARG, "null batch");
+  if (count) *count = B->count;
+  if (total_rows) *total_rows = B->total_rows;
+  if (total_nnz) *total_nnz = B->total_nnz;
+  if (warp_rows) *warp_rows = B->threshold;
+  if (n_items) *n_items = B->n_items;
+  return GKO_OK;
+}
+
+int gko_batch_cg(gko_batch B, const double* b, double* x, double rel_tol, int32_t max_iters, int32_t* iterations,
+                 double* rel_residuals, int32_t* statuses, void* stream) {
+  if (!B || !b || !x || !(rel_tol >= 0.0) || max_iters < 0) return fail(GKO_INVALID_ARG, "bad batch solve arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  GKO_TRY(batch_run(B, b, x, rel_tol, max_iters, s));
+  if (iterations)
+    GKO_TRY_CUDA(cudaMemcpyAsync(iterations, B->iters->ptr, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost, s));
+  if (rel_residuals)
+    GKO_TRY_CUDA(
+        cudaMemcpyAsync(rel_residuals, B->relres->ptr, sizeof(double) * B->count, cudaMemcpyDeviceToHost, s));
+  std::vector<int32_t> st(B->count);
+  GKO_TRY_CUDA(cudaMemcpyAsync(st.data(), B->status->ptr, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  int worst = GKO_OK;
+  for (int32_t i = 0; i < B->count; ++i) {
+    const int code = st[i] == kBOk ? GKO_OK : st[i] == kBBreak ? GKO_BREAKDOWN : GKO_NOT_CONVERGED;
+    if (statuses) statuses[i] = code;
+    if (code == GKO_BREAKDOWN || (code == GKO_NOT_CONVERGED && worst == GKO_OK)) worst = code;
+  }
+  return worst;
+}
+
+// Autotuner: time the whole batch for each candidate warp-mode threshold
+// (on a scratch copy of x0) and keep the fastest.
+int gko_batch_tune(gko_batch B, const double* b, const double* x0, double rel_tol, int32_t max_iters,
+                   int32_t* chosen, float* best_ms, void* stream) {
+  if (!B || !b || !x0) return fail(GKO_INVALID_ARG, "bad tune arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch xs;
+  GKO_TRY(xs.get(sizeof(double) * B->total_rows, s));
+  const int32_t cands[] = {0, 64, 100, 144, 196, 256};
+  cudaEvent_t e0, e1;
+  GKO_TRY_CUDA(cudaEventCreate(&e0));
+  GKO_TRY_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int32_t best_t = B->threshold;
+  for (int32_t t : cands) {
+    GKO_TRY(build_items(B, t, s));
+    for (int rep = 0; rep < 2; ++rep) {
+      GKO_TRY_CUDA(cudaMemcpyAsync(xs.data(), x0, sizeof(double) * B->total_rows, cudaMemcpyDeviceToDevice, s));
+      GKO_TRY_CUDA(cudaEventRecord(e0, s));
+      GKO_TRY(batch_run(B, b, xs.as<double>(), rel_tol, max_iters, s));
+      GKO_TRY_CUDA(cudaEventRecord(e1, s));
+      GKO_TRY_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GKO_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GKO_TRY(build_items(B, best_t, s));
+  if (chosen) *chosen = best_t;
+  if (best_ms) *best_ms = best;
+  return GKO_OK;
+}
+
+int gko_batch_destroy(gko_batch B) {
+  delete B;
+  return GKO_OK;
+}
+
+}  // extern "C"

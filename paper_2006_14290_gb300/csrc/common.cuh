@@ -187,6 +187,21 @@ __device__ __forceinline__ T subwarp_sum(T v, unsigned mask) {
   return v;
 }
 
+// Exact float -> double widening with integer operations (GB300 runs the
+// F2F conversion instruction on its narrow FP64/conversion path).  Normal
+// numbers, zeros, infinities and NaNs convert exactly; FP32 subnormals
+// (|v| < 2^-126) become signed zero.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t mant = (uint64_t)(u & 0x7fffffu) << 29;
+  const uint64_t expo = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
+  const uint64_t bits = e == 0u ? sign : (sign | (expo << 52) | mant);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 inline unsigned ceil_div_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace gko

@@ -45,7 +45,34 @@ struct Ctl {
 };
 
 __device__ __forceinline__ double wd(double v) { return v; }
-__device__ __forceinline__ double wd(float v) { return (double)v; }
+__device__ __forceinline__ double wd(float v) { return widen(v); }
+
+// y + a*x stored as T for an FP64 scalar a.  FP64 vectors: one FP64 FMA.
+// FP32 vectors: a is applied as the float pair hi + lo (hi = fl32(a),
+// lo = fl32(a - hi)) in two FP32 FMAs, so the scalar keeps FP64 accuracy
+// while the arithmetic stays on GB300's FP32 pipe (its FP64 rate is about
+// 1/64 of FP32).
+template <typename T>
+struct Lin;
+template <>
+struct Lin<double> {
+  double a;
+  __device__ explicit Lin(double a_) : a(a_) {}
+  __device__ double operator()(double x, double y) const { return __fma_rn(a, x, y); }
+  __device__ double scale(double x) const { return a * x; }
+};
+template <>
+struct Lin<float> {
+  float hi, lo;
+  __device__ explicit Lin(double a) {
+    hi = __double2float_rn(a);
+    lo = __double2float_rn(a - (double)hi);
+  }
+  __device__ float operator()(float x, float y) const { return __fmaf_rn(lo, x, __fmaf_rn(hi, x, y)); }
+  __device__ float scale(float x) const { return __fmaf_rn(lo, x, hi * x); }
+};
+
+__device__ __forceinline__ double dsq(double a) { return a * a; }
 
 template <int NV, typename Op>
 __device__ __forceinline__ void reduce_op(double (&v)[NV], RedWs ws, Op op) {
@@ -203,11 +230,13 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
   const double alpha = ok ? c->rho / pq : 0.0;
   double acc[1] = {0.0};
   if (ok) {
+    const Lin<T> ax(alpha), ar(-alpha);
     GKO_GRID_LOOP(i, n) {
-      x[i] = (T)__fma_rn(alpha, wd(p[i]), wd(x[i]));
-      const T ri = (T)__fma_rn(-alpha, wd(q[i]), wd(r[i]));
+      x[i] = ax(p[i], x[i]);
+      const T ri = ar(q[i], r[i]);
       r[i] = ri;
-      acc[0] += wd(ri) * wd(ri);
+      const double rw = wd(ri);
+      acc[0] = __fma_rn(rw, rw, acc[0]);
     }
   }
   reduce_op<1>(acc, ws, CgUpdateOp{c});
@@ -216,8 +245,8 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
 template <typename T>
 __global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c) {
   if (gated(&c->done)) return;
-  const double beta = c->beta;
-  GKO_GRID_LOOP(i, n) p[i] = (T)__fma_rn(beta, wd(p[i]), wd(r[i]));
+  const Lin<T> bp(c->beta);
+  GKO_GRID_LOOP(i, n) p[i] = bp(p[i], r[i]);
 }
 
 // after a failed true-residual check: r = t, beta = rho_new/rho, p = r + beta p
@@ -233,12 +262,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
                                                          const T* __restrict__ t, Ctl* c, RedWs ws) {
   if (!*(volatile int*)&c->replace) return;
-  const double beta = c->rho_new / c->rho;
+  const Lin<T> bp(c->rho_new / c->rho);
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
     const T ri = t[i];
     r[i] = ri;
-    p[i] = (T)__fma_rn(beta, wd(p[i]), wd(ri));
+    p[i] = bp(p[i], ri);
   }
   reduce_op<1>(acc, ws, CgReplaceOp{c});
 }
@@ -250,8 +279,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
                                                      const T* __restrict__ v, Ctl* c) {
   if (gated(&c->done)) return;
-  const double beta = c->beta, omega = c->omega;
-  GKO_GRID_LOOP(i, n) p[i] = (T)__fma_rn(beta, __fma_rn(-omega, wd(v[i]), wd(p[i])), wd(r[i]));
+  const Lin<T> bp(c->beta), wv(-c->omega);
+  GKO_GRID_LOOP(i, n) p[i] = bp(wv(v[i], p[i]), r[i]);
 }
 
 struct BicgSOp {
@@ -278,10 +307,12 @@ __global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restr
   const double alpha = rv != 0.0 ? c->rho_new / rv : 0.0;
   double acc[1] = {0.0};
   if (rv != 0.0) {
+    const Lin<T> av(-alpha);
     GKO_GRID_LOOP(i, n) {
-      const T si = (T)__fma_rn(-alpha, wd(v[i]), wd(r[i]));
+      const T si = av(v[i], r[i]);
       s[i] = si;
-      acc[0] += wd(si) * wd(si);
+      const double sw = wd(si);
+      acc[0] = __fma_rn(sw, sw, acc[0]);
     }
   }
   reduce_op<1>(acc, ws, BicgSOp{c});
@@ -334,19 +365,22 @@ __global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ 
   if (gated(&c->done)) return;
   const double alpha = c->alpha;
   double acc[2] = {0.0, 0.0};
+  const Lin<T> ap(alpha);
   if (*(volatile int*)&c->phase) {
-    GKO_GRID_LOOP(i, n) x[i] = (T)__fma_rn(alpha, wd(p[i]), wd(x[i]));
+    GKO_GRID_LOOP(i, n) x[i] = ap(p[i], x[i]);
   } else {
     const double tt = c->red[1];
     if (tt != 0.0) {
       const double omega = c->red[0] / tt;
+      const Lin<T> os(omega), ot(-omega);
       GKO_GRID_LOOP(i, n) {
-        const double si = wd(s[i]);
-        x[i] = (T)__fma_rn(omega, si, __fma_rn(alpha, wd(p[i]), wd(x[i])));
-        const T ri = (T)__fma_rn(-omega, wd(t[i]), si);
+        const T si = s[i];
+        x[i] = os(si, ap(p[i], x[i]));
+        const T ri = ot(t[i], si);
         r[i] = ri;
-        acc[0] += wd(ri) * wd(ri);
-        acc[1] += wd(rh[i]) * wd(ri);
+        const double rw = wd(ri);
+        acc[0] = __fma_rn(rw, rw, acc[0]);
+        acc[1] = __fma_rn(wd(rh[i]), rw, acc[1]);
       }
     }
   }
@@ -433,8 +467,8 @@ __global__ void __launch_bounds__(256) gm_start_kernel(int64_t n, const double* 
 template <typename T>
 __global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict__ v, const double* den, Ctl* c) {
   if (gated(&c->phase)) return;
-  const double inv = 1.0 / *den;
-  GKO_GRID_LOOP(i, n) v[i] = (T)(wd(v[i]) * inv);
+  const Lin<T> sc(1.0 / *den);
+  GKO_GRID_LOOP(i, n) v[i] = sc.scale(v[i]);
 }
 
 // gated multi-dot: partial sums of V_j . w for j <= jmax (blockIdx.y = j)
@@ -446,7 +480,7 @@ __global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __
   const int j = blockIdx.y;
   const T* v = V + (int64_t)j * ldv;
   double acc = 0.0;
-  GKO_GRID_LOOP(i, n) acc += wd(v[i]) * wd(__ldg(w + i));
+  GKO_GRID_LOOP(i, n) acc = __fma_rn(wd(v[i]), wd(__ldg(w + i)), acc);
   const double sblk = block_sum<256>(acc);
   if (threadIdx.x == 0) partials[(int64_t)j * kMultiSlots + blockIdx.x] = sblk;
 }
@@ -475,11 +509,13 @@ __global__ void __launch_bounds__(256) gm_axpy_kernel(int64_t n, int jcount, con
   if (gated(&c->phase)) return;
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
-    double v = wd(w[i]);
-    for (int j = 0; j < jcount; ++j) v = __fma_rn(-__ldg(h + j), wd(V[(int64_t)j * ldv + i]), v);
-    const T o = (T)v;
-    w[i] = o;
-    if (NORM) acc[0] += wd(o) * wd(o);
+    T v = w[i];
+    for (int j = 0; j < jcount; ++j) v = Lin<T>(-__ldg(h + j))(V[(int64_t)j * ldv + i], v);
+    w[i] = v;
+    if (NORM) {
+      const double ow = wd(v);
+      acc[0] = __fma_rn(ow, ow, acc[0]);
+    }
   }
   if (NORM) reduce_op<1>(acc, ws, StoreRr{c});
 }
@@ -526,8 +562,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
                                                       Ctl* c) {
   if (gated(&c->phase)) return;
-  const double inv = 1.0 / c->rho;
-  GKO_GRID_LOOP(i, n) vn[i] = (T)(wd(w[i]) * inv);
+  const Lin<T> sc(1.0 / c->rho);
+  GKO_GRID_LOOP(i, n) vn[i] = sc.scale(w[i]);
 }
 
 // Back substitution H[0:k,0:k] y = g[0:k]; stores -y for the x update.
@@ -552,9 +588,9 @@ __global__ void __launch_bounds__(256) gm_update_x_kernel(int64_t n, const doubl
   if (gated(&c->done)) return;
   const int k = c->k;
   GKO_GRID_LOOP(i, n) {
-    double v = wd(x[i]);
-    for (int j = 0; j < k; ++j) v = __fma_rn(-__ldg(ny + j), wd(V[(int64_t)j * ldv + i]), v);
-    x[i] = (T)v;
+    T v = x[i];
+    for (int j = 0; j < k; ++j) v = Lin<T>(-__ldg(ny + j))(V[(int64_t)j * ldv + i], v);
+    x[i] = v;
   }
 }
 
@@ -684,10 +720,11 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   Ctl* hc = host_ctl();
   const int vg = vec_grid(n), rg = reduce_grid(n);
   const bool fused = spmv_fuses_dot(A);
-  auto spmv = [&](const T* in, T* outv, const T* w, const int* gate) -> int {
+  auto spmv = [&](const T* in, T* outv, const T* w, const int* gate, bool want_yy = false) -> int {
     if (w && fused) {
       DotSpec d;
       d.w = w;
+      d.want_yy = want_yy ? 1 : 0;
       d.partials = partials;
       d.counter = counter;
       d.result = c->red;
@@ -740,7 +777,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           bicg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, v, c);
           GKO_TRY(spmv(p, v, rh, &c->done));
           bicg_s_kernel<T><<<rg, 256, 0, s>>>(n, r, v, sv, c, ws);
-          GKO_TRY(spmv(sv, tv, sv, &c->phase));
+          GKO_TRY(spmv(sv, tv, sv, &c->phase, true));
           bicg_x_kernel<T><<<rg, 256, 0, s>>>(n, x, p, sv, tv, r, rh, c, ws);
         }
         GKO_TRY_CUDA(cudaGetLastError());
@@ -954,8 +991,12 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
       break;
     }
     if (outer >= max_outer) break;
+    // ask the inner solve only for the reduction still needed (with a factor
+    // 2 margin), never tighter than inner_tol
+    SolveSpec step = in;
+    step.rel_tol = std::max(in.rel_tol, std::min(0.5, 0.5 * rel_tol * nb / nr));
     SolveOut so{};
-    GKO_TRY(krylov_core<float>(A32, r, d, true, in, s, &so));
+    GKO_TRY(krylov_core<float>(A32, r, d, true, step, s, &so));
     total_inner += so.iterations;
     outer += 1;
     add_f32_kernel<<<vg, 256, 0, s>>>(n, x, d);

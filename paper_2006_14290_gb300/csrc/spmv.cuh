@@ -18,6 +18,7 @@ struct DotSpec {
   double* partials = nullptr;  // 2 * kDotSlots doubles
   unsigned* counter = nullptr;  // zero on entry; the last block resets it
   double* result = nullptr;     // 2 doubles
+  int want_yy = 1;              // 0: skip y.y (result[1] = 0)
 };
 constexpr int kDotSlots = 4096;  // blocks a fused reduction may use
 

@@ -33,9 +33,9 @@ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ?
 
 template <typename XT>
 __device__ __forceinline__ void dot_accum(const DotSpec& d, int64_t i, XT v, double& wy, double& yy) {
-  const double yv = (double)v;
-  wy += (double)to_acc(static_cast<const XT*>(d.w)[i]) * yv;
-  yy += yv * yv;
+  const double yv = widen(v);
+  wy = __fma_rn(widen(static_cast<const XT*>(d.w)[i]), yv, wy);
+  if (d.want_yy) yy = __fma_rn(yv, yv, yy);
 }
 
 // ------------------------------------------------------------------- CSR --

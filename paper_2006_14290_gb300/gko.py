@@ -85,6 +85,22 @@ SIGNATURES = {
     "gko_solve_bicgstab": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "gko_solve_gmres": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
 }
+SIGNATURES.update({
+    "gko_batch_create": (C.c_int, [_I32, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)]),
+    "gko_batch_cg": (C.c_int, [_P, _P, _P, _D, _I32, _P, _P, _P, _P]),
+    "gko_batch_tune": (C.c_int, [_P, _P, _P, _D, _I32, _PI32, C.POINTER(C.c_float), _P]),
+    "gko_batch_set_threshold": (C.c_int, [_P, _I32, _P]),
+    "gko_batch_info": (C.c_int, [_P, _PI32, _PI64, _PI64, _PI32, _PI32]),
+    "gko_batch_destroy": (C.c_int, [_P]),
+})
+SIGNATURES.update({
+    "gko_server_create": (C.c_int, [_I32, _I64, C.POINTER(_P)]),
+    "gko_server_add_matrix": (C.c_int, [_P, _P, _PI32]),
+    "gko_server_submit": (C.c_int, [_P, _I32, _I32, _P, _D, _I32, C.POINTER(SolveOpts), _PI64]),
+    "gko_server_result": (C.c_int, [_P, _I64, C.c_int, _PI32, C.POINTER(SolveResult), _P, C.POINTER(_D)]),
+    "gko_server_stats": (C.c_int, [_P, _PI64, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D), _PI32]),
+    "gko_server_destroy": (C.c_int, [_P]),
+})
 OPTIONAL = {}
 
 
@@ -353,6 +369,130 @@ def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_
 def gko_device_status(stream=None):
     """Raise if a kernel recorded a device-side failure (bounded wait timeout)."""
     _check(lib().gko_device_status(_stream(stream)), "gko_device_status")
+
+
+class Batch:
+    """Owning wrapper of a gko_batch handle (batched CG)."""
+
+    def __init__(self, systems, storage=F64, stream=None):
+        """systems: list of objects with n_rows, row_ptr, col, val (host CSR)."""
+        count = len(systems)
+        rows = np.array([S.n_rows for S in systems], np.int64)
+        nnzs = np.array([int(S.row_ptr[-1]) for S in systems], np.int64)
+        self.row_off = np.zeros(count + 1, np.int64)
+        np.cumsum(rows, out=self.row_off[1:])
+        self.nnz_off = np.zeros(count + 1, np.int64)
+        np.cumsum(nnzs, out=self.nnz_off[1:])
+        rp = np.concatenate([np.asarray(S.row_ptr, np.int32) for S in systems])
+        col = np.concatenate([np.asarray(S.col, np.int32) for S in systems])
+        vdt = np.float64 if storage == F64 else np.float32
+        val = np.concatenate([np.asarray(S.val, np.float64) for S in systems]).astype(vdt)
+        h = C.c_void_p()
+        _check(lib().gko_batch_create(count, _hptr(self.row_off), _hptr(self.nnz_off), _hptr(rp), _hptr(col),
+                                      _hptr(val), storage, _stream(stream), C.byref(h)), "gko_batch_create")
+        self.handle = h
+        self.count = count
+        self.total_rows = int(self.row_off[-1])
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.gko_batch_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    def cg(self, b, x, rel_tol=1e-10, max_iters=10000, stream=None):
+        it = np.zeros(self.count, np.int32)
+        rr = np.zeros(self.count, np.float64)
+        st = np.zeros(self.count, np.int32)
+        code = lib().gko_batch_cg(self.handle, _dptr(b), _dptr(x), rel_tol, max_iters, _hptr(it), _hptr(rr),
+                                  _hptr(st), _stream(stream))
+        if code not in (OK, NOT_CONVERGED, BREAKDOWN):
+            _check(code, "gko_batch_cg")
+        return code, it, rr, st
+
+    def tune(self, b, x0, rel_tol=1e-10, max_iters=10000, stream=None):
+        ch = C.c_int32()
+        ms = C.c_float()
+        _check(lib().gko_batch_tune(self.handle, _dptr(b), _dptr(x0), rel_tol, max_iters, C.byref(ch), C.byref(ms),
+                                    _stream(stream)), "gko_batch_tune")
+        return ch.value, ms.value
+
+    def set_threshold(self, warp_rows, stream=None):
+        _check(lib().gko_batch_set_threshold(self.handle, warp_rows, _stream(stream)), "gko_batch_set_threshold")
+
+    def info(self):
+        c, wr, ni = C.c_int32(), C.c_int32(), C.c_int32()
+        tr, tn = C.c_int64(), C.c_int64()
+        _check(lib().gko_batch_info(self.handle, C.byref(c), C.byref(tr), C.byref(tn), C.byref(wr), C.byref(ni)),
+               "gko_batch_info")
+        return dict(count=c.value, total_rows=tr.value, total_nnz=tn.value, warp_rows=wr.value, n_items=ni.value)
+
+
+class Server:
+    """Owning wrapper of a gko_server (continuous-batching request loop)."""
+
+    def __init__(self, slots=4, budget_bytes=0):
+        h = C.c_void_p()
+        _check(lib().gko_server_create(slots, int(budget_bytes), C.byref(h)), "gko_server_create")
+        self.handle = h
+        self._mats = []
+        self._n = {}
+
+    def add_matrix(self, M: Matrix) -> int:
+        mid = C.c_int32()
+        _check(lib().gko_server_add_matrix(self.handle, M.handle, C.byref(mid)), "gko_server_add_matrix")
+        self._mats.append(M)
+        self._n[mid.value] = M.info()["n_rows"]
+        return mid.value
+
+    def submit(self, matrix_id: int, solver: int, b: np.ndarray, rel_tol=1e-8, max_iters=1000, opts=None) -> int:
+        b = np.ascontiguousarray(b, np.float64)
+        rid = C.c_int64()
+        _check(lib().gko_server_submit(self.handle, matrix_id, solver, _hptr(b), rel_tol, max_iters,
+                                       C.byref(opts) if opts is not None else None, C.byref(rid)), "gko_server_submit")
+        self._pending = getattr(self, "_pending", {})
+        self._pending[rid.value] = self._n[matrix_id]
+        return rid.value
+
+    def result(self, request_id: int, wait=True):
+        """(status, SolveResult, x, latency_ms) or None while still running."""
+        n = self._pending.get(request_id, 0)
+        x = np.empty(n, np.float64)
+        done = C.c_int32()
+        res = SolveResult()
+        lat = C.c_double()
+        st = lib().gko_server_result(self.handle, request_id, 1 if wait else 0, C.byref(done), C.byref(res),
+                                     _hptr(x), C.byref(lat))
+        if not done.value:
+            if st != OK:
+                _check(st, "gko_server_result")
+            return None
+        self._pending.pop(request_id, None)
+        if st not in (OK, NOT_CONVERGED, BREAKDOWN):
+            _check(st, "gko_server_result")
+        return st, res, x, lat.value
+
+    def stats(self):
+        c = C.c_int64()
+        p50, p99, sps = C.c_double(), C.c_double(), C.c_double()
+        pk = C.c_int32()
+        _check(lib().gko_server_stats(self.handle, C.byref(c), C.byref(p50), C.byref(p99), C.byref(sps),
+                                      C.byref(pk)), "gko_server_stats")
+        return dict(completed=c.value, p50_ms=p50.value, p99_ms=p99.value, solves_per_s=sps.value,
+                    peak_active=pk.value)
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.gko_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_memory_budget(nbytes: int):

@@ -1,0 +1,128 @@
+"""GPU parity of the batched persistent CG against per-system oracle CG."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, host
+from paper_2006_14290_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def batch_problem(count, seed=0, extra_sides=(8, 64, 11)):
+    sides = list(I.batch_sides(count, seed=seed)) + list(extra_sides)
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, int(sd), seed=seed)
+        systems.append(A)
+        bs.append(b)
+    return systems, bs
+
+
+def concat(v):
+    return np.concatenate([np.asarray(a, np.float64) for a in v])
+
+
+@pytest.mark.parametrize("threshold", [0, 64, 144, 256])
+def test_batch_cg_matches_oracle(gko, threshold):
+    G = gko
+    systems, bs = batch_problem(120)
+    bs[5] = np.zeros_like(bs[5])  # a zero right-hand side
+    B = G.Batch(systems)
+    B.set_threshold(threshold)
+    b = concat(bs)
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-12, 20000)
+    assert code == G.OK and np.all(st == G.OK)
+    x = host(xd)
+    off = B.row_off
+    for i in list(range(0, len(systems), 9)) + [5, len(systems) - 3, len(systems) - 2, len(systems) - 1]:
+        A = systems[i]
+        xi = x[off[i]:off[i + 1]]
+        if i == 5:
+            assert it[i] == 0 and np.all(xi == 0) and rr[i] == 0
+            continue
+        xo, ro = O.cg(A, bs[i], tol=1e-12, maxit=20000)
+        assert ro.status == 0
+        assert np.linalg.norm(xi - xo) <= 1e-8 * np.linalg.norm(xo), i
+        assert abs(int(it[i]) - ro.iterations) <= max(2, 0.1 * ro.iterations), (i, it[i], ro.iterations)
+        true = np.linalg.norm(bs[i] - O.spmv_csr(A, xi)) / np.linalg.norm(bs[i])
+        assert true <= 1.01e-12 and abs(true - rr[i]) <= 1e-14
+
+
+def test_batch_deterministic_graph_replay_and_x0(gko):
+    G = gko
+    systems, bs = batch_problem(60, seed=3)
+    B = G.Batch(systems)
+    b = dev(concat(bs))
+    x0 = np.random.default_rng(2).uniform(-1, 1, B.total_rows)
+    outs = []
+    for _ in range(3):  # first call captures the graph, later calls replay it
+        xd = dev(x0)
+        code, it, rr, st = B.cg(b, xd, 1e-11, 20000)
+        assert code == G.OK
+        outs.append((host(xd).tobytes(), it.tobytes()))
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_batch_fp32_storage_and_caps(gko):
+    G = gko
+    systems, bs = batch_problem(40, seed=4)
+    B = G.Batch(systems, storage=G.F32)
+    b = concat(bs)
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-10, 20000)
+    assert code == G.OK
+    x = host(xd)
+    for i in range(0, len(systems), 7):
+        A = systems[i]
+        A32 = I.Csr(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+        xi = x[B.row_off[i]:B.row_off[i + 1]]
+        true32 = np.linalg.norm(bs[i] - O.spmv_csr(A32, xi)) / np.linalg.norm(bs[i])
+        assert true32 <= 1.01e-10
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-14, 3)
+    assert code == G.NOT_CONVERGED and np.all(it == 3) and np.all(st == G.NOT_CONVERGED)
+
+
+def test_batch_tuner_and_invalid_input(gko):
+    G = gko
+    systems, bs = batch_problem(200, seed=5)
+    B = G.Batch(systems)
+    b = dev(concat(bs))
+    x0 = dev(np.zeros(B.total_rows))
+    chosen, ms = B.tune(b, x0, 1e-10, 20000)
+    assert chosen in (0, 64, 100, 144, 196, 256) and ms > 0
+    assert B.info()["warp_rows"] == chosen
+    assert np.all(host(x0) == 0)
+    bad = I.laplace2d_5pt(4)
+    bad.col = bad.col.copy()
+    bad.col[0] = 99
+    with pytest.raises(G.GkoError):
+        G.Batch([bad])
+
+
+@pytest.mark.slow
+def test_batch_full_size_4096(gko):
+    """The batched workload of the benchmark: 4096 systems, sides in [8, 64]."""
+    G = gko
+    sides = I.batch_sides(4096)
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, int(sd))
+        systems.append(A)
+        bs.append(b)
+    B = G.Batch(systems)
+    assert B.info()["total_rows"] == 3914078 and B.info()["total_nnz"] == 19132534
+    b = concat(bs)
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-10, 20000)
+    assert code == G.OK and np.all(rr <= 1e-10)
+    x = host(xd)
+    for i in np.random.default_rng(0).choice(4096, 12, replace=False):
+        A = systems[i]
+        xi = x[B.row_off[i]:B.row_off[i + 1]]
+        true = np.linalg.norm(bs[i] - O.spmv_csr(A, xi)) / np.linalg.norm(bs[i])
+        assert true <= 1.01e-10
+        xo, ro = O.cg(A, bs[i], tol=1e-10, maxit=20000)
+        assert abs(int(it[i]) - ro.iterations) <= max(2, 0.1 * ro.iterations)
