@@ -218,7 +218,7 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
 typedef struct {
   int32_t restart;      /* GMRES restart length m (<= 0: 30)                     */
   int32_t precision;    /* GKO_PRECISION_*                                       */
-  double inner_tol;     /* mixed: inner relative tolerance (<= 0: 1e-4)          */
+  double inner_tol;     /* mixed: inner relative tolerance (<= 0: 1e-5)          */
   int32_t max_outer;    /* mixed: refinement steps (<= 0: 30)                    */
   int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters) */
   int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */

@@ -15,7 +15,7 @@ struct StoreOp1 {
 
 int reduce_grid(int64_t n) {
   int64_t g = (n + 1023) / 1024;
-  const int64_t cap = std::min<int64_t>((int64_t)sm_count() * 4, kDotSlots);
+  const int64_t cap = std::min<int64_t>((int64_t)sm_count() * 8, kDotSlots);
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

@@ -74,6 +74,56 @@ struct Lin<float> {
 
 __device__ __forceinline__ double dsq(double a) { return a * a; }
 
+// 16-byte vectors of T for the streaming solver kernels: VN elements per
+// load/store (2 doubles or 4 floats).  The vector path runs when every
+// pointer of the kernel is 16-byte aligned; the last n % VN elements and
+// unaligned callers take the scalar path.
+template <typename T>
+struct Vec16 {
+  static constexpr int N = 16 / sizeof(T);
+  T v[16 / sizeof(T)];
+};
+template <typename T>
+__device__ __forceinline__ Vec16<T> vload(const T* p) {
+  Vec16<T> r;
+  if constexpr (sizeof(T) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r.v[0] = t.x;
+    r.v[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.v[0] = t.x;
+    r.v[1] = t.y;
+    r.v[2] = t.z;
+    r.v[3] = t.w;
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, const Vec16<T>& r) {
+  if constexpr (sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  }
+}
+__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// vf(i0) handles elements i0 .. i0+VN-1 (16-byte aligned); sf(i) one element.
+template <typename T, typename VF, typename SF>
+__device__ __forceinline__ void vec_loop(int64_t n, bool aligned, VF vf, SF sf) {
+  constexpr int VN = Vec16<T>::N;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t done = 0;
+  if (aligned) {
+    const int64_t nv = n / VN;
+    for (int64_t iv = tid; iv < nv; iv += nth) vf(iv * VN);
+    done = nv * VN;
+  }
+  for (int64_t i = done + tid; i < n; i += nth) sf(i);
+}
+
 template <int NV, typename Op>
 __device__ __forceinline__ void reduce_op(double (&v)[NV], RedWs ws, Op op) {
   grid_reduce<256, NV>(v, ws.partials, ws.counter, blockIdx.x, gridDim.x, op);
@@ -231,13 +281,26 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
   double acc[1] = {0.0};
   if (ok) {
     const Lin<T> ax(alpha), ar(-alpha);
-    GKO_GRID_LOOP(i, n) {
-      x[i] = ax(p[i], x[i]);
-      const T ri = ar(q[i], r[i]);
-      r[i] = ri;
-      const double rw = wd(ri);
-      acc[0] = __fma_rn(rw, rw, acc[0]);
-    }
+    const bool aligned = al16(x) && al16(r) && al16(p) && al16(q);
+    vec_loop<T>(n, aligned, [&](int64_t i0) {
+          Vec16<T> xv = vload(x + i0), rv = vload(r + i0);
+          const Vec16<T> pv = vload(p + i0), qv = vload(q + i0);
+#pragma unroll
+          for (int k = 0; k < Vec16<T>::N; ++k) {
+            xv.v[k] = ax(pv.v[k], xv.v[k]);
+            rv.v[k] = ar(qv.v[k], rv.v[k]);
+            const double rw = wd(rv.v[k]);
+            acc[0] = __fma_rn(rw, rw, acc[0]);
+          }
+          vstore(x + i0, xv);
+          vstore(r + i0, rv);
+        }, [&](int64_t i) {
+          x[i] = ax(p[i], x[i]);
+          const T ri = ar(q[i], r[i]);
+          r[i] = ri;
+          const double rw = wd(ri);
+          acc[0] = __fma_rn(rw, rw, acc[0]);
+        });
   }
   reduce_op<1>(acc, ws, CgUpdateOp{c});
 }
@@ -246,7 +309,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c) {
   if (gated(&c->done)) return;
   const Lin<T> bp(c->beta);
-  GKO_GRID_LOOP(i, n) p[i] = bp(p[i], r[i]);
+  const bool aligned = al16(r) && al16(p);
+  vec_loop<T>(n, aligned, [&](int64_t i0) {
+        Vec16<T> pv = vload(p + i0);
+        const Vec16<T> rv = vload(r + i0);
+#pragma unroll
+        for (int k = 0; k < Vec16<T>::N; ++k) pv.v[k] = bp(pv.v[k], rv.v[k]);
+        vstore(p + i0, pv);
+      }, [&](int64_t i) { p[i] = bp(p[i], r[i]); });
 }
 
 // after a failed true-residual check: r = t, beta = rho_new/rho, p = r + beta p
@@ -280,7 +350,14 @@ __global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restr
                                                      const T* __restrict__ v, Ctl* c) {
   if (gated(&c->done)) return;
   const Lin<T> bp(c->beta), wv(-c->omega);
-  GKO_GRID_LOOP(i, n) p[i] = bp(wv(v[i], p[i]), r[i]);
+  const bool aligned = al16(r) && al16(p) && al16(v);
+  vec_loop<T>(n, aligned, [&](int64_t i0) {
+        Vec16<T> pv = vload(p + i0);
+        const Vec16<T> rv = vload(r + i0), vv = vload(v + i0);
+#pragma unroll
+        for (int k = 0; k < Vec16<T>::N; ++k) pv.v[k] = bp(wv(vv.v[k], pv.v[k]), rv.v[k]);
+        vstore(p + i0, pv);
+      }, [&](int64_t i) { p[i] = bp(wv(v[i], p[i]), r[i]); });
 }
 
 struct BicgSOp {
@@ -308,12 +385,23 @@ __global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restr
   double acc[1] = {0.0};
   if (rv != 0.0) {
     const Lin<T> av(-alpha);
-    GKO_GRID_LOOP(i, n) {
-      const T si = av(v[i], r[i]);
-      s[i] = si;
-      const double sw = wd(si);
-      acc[0] = __fma_rn(sw, sw, acc[0]);
-    }
+    const bool aligned = al16(r) && al16(v) && al16(s);
+    vec_loop<T>(n, aligned, [&](int64_t i0) {
+          const Vec16<T> vv = vload(v + i0), rr = vload(r + i0);
+          Vec16<T> sv;
+#pragma unroll
+          for (int k = 0; k < Vec16<T>::N; ++k) {
+            sv.v[k] = av(vv.v[k], rr.v[k]);
+            const double sw = wd(sv.v[k]);
+            acc[0] = __fma_rn(sw, sw, acc[0]);
+          }
+          vstore(s + i0, sv);
+        }, [&](int64_t i) {
+          const T si = av(v[i], r[i]);
+          s[i] = si;
+          const double sw = wd(si);
+          acc[0] = __fma_rn(sw, sw, acc[0]);
+        });
   }
   reduce_op<1>(acc, ws, BicgSOp{c});
 }
@@ -373,15 +461,29 @@ __global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ 
     if (tt != 0.0) {
       const double omega = c->red[0] / tt;
       const Lin<T> os(omega), ot(-omega);
-      GKO_GRID_LOOP(i, n) {
-        const T si = s[i];
-        x[i] = os(si, ap(p[i], x[i]));
-        const T ri = ot(t[i], si);
-        r[i] = ri;
-        const double rw = wd(ri);
-        acc[0] = __fma_rn(rw, rw, acc[0]);
-        acc[1] = __fma_rn(wd(rh[i]), rw, acc[1]);
-      }
+      const bool aligned = al16(x) && al16(p) && al16(s) && al16(t) && al16(r) && al16(rh);
+      vec_loop<T>(n, aligned, [&](int64_t i0) {
+            Vec16<T> xv = vload(x + i0), rv;
+            const Vec16<T> sv = vload(s + i0), pv = vload(p + i0), tv = vload(t + i0), hv = vload(rh + i0);
+#pragma unroll
+            for (int k = 0; k < Vec16<T>::N; ++k) {
+              xv.v[k] = os(sv.v[k], ap(pv.v[k], xv.v[k]));
+              rv.v[k] = ot(tv.v[k], sv.v[k]);
+              const double rw = wd(rv.v[k]);
+              acc[0] = __fma_rn(rw, rw, acc[0]);
+              acc[1] = __fma_rn(wd(hv.v[k]), rw, acc[1]);
+            }
+            vstore(x + i0, xv);
+            vstore(r + i0, rv);
+          }, [&](int64_t i) {
+            const T si = s[i];
+            x[i] = os(si, ap(p[i], x[i]));
+            const T ri = ot(t[i], si);
+            r[i] = ri;
+            const double rw = wd(ri);
+            acc[0] = __fma_rn(rw, rw, acc[0]);
+            acc[1] = __fma_rn(wd(rh[i]), rw, acc[1]);
+          });
     }
   }
   reduce_op<2>(acc, ws, BicgXOp{c});
@@ -965,7 +1067,7 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   GKO_TRY(lowp_copy(A, o.precision == GKO_PRECISION_MIXED_F32 ? GKO_F32 : GKO_BF16, s, &A32));
   // mixed-precision iterative refinement: FP64 residual, FP32-stored inner solve
   SolveSpec in = sp;
-  in.rel_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+  in.rel_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
   in.maxit = o.inner_maxit > 0 ? o.inner_maxit : max_iters;
   in.check_true = 0;
   const int max_outer = o.max_outer > 0 ? o.max_outer : 30;

@@ -531,12 +531,14 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
 // Tiled segmented reduction over row-sorted COO.  Each 256-thread block owns
 // a tile of 256*kCooItems entries; each thread owns kCooItems consecutive
 // entries (vector loads) and folds them with one FMA per entry, finishing
-// the rows that start and end inside its entries on the spot.  A block-wide
-// segmented scan of (has a row end, trailing sum) supplies the running sum
-// that enters the thread's first row from earlier threads.  The tile's open
-// first/last segment partials go to carry[2*tile] / carry[2*tile+1] for
-// coo_fixup_kernel.  ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows
-// absent from the COO arrays are scaled by beta here too.
+// the rows that start and end inside its entries on the spot.  The running
+// sum entering a thread's first row is the sum of the trailing partials of
+// the preceding threads back to the nearest one that ended a row: the thread
+// that ends the row walks back over them in shared memory (about one FP64
+// add per thread; no shuffle scan).  The tile's open first/last segment
+// partials go to carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
+// ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows absent from the COO
+// arrays are scaled by beta here too.
 template <typename VT, typename XT, bool ACCUM>
 __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
                                                           const int* gate) {
@@ -544,13 +546,11 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
   constexpr int IPT = kCooItems;
   __shared__ int32_t s_first[kCooThreads + 1];
   __shared__ int32_t s_last[kCooThreads];
-  __shared__ AT s_wv[kCooThreads / kWarp];
-  __shared__ int s_wf[kCooThreads / kWarp];
-  __shared__ AT s_pv[kCooThreads / kWarp + 1];
-  __shared__ int s_pf[kCooThreads / kWarp + 1];
+  __shared__ AT s_tail[kCooThreads];
+  __shared__ int s_end[kCooThreads];
   __shared__ int32_t s_prev_row;
   if (gated(gate)) return;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int t = threadIdx.x;
   const int64_t tile = blockIdx.x;
   const int64_t base = tile * kCooTile;
   const int cnt = (int)min((int64_t)kCooTile, a.nnz - base);
@@ -620,57 +620,38 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
     }
   }
   if (!ACCUM && my > 0 && base + j0 + my == a.nnz) coo_empty_rows(a.y, (int64_t)rows[my - 1] + 1, a.n_rows, a.beta);
-
-  // segmented scan of (has an end, trailing sum) over the block
-  int f = nends > 0;
-  AT v = run;
-#pragma unroll
-  for (int dlt = 1; dlt < 32; dlt <<= 1) {
-    const int fp = __shfl_up_sync(0xffffffffu, f, dlt);
-    const AT vp = __shfl_up_sync(0xffffffffu, v, dlt);
-    if (lane >= dlt) seg_combine(fp, vp, f, v);
-  }
-  if (lane == 31) {
-    s_wf[w] = f;
-    s_wv[w] = v;
-  }
-  int ef = __shfl_up_sync(0xffffffffu, f, 1);
-  AT ev = __shfl_up_sync(0xffffffffu, v, 1);
-  if (lane == 0) {
-    ef = 0;
-    ev = AT(0);
-  }
+  s_tail[t] = run;  // sum after this thread's last row end (all of it without one)
+  s_end[t] = nends > 0;
   __syncthreads();
-  if (t == 0) {  // exclusive prefixes of the warp aggregates, and the tile total
-    int pf = 0;
-    AT pv = AT(0);
-    for (int i = 0; i < kCooThreads / kWarp; ++i) {
-      s_pf[i] = pf;
-      s_pv[i] = pv;
-      int ff = s_wf[i];
-      AT vv = s_wv[i];
-      seg_combine(pf, pv, ff, vv);
-      pf = ff;
-      pv = vv;
-    }
-    s_pf[kCooThreads / kWarp] = pf;
-    s_pv[kCooThreads / kWarp] = pv;
-  }
-  __syncthreads();
-  seg_combine(s_pf[w], s_pv[w], ef, ev);  // exclusive prefix of this thread
 
   if (nends > 0) {
-    const AT total = ev + first_sum;
-    if (!ef && first_open)
+    AT in = AT(0);
+    bool from_before_tile = true;
+    for (int u = t - 1; u >= 0; --u) {
+      in += s_tail[u];
+      if (s_end[u]) {
+        from_before_tile = false;
+        break;
+      }
+    }
+    const AT total = in + first_sum;
+    if (from_before_tile && first_open)
       carry[2 * tile] = total;  // the tile's first row began in an earlier tile
     else
       coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM);
   }
   if (t == 0) {
-    const int tf = s_pf[kCooThreads / kWarp];
-    const AT tv = s_pv[kCooThreads / kWarp];
+    AT tv = AT(0);
+    bool any_end = false;
+    for (int u = kCooThreads - 1; u >= 0; --u) {
+      tv += s_tail[u];
+      if (s_end[u]) {
+        any_end = true;
+        break;
+      }
+    }
     // tv: sum of the tile's last segment; without any end the whole tile
-    if (!tf) carry[2 * tile] = tv;
+    if (!any_end) carry[2 * tile] = tv;
     carry[2 * tile + 1] = tv;
   }
 }
