@@ -55,11 +55,11 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def workload_matrices():
+def workload_matrices(small=False):
     from paper_2006_14290_gb300 import inputs as I
 
-    return [("stencil27_128", I.stencil3d_27pt(128)), ("powerlaw_1m", I.powerlaw(1_000_000, seed=0)),
-            ("banded_1m", I.banded(1_000_000, 64, 0.3, seed=0))]
+    st = ("stencil27_96", I.stencil3d_27pt(96)) if small else ("stencil27_128", I.stencil3d_27pt(128))
+    return [st, ("powerlaw_1m", I.powerlaw(1_000_000, seed=0)), ("banded_1m", I.banded(1_000_000, 64, 0.3, seed=0))]
 
 
 def spmv_bytes(fmt, n_rows, n_cols, nnz, ell_nnz, tail_nnz, sv, sx, sy):
@@ -175,6 +175,8 @@ def solver_suite(G, dev, stream):
         if solver == "bicgstab":
             maxit = 2000
         opts = G.opts(precision=prec, restart=restart, inner_maxit=2000, max_outer=12)
+        if tag == "bicgstab_convdiff128_mixed_f32":  # known not to converge: keep it short
+            opts = G.opts(precision=prec, inner_maxit=500, max_outer=3)
         xd = torch.zeros(n, dtype=torch.float64, device=dev)
         fn(M, bd, xd, tol, maxit, opts, stream=stream)  # warm-up (also builds the low-precision copy)
         xd.zero_()
@@ -420,24 +422,13 @@ def cpu_baseline(mats, budget_s=12.0):
 
 # ---------------------------------------------------------------- our path --
 
-def run_ours(args):
+def build_cases(G, mats, dev):
+    """Every (matrix, format, value type) SpMV case of the sweep, resident on
+    the device, with its algorithmic bytes and the number of kernel launches
+    one gko_spmv call makes for it."""
     import torch
 
-    rank, world, local_rank = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local_rank)
-    from paper_2006_14290_gb300 import gko as G
-
-    G.load()
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream()
-    mats = workload_matrices()
-
-    cases = []  # dicts: label, handle, x, y, xh, yh, bytes, launches
-    skipped = []
+    cases, skipped = [], []
     for name, A in mats:
         M64 = G.from_csr(A)
         plan = M64.plan()
@@ -459,13 +450,55 @@ def run_ours(args):
                 sv = 8 if dt == "f64" else 4
                 ell_nnz = inf["nnz"] - inf["coo_nnz"] if fmt == "hybrid" else 0
                 nb = spmv_bytes(fmt, A.n_rows, A.n_cols, A.nnz, ell_nnz, inf["coo_nnz"], sv, sv, sv)
-                launches = {"csr": 1 + (2 if plan["n_long_rows"] > 0 else 0), "ell": 1, "coo": 2, "hybrid": 3}[fmt]
+                coo_launches = 2 if inf["coo_nnz"] > 0 else 0
+                launches = {"csr": 1 + (2 if plan["n_long_rows"] > 0 else 0), "ell": 1,
+                            "coo": coo_launches if coo_launches else 1, "hybrid": 1 + coo_launches}[fmt]
                 x = x64 if dt == "f64" else x32
                 y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
                 cases.append({"label": f"{name}/{fmt}/{dt}", "M": H, "x": x, "y": y, "bytes": nb,
-                              "launches": launches, "xh": x.cpu().pin_memory(),
+                              "launches": launches, "nnz": int(A.nnz), "xh": x.cpu().pin_memory(),
                               "yh": torch.empty(A.n_rows, dtype=x.dtype).pin_memory()})
         del A
+    return cases, skipped
+
+
+def profile_cases(args):
+    """One SpMV per case (after one untimed pass), for ncu: prints the cases
+    in launch order with their launch counts, algorithmic bytes and nnz."""
+    import torch
+    from paper_2006_14290_gb300 import gko as G
+
+    G.load()
+    dev = torch.device("cuda", 0)
+    cases, _ = build_cases(G, workload_matrices(small=args.small), dev)
+    for c in cases:
+        G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile_cases")
+    for c in cases:
+        G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    G.gko_device_status()
+    print(json.dumps([[c["label"], c["launches"], int(c["bytes"]), c["nnz"]] for c in cases]))
+
+def run_ours(args):
+    import torch
+
+    rank, world, local_rank = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_2006_14290_gb300 import gko as G
+
+    G.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    mats = workload_matrices()
+
+    cases, skipped = build_cases(G, mats, dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(events=None):
@@ -501,11 +534,13 @@ def run_ours(args):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     barrier()
+    torch.cuda.nvtx.range_push("timed_steps")
     t_start.record(stream)
     for k in range(args.steps):
         step(ev[k])
     t_end.record(stream)
     barrier()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     per_case_ms = [sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)) / args.steps
                    for i in range(len(cases))]
@@ -595,7 +630,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile-cases", action="store_true",
+                    help="run each SpMV case once (for ncu) and print the case order")
+    ap.add_argument("--small", action="store_true", help="with --profile-cases: 27-point stencil at 96^3")
     args = ap.parse_args()
+    if args.profile_cases:
+        profile_cases(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -141,9 +141,12 @@ GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void
  * mean): row blocks stream into shared memory by bulk copies in stages of
  * stage_cap entries; `subwarp` lanes sum each row, each subwarp owning
  * rows_per_subwarp interleaved rows of a block of 128 threads.
- * kernel 0, the subwarp kernel (skewed matrices): `subwarp` lanes per row,
- * rows_per_subwarp rows per pass, and rows longer than long_threshold split
- * into fixed-size nonzero chunks (n_long_rows rows, n_long_chunks chunks).
+ * kernel 2, the merge-path kernel (skewed matrices, the default there): the
+ * merged sequence of row ends and nonzeros is split into equal shares per
+ * thread, so long rows spread over many threads and tiles.
+ * kernel 0, the subwarp kernel: `subwarp` lanes per row, rows_per_subwarp
+ * rows per pass, and rows longer than long_threshold split into fixed-size
+ * nonzero chunks (n_long_rows rows, n_long_chunks chunks).
  * hist33: row-length histogram in log2 classes (hist[0]: empty rows;
  * hist[b], b >= 1: lengths in [2^(b-1), 2^b)).  Any output may be NULL. */
 GKO_API int gko_matrix_plan(gko_matrix csr, int32_t *kernel, int32_t *subwarp, int32_t *rows_per_subwarp,
@@ -153,7 +156,7 @@ GKO_API int gko_matrix_plan(gko_matrix csr, int32_t *kernel, int32_t *subwarp, i
 /* Override the CSR plan (the autotuner's knob).  kernel 0: subwarp S in
  * 1,2,4,8,16,32, R in 1,2,4, long-row threshold 32*S; kernel 1: row-block,
  * S in 1,2,4,8, R in 1,2,4, stage_cap a power of two in 512..8192 (ignored
- * for kernel 0).  Low-precision copies made by gko_matrix_convert_values
+ * otherwise); kernel 2: merge path (S, R still validated, unused).  Low-precision copies made by gko_matrix_convert_values
  * keep their own plan.  Synchronises `stream`. */
 GKO_API int gko_matrix_set_plan(gko_matrix csr, int32_t kernel, int32_t subwarp, int32_t rows_per_subwarp,
                                 int32_t stage_cap, void *stream);

@@ -102,6 +102,8 @@ struct CsrPlan {
   Buf long_chunk_ptr;  // int32[n_long+1]   first chunk of each long row
   Buf chunk_row;       // int32[n_chunks]   row index of each chunk
   Buf chunk_start;     // int32[n_chunks]   first nonzero of each chunk
+  Buf merge_x;         // int32[tiles+1]    merge-path row coordinate of each tile corner
+  int64_t merge_tiles = 0;
 };
 
 }  // namespace gko

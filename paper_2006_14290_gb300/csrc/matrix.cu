@@ -205,9 +205,11 @@ static unsigned grid_for(int64_t work, int threads = 256) {
 //    (interleaved rows per subwarp) the largest power of two <= 4 with
 //    (128/S)*R*m <= cap, so one row block fills about a stage.
 //    No row is split.
-//  * Skewed matrices use the subwarp kernel: S = the smallest power of two
-//    (<= 32) not below the mean length of rows shorter than 1024, R = 2 rows
-//    per pass, and rows longer than 32*S go to the nonzero split.
+//  * Skewed matrices use the merge-path kernel (equal shares of row ends plus
+//    nonzeros per thread).  The subwarp kernel with a nonzero split of long
+//    rows stays available through gko_matrix_set_plan (kernel 0): S = the
+//    smallest power of two (<= 32) not below the mean length of rows shorter
+//    than 1024, R = 2 rows per pass, rows longer than 32*S split.
 static void choose_plan(CsrPlan& p, int64_t n) {
   int64_t nz_all = 0;
   for (int b = 0; b < kHistBins; ++b) nz_all += p.hist_nnz[b];
@@ -232,10 +234,47 @@ static void choose_plan(CsrPlan& p, int64_t n) {
   const double mean = rows ? (double)nz / (double)rows : 1.0;
   int32_t S = 1;
   while (S < 32 && (double)S < mean) S *= 2;
-  p.kind = 0;
+  p.kind = 2;
   p.S = S;
   p.R = 2;
-  p.long_thr = 32 * S;
+  p.long_thr = INT32_MAX;  // merge path needs no long-row split
+}
+
+// Row coordinate of every merge-path tile corner (diagonal t * tile, t =
+// 0..tiles; the last corner is the end of the path).  Same search as the
+// kernel's, once per matrix.
+__global__ void merge_corners_kernel(int64_t n, int64_t nnz, int64_t tiles, int64_t tile_items,
+                                     const int32_t* __restrict__ rp, int32_t* __restrict__ cx) {
+  const int64_t total = n + nnz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = t * tile_items < total ? t * tile_items : total;
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < n ? d : n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)rp[mid + 1] <= d - mid - 1)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    cx[t] = (int32_t)lo;
+  }
+}
+
+static int build_merge_corners(gko_matrix m, cudaStream_t s) {
+  CsrPlan& p = m->plan;
+  p.merge_x.reset();
+  p.merge_tiles = 0;
+  if (p.kind != 2) return GKO_OK;
+  const int64_t tile_items = 256 * 8;  // the merge kernel's tile (256 threads x 8 items)
+  const int64_t tiles = (m->n_rows + m->nnz + tile_items - 1) / tile_items;
+  GKO_TRY(alloc(sizeof(int32_t) * (tiles + 1), &p.merge_x));
+  merge_corners_kernel<<<grid_for(tiles + 1), 256, 0, s>>>(m->n_rows, m->nnz, tiles, tile_items,
+                                                           ptr<int32_t>(m->row_ptr), ptr<int32_t>(p.merge_x));
+  GKO_TRY_CUDA(cudaGetLastError());
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  p.merge_tiles = tiles;
+  return GKO_OK;
 }
 
 static bool valid_S(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32; }
@@ -296,6 +335,7 @@ static int build_plan(gko_matrix m, cudaStream_t s) {
   }
   p.max_len = mx;
   choose_plan(p, n);
+  GKO_TRY(build_merge_corners(m, s));
   return build_long_split(m, s);
 }
 
@@ -414,16 +454,18 @@ int gko_matrix_plan(gko_matrix m, int32_t* kernel, int32_t* S, int32_t* R, int32
 int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int32_t cap, void* stream) {
   if (!m || m->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "plan needs a CSR handle");
   const bool rb = kernel == 1;
-  if ((kernel != 0 && kernel != 1) || !valid_S(S) || !valid_R(R) || (rb && S > 8) ||
+  if ((kernel < 0 || kernel > 2) || !valid_S(S) || !valid_R(R) || (rb && S > 8) ||
       (rb && (cap < 512 || cap > 8192 || (cap & (cap - 1)))))
     return fail(GKO_INVALID_ARG,
-                "kernel 0 (subwarp: S 1..32, R 1,2,4) or 1 (row-block: S 1..8, R 1,2,4, cap 512..8192, powers of 2)");
+                "kernel 0 (subwarp: S 1..32, R 1,2,4), 1 (row-block: S 1..8, R 1,2,4, cap 512..8192, powers of 2) "
+                "or 2 (merge path)");
   std::lock_guard<std::mutex> lk(m->mu);
   m->plan.kind = kernel;
   m->plan.S = S;
   m->plan.R = R;
   if (rb) m->plan.cap = cap;
-  m->plan.long_thr = rb ? INT32_MAX : 32 * S;
+  m->plan.long_thr = kernel == 0 ? 32 * S : INT32_MAX;
+  GKO_TRY(build_merge_corners(m, (cudaStream_t)stream));
   GKO_TRY(build_long_split(m, (cudaStream_t)stream));
   for (auto& kv : m->lowp) {  // low-precision copies share the pattern
     if (kv.second->fmt == GKO_CSR) {
@@ -439,6 +481,8 @@ int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int3
       q.long_chunk_ptr = m->plan.long_chunk_ptr;
       q.chunk_row = m->plan.chunk_row;
       q.chunk_start = m->plan.chunk_start;
+      q.merge_x = m->plan.merge_x;
+      q.merge_tiles = m->plan.merge_tiles;
     }
   }
   return GKO_OK;
@@ -585,6 +629,8 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   m->plan.long_chunk_ptr = src->plan.long_chunk_ptr;
   m->plan.chunk_row = src->plan.chunk_row;
   m->plan.chunk_start = src->plan.chunk_start;
+  m->plan.merge_x = src->plan.merge_x;
+  m->plan.merge_tiles = src->plan.merge_tiles;
   m->K = src->K;
   m->stride = src->stride;
   m->ell_col = src->ell_col;
@@ -629,7 +675,7 @@ int gko_matrix_info(gko_matrix m, gko_format* format, gko_dtype* dtype, int64_t*
     int64_t b = 0;
     for (const Buf* x : {&m->row_ptr, &m->col, &m->val, &m->ell_col, &m->ell_val, &m->coo_row, &m->coo_col,
                          &m->coo_val, &m->plan.long_rows, &m->plan.long_chunk_ptr, &m->plan.chunk_row,
-                         &m->plan.chunk_start})
+                         &m->plan.chunk_start, &m->plan.merge_x})
       if (*x) b += (int64_t)(*x)->bytes;
     *bytes = b;
   }

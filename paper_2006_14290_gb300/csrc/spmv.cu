@@ -7,6 +7,7 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
   const size_t at = A->dtype == GKO_F64 ? 8 : 4;
   switch (A->fmt) {
     case GKO_CSR:
+      if (A->plan.kind == 2) return at * 2 * (size_t)((A->n_rows + A->nnz + 2047) / 2048 + 1);
       return at * (size_t)A->plan.n_chunks;
     case GKO_ELL:
       return 0;
@@ -17,7 +18,9 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
   return 0;
 }
 
-bool spmv_fuses_dot(const gko_matrix_s* A) { return A->fmt == GKO_CSR || A->fmt == GKO_ELL; }
+bool spmv_fuses_dot(const gko_matrix_s* A) {
+  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL;
+}
 
 int spmv_run(const gko_matrix_s* A, const void* x, void* y, double alpha, double beta, cudaStream_t s, void* scratch,
              const DotSpec* dot, const int* gate) {

@@ -276,6 +276,162 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
   if (DOT && !timed_out) dot_epilogue2<kRbThreads>(dwy, dyy, d, blockIdx.x, expected);
 }
 
+// ------------------------------------------------------- merge-path CSR --
+//
+// Merge-path CSR (skewed matrices): the merged sequence of n row ends and
+// nnz nonzeros is cut into equal pieces of kMergeItems per thread (tiles of
+// 256 threads), so a row of any length spreads over as many threads and
+// tiles as it needs.  The tile corners on the merge path are computed once
+// per matrix (plan); a tile stages its row pointers and nonzeros in shared
+// memory, each thread finds its start (row x, nonzero y) by binary search
+// there, then walks its items: a nonzero adds one FMA, a row end finishes
+// the row.  Rows entering a thread take the trailing
+// partials of the preceding threads (shared-memory walk back, as in the COO
+// kernel); rows crossing tiles are finished by csr_merge_fixup_kernel from
+// per-tile carries, in tile order.
+
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = 256 * kMergeItems;
+
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256) csr_merge_kernel(CsrArgs<VT, XT> a, int64_t nnz,
+                                                        const int32_t* __restrict__ corner_x,
+                                                        acc_t<VT>* __restrict__ carry, const int* gate) {
+  using AT = acc_t<VT>;
+  __shared__ int32_t s_rp[kMergeTile + 2];  // rp[x0 .. x1 + 1] of the tile
+  __shared__ int32_t s_col[kMergeTile];
+  __shared__ VT s_val[kMergeTile];
+  __shared__ AT s_tail[256];
+  __shared__ int s_end[256];
+  if (gated(gate)) return;
+  const int t = threadIdx.x;
+  const int64_t total = a.n + nnz;
+  const int64_t tile = blockIdx.x;
+  const int64_t dt0 = tile * kMergeTile;
+  const int64_t dt1 = dt0 + kMergeTile < total ? dt0 + kMergeTile : total;
+  // the tile's corners on the merge path (computed once per matrix)
+  const int64_t x0 = __ldg(corner_x + tile), x1 = __ldg(corner_x + tile + 1);
+  const int64_t y0 = dt0 - x0, y1 = dt1 - x1;
+  const int nrows = (int)(x1 - x0), nnzt = (int)(y1 - y0);
+  // stage the tile's row pointers and nonzeros (coalesced, loads first)
+  for (int i = t; i <= nrows + 1; i += 256) s_rp[i] = (x0 + i <= a.n) ? __ldg(a.rp + x0 + i) : (int32_t)nnz;
+#pragma unroll
+  for (int h = 0; h < kMergeItems; ++h) {
+    const int k = t + 256 * h;
+    if (k < nnzt) {
+      s_col[k] = ld_stream(a.col + y0 + k);
+      s_val[k] = ld_stream(a.val + y0 + k);
+    }
+  }
+  __syncthreads();
+  const bool first_open = x0 < a.n && y0 > (int64_t)s_rp[0];
+  // this thread's start inside the tile: local merge path over s_rp[1..]
+  const int dl = t * kMergeItems;
+  const int tile_items = (int)(dt1 - dt0);
+  int xl = 0, yl = 0;
+  if (dl < tile_items) {
+    int lo = dl - nnzt > 0 ? dl - nnzt : 0;
+    int hi = dl < nrows ? dl : nrows;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)s_rp[mid + 1] <= y0 + (dl - mid - 1))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    xl = lo;
+    yl = dl - lo;
+  }
+  const int steps = dl < tile_items ? min(kMergeItems, tile_items - dl) : 0;
+  AT run = AT(0), first_sum = AT(0);
+  int64_t first_row = -1;
+  int nends = 0;
+  int64_t y = y0 + yl;
+  int64_t row_end = s_rp[xl + 1];
+  for (int st = 0; st < steps; ++st) {
+    if (y < row_end) {
+      const int k = (int)(y - y0);
+      run = madd(to_acc(s_val[k]), to_acc(ld_vec(a.x + s_col[k])), run);
+      ++y;
+    } else {
+      const int64_t row = x0 + xl;
+      if (nends == 0) {
+        first_sum = run;
+        first_row = row;
+      } else {
+        a.y[row] = (XT)finish_row(a.y, row, run, a.alpha, a.beta, a.plain);
+      }
+      ++nends;
+      run = AT(0);
+      ++xl;
+      row_end = s_rp[xl + 1];
+    }
+  }
+  s_tail[t] = run;
+  s_end[t] = nends > 0;
+  __syncthreads();
+  if (nends > 0) {
+    AT in = AT(0);
+    bool from_before_tile = true;
+    for (int u = t - 1; u >= 0; --u) {
+      in += s_tail[u];
+      if (s_end[u]) {
+        from_before_tile = false;
+        break;
+      }
+    }
+    const AT tot = in + first_sum;
+    if (from_before_tile && first_open)
+      carry[2 * tile] = tot;
+    else
+      a.y[first_row] = (XT)finish_row(a.y, first_row, tot, a.alpha, a.beta, a.plain);
+  }
+  if (t == 0) {
+    AT tv = AT(0);
+    bool any_end = false;
+    for (int u = 255; u >= 0; --u) {
+      tv += s_tail[u];
+      if (s_end[u]) {
+        any_end = true;
+        break;
+      }
+    }
+    if (!any_end) carry[2 * tile] = tv;
+    carry[2 * tile + 1] = tv;
+  }
+}
+
+// Rows that cross tiles: the tile where such a row starts adds its trailing
+// partial and the first-segment partials of the following tiles.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256)
+    csr_merge_fixup_kernel(CsrArgs<VT, XT> a, int64_t nnz, int64_t tiles, const int32_t* __restrict__ corner_x,
+                           const acc_t<VT>* __restrict__ carry, const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  const int64_t total = a.n + nnz;
+  auto corner = [&](int64_t u, int64_t& cx, int64_t& cy) {
+    const int64_t d = u * kMergeTile < total ? u * kMergeTile : total;
+    cx = __ldg(corner_x + u);
+    cy = d - cx;
+  };
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t xs, ys, xe, ye;
+    corner(t, xs, ys);
+    corner(t + 1, xe, ye);
+    if (xe >= a.n) continue;
+    if (!(ye > (int64_t)__ldg(a.rp + xe))) continue;  // row xe has not started: nothing open
+    const bool starts_here = xe > xs || ys <= (int64_t)__ldg(a.rp + xs);
+    if (!starts_here) continue;  // middle of a longer row
+    AT s = carry[2 * t + 1];
+    for (int64_t u = t + 1; u < tiles; ++u) {
+      s += carry[2 * u];
+      if (__ldg(corner_x + u + 1) > __ldg(corner_x + u)) break;  // the row ends in tile u
+    }
+    a.y[xe] = (XT)finish_row(a.y, xe, s, a.alpha, a.beta, a.plain);
+  }
+}
+
 // Nonzero split of long rows: one warp per fixed-size chunk of a long row,
 // partial sums to scratch.
 template <typename VT, typename XT>
@@ -774,6 +930,18 @@ struct SpmvImpl {
 
   static int csr(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s, void* scratch,
                  const DotSpec* dot, const int* gate) {
+    if (A->plan.kind == 2) {  // merge path (no fused dot)
+      const int64_t total = A->n_rows + A->nnz;
+      const int64_t tiles = (total + kMergeTile - 1) / kMergeTile;
+      AT* carry = static_cast<AT*>(scratch);
+      const CsrArgs<VT, XT> ca = csr_args(A, x, y, alpha, beta);
+      const int32_t* cx = ptr<int32_t>(A->plan.merge_x);
+      csr_merge_kernel<VT, XT><<<(unsigned)tiles, 256, 0, s>>>(ca, A->nnz, cx, carry, gate);
+      const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tiles + 255) / 256, 4096));
+      csr_merge_fixup_kernel<VT, XT><<<fg, 256, 0, s>>>(ca, A->nnz, tiles, cx, carry, gate);
+      GKO_TRY_CUDA(cudaGetLastError());
+      return GKO_OK;
+    }
     const bool has_long = A->plan.n_long > 0;
     DotSpec d = dot ? *dot : DotSpec{};
     const int64_t fix_blocks =

@@ -135,20 +135,19 @@ def test_plan_histogram_and_split(gko):
             assert (p["kernel"], p["subwarp"], p["rows_per_subwarp"], p["stage_cap"], p["n_long_rows"]) == \
                 (1, S, R, 1024, 0)
             continue
-        short = L[L < 1024]
-        mean = short.mean() if short.size else 1.0
-        S = 1
-        while S < 32 and S < mean:
-            S *= 2
-        assert p["kernel"] == 0 and p["subwarp"] == S and p["long_threshold"] == 32 * S and p["rows_per_subwarp"] == 2
-        longs = L[L > 32 * S]
+        assert p["kernel"] == 2 and p["n_long_rows"] == 0  # skewed: merge path
+        M = G.from_csr(A)
+        M.set_plan(0, 8, 2)
+        p = M.plan()
+        longs = L[L > 32 * 8]
+        assert p["kernel"] == 0 and p["long_threshold"] == 256
         assert p["n_long_rows"] == longs.size
         assert p["n_long_chunks"] == int(np.sum((longs + 1023) // 1024))
 
 
 PLANS = ([(0, S, R, 2048) for S in (1, 2, 4, 8, 16, 32) for R in (1, 2, 4)]
          + [(1, S, R, cap) for S in (1, 2, 4, 8) for R in (1, 2, 4) for cap in (512, 2048)]
-         + [(1, 1, 4, 8192), (1, 2, 1, 1024)])
+         + [(1, 1, 4, 8192), (1, 2, 1, 1024), (2, 1, 1, 2048)])
 
 
 @pytest.mark.parametrize("kernel,S,R,cap", PLANS)
