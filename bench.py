@@ -420,6 +420,26 @@ def cpu_baseline(mats, budget_s=12.0):
             "sample": f"FP64 CSR SpMV on the three sweep matrices, {reps} passes ({dt:.1f} s), OpenMP over rows"}
 
 
+# ------------------------------------------------------------ multi-rank --
+
+def ranks_max(values, device):
+    """Element-wise maximum over all ranks (the slowest rank's times); the
+    identity on one rank.  Works with NCCL (CUDA tensors) and gloo (CPU)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_gbs(world, bytes_per_rank, ms):
+    """Whole-job throughput: every rank processes bytes_per_rank per step
+    (replicas, weak scaling); time is the slowest rank's."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- our path --
 
 def build_cases(G, mats, dev):
@@ -571,11 +591,7 @@ def run_ours(args):
     flush_ms = f0.elapsed_time(f1)
     e2e_ms = max(e2e_ms_step - flush_ms, 1e-9)
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([kernel_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        kernel_ms, e2e_ms = float(t[0]), float(t[1])
+    kernel_ms, e2e_ms = ranks_max([kernel_ms, e2e_ms], dev)
 
     peak, peak_kind = measured_peaks()
     dom = int(np.argmax(per_case_ms))
@@ -585,7 +601,7 @@ def run_ours(args):
     tr = traffic_record()
     if tr and dom_case["label"] in tr.get("per_case_bytes", {}):
         traffic = tr["per_case_bytes"][dom_case["label"]]
-    value = world * step_bytes / (kernel_ms * 1e-3) / 1e9
+    value = whole_job_gbs(world, step_bytes, kernel_ms)
     if rank == 0:
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -602,7 +618,7 @@ def run_ours(args):
                                       "GB_s": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9, 1),
                                       "frac": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9 / peak, 4)}
                          for i, c in enumerate(cases)},
-            "e2e": {"value": round(world * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "e2e": {"value": round(whole_job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(sum(c["x"].numel() * c["x"].element_size() for c in cases)),
                     "d2h_bytes_per_step": int(sum(c["y"].numel() * c["y"].element_size() for c in cases))},
             "wall_ms_per_step_incl_flush": round(wall_ms, 4),

@@ -276,3 +276,20 @@ def test_full_size_sampled(gko, name):
     yd = dev(np.zeros(A.n_rows, np.float32))
     G.gko_spmv(1.0, M32, dev(x32), 0.0, yd)
     check_spmv_f32(host(yd)[idx], sub, x32.astype(np.float64), 1.0, 0.0, None, sub.val.astype(np.float32).astype(np.float64))
+
+
+def test_memory_budget_refuses_and_recovers(gko):
+    G = gko
+    A = I.laplace2d_5pt(64)
+    used = G.memory_in_use()
+    G.set_memory_budget(used + 1024)
+    try:
+        with pytest.raises(G.GkoError) as e:
+            G.from_csr(A)
+        assert e.value.status == G.BUDGET_EXCEEDED
+        assert G.memory_in_use() == used
+    finally:
+        G.set_memory_budget(0)
+    M = G.from_csr(A)
+    assert G.memory_in_use() > used
+    del M
