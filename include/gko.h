@@ -219,7 +219,7 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
 #define GKO_PRECISION_MIXED_BF16 2 /* BF16-valued inner SpMV + FP64 refinement   */
 
 typedef struct {
-  int32_t restart;      /* GMRES restart length m (<= 0: 30)                     */
+  int32_t restart;      /* GMRES restart length m (<= 0: 30; at most 128)        */
   int32_t precision;    /* GKO_PRECISION_*                                       */
   double inner_tol;     /* mixed: inner relative tolerance (<= 0: 1e-5)          */
   int32_t max_outer;    /* mixed: refinement steps (<= 0: 30)                    */
@@ -249,8 +249,10 @@ typedef struct {
  * CG: Hestenes-Stiefel (Saad Alg. 6.18); breakdown when p.Ap <= 0.
  * BiCGSTAB: van der Vorst 1992 (Saad Alg. 7.7); breakdown on exact zeros
  *      of rhat.r, rhat.v, t.t or omega.
- * GMRES(m): Saad-Schultz restarted GMRES with classical Gram-Schmidt applied
- *      twice (CGS2) and Givens rotations on the device; iterations count
+ * GMRES(m): Saad-Schultz restarted GMRES with classical Gram-Schmidt and
+ *      selective reorthogonalisation (a second pass when the first shrinks
+ *      ||w|| below 1/sqrt(2) of its norm after A v_j) and Givens rotations on
+ *      the device; iterations count
  *      Arnoldi steps, outer_iterations restart cycles; each cycle starts
  *      from the true residual.
  * Mixed precision (opts->precision): x stays FP64; each refinement step

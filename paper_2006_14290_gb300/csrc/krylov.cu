@@ -36,8 +36,9 @@ struct Ctl {
   int replace;
   int check_true;
   int cycles;
-  int k;  // GMRES: columns of the finished cycle
-  int pad[2];
+  int k;         // GMRES: columns of the finished cycle
+  int noreorth;  // GMRES: this step skips the second Gram-Schmidt pass
+  int pad;
   double nb, tol_abs;
   double rho, rho_new, alpha, beta, omega;
   double red[4];  // fused SpMV dots: red[0] = w.y, red[1] = y.y
@@ -577,8 +578,8 @@ __global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ldv,
                                                           const T* __restrict__ w, double* __restrict__ partials,
-                                                          Ctl* c) {
-  if (gated(&c->phase)) return;
+                                                          Ctl* c, int pass) {
+  if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
   const int j = blockIdx.y;
   const T* v = V + (int64_t)j * ldv;
   double acc = 0.0;
@@ -588,8 +589,9 @@ __global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __
 }
 
 __global__ void __launch_bounds__(256) gm_multidot_finish_kernel(int g, const double* __restrict__ partials,
-                                                                 double* __restrict__ h, int accumulate, Ctl* c) {
-  if (gated(&c->phase)) return;
+                                                                 double* __restrict__ h, int accumulate, Ctl* c,
+                                                                 int pass) {
+  if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
   const int j = blockIdx.x;
   double acc = 0.0;
   for (int i = threadIdx.x; i < g; i += 256) acc += partials[(int64_t)j * kMultiSlots + i];
@@ -599,27 +601,58 @@ __global__ void __launch_bounds__(256) gm_multidot_finish_kernel(int g, const do
 
 struct StoreRr {
   Ctl* c;
-  __device__ void operator()(const double (&t)[1]) const { c->rr = t[0]; }
+  int decide;  // first pass: skip the second pass unless ||w|| fell below ||w0|| / sqrt(2)
+  __device__ void operator()(const double (&t)[1]) const {
+    c->rr = t[0];
+    if (decide) c->noreorth = t[0] >= 0.5 * c->red[0] ? 1 : 0;
+  }
 };
 
 // w -= sum_{j<=jmax} h_j V_j (h: device, the pass's coefficients); with
 // NORM also reduces ||w||^2 into c->rr.
+constexpr int kMaxRestart = 128;
+
+// -h_j as the coefficient pair of Lin<T>, built once per block
+template <typename T>
+__device__ __forceinline__ void load_coefs(const double* h, int count, double sign, T* hi, T* lo) {
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const double a = sign * h[j];
+    if constexpr (sizeof(T) == 4) {
+      const float f = __double2float_rn(a);
+      hi[j] = f;
+      lo[j] = __double2float_rn(a - (double)f);
+    } else {
+      hi[j] = a;
+      lo[j] = 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T lin_apply(T hi, T lo, T x, T y) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(lo, x, __fmaf_rn(hi, x, y));
+  else return __fma_rn(hi, x, y);
+}
+
 template <typename T, bool NORM>
 __global__ void __launch_bounds__(256) gm_axpy_kernel(int64_t n, int jcount, const double* __restrict__ h,
                                                       const T* __restrict__ V, int64_t ldv, T* __restrict__ w, Ctl* c,
-                                                      RedWs ws) {
-  if (gated(&c->phase)) return;
+                                                      RedWs ws, int pass) {
+  __shared__ T s_hi[kMaxRestart + 1], s_lo[kMaxRestart + 1];
+  if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
+  load_coefs<T>(h, jcount, -1.0, s_hi, s_lo);
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
     T v = w[i];
-    for (int j = 0; j < jcount; ++j) v = Lin<T>(-__ldg(h + j))(V[(int64_t)j * ldv + i], v);
+    for (int j = 0; j < jcount; ++j) v = lin_apply<T>(s_hi[j], s_lo[j], V[(int64_t)j * ldv + i], v);
     w[i] = v;
     if (NORM) {
       const double ow = wd(v);
       acc[0] = __fma_rn(ow, ow, acc[0]);
     }
   }
-  if (NORM) reduce_op<1>(acc, ws, StoreRr{c});
+  if (NORM) reduce_op<1>(acc, ws, StoreRr{c, pass == 0});
 }
 
 // Column j of the Hessenberg matrix from the two CGS passes, previous Givens
@@ -630,7 +663,8 @@ __global__ void gm_givens_kernel(int j, int m, const double* __restrict__ h1, co
                                  double* __restrict__ g, Ctl* c) {
   if (gated(&c->phase)) return;
   double* col = H + (int64_t)j;  // H[i*m + j]
-  for (int i = 0; i <= j; ++i) col[(int64_t)i * m] = h1[i] + h2[i];
+  const bool two = !c->noreorth;
+  for (int i = 0; i <= j; ++i) col[(int64_t)i * m] = two ? h1[i] + h2[i] : h1[i];
   const double hn = sqrt(c->rr);
   col[(int64_t)(j + 1) * m] = hn;
   for (int i = 0; i < j; ++i) {
@@ -687,11 +721,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) gm_update_x_kernel(int64_t n, const double* __restrict__ ny,
                                                           const T* __restrict__ V, int64_t ldv, T* __restrict__ x,
                                                           Ctl* c) {
+  __shared__ T s_hi[kMaxRestart + 1], s_lo[kMaxRestart + 1];
   if (gated(&c->done)) return;
   const int k = c->k;
+  load_coefs<T>(ny, k, -1.0, s_hi, s_lo);
   GKO_GRID_LOOP(i, n) {
     T v = x[i];
-    for (int j = 0; j < k; ++j) v = Lin<T>(-__ldg(ny + j))(V[(int64_t)j * ldv + i], v);
+    for (int j = 0; j < k; ++j) v = lin_apply<T>(s_hi[j], s_lo[j], V[(int64_t)j * ldv + i], v);
     x[i] = v;
   }
 }
@@ -934,15 +970,15 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       gm_scale_kernel<T><<<vg, 256, 0, s>>>(n, V, &c->beta, c);
       for (int j = 0; j < m; ++j) {
         T* vj = V + (int64_t)j * ld;
-        GKO_TRY(spmv(vj, w, nullptr, &c->phase));
+        // w = A v_j with ||w||^2 from the SpMV epilogue (red[0])
+        GKO_TRY(spmv(vj, w, w, &c->phase));
+        // classical Gram-Schmidt; the second pass runs only when the first
+        // shrank ||w|| below ||w0|| / sqrt(2) (selective reorthogonalisation)
         for (int pass = 0; pass < 2; ++pass) {
           double* hp = pass == 0 ? h1 : h2;
-          gm_multidot_kernel<T><<<dim3((unsigned)mg, (unsigned)(j + 1)), 256, 0, s>>>(n, V, ld, w, mpart, c);
-          gm_multidot_finish_kernel<<<j + 1, 256, 0, s>>>((int)mg, mpart, hp, 0, c);
-          if (pass == 0)
-            gm_axpy_kernel<T, false><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws);
-          else
-            gm_axpy_kernel<T, true><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws);
+          gm_multidot_kernel<T><<<dim3((unsigned)mg, (unsigned)(j + 1)), 256, 0, s>>>(n, V, ld, w, mpart, c, pass);
+          gm_multidot_finish_kernel<<<j + 1, 256, 0, s>>>((int)mg, mpart, hp, 0, c, pass);
+          gm_axpy_kernel<T, true><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws, pass);
         }
         gm_givens_kernel<<<1, 1, 0, s>>>(j, m, h1, h2, H, cs, sn, g, c);
         if (j + 1 <= m) gm_next_kernel<T><<<vg, 256, 0, s>>>(n, w, V + (int64_t)(j + 1) * ld, c);
@@ -1047,6 +1083,7 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   sp.rel_tol = rel_tol;
   sp.maxit = max_iters;
   sp.restart = o.restart > 0 ? o.restart : 30;
+  if (sp.restart > kMaxRestart) return fail(GKO_INVALID_ARG, "GMRES restart length is limited to 128");
   sp.check_true = 1;
   sp.check_every = o.check_every;
   double nb = 0.0;
