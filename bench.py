@@ -472,6 +472,8 @@ def build_cases(G, mats, dev):
                 nb = spmv_bytes(fmt, A.n_rows, A.n_cols, A.nnz, ell_nnz, inf["coo_nnz"], sv, sv, sv)
                 coo_launches = 2 if inf["coo_nnz"] > 0 else 0
                 csr_launches = 2 if plan["kernel"] == 2 else 1 + (2 if plan["n_long_rows"] > 0 else 0)
+                if fmt == "coo" and M.plan()["kernel"] == 1:
+                    coo_launches = 1  # row-block COO: one launch, no tile fix-up
                 launches = {"csr": csr_launches, "ell": 1,
                             "coo": coo_launches if coo_launches else 1, "hybrid": 1 + coo_launches}[fmt]
                 x = x64 if dt == "f64" else x32

@@ -136,29 +136,40 @@ GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void
                       void *ell_val, int32_t *coo_row, int32_t *coo_col, void *coo_val,
                       void *stream);
 
-/* CSR load-balancing plan (built at creation from the row-length histogram).
- * kernel 1, the row-block kernel (regular matrices: longest row <= 4x the
- * mean): row blocks stream into shared memory by bulk copies in stages of
- * stage_cap entries; `subwarp` lanes sum each row, each subwarp owning
+/* Load-balancing plan of a CSR or COO handle (CSR: built at creation from
+ * the row-length histogram; COO: taken from the CSR it was converted from).
+ * CSR kernel 1, the row-block kernel (regular matrices: longest row <= 4x
+ * the mean): row blocks stream into shared memory by bulk copies in stages
+ * of stage_cap entries; `subwarp` lanes sum each row, each subwarp owning
  * rows_per_subwarp interleaved rows of a block of 128 threads.
- * kernel 2, the merge-path kernel (skewed matrices, the default there): the
- * merged sequence of row ends and nonzeros is split into equal shares per
- * thread, so long rows spread over many threads and tiles.
- * kernel 0, the subwarp kernel: `subwarp` lanes per row, rows_per_subwarp
- * rows per pass, and rows longer than long_threshold split into fixed-size
- * nonzero chunks (n_long_rows rows, n_long_chunks chunks).
+ * Handles with FP32 or BF16 values use a quarter of the FP64 lanes per row
+ * (at least 1) and, when that changes the width, two rows per subwarp.
+ * CSR kernel 2, the merge-path kernel (skewed matrices, the default there):
+ * the merged sequence of row ends and nonzeros is split into equal shares
+ * per thread, so long rows spread over many threads and tiles.
+ * CSR kernel 0, the subwarp kernel: `subwarp` lanes per row,
+ * rows_per_subwarp rows per pass, and rows longer than long_threshold split
+ * into fixed-size nonzero chunks (n_long_rows rows, n_long_chunks chunks).
+ * COO kernel 1: the row-block schedule over the COO arrays (row blocks start
+ * at precomputed entries; each stage also carries the row indices, from
+ * which the block finds its rows' ranges); COO kernel 0: the tiled segmented
+ * reduction (the paper's COO scheme, the default for skewed matrices).
  * hist33: row-length histogram in log2 classes (hist[0]: empty rows;
- * hist[b], b >= 1: lengths in [2^(b-1), 2^b)).  Any output may be NULL. */
-GKO_API int gko_matrix_plan(gko_matrix csr, int32_t *kernel, int32_t *subwarp, int32_t *rows_per_subwarp,
+ * hist[b], b >= 1: lengths in [2^(b-1), 2^b)).  Any output may be NULL.
+ * GKO_INVALID_ARG for other formats. */
+GKO_API int gko_matrix_plan(gko_matrix m, int32_t *kernel, int32_t *subwarp, int32_t *rows_per_subwarp,
                             int32_t *stage_cap, int32_t *long_threshold, int64_t *n_long_rows,
                             int64_t *n_long_chunks, int64_t *hist33);
 
-/* Override the CSR plan (the autotuner's knob).  kernel 0: subwarp S in
- * 1,2,4,8,16,32, R in 1,2,4, long-row threshold 32*S; kernel 1: row-block,
- * S in 1,2,4,8, R in 1,2,4, stage_cap a power of two in 512..8192 (ignored
- * otherwise); kernel 2: merge path (S, R still validated, unused).  Low-precision copies made by gko_matrix_convert_values
- * keep their own plan.  Synchronises `stream`. */
-GKO_API int gko_matrix_set_plan(gko_matrix csr, int32_t kernel, int32_t subwarp, int32_t rows_per_subwarp,
+/* Override the plan (the autotuner's knob).  CSR kernel 0: subwarp S in
+ * 1,2,4,8,16,32, R in 1,2,4, long-row threshold 32*S; CSR kernel 1:
+ * row-block, S in 1,2,4,8, R in 1,2,4, stage_cap a power of two in
+ * 512..8192 (ignored otherwise); CSR kernel 2: merge path (S, R still
+ * validated, unused).  COO kernel 1: row-block, S in 1,2,4,8, R in 1,2,4,
+ * stage_cap a power of two in 512..4096; COO kernel 0 or 2: segmented
+ * reduction.  The solvers' cached low-precision copies follow; handles made by
+ * gko_matrix_convert_values keep their own plan.  Synchronises `stream`. */
+GKO_API int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t subwarp, int32_t rows_per_subwarp,
                                 int32_t stage_cap, void *stream);
 
 GKO_API int gko_matrix_destroy(gko_matrix m);

@@ -86,6 +86,16 @@ size_t dtype_size(gko_dtype t);
 constexpr int kHistBins = 33;
 constexpr int32_t kLongChunk = 1024;  // nonzeros per chunk of a long CSR row
 constexpr int kRbThreads = 128;      // TMA row-block CSR kernel: threads per block
+constexpr int kCooRbMaxCap = 4096;   // row-block COO: largest stage
+constexpr unsigned kRbStages = 2;    // row-block kernels: shared-memory stages (double buffering)
+
+// Dynamic shared memory of a row-block launch: barriers, kRbStages buffers
+// of `cap` entries (column, value and, for COO, row) and the COO row-start
+// table.
+inline size_t rb_smem_need(int cap, size_t value_bytes, bool coo) {
+  const size_t per = sizeof(int32_t) + value_bytes + (coo ? sizeof(int32_t) : 0);
+  return 128 + (size_t)kRbStages * (size_t)cap * per + (coo ? 4 * (size_t)(4 * kRbThreads + 4) : 0);
+}
 
 // Load-balancing plan of the CSR SpMV, built from the row-length histogram.
 struct CsrPlan {
@@ -104,6 +114,10 @@ struct CsrPlan {
   Buf chunk_start;     // int32[n_chunks]   first nonzero of each chunk
   Buf merge_x;         // int32[tiles+1]    merge-path row coordinate of each tile corner
   int64_t merge_tiles = 0;
+  // COO handles: kind 1 runs the row-block kernel over the COO arrays, any
+  // other kind the tiled segmented reduction.
+  Buf coo_rb;          // int32[n_rb+1]     first COO entry of each row block of (128/S)*R rows
+  int64_t coo_rb_n = 0;
 };
 
 }  // namespace gko

@@ -12,6 +12,8 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
     case GKO_ELL:
       return 0;
     case GKO_COO:
+      if (A->plan.kind == 1) return 0;
+      return at * 2 * (size_t)((A->coo_nnz + kCooTile - 1) / kCooTile);
     case GKO_HYBRID:
       return at * 2 * (size_t)((A->coo_nnz + kCooTile - 1) / kCooTile);
   }
@@ -19,7 +21,8 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
 }
 
 bool spmv_fuses_dot(const gko_matrix_s* A) {
-  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL;
+  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL ||
+         (A->fmt == GKO_COO && A->plan.kind == 1 && A->coo_nnz > 0);
 }
 
 int spmv_run(const gko_matrix_s* A, const void* x, void* y, double alpha, double beta, cudaStream_t s, void* scratch,

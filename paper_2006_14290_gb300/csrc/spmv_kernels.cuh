@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "reduce.cuh"
 #include "spmv.cuh"
@@ -51,6 +52,10 @@ struct CsrArgs {
   acc_t<VT> alpha, beta;
   int32_t long_thr;
   bool plain;
+  // row-block COO only: the row index of every entry and the first entry of
+  // every row block (rb_ptr[b] = first k with row[k] >= b*RB)
+  const int32_t* row = nullptr;
+  const int32_t* rb_ptr = nullptr;
 };
 
 // Subwarp-per-row CSR (irregular matrices): a subwarp of S lanes owns R
@@ -129,22 +134,33 @@ __global__ void __launch_bounds__(256) csr_subwarp_kernel(CsrArgs<VT, XT> a, Dot
 // block fits one stage, so every thread has work in every stage.  Global
 // loads are bulk and coalesced, and with S = 1 a row needs no reduction, so
 // every FP64 FMA lane is busy.
+//
+// The COO variant (coo_rowblock_kernel, regular matrices in COO) keeps the
+// same schedule; row blocks start at rb_ptr[b], computed once per matrix from
+// the row indices.  Its stages also carry the row index of every entry, and
+// before a stage is consumed the block turns those indices into the stage
+// offset where each of its rows begins (sb[j] = first staged entry whose row
+// is >= the block's row j, entries outside the row block clamped to the
+// ends).  Row j then sums staged entries [sb[j], sb[j+1]), so no partial sum
+// crosses a thread and no row needs a carry or a second launch.
 template <typename VT>
-inline size_t rb_smem_bytes(int cap) {
-  return 128 + 2 * (size_t)cap * (sizeof(int32_t) + sizeof(VT));
+inline size_t rb_smem_bytes(int cap, bool coo = false) {
+  return rb_smem_need(cap, sizeof(VT), coo);
 }
 
-template <int S, int R, typename VT, typename XT, bool DOT>
-__global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
-                                                                   int expected, const int* gate, int* err) {
+template <int S, int R, typename VT, typename XT, bool DOT, bool COO>
+__device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap, const DotSpec& d, int expected,
+                                              int* err) {
+  constexpr unsigned NS = kRbStages;
   using AT = acc_t<VT>;
   constexpr int G = kRbThreads / S;  // subwarps per block
   constexpr int RB = G * R;          // rows per row block
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
-  VT* sval = reinterpret_cast<VT*>(smem + 128 + 2 * (size_t)cap * sizeof(int32_t));
-  if (gated(gate)) return;
+  int32_t* srow = reinterpret_cast<int32_t*>(smem + 128 + (size_t)NS * cap * sizeof(int32_t));
+  VT* sval = reinterpret_cast<VT*>(smem + 128 + (size_t)NS * cap * sizeof(int32_t) * (COO ? 2 : 1));
+  int32_t* sb = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(sval) + (size_t)NS * cap * sizeof(VT));
   const int64_t nrb = (a.n + RB - 1) / RB;
   if ((int64_t)blockIdx.x >= nrb) return;
   const int tid = threadIdx.x;
@@ -153,19 +169,20 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
   const unsigned mask = subwarp_mask<S>();
 
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (unsigned i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
     mbar_fence_init();
   }
   __syncthreads();
 
   struct Cur {
-    int64_t b, kb, ke;
+    int64_t b, kb, ke, k0, k1;
     int j, nch;
   };
   auto open = [&](Cur& c) {
-    const int32_t k0 = __ldg(a.rp + c.b * RB);
-    const int32_t k1 = __ldg(a.rp + min((c.b + 1) * RB, a.n));
+    const int32_t k0 = COO ? __ldg(a.rb_ptr + c.b) : __ldg(a.rp + c.b * RB);
+    const int32_t k1 = COO ? __ldg(a.rb_ptr + c.b + 1) : __ldg(a.rp + min((c.b + 1) * RB, a.n));
+    c.k0 = k0;
+    c.k1 = k1;
     c.kb = (int64_t)(k0 & ~7);
     c.ke = ((int64_t)k1 + 7) & ~7ll;
     c.nch = (int)imax64(1, (c.ke - c.kb + cap - 1) / cap);
@@ -185,8 +202,9 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
       mbar_arrive(&bar[stage]);
     } else {
       const unsigned bc = (unsigned)(len * sizeof(int32_t)), bv = (unsigned)(len * sizeof(VT));
-      mbar_arrive_expect_tx(&bar[stage], bc + bv);
+      mbar_arrive_expect_tx(&bar[stage], (COO ? 2 * bc : bc) + bv);
       bulk_g2s(scol + (size_t)stage * cap, a.col + cs, bc, &bar[stage]);
+      if (COO) bulk_g2s(srow + (size_t)stage * cap, a.row + cs, bc, &bar[stage]);
       bulk_g2s(sval + (size_t)stage * cap, a.val + cs, bv, &bar[stage]);
     }
   };
@@ -196,16 +214,17 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
   open(c);
   Cur p = c;
   bool p_ok = true;
+  unsigned issued = 0;  // stages issued so far (thread 0)
   if (tid == 0) {
-    issue(p, 0);
-    p_ok = advance(p);
-    if (p_ok) {
-      issue(p, 1);
+    for (unsigned i = 0; i < NS && p_ok; ++i) {
+      issue(p, i);
+      ++issued;
       p_ok = advance(p);
     }
   }
   int32_t rs[R], re[R];
   auto row_bounds = [&](int64_t b) {
+    if (COO) return;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t i = b * RB + sg + (int64_t)r * G;
@@ -223,20 +242,58 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
   double dwy = 0.0, dyy = 0.0;
   bool timed_out = false;
   for (unsigned q = 0;; ++q) {
-    const int stage = q & 1;
-    const bool ok = mbar_wait(&bar[stage], (q >> 1) & 1u, err);
+    const int stage = (int)(q % NS);
+    const bool ok = mbar_wait(&bar[stage], (q / NS) & 1u, err);
     if (__syncthreads_or(!ok)) {
-      if (!ok) mbar_wait(&bar[stage], (q >> 1) & 1u, err);  // let our own copy land before leaving
+      // let every copy still in flight land before the block's shared memory goes
+      if (tid == 0)
+        for (unsigned u = q; u < issued; ++u) mbar_wait(&bar[u % NS], (u / NS) & 1u, err);
       timed_out = true;
       break;
     }
     const int32_t* sc = scol + (size_t)stage * cap;
     const VT* sv = sval + (size_t)stage * cap;
     const int64_t cs = c.kb + (int64_t)c.j * cap;
+    if (COO) {
+      // sb[j], j = 0..RB: first staged entry whose position is >= j, where
+      // an entry's position is its row minus the block's first row, -1 for
+      // entries staged before the row block and RB for entries after it (or
+      // past the copied length).  Positions never decrease, so each thread
+      // walks its own cap/128 consecutive entries (16-byte shared loads) and
+      // writes sb only where the position changes.
+      const int len = (int)imin64(cap, c.ke - cs);
+      const int lo_k = (int)imax64(0, imin64(len, c.k0 - cs));
+      const int hi_k = (int)imax64(0, imin64(len, c.k1 - cs));
+      const int32_t base = (int32_t)(c.b * RB);
+      const int32_t* sr = srow + (size_t)stage * cap;
+      auto pos = [&](int k, int32_t r) -> int { return k < lo_k ? -1 : (k >= hi_k ? RB : (int)(r - base)); };
+      const int E = cap / kRbThreads;  // multiple of 4 (cap >= 512)
+      const int k_begin = tid * E;
+      int pp = k_begin == 0 ? -1 : pos(k_begin - 1, sr[k_begin - 1]);
+      for (int e = 0; e < E; e += 4) {
+        const int4 v = *reinterpret_cast<const int4*>(sr + k_begin + e);
+        const int k4 = k_begin + e;
+        // common case: four entries of the row block, all in the row of the previous one
+        if (k4 >= lo_k && k4 + 4 <= hi_k && v.w - base == pp && v.x == v.w) continue;
+        const int32_t rr[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k_begin + e + u;
+          const int pk = pos(k, rr[u]);
+          if (pk != pp) {
+            for (int j = pp + 1; j <= pk; ++j) sb[j] = k;
+            pp = pk;
+          }
+        }
+      }
+      if (tid == kRbThreads - 1)
+        for (int j = pp + 1; j <= RB; ++j) sb[j] = cap;  // rows that reach the end of a full stage
+      __syncthreads();
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int lo = (int)(imax64(rs[r], cs) - cs);
-      const int hi = (int)(imin64(re[r], cs + cap) - cs);
+      const int lo = COO ? sb[sg + r * G] : (int)(imax64(rs[r], cs) - cs);
+      const int hi = COO ? sb[sg + r * G + 1] : (int)(imin64(re[r], cs + cap) - cs);
       AT acc = sum[r];
       int k = lo + rank;
       for (; k + 3 * S < hi; k += 4 * S) {
@@ -254,6 +311,7 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
     __syncthreads();  // stage consumed by everyone
     if (tid == 0 && p_ok) {
       issue(p, stage);
+      ++issued;
       p_ok = advance(p);
     }
     const bool last = c.j + 1 >= c.nch;
@@ -274,6 +332,20 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
     if (last) row_bounds(c.b);
   }
   if (DOT && !timed_out) dot_epilogue2<kRbThreads>(dwy, dyy, d, blockIdx.x, expected);
+}
+
+template <int S, int R, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
+                                                                   int expected, const int* gate, int* err) {
+  if (gated(gate)) return;
+  rowblock_body<S, R, VT, XT, DOT, false>(a, cap, d, expected, err);
+}
+
+template <int S, int R, typename VT, typename XT, bool DOT>
+__global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
+                                                                   int expected, const int* gate, int* err) {
+  if (gated(gate)) return;
+  rowblock_body<S, R, VT, XT, DOT, true>(a, cap, d, expected, err);
 }
 
 // ------------------------------------------------------- merge-path CSR --
@@ -611,6 +683,7 @@ struct CooArgs {
   const XT* x;
   XT* y;
   acc_t<VT> alpha, beta;
+  bool plain;  // alpha == 1 and beta == 0
 };
 
 template <typename VT>
@@ -666,11 +739,13 @@ __device__ __forceinline__ void seg_combine(int fp, AT vp, int& f, AT& v) {
   f = f | fp;
 }
 
+// plain: alpha == 1 and beta == 0, decided once on the host (no FP64
+// compare per row on the device)
 template <typename XT, typename AT>
-__device__ __forceinline__ void coo_store(XT* y, int32_t r, AT s, AT alpha, AT beta, bool accum) {
+__device__ __forceinline__ void coo_store(XT* y, int32_t r, AT s, AT alpha, AT beta, bool accum, bool plain) {
   if (accum) {
     y[r] = (XT)(alpha == AT(1) ? s + to_acc(y[r]) : madd(alpha, s, to_acc(y[r])));
-  } else if (alpha == AT(1) && beta == AT(0)) {
+  } else if (plain) {
     y[r] = (XT)s;
   } else {
     AT v = alpha * s;
@@ -684,6 +759,14 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
   for (int64_t r = r0; r < r1; ++r) y[r] = beta == AT(0) ? XT(0) : (XT)(beta * to_acc(y[r]));
 }
 
+// Resident blocks per SM the COO kernel's register budget is held to: 5 for
+// FP64 values (48 registers), 6 for FP32/BF16 (40).  Measured 5-10% faster
+// than the unconstrained 63/48 registers at 4/5 blocks.
+template <typename VT>
+constexpr int coo_min_blocks() {
+  return std::is_same<VT, double>::value ? 5 : 6;
+}
+
 // Tiled segmented reduction over row-sorted COO.  Each 256-thread block owns
 // a tile of 256*kCooItems entries; each thread owns kCooItems consecutive
 // entries (vector loads) and folds them with one FMA per entry, finishing
@@ -695,21 +778,20 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
 // partials go to carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
 // ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows absent from the COO
 // arrays are scaled by beta here too.
-template <typename VT, typename XT, bool ACCUM>
-__global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
-                                                          const int* gate) {
+template <typename VT, typename XT, bool ACCUM, int IPT = kCooItems, int MINB = 1>
+__global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
+                                                                const int* gate) {
   using AT = acc_t<VT>;
-  constexpr int IPT = kCooItems;
+  constexpr int kTile = kCooThreads * IPT;
   __shared__ int32_t s_first[kCooThreads + 1];
-  __shared__ int32_t s_last[kCooThreads];
   __shared__ AT s_tail[kCooThreads];
   __shared__ int s_end[kCooThreads];
   __shared__ int32_t s_prev_row;
   if (gated(gate)) return;
   const int t = threadIdx.x;
   const int64_t tile = blockIdx.x;
-  const int64_t base = tile * kCooTile;
-  const int cnt = (int)min((int64_t)kCooTile, a.nnz - base);
+  const int64_t base = tile * kTile;
+  const int cnt = (int)min((int64_t)kTile, a.nnz - base);
   const int j0 = t * IPT;
   const int my = max(0, min(IPT, cnt - j0));
 
@@ -739,43 +821,54 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
     }
   }
   s_first[t] = my > 0 ? rows[0] : INT_MAX;
-  s_last[t] = my > 0 ? rows[my - 1] : INT_MAX;
   if (t == 0) {
     s_first[kCooThreads] = (base + cnt < a.nnz) ? a.row[base + cnt] : -1;
     s_prev_row = base > 0 ? a.row[base - 1] : -1;
   }
   __syncthreads();
   const int32_t next_row = (j0 + IPT < cnt) ? s_first[t + 1] : s_first[kCooThreads];
-  const int32_t prev_tile_row = s_prev_row;
-  const bool first_open = base > 0 && prev_tile_row == s_first[0];
+  const bool first_open = base > 0 && s_prev_row == s_first[0];
+  // rows before the first entry of the matrix have no entries
+  if (!ACCUM && base == 0 && t == 0 && my > 0) coo_empty_rows(a.y, 0, (int64_t)rows[0], a.beta);
 
-  // one pass: FMA per entry; rows that start and end here are finished now
+  // one pass: FMA per entry; rows that start and end here are finished now.
+  // Rows without entries lie between a row's end and the next entry's row;
+  // the thread that owns that row end scales them by beta (rare: flagged
+  // here, done after the pass from the row indices in memory).
   AT run = AT(0), first_sum = AT(0);
   int32_t first_row = -1;
   int nends = 0;
+  bool gap = false;
+  const int32_t n_rows32 = (int32_t)a.n_rows;
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     if (u < my) {
       const int32_t r = rows[u];
-      if (!ACCUM) {
-        const int32_t pr = (u > 0) ? rows[u - 1] : (t > 0 ? s_last[t - 1] : prev_tile_row);
-        if (r != pr) coo_empty_rows(a.y, (int64_t)pr + 1, (int64_t)r, a.beta);
-      }
       run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
-      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;
+      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;  // -1 after the last entry
       if (r != nr) {
         if (nends == 0) {
           first_sum = run;
           first_row = r;
         } else {
-          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM);
+          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM, a.plain);
         }
+        if (!ACCUM) gap |= r + 1 < (nr < 0 ? n_rows32 : nr);
         ++nends;
         run = AT(0);
       }
     }
   }
-  if (!ACCUM && my > 0 && base + j0 + my == a.nnz) coo_empty_rows(a.y, (int64_t)rows[my - 1] + 1, a.n_rows, a.beta);
+  if (!ACCUM && gap) {
+#pragma unroll 1
+    for (int u = 0; u < my; ++u) {
+      const int64_t k = base + j0 + u;
+      const int32_t r = a.row[k];
+      const int32_t nr = (u + 1 < my) ? a.row[k + 1] : next_row;
+      const int32_t gap_end = nr < 0 ? n_rows32 : nr;
+      if (r != nr && r + 1 < gap_end) coo_empty_rows(a.y, (int64_t)r + 1, (int64_t)gap_end, a.beta);
+    }
+  }
   s_tail[t] = run;  // sum after this thread's last row end (all of it without one)
   s_end[t] = nends > 0;
   __syncthreads();
@@ -794,7 +887,7 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
     if (from_before_tile && first_open)
       carry[2 * tile] = total;  // the tile's first row began in an earlier tile
     else
-      coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM);
+      coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM, a.plain);
   }
   if (t == 0) {
     AT tv = AT(0);
@@ -818,24 +911,25 @@ __global__ void __launch_bounds__(kCooThreads) coo_kernel(CooArgs<VT, XT> a, acc
 template <typename VT, typename XT, bool ACCUM>
 __global__ void __launch_bounds__(256)
     coo_fixup_kernel(int64_t nnz, int64_t tiles, const int32_t* __restrict__ row, const acc_t<VT>* __restrict__ carry,
-                     XT* __restrict__ y, acc_t<VT> alpha, acc_t<VT> beta, const int* gate) {
+                     XT* __restrict__ y, acc_t<VT> alpha, acc_t<VT> beta, const int* gate,
+                     int64_t tile_size = kCooTile) {
   using AT = acc_t<VT>;
   if (gated(gate)) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t * kCooTile;
-    const int64_t e = min(b + kCooTile, nnz);  // one past the tile
+    const int64_t b = t * tile_size;
+    const int64_t e = min(b + tile_size, nnz);  // one past the tile
     if (e >= nnz || row[e - 1] != row[e]) continue;  // last segment closed
     const bool first_open = b > 0 && row[b - 1] == row[b];
     if (first_open && row[b] == row[e - 1]) continue;  // middle of a longer row
     const int32_t r = row[e - 1];
     AT s = carry[2 * t + 1];
     for (int64_t u = t + 1; u < tiles; ++u) {
-      const int64_t bu = u * kCooTile, eu = min(bu + kCooTile, nnz);
+      const int64_t bu = u * tile_size, eu = min(bu + tile_size, nnz);
       s += carry[2 * u];
       const bool open = eu < nnz && row[eu - 1] == row[eu];
       if (!(open && row[bu] == row[eu - 1])) break;
     }
-    coo_store(y, r, s, alpha, beta, ACCUM);
+    coo_store(y, r, s, alpha, beta, ACCUM, alpha == acc_t<VT>(1) && beta == acc_t<VT>(0));
   }
 }
 
@@ -857,6 +951,8 @@ int resident_blocks(K kernel, int threads, size_t smem = 0) {
   }
   return nb;
 }
+
+constexpr int kLaunchCudaError = -2;  // a launch helper's "CUDA refused", status already recorded
 
 template <typename VT, typename XT>
 struct SpmvImpl {
@@ -882,43 +978,63 @@ struct SpmvImpl {
     return (int)g;
   }
 
-  template <int S, int R, bool DOT>
+  // Row-block launch, CSR or COO (COO: col/val/row from the COO arrays and
+  // row blocks from the plan's rb_ptr).
+  template <int S, int R, bool DOT, bool COO>
   static int rowblock_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                              const DotSpec& d, int extra, const int* gate) {
-    auto kern = csr_rowblock_kernel<S, R, VT, XT, DOT>;
+    auto kern = COO ? coo_rowblock_kernel<S, R, VT, XT, DOT> : csr_rowblock_kernel<S, R, VT, XT, DOT>;
     const int cap = A->plan.cap;
-    const size_t smem = rb_smem_bytes<VT>(cap);
-    static int per_sm_cache[8] = {0};  // by log2(cap / 512)
+    const size_t smem = rb_smem_bytes<VT>(cap, COO);
+    static int per_sm_cache[8] = {};                    // by log2(cap / 512)
+    static size_t smem_allowed = 48 * 1024;             // this kernel's dynamic shared memory limit
     int slot = 0;
     while ((512 << slot) < cap && slot < 7) ++slot;
-    if (!per_sm_cache[slot]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb_smem_bytes<VT>(8192));
-      per_sm_cache[slot] = resident_blocks(kern, kRbThreads, smem);
+    if (smem > smem_allowed) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        fail(GKO_CUDA_ERROR, "row-block kernel: shared memory request refused");
+        return kLaunchCudaError;
+      }
+      smem_allowed = smem;
     }
+    if (!per_sm_cache[slot]) per_sm_cache[slot] = resident_blocks(kern, kRbThreads, smem);
     constexpr int RB = (kRbThreads / S) * R;
     int64_t g = (A->n_rows + RB - 1) / RB;
     int64_t cap_g = (int64_t)per_sm_cache[slot] * sm_count();
     if (DOT && cap_g > kDotSlots - extra) cap_g = kDotSlots - extra;
     if (g > cap_g) g = cap_g;
     if (g < 1) g = 1;
-    kern<<<(unsigned)g, kRbThreads, smem, s>>>(csr_args(A, x, y, alpha, beta), cap, d, (int)g + extra, gate,
-                                                device_error_word());
+    CsrArgs<VT, XT> ca = csr_args(A, x, y, alpha, beta);
+    if (COO) {
+      ca.rp = nullptr;
+      ca.col = ptr<int32_t>(A->coo_col);
+      ca.val = ptr<VT>(A->coo_val);
+      ca.row = ptr<int32_t>(A->coo_row);
+      ca.rb_ptr = ptr<int32_t>(A->plan.coo_rb);
+    }
+    kern<<<(unsigned)g, kRbThreads, smem, s>>>(ca, cap, d, (int)g + extra, gate, device_error_word());
     return (int)g;
+  }
+
+  template <bool DOT, bool COO>
+  static int rowblock_dispatch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
+                               const DotSpec& d, int extra, const int* gate) {
+    const int S = A->plan.S, R = A->plan.R;
+#define GKO_RB_CASE(SS, RR) \
+  if (S == SS && R == RR) return rowblock_launch<SS, RR, DOT, COO>(A, x, y, alpha, beta, s, d, extra, gate);
+#define GKO_RB_ROW(SS) GKO_RB_CASE(SS, 1) GKO_RB_CASE(SS, 2) GKO_RB_CASE(SS, 4)
+    GKO_RB_ROW(1) GKO_RB_ROW(2) GKO_RB_ROW(4) GKO_RB_ROW(8)
+#undef GKO_RB_ROW
+#undef GKO_RB_CASE
+    return -1;
   }
 
   template <bool DOT>
   static int csr_dispatch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                           const DotSpec& d, int extra, const int* gate) {
     const int S = A->plan.S, R = A->plan.R;
-    if (A->plan.kind == 1) {
-#define GKO_RB_CASE(SS, RR) \
-  if (S == SS && R == RR) return rowblock_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
-#define GKO_RB_ROW(SS) GKO_RB_CASE(SS, 1) GKO_RB_CASE(SS, 2) GKO_RB_CASE(SS, 4)
-      GKO_RB_ROW(1) GKO_RB_ROW(2) GKO_RB_ROW(4) GKO_RB_ROW(8)
-#undef GKO_RB_ROW
-#undef GKO_RB_CASE
-      return -1;
-    }
+    if (A->plan.kind == 1) return rowblock_dispatch<DOT, false>(A, x, y, alpha, beta, s, d, extra, gate);
 #define GKO_CSR_CASE(SS, RR) \
   if (S == SS && R == RR) return csr_launch<SS, RR, DOT>(A, x, y, alpha, beta, s, d, extra, gate);
 #define GKO_CSR_ROW(SS) GKO_CSR_CASE(SS, 1) GKO_CSR_CASE(SS, 2) GKO_CSR_CASE(SS, 4)
@@ -949,6 +1065,7 @@ struct SpmvImpl {
     const int extra = (int)fix_blocks;
     int g = dot ? csr_dispatch<true>(A, x, y, alpha, beta, s, d, extra, gate)
                 : csr_dispatch<false>(A, x, y, alpha, beta, s, d, extra, gate);
+    if (g == kLaunchCudaError) return GKO_CUDA_ERROR;
     if (g < 0) return fail(GKO_INVALID_ARG, "unsupported CSR plan");
     if (has_long) {
       AT* partial = static_cast<AT*>(scratch);
@@ -1007,16 +1124,17 @@ struct SpmvImpl {
       }
       return GKO_OK;
     }
-    const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
     AT* carry = static_cast<AT*>(scratch);
     CooArgs<VT, XT> a{A->n_rows, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col), ptr<VT>(A->coo_val),
-                      x, y, alpha, beta};
+                      x, y, alpha, beta, alpha == AT(1) && beta == AT(0)};
+    constexpr int kMinB = coo_min_blocks<VT>();
+    const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
     const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
     if (accum) {
-      coo_kernel<VT, XT, true><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+      coo_kernel<VT, XT, true, kCooItems, kMinB><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
       coo_fixup_kernel<VT, XT, true><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
     } else {
-      coo_kernel<VT, XT, false><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+      coo_kernel<VT, XT, false, kCooItems, kMinB><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
       coo_fixup_kernel<VT, XT, false><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
     }
     GKO_TRY_CUDA(cudaGetLastError());
@@ -1034,6 +1152,14 @@ struct SpmvImpl {
         return dot ? ell_launch<true>(A, x, y, alpha, beta, s, d, gate)
                    : ell_launch<false>(A, x, y, alpha, beta, s, d, gate);
       case GKO_COO:
+        if (A->plan.kind == 1 && A->coo_nnz > 0) {
+          const int g = dot ? rowblock_dispatch<true, true>(A, x, y, alpha, beta, s, d, 0, gate)
+                            : rowblock_dispatch<false, true>(A, x, y, alpha, beta, s, d, 0, gate);
+          if (g == kLaunchCudaError) return GKO_CUDA_ERROR;
+          if (g < 0) return fail(GKO_INVALID_ARG, "unsupported COO plan");
+          GKO_TRY_CUDA(cudaGetLastError());
+          return GKO_OK;
+        }
         return coo_part(A, x, y, alpha, beta, s, scratch, false, gate);
       case GKO_HYBRID:
         GKO_TRY(ell_launch<false>(A, x, y, alpha, beta, s, d, gate));

@@ -43,16 +43,29 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
+// try_wait: may suspend the thread in hardware until the phase completes or
+// a hardware time limit passes, so waiting warps neither spin nor oversleep.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the barrier phase with the given parity.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
+  while (!mbar_try(bar, parity)) {
     if (clock64() - t0 > kWaitCycles) {
       if (err) atomicOr(err, 1 << GKO_TIMEOUT);
       return false;
     }
-    __nanosleep(64);
   }
   return true;
 }

@@ -169,6 +169,82 @@ def test_every_plan_matches_oracle(gko, kernel, S, R, cap, mat):
     check_spmv_f64(host(yd), A, x, 2.0, -1.0, y0)
 
 
+def test_coo_plan_defaults(gko):
+    """COO starts on the segmented reduction with the CSR histogram; the
+    row-block schedule is opt-in."""
+    G = gko
+    for A in (I.laplace2d_5pt(64), I.stencil3d_27pt(10), I.banded(5000, 16, 0.3, seed=2), I.powerlaw(20000, seed=1)):
+        M = G.from_csr(A)
+        pc, po = M.plan(), G.gko_matrix_convert_to_coo(M).plan()
+        assert po["kernel"] == 0
+        np.testing.assert_array_equal(po["hist"], pc["hist"])
+
+
+COO_PLANS = ([(1, S, R, cap) for S in (1, 2, 4, 8) for R in (1, 2, 4) for cap in (512, 4096)]
+             + [(1, 1, 1, 1024), (0, 1, 1, 2048)])
+
+
+def _coo_plan_matrix(mat):
+    rng = np.random.default_rng(12)
+    if mat == "powerlaw":  # rows far longer than a stage: row blocks over many stages
+        return I.powerlaw(30000, seed=3)
+    if mat == "banded":
+        return I.banded(40000, 200, 0.7, seed=5)
+    # empty rows (also whole empty row blocks), unsorted columns, ragged last block
+    L = rng.integers(0, 9, 20011)
+    L[100:700] = 0
+    L[-3:] = 0
+    return I.rows_csr(L, 9000, rng)
+
+
+@pytest.mark.parametrize("kernel,S,R,cap", COO_PLANS)
+@pytest.mark.parametrize("mat", ["powerlaw", "banded", "gaps"])
+def test_every_coo_plan_matches_oracle(gko, kernel, S, R, cap, mat):
+    """Row-block COO under every lanes/rows/stage choice, on skewed rows
+    spanning many stages, on dense bands, and on matrices with empty rows and
+    empty row blocks; kernel 0 is the segmented reduction."""
+    G = gko
+    A = _coo_plan_matrix(mat)
+    M = G.gko_matrix_convert_to_coo(G.from_csr(A))
+    M.set_plan(kernel, S, R, cap)
+    p = M.plan()
+    assert p["kernel"] == kernel
+    if kernel == 1:
+        assert (p["subwarp"], p["rows_per_subwarp"], p["stage_cap"]) == (S, R, cap)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    for alpha, beta in [(1.0, 0.0), (2.0, -1.0)]:
+        yd = dev(y0)
+        G.gko_spmv(alpha, M, dev(x), beta, yd)
+        check_spmv_f64(host(yd), A, x, alpha, beta, y0)
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_coo_rowblock_low_precision_shares_plan(gko, dt):
+    """Value conversions of a row-block COO handle keep its row-block starts."""
+    G = gko
+    A = I.stencil3d_27pt(14)
+    M = G.gko_matrix_convert_to_coo(G.from_csr(A))
+    M.set_plan(1, 2, 2, 512)
+    L = G.gko_matrix_convert_values(M, G.F32 if dt == "f32" else G.BF16)
+    assert L.plan()["kernel"] == 1
+    x32 = np.random.default_rng(3).uniform(-1, 1, A.n_cols).astype(np.float32)
+    yd = dev(np.zeros(A.n_rows), np.float32)
+    G.gko_spmv(1.0, L, dev(x32), 0.0, yd)
+    vals = A.val.astype(np.float32).astype(np.float64) if dt == "f32" else bf16_round(A.val)
+    check_spmv_f32(host(yd), A, x32.astype(np.float64), 1.0, 0.0, None, vals)
+
+
+def test_coo_plan_rejects_bad_values(gko):
+    G = gko
+    M = G.gko_matrix_convert_to_coo(G.from_csr(I.laplace2d_5pt(8)))
+    for bad in [(1, 16, 1, 1024), (1, 1, 3, 1024), (1, 1, 1, 8192), (1, 1, 1, 768), (3, 1, 1, 1024)]:
+        with pytest.raises(G.GkoError) as e:
+            M.set_plan(*bad)
+        assert e.value.status == G.INVALID_ARG
+
+
 def test_edge_cases(gko):
     G = gko
     # zero rows
