@@ -348,6 +348,107 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
   rowblock_body<S, R, VT, XT, DOT, true>(a, cap, d, expected, err);
 }
 
+// ------------------------------------------------- segmented tile carries --
+//
+// Carries of a 256-thread segmented pass (COO and merge-path kernels).  Each
+// thread publishes `tail` (its sum after its last row end, or all of its sum
+// without one) and whether it ended a row.  A thread that ended a row gets
+// `in`, the sum of the tails of the preceding threads back to the nearest one
+// that ended a row, and `from_before` (no such thread: the row began before
+// the tile).  The tile's last-segment sum goes to carry[2*tile+1], and also
+// to carry[2*tile] when no thread ended a row.
+// Every warp holding a row end (short rows): each ending thread walks back
+// through shared memory, about one FP64 add per thread in total.  A warp
+// without a row end (a row longer than a warp's entries) would make some
+// walk long and serial, so the whole block then takes a log-step segmented
+// scan instead: 5 shuffle steps per warp, then a walk over at most 7 warp
+// totals.  The choice depends only on the sparsity pattern, so results stay
+// reproducible.
+template <typename AT, int NT>
+__device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, int* s_end, AT* carry, int64_t tile,
+                                             AT& in, bool& from_before) {
+  constexpr int NW = NT / 32;
+  __shared__ AT s_wv[NW];
+  __shared__ int s_wf[NW];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  s_tail[t] = tail;
+  s_end[t] = has_end;
+  const unsigned ends = __ballot_sync(0xffffffffu, has_end);
+  const bool scan = __syncthreads_or(ends == 0u);
+  in = AT(0);
+  from_before = true;
+  if (!scan) {
+    if (has_end) {
+      for (int u = t - 1; u >= 0; --u) {
+        in += s_tail[u];
+        if (s_end[u]) {
+          from_before = false;
+          break;
+        }
+      }
+    }
+    if (t == 0) {
+      AT tv = AT(0);
+      bool any_end = false;
+      for (int u = NT - 1; u >= 0; --u) {
+        tv += s_tail[u];
+        if (s_end[u]) {
+          any_end = true;
+          break;
+        }
+      }
+      if (!any_end) carry[2 * tile] = tv;
+      carry[2 * tile + 1] = tv;
+    }
+    return;
+  }
+  // inclusive segmented scan over the warp: (f, v) combines as (f | f', f' ? v' : v + v')
+  AT v = tail;
+  int f = has_end;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const AT vu = __shfl_up_sync(0xffffffffu, v, d);
+    const int fu = __shfl_up_sync(0xffffffffu, f, d);
+    if (lane >= d) {
+      if (!f) v = vu + v;
+      f |= fu;
+    }
+  }
+  if (lane == 31) {
+    s_wv[w] = v;
+    s_wf[w] = f;
+  }
+  __syncthreads();
+  AT cw = AT(0);  // segment entering this warp from the warps before it
+  int cf = 0;
+  for (int u = w - 1; u >= 0; --u) {
+    cw = s_wv[u] + cw;
+    if (s_wf[u]) {
+      cf = 1;
+      break;
+    }
+  }
+  AT ve = __shfl_up_sync(0xffffffffu, v, 1);  // exclusive: lanes before this one
+  int fe = __shfl_up_sync(0xffffffffu, f, 1);
+  if (lane == 0) {
+    ve = AT(0);
+    fe = 0;
+  }
+  if (!fe) {
+    ve = cw + ve;
+    fe = cf;
+  }
+  if (has_end) {
+    in = ve;
+    from_before = !fe;
+  }
+  if (t == NT - 1) {
+    const AT tv = f ? v : cw + v;
+    if (!(f || cf)) carry[2 * tile] = tv;
+    carry[2 * tile + 1] = tv;
+  }
+}
+
 // ------------------------------------------------------- merge-path CSR --
 //
 // Merge-path CSR (skewed matrices): the merged sequence of n row ends and
@@ -357,16 +458,16 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
 // per matrix (plan); a tile stages its row pointers and nonzeros in shared
 // memory, each thread finds its start (row x, nonzero y) by binary search
 // there, then walks its items: a nonzero adds one FMA, a row end finishes
-// the row.  Rows entering a thread take the trailing
-// partials of the preceding threads (shared-memory walk back, as in the COO
-// kernel); rows crossing tiles are finished by csr_merge_fixup_kernel from
-// per-tile carries, in tile order.
+// the row.  Rows entering a thread take the trailing partials of the
+// preceding threads (tile_carries, as in the COO kernel); rows crossing tiles
+// are finished by csr_merge_fixup_kernel from per-tile carries, in tile
+// order.
 
 constexpr int kMergeItems = 8;
 constexpr int kMergeTile = 256 * kMergeItems;
 
 template <typename VT, typename XT>
-__global__ void __launch_bounds__(256) csr_merge_kernel(CsrArgs<VT, XT> a, int64_t nnz,
+__global__ void __launch_bounds__(256, 5) csr_merge_kernel(CsrArgs<VT, XT> a, int64_t nnz,
                                                         const int32_t* __restrict__ corner_x,
                                                         acc_t<VT>* __restrict__ carry, const int* gate) {
   using AT = acc_t<VT>;
@@ -414,62 +515,56 @@ __global__ void __launch_bounds__(256) csr_merge_kernel(CsrArgs<VT, XT> a, int64
     xl = lo;
     yl = dl - lo;
   }
-  const int steps = dl < tile_items ? min(kMergeItems, tile_items - dl) : 0;
+  int items = dl < tile_items ? min(kMergeItems, tile_items - dl) : 0;
+  // The thread's nonzeros are a prefix of the kMergeItems entries from yl:
+  // gather their x values up front so the walk below never waits on one.
+  VT pv[kMergeItems];
+  XT px[kMergeItems];
+#pragma unroll
+  for (int u = 0; u < kMergeItems; ++u) {
+    const bool in_tile = yl + u < nnzt && u < items;
+    pv[u] = in_tile ? s_val[yl + u] : VT(0);
+    px[u] = in_tile ? ld_vec(a.x + s_col[yl + u]) : XT(0);
+  }
   AT run = AT(0), first_sum = AT(0);
   int64_t first_row = -1;
   int nends = 0;
   int64_t y = y0 + yl;
   int64_t row_end = s_rp[xl + 1];
-  for (int st = 0; st < steps; ++st) {
-    if (y < row_end) {
-      const int k = (int)(y - y0);
-      run = madd(to_acc(s_val[k]), to_acc(ld_vec(a.x + s_col[k])), run);
-      ++y;
+  auto end_row = [&]() {
+    const int64_t row = x0 + xl;
+    if (nends == 0) {
+      first_sum = run;
+      first_row = row;
     } else {
-      const int64_t row = x0 + xl;
-      if (nends == 0) {
-        first_sum = run;
-        first_row = row;
-      } else {
-        a.y[row] = (XT)finish_row(a.y, row, run, a.alpha, a.beta, a.plain);
-      }
-      ++nends;
-      run = AT(0);
-      ++xl;
-      row_end = s_rp[xl + 1];
+      a.y[row] = (XT)finish_row(a.y, row, run, a.alpha, a.beta, a.plain);
+    }
+    ++nends;
+    run = AT(0);
+    ++xl;
+    row_end = s_rp[xl + 1];
+    --items;
+  };
+  // merge-path walk, unrolled over the thread's nonzeros (register index u)
+#pragma unroll
+  for (int u = 0; u < kMergeItems; ++u) {
+    while (items > 0 && y >= row_end) end_row();
+    if (items > 0) {
+      run = madd(to_acc(pv[u]), to_acc(px[u]), run);
+      ++y;
+      --items;
     }
   }
-  s_tail[t] = run;
-  s_end[t] = nends > 0;
-  __syncthreads();
+  while (items > 0) end_row();
+  AT in;
+  bool from_before_tile;
+  tile_carries<AT, 256>(run, nends > 0, s_tail, s_end, carry, tile, in, from_before_tile);
   if (nends > 0) {
-    AT in = AT(0);
-    bool from_before_tile = true;
-    for (int u = t - 1; u >= 0; --u) {
-      in += s_tail[u];
-      if (s_end[u]) {
-        from_before_tile = false;
-        break;
-      }
-    }
     const AT tot = in + first_sum;
     if (from_before_tile && first_open)
       carry[2 * tile] = tot;
     else
       a.y[first_row] = (XT)finish_row(a.y, first_row, tot, a.alpha, a.beta, a.plain);
-  }
-  if (t == 0) {
-    AT tv = AT(0);
-    bool any_end = false;
-    for (int u = 255; u >= 0; --u) {
-      tv += s_tail[u];
-      if (s_end[u]) {
-        any_end = true;
-        break;
-      }
-    }
-    if (!any_end) carry[2 * tile] = tv;
-    carry[2 * tile + 1] = tv;
   }
 }
 
@@ -772,10 +867,9 @@ constexpr int coo_min_blocks() {
 // entries (vector loads) and folds them with one FMA per entry, finishing
 // the rows that start and end inside its entries on the spot.  The running
 // sum entering a thread's first row is the sum of the trailing partials of
-// the preceding threads back to the nearest one that ended a row: the thread
-// that ends the row walks back over them in shared memory (about one FP64
-// add per thread; no shuffle scan).  The tile's open first/last segment
-// partials go to carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
+// the preceding threads back to the nearest one that ended a row
+// (tile_carries).  The tile's open first/last segment partials go to
+// carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
 // ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows absent from the COO
 // arrays are scaled by beta here too.
 template <typename VT, typename XT, bool ACCUM, int IPT = kCooItems, int MINB = 1>
@@ -869,39 +963,15 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
       if (r != nr && r + 1 < gap_end) coo_empty_rows(a.y, (int64_t)r + 1, (int64_t)gap_end, a.beta);
     }
   }
-  s_tail[t] = run;  // sum after this thread's last row end (all of it without one)
-  s_end[t] = nends > 0;
-  __syncthreads();
-
+  AT in;
+  bool from_before_tile;
+  tile_carries<AT, kCooThreads>(run, nends > 0, s_tail, s_end, carry, tile, in, from_before_tile);
   if (nends > 0) {
-    AT in = AT(0);
-    bool from_before_tile = true;
-    for (int u = t - 1; u >= 0; --u) {
-      in += s_tail[u];
-      if (s_end[u]) {
-        from_before_tile = false;
-        break;
-      }
-    }
     const AT total = in + first_sum;
     if (from_before_tile && first_open)
       carry[2 * tile] = total;  // the tile's first row began in an earlier tile
     else
       coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM, a.plain);
-  }
-  if (t == 0) {
-    AT tv = AT(0);
-    bool any_end = false;
-    for (int u = kCooThreads - 1; u >= 0; --u) {
-      tv += s_tail[u];
-      if (s_end[u]) {
-        any_end = true;
-        break;
-      }
-    }
-    // tv: sum of the tile's last segment; without any end the whole tile
-    if (!any_end) carry[2 * tile] = tv;
-    carry[2 * tile + 1] = tv;
   }
 }
 
