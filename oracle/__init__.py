@@ -58,6 +58,10 @@ _SIGS = {
     "or_ell_width": (_I32, [_I64, _P]),
     "or_csr_to_ell": (None, [_I64, _P, _P, _P, _I32, _I64, _P, _P]),
     "or_spmv_ell": (None, [_I64, _I32, _I64, _P, _P, _P, _D, _D, _P]),
+    "or_sellp_slices": (_I64, [_I64, _I32]),
+    "or_sellp_sets": (_I64, [_I64, _P, _I32, _P]),
+    "or_csr_to_sellp": (None, [_I64, _P, _P, _P, _I32, _P, _P, _P]),
+    "or_spmv_sellp": (None, [_I64, _I32, _P, _P, _P, _P, _D, _D, _P]),
     "or_csr_to_coo": (None, [_I64, _P, _P, _P, _P, _P, _P]),
     "or_spmv_coo": (C.c_int, [_I64, _I64, _P, _P, _P, _P, _D, _D, _P]),
     "or_hybrid_width": (_I32, [_I64, _P]),
@@ -186,6 +190,35 @@ def spmv_ell(E: Ell, x, alpha=1.0, beta=0.0, y=None):
     x = _f64(x)
     out = _y0(E.n_rows, y, beta)
     lib().or_spmv_ell(E.n_rows, E.K, E.stride, _p(E.col), _p(E.val), _p(x), alpha, beta, _p(out))
+    return out
+
+
+@dataclass
+class Sellp:
+    n_rows: int
+    C: int            # slice height
+    sets: np.ndarray  # int64[n_slices+1], prefix sums of the slice widths
+    col: np.ndarray   # int32[sets[-1]*C]
+    val: np.ndarray   # float64[sets[-1]*C]
+
+
+def csr_to_sellp(A, C=64) -> Sellp:
+    """SELL-P (Section 1 Sellp; Anzt, Tomov & Dongarra 2014 layout): slices of
+    C rows, each as wide as its longest row, column-major within the slice."""
+    rp, col, val = _i32(A.row_ptr), _i32(A.col), _f64(A.val)
+    ns = int(lib().or_sellp_slices(A.n_rows, C))
+    sets = np.empty(ns + 1, np.int64)
+    total = int(lib().or_sellp_sets(A.n_rows, _p(rp), C, _p(sets)))
+    scol = np.empty(total * C, np.int32)
+    sval = np.empty(total * C, np.float64)
+    lib().or_csr_to_sellp(A.n_rows, _p(rp), _p(col), _p(val), C, _p(sets), _p(scol), _p(sval))
+    return Sellp(A.n_rows, C, sets, scol, sval)
+
+
+def spmv_sellp(S: Sellp, x, alpha=1.0, beta=0.0, y=None):
+    x = _f64(x)
+    out = _y0(S.n_rows, y, beta)
+    lib().or_spmv_sellp(S.n_rows, S.C, _p(S.sets), _p(S.col), _p(S.val), _p(x), alpha, beta, _p(out))
     return out
 
 

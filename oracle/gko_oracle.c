@@ -9,7 +9,7 @@
  * double (compiled with -ffp-contract=off, so no fused multiply-adds):
  *
  *   SpMV      y = alpha*A*x + beta*y  for the formats the paper lists
- *             (Coo, Csr, Ell, Hybrid; Section 1, contributions list).
+ *             (Coo, Csr, Ell, Hybrid, Sellp; Section 1, contributions list).
  *             Each row sum runs left to right in storage order.  beta == 0
  *             overwrites y without reading it (BLAS convention).
  *   Formats   ELL / COO / HYB as defined by Bell & Garland, "Implementing
@@ -158,6 +158,60 @@ void or_spmv_ell(int64_t n, int32_t K, int64_t stride, const int32_t *ecol, cons
     for (int32_t k = 0; k < K; ++k) {
       int32_t c = ecol[(int64_t)k * stride + i];
       if (c >= 0) s += eval[(int64_t)k * stride + i] * x[c];
+    }
+    y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
+  }
+}
+
+/* SELL-P (sliced ELL with padding; the Sellp format of Section 1 and the
+ * SpMV of Section 4, layout as defined by Anzt, Tomov & Dongarra, "Implementing
+ * a sparse matrix vector product for the SELL-C/SELL-P format on NVIDIA GPUs",
+ * 2014): rows are cut into slices of C consecutive rows (no reordering); slice
+ * s is as wide as its longest row, w_s, and holds its entries column-major:
+ * entry k of row i (slice s = i / C) sits at (sets[s] + k) * C + i % C, with
+ * sets[s] = w_0 + ... + w_{s-1}.  Padding col = -1, val = +0.0. */
+int64_t or_sellp_slices(int64_t n, int32_t C) { return (n + C - 1) / C; }
+
+/* sets[0..n_slices]: prefix sums of the slice widths; returns sets[n_slices]. */
+int64_t or_sellp_sets(int64_t n, const int32_t *rp, int32_t C, int64_t *sets) {
+  int64_t ns = or_sellp_slices(n, C);
+  sets[0] = 0;
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int32_t w = 0;
+    for (int64_t i = sl * C; i < n && i < (sl + 1) * C; ++i) {
+      int32_t len = rp[i + 1] - rp[i];
+      if (len > w) w = len;
+    }
+    sets[sl + 1] = sets[sl] + w;
+  }
+  return sets[ns];
+}
+
+void or_csr_to_sellp(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t C,
+                     const int64_t *sets, int32_t *scol, double *sval) {
+  int64_t ns = or_sellp_slices(n, C);
+  for (int64_t q = 0; q < sets[ns] * C; ++q) {
+    scol[q] = -1;
+    sval[q] = 0.0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t sl = i / C;
+    for (int32_t k = 0; k < rp[i + 1] - rp[i]; ++k) {
+      int64_t q = (sets[sl] + k) * C + i % C;
+      scol[q] = col[rp[i] + k];
+      sval[q] = val[rp[i] + k];
+    }
+  }
+}
+
+void or_spmv_sellp(int64_t n, int32_t C, const int64_t *sets, const int32_t *scol, const double *sval,
+                   const double *x, double alpha, double beta, double *y) {
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t sl = i / C;
+    double s = 0.0;
+    for (int64_t k = 0; k < sets[sl + 1] - sets[sl]; ++k) {
+      int64_t q = (sets[sl] + k) * C + i % C;
+      if (scol[q] >= 0) s += sval[q] * x[scol[q]];
     }
     y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
   }

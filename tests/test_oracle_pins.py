@@ -195,6 +195,68 @@ def test_ell_padding_never_reads_x():
     assert np.all(np.isfinite(O.spmv_ell(E, x)))
 
 
+def _sellp_to_csr(S):
+    rows = []
+    for i in range(S.n_rows):
+        sl = i // S.C
+        cols, vals = [], []
+        for k in range(int(S.sets[sl + 1] - S.sets[sl])):
+            q = (int(S.sets[sl]) + k) * S.C + i % S.C
+            if S.col[q] >= 0:
+                cols.append(int(S.col[q]))
+                vals.append(float(S.val[q]))
+        rows.append((cols, vals))
+    return rows
+
+
+def test_sellp_layout_golden():
+    """A case laid out by hand from the SELL-P definition (C = 4)."""
+    with open(os.path.join(GOLDEN, "sellp_layout_case.json")) as f:
+        g = json.load(f)
+    lens = [len(r[0]) for r in g["rows"]]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    col = np.array([c for r in g["rows"] for c in r[0]], np.int32)
+    val = np.array([v for r in g["rows"] for v in r[1]], np.float64)
+    A = I.Csr(g["n_rows"], g["n_cols"], rp, col, val)
+    S = O.csr_to_sellp(A, C=g["C"])
+    np.testing.assert_array_equal(S.sets, g["sets"])
+    np.testing.assert_array_equal(S.col, g["col"])
+    np.testing.assert_array_equal(S.val, g["val"])
+
+
+@pytest.mark.parametrize("C", [4, 32, 64])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_sellp_round_trip_dense_and_padding(C, seed):
+    """Inverse written here recovers the CSR rows; integer SpMV equals the
+    dense product exactly; padding slots are col -1 / +0.0 and a slice whose
+    rows are all empty has width 0."""
+    rng = np.random.default_rng(seed)
+    L = rng.integers(0, 9, 150)
+    L[64:128] = 0  # a whole empty slice at C = 64 and C = 32
+    A = I.rows_csr(L, 70, rng)
+    A.val[:] = rng.integers(-4, 5, A.nnz)
+    S = O.csr_to_sellp(A, C=C)
+    assert _sellp_to_csr(S) == _csr_rows(A)
+    widths = np.diff(S.sets)
+    if C in (32, 64):
+        assert widths[64 // C] == 0
+    pad = S.col < 0
+    assert pad.sum() == S.sets[-1] * C - A.nnz
+    assert np.all(S.val[pad] == 0.0) and not np.any(np.signbit(S.val[pad]))
+    x = rng.integers(-3, 4, 70).astype(float)
+    y0 = rng.integers(-3, 4, 150).astype(float)
+    np.testing.assert_array_equal(O.spmv_sellp(S, x, 2.0, -1.0, y0), 2.0 * (dense(A) @ x) - y0)
+
+
+def test_sellp_padding_never_reads_x():
+    A = I.rows_csr([1, 3, 0, 2, 5], 6, np.random.default_rng(0))
+    S = O.csr_to_sellp(A, C=4)
+    x = np.arange(1.0, 7.0)
+    for c in set(range(6)) - set(A.col.tolist()):
+        x[c] = np.inf
+    assert np.all(np.isfinite(O.spmv_sellp(S, x)))
+
+
 def test_coo_round_trip_and_dense():
     rng = np.random.default_rng(4)
     A = I.random_csr(50, 50, 0.1, rng, integer_values=True, empty_rows=0.3, sort_cols=False)
