@@ -7,6 +7,9 @@ sweep: 3D 27-point stencil 128^3 (n = 2,097,152, nnz = 55,742,968), the
 power-law matrix n = 10^6 (Zipf(2) row lengths clipped to [1, 10^4]) and the
 banded matrix n = 10^6 (half-bandwidth 64, fill 0.3).  ELL on the power-law
 matrix is rejected by the padding limit and is not part of the step.
+SELL-P (slices of 64 rows) is timed the same way after the step and reported
+under `extra_formats`, outside `value` (the sweep's formats are CSR, ELL, COO
+and hybrid); on the power-law matrix it is rejected by the padding limit too.
 value = algorithmic bytes of all SpMVs / their summed device time (GB/s);
 L2 is flushed (256 MB write) before every SpMV.  Matrices stay resident in
 HBM; `e2e` repeats the step through the same C ABI calls with x copied in
@@ -39,6 +42,8 @@ METRIC = "SpMV GB/s (% HBM peak) per format; solves/s + p99 latency at 1e-8 resi
 WORKLOAD = ("SpMV format sweep: CSR/ELL/COO/hybrid x FP64/FP32 (int32 indices) on 27-pt stencil 128^3, "
             "power-law n=1e6 (Zipf s=2, clip [1,1e4], seed 0), banded n=1e6 (hb 64, fill 0.3, seed 0)")
 FALLBACK_HBM_GBS = 6800.0
+SWEEP_FORMATS = ("csr", "ell", "coo", "hybrid")
+EXTRA_FORMATS = ("sellp",)  # timed the same way, reported beside the sweep, not part of `value`
 
 
 def env_rank():
@@ -67,7 +72,7 @@ def spmv_bytes(fmt, n_rows, n_cols, nnz, ell_nnz, tail_nnz, sv, sx, sy):
     x once, y written once; padding, x re-reads and misses excluded."""
     if fmt == "csr":
         return nnz * (sv + 4) + 4 * (n_rows + 1) + sx * n_cols + sy * n_rows
-    if fmt == "ell":
+    if fmt in ("ell", "sellp"):
         return nnz * (sv + 4) + sx * n_cols + sy * n_rows
     if fmt == "coo":
         return nnz * (sv + 8) + sx * n_cols + sy * n_rows
@@ -442,25 +447,28 @@ def whole_job_gbs(world, bytes_per_rank, ms):
 
 # ---------------------------------------------------------------- our path --
 
-def build_cases(G, mats, dev):
+def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid")):
     """Every (matrix, format, value type) SpMV case of the sweep, resident on
     the device, with its algorithmic bytes and the number of kernel launches
     one gko_spmv call makes for it."""
     import torch
 
+    convs = {"ell": lambda m: G.gko_matrix_convert_to_ell(m), "coo": G.gko_matrix_convert_to_coo,
+             "hybrid": lambda m: G.gko_matrix_convert_to_hybrid(m), "sellp": lambda m: G.gko_matrix_convert_to_sellp(m)}
     cases, skipped = [], []
     for name, A in mats:
         M64 = G.from_csr(A)
         plan = M64.plan()
-        base = {"csr": M64}
-        for fmt, conv in (("ell", lambda m: G.gko_matrix_convert_to_ell(m)),
-                          ("coo", G.gko_matrix_convert_to_coo), ("hybrid", lambda m: G.gko_matrix_convert_to_hybrid(m))):
+        base = {"csr": M64} if "csr" in formats else {}
+        for fmt in formats:
+            if fmt == "csr":
+                continue
             try:
-                base[fmt] = conv(M64)
+                base[fmt] = convs[fmt](M64)
             except G.GkoError as e:
                 if e.status != G.FORMAT_UNSUITABLE:
                     raise
-                skipped.append(f"{name}/{fmt}: ELL padding over the limit")
+                skipped.append(f"{name}/{fmt}: padding over the limit")
         x64 = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, A.n_cols)).to(dev)
         x32 = x64.float()
         for fmt, M in base.items():
@@ -470,11 +478,11 @@ def build_cases(G, mats, dev):
                 sv = 8 if dt == "f64" else 4
                 ell_nnz = inf["nnz"] - inf["coo_nnz"] if fmt == "hybrid" else 0
                 nb = spmv_bytes(fmt, A.n_rows, A.n_cols, A.nnz, ell_nnz, inf["coo_nnz"], sv, sv, sv)
-                coo_launches = 2 if inf["coo_nnz"] > 0 else 0
+                coo_launches = 2 if inf["coo_nnz"] > 0 and fmt in ("coo", "hybrid") else 0
                 csr_launches = 2 if plan["kernel"] == 2 else 1 + (2 if plan["n_long_rows"] > 0 else 0)
                 if fmt == "coo" and M.plan()["kernel"] == 1:
                     coo_launches = 1  # row-block COO: one launch, no tile fix-up
-                launches = {"csr": csr_launches, "ell": 1,
+                launches = {"csr": csr_launches, "ell": 1, "sellp": 1,
                             "coo": coo_launches if coo_launches else 1, "hybrid": 1 + coo_launches}[fmt]
                 x = x64 if dt == "f64" else x32
                 y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
@@ -493,7 +501,7 @@ def profile_cases(args):
 
     G.load()
     dev = torch.device("cuda", 0)
-    cases, _ = build_cases(G, workload_matrices(small=args.small), dev)
+    cases, _ = build_cases(G, workload_matrices(small=args.small), dev, formats=SWEEP_FORMATS + EXTRA_FORMATS)
     for c in cases:
         G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"])
     torch.cuda.synchronize()
@@ -596,6 +604,23 @@ def run_ours(args):
 
     kernel_ms, e2e_ms = ranks_max([kernel_ms, e2e_ms], dev)
 
+    # formats beyond the sweep (SELL-P): same protocol, own timing loop
+    extra, extra_skipped = build_cases(G, mats, dev, formats=EXTRA_FORMATS)
+    for _ in range(max(args.warmup, 3)):
+        for c in extra:
+            G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"], stream=stream)
+    xev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in extra]
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        for i, c in enumerate(extra):
+            flush.fill_(float(i))
+            xev[k][i][0].record(stream)
+            G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"], stream=stream)
+            xev[k][i][1].record(stream)
+    torch.cuda.synchronize()
+    extra_ms = [sum(xev[k][i][0].elapsed_time(xev[k][i][1]) for k in range(args.steps)) / args.steps
+                for i in range(len(extra))]
+
     peak, peak_kind = measured_peaks()
     dom = int(np.argmax(per_case_ms))
     dom_case = cases[dom]
@@ -624,6 +649,11 @@ def run_ours(args):
             "e2e": {"value": round(whole_job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(sum(c["x"].numel() * c["x"].element_size() for c in cases)),
                     "d2h_bytes_per_step": int(sum(c["y"].numel() * c["y"].element_size() for c in cases))},
+            "extra_formats": {c["label"]: {"ms": round(extra_ms[i], 4),
+                                           "GB_s": round(c["bytes"] / (extra_ms[i] * 1e-3) / 1e9, 1),
+                                           "frac": round(c["bytes"] / (extra_ms[i] * 1e-3) / 1e9 / peak, 4)}
+                              for i, c in enumerate(extra)},
+            "extra_skipped": extra_skipped,
             "wall_ms_per_step_incl_flush": round(wall_ms, 4),
             "clocks": clocks,
             "gpu_launches": int(sum(c["launches"] for c in cases) * args.steps),

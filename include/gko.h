@@ -60,7 +60,7 @@ typedef struct gko_matrix_s *gko_matrix;
 typedef enum { GKO_F64 = 0, GKO_F32 = 1, GKO_BF16 = 2 } gko_dtype;
 
 /* Storage formats (paper, Section 1: Coo, Csr, Ell, Hybrid). */
-typedef enum { GKO_CSR = 0, GKO_ELL = 1, GKO_COO = 2, GKO_HYBRID = 3 } gko_format;
+typedef enum { GKO_CSR = 0, GKO_ELL = 1, GKO_COO = 2, GKO_HYBRID = 3, GKO_SELLP = 4 } gko_format;
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 GKO_API const char *gko_last_error(void);
@@ -114,6 +114,18 @@ GKO_API int gko_matrix_convert_to_coo(gko_matrix csr, void *stream, gko_matrix *
  * #{rows: len >= k} >= max(4096, n_rows/3); K = 0 gives a pure COO tail. */
 GKO_API int gko_matrix_convert_to_hybrid(gko_matrix csr, int32_t ell_width, void *stream, gko_matrix *out);
 
+/* SELL-P, sliced ELL with padding (paper, Section 1: Sellp, the format of its
+ * Section 4 SpMV and CG measurements; layout of Anzt, Tomov & Dongarra 2014):
+ * rows are cut into slices of `slice_size` consecutive rows (32, 64, 128 or
+ * 256; <= 0 means 64), no reordering; slice s is as wide as its longest row
+ * w_s and stores its entries column-major: entry k of row i (s = i /
+ * slice_size) at (sets[s] + k) * slice_size + i % slice_size, sets[s] = w_0 +
+ * ... + w_{s-1}.  Padding col = -1 and value +0.0; entries keep CSR storage
+ * order.  Returns GKO_FORMAT_UNSUITABLE when the stored slots exceed
+ * max_fill * nnz (max_fill <= 0 means the default limit of 8). */
+GKO_API int gko_matrix_convert_to_sellp(gko_matrix csr, int32_t slice_size, double max_fill, void *stream,
+                                        gko_matrix *out);
+
 /* Copy of `m` (any format) with values converted to `to` (round to nearest
  * even); index arrays are shared with `m`, which must outlive the copy only
  * as far as the caller's own handle goes (sharing is reference counted). */
@@ -121,7 +133,9 @@ GKO_API int gko_matrix_convert_values(gko_matrix m, gko_dtype to, void *stream, 
 
 /* Sizes and layout of a handle.  Any output pointer may be NULL.
  * ell_width / coo_nnz are 0 where the format has no such part; bytes is the
- * device memory owned (shared index arrays counted in full). */
+ * device memory owned (shared index arrays counted in full).  For SELL-P,
+ * ell_width is the widest slice, ell_stride the slice size and coo_nnz the
+ * number of stored slots (entries plus padding). */
 GKO_API int gko_matrix_info(gko_matrix m, gko_format *format, gko_dtype *dtype, int64_t *n_rows,
                     int64_t *n_cols, int64_t *nnz, int32_t *ell_width, int64_t *ell_stride,
                     int64_t *coo_nnz, int64_t *bytes);
@@ -131,6 +145,8 @@ GKO_API int gko_matrix_info(gko_matrix m, gko_format *format, gko_dtype *dtype, 
  *   ELL:    ell_col[K*stride], ell_val[K*stride]
  *   COO:    coo_row[nnz], coo_col[nnz], coo_val[nnz]
  *   HYBRID: ell_* for the ELL part and coo_* for the tail
+ *   SELLP:  row_ptr[n_slices+1] receives the slice offsets sets[], ell_col /
+ *           ell_val the stored slots (coo_nnz of gko_matrix_info of them)
  * Values are written in the handle's dtype.  Synchronises `stream`. */
 GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void *val, int32_t *ell_col,
                       void *ell_val, int32_t *coo_row, int32_t *coo_col, void *coo_val,

@@ -137,6 +137,11 @@ struct gko_matrix_s {
   // COO (also the tail of HYBRID)
   int64_t coo_nnz = 0;
   gko::Buf coo_row, coo_col, coo_val;
+  // SELL-P: slices of `slice` rows; sellp_sets int32[n_slices+1] (slice
+  // offsets in columns), slots column-major within each slice
+  int32_t slice = 0;
+  int64_t n_slices = 0, sellp_slots = 0;
+  gko::Buf sellp_sets, sellp_col, sellp_val;
   // cached low-precision copies used by mixed-precision solves
   std::mutex mu;
   std::map<int, gko_matrix> lowp;

@@ -422,6 +422,41 @@ static int ell_fill(gko_matrix src, gko_matrix dst, int32_t K, cudaStream_t s) {
   return GKO_OK;
 }
 
+// SELL-P: width of slice s = longest row among rows [s*C, (s+1)*C).
+struct SliceWidth {
+  const int32_t* rp;
+  int64_t n;
+  int32_t C;
+  __device__ int64_t operator()(int64_t s) const {
+    int32_t w = 0;
+    const int64_t i1 = (s + 1) * C < n ? (s + 1) * C : n;
+    for (int64_t i = s * C; i < i1; ++i) w = max(w, rp[i + 1] - rp[i]);
+    return w;
+  }
+};
+
+// SELL-P fill: thread per row slot i of the padded slice grid; entry k of
+// row i at (sets[s] + k) * C + i % C, padding col = -1 and value bits 0.
+template <typename E>
+__global__ void sellp_fill_kernel(int64_t n, int64_t n_slices, int32_t C, const int32_t* __restrict__ rp,
+                                  const int32_t* __restrict__ col, const E* __restrict__ val,
+                                  const int32_t* __restrict__ sets, int32_t* __restrict__ scol,
+                                  E* __restrict__ sval) {
+  const int64_t rows = n_slices * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i / C, lr = i - sl * C;
+    const int64_t base = sets[sl];
+    const int32_t w = sets[sl + 1] - sets[sl];
+    const int32_t r0 = i < n ? rp[i] : 0;
+    const int32_t len = i < n ? rp[i + 1] - r0 : 0;
+    for (int32_t k = 0; k < w; ++k) {
+      const int64_t q = (base + k) * C + lr;
+      scol[q] = k < len ? col[r0 + k] : -1;
+      sval[q] = k < len ? val[r0 + k] : E(0);
+    }
+  }
+}
+
 static gko_matrix new_like(gko_matrix src, gko_format fmt) {
   gko_matrix m = new gko_matrix_s();
   m->fmt = fmt;
@@ -586,6 +621,60 @@ int gko_matrix_convert_to_ell(gko_matrix csr, double max_fill, void* stream, gko
   return GKO_OK;
 }
 
+int gko_matrix_convert_to_sellp(gko_matrix csr, int32_t slice_size, double max_fill, void* stream,
+                                gko_matrix* out) {
+  if (!csr || !out) return fail(GKO_INVALID_ARG, "null argument");
+  if (csr->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "conversion source must be CSR");
+  *out = nullptr;
+  const int32_t C = slice_size <= 0 ? 64 : slice_size;
+  if (C != 32 && C != 64 && C != 128 && C != 256) return fail(GKO_INVALID_ARG, "slice_size must be 32, 64, 128 or 256");
+  if (max_fill <= 0) max_fill = 8.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<gko_matrix_s> m(new_like(csr, GKO_SELLP));
+  const int64_t n = csr->n_rows;
+  const int64_t ns = (n + C - 1) / C;
+  GKO_TRY(alloc(sizeof(int32_t) * (ns + 1), &m->sellp_sets));
+  int64_t total = 0;
+  GKO_TRY(exclusive_scan(SliceWidth{ptr<int32_t>(csr->row_ptr), n, C}, ns, ptr<int32_t>(m->sellp_sets), &total, s));
+  if (total > INT32_MAX) return fail(GKO_FORMAT_UNSUITABLE, "SELL-P slice widths exceed int32");
+  const int64_t slots = total * C;
+  if ((double)slots > max_fill * (double)std::max<int64_t>(csr->nnz, 1)) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "SELL-P padding: %lld slots exceed %.1f x nnz (%lld)", (long long)slots, max_fill,
+             (long long)csr->nnz);
+    return fail(GKO_FORMAT_UNSUITABLE, msg);
+  }
+  const int32_t total32 = (int32_t)total;
+  GKO_TRY_CUDA(cudaMemcpyAsync(ptr<int32_t>(m->sellp_sets) + ns, &total32, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  const size_t vs = dtype_size(csr->dtype);
+  GKO_TRY(alloc(sizeof(int32_t) * slots, &m->sellp_col));
+  GKO_TRY(alloc(vs * slots, &m->sellp_val));
+  if (slots > 0) {
+    const int32_t* rp = ptr<int32_t>(csr->row_ptr);
+    const int32_t* col = ptr<int32_t>(csr->col);
+    const int32_t* sets = ptr<int32_t>(m->sellp_sets);
+    const unsigned g = grid_for(ns * C);
+    if (vs == 8)
+      sellp_fill_kernel<unsigned long long><<<g, 256, 0, s>>>(n, ns, C, rp, col, ptr<unsigned long long>(csr->val),
+          sets, ptr<int32_t>(m->sellp_col), ptr<unsigned long long>(m->sellp_val));
+    else if (vs == 4)
+      sellp_fill_kernel<unsigned int><<<g, 256, 0, s>>>(n, ns, C, rp, col, ptr<unsigned int>(csr->val), sets,
+          ptr<int32_t>(m->sellp_col), ptr<unsigned int>(m->sellp_val));
+    else
+      sellp_fill_kernel<unsigned short><<<g, 256, 0, s>>>(n, ns, C, rp, col, ptr<unsigned short>(csr->val), sets,
+          ptr<int32_t>(m->sellp_col), ptr<unsigned short>(m->sellp_val));
+    GKO_TRY_CUDA(cudaGetLastError());
+  }
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  m->slice = C;
+  m->n_slices = ns;
+  m->sellp_slots = slots;
+  m->K = csr->plan.max_len;  // the widest slice
+  m->stride = C;
+  *out = m.release();
+  return GKO_OK;
+}
+
 int gko_matrix_convert_to_coo(gko_matrix csr, void* stream, gko_matrix* out) {
   if (!csr || !out) return fail(GKO_INVALID_ARG, "null argument");
   if (csr->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "conversion source must be CSR");
@@ -732,6 +821,11 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   m->coo_nnz = src->coo_nnz;
   m->coo_row = src->coo_row;
   m->coo_col = src->coo_col;
+  m->slice = src->slice;
+  m->n_slices = src->n_slices;
+  m->sellp_slots = src->sellp_slots;
+  m->sellp_sets = src->sellp_sets;
+  m->sellp_col = src->sellp_col;
   auto convert = [&](const Buf& a, int64_t count, Buf* b) -> int {
     GKO_TRY(alloc(dtype_size(to) * count, b));
     if (count == 0) return GKO_OK;
@@ -750,6 +844,7 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   if (src->val) GKO_TRY(convert(src->val, src->nnz, &m->val));
   if (src->ell_val) GKO_TRY(convert(src->ell_val, (int64_t)src->K * src->stride, &m->ell_val));
   if (src->coo_val) GKO_TRY(convert(src->coo_val, src->coo_nnz, &m->coo_val));
+  if (src->sellp_val) GKO_TRY(convert(src->sellp_val, src->sellp_slots, &m->sellp_val));
   GKO_TRY_CUDA(cudaStreamSynchronize(s));
   *out = m.release();
   return GKO_OK;
@@ -765,12 +860,13 @@ int gko_matrix_info(gko_matrix m, gko_format* format, gko_dtype* dtype, int64_t*
   if (nnz) *nnz = m->nnz;
   if (ell_width) *ell_width = m->K;
   if (ell_stride) *ell_stride = m->stride;
-  if (coo_nnz) *coo_nnz = m->coo_nnz;
+  if (coo_nnz) *coo_nnz = m->fmt == GKO_SELLP ? m->sellp_slots : m->coo_nnz;
   if (bytes) {
     int64_t b = 0;
     for (const Buf* x : {&m->row_ptr, &m->col, &m->val, &m->ell_col, &m->ell_val, &m->coo_row, &m->coo_col,
                          &m->coo_val, &m->plan.long_rows, &m->plan.long_chunk_ptr, &m->plan.chunk_row,
-                         &m->plan.chunk_start, &m->plan.merge_x, &m->plan.coo_rb})
+                         &m->plan.chunk_start, &m->plan.merge_x, &m->plan.coo_rb, &m->sellp_sets,
+                         &m->sellp_col, &m->sellp_val})
       if (*x) b += (int64_t)(*x)->bytes;
     *bytes = b;
   }
@@ -795,6 +891,11 @@ int gko_matrix_export(gko_matrix m, int32_t* row_ptr, int32_t* col, void* val, i
     const int64_t slots = (int64_t)m->K * m->stride;
     GKO_TRY(d2h(ell_col, m->ell_col, sizeof(int32_t) * slots));
     GKO_TRY(d2h(ell_val, m->ell_val, vs * slots));
+  }
+  if (m->fmt == GKO_SELLP) {
+    GKO_TRY(d2h(row_ptr, m->sellp_sets, sizeof(int32_t) * (m->n_slices + 1)));
+    GKO_TRY(d2h(ell_col, m->sellp_col, sizeof(int32_t) * m->sellp_slots));
+    GKO_TRY(d2h(ell_val, m->sellp_val, vs * m->sellp_slots));
   }
   if (m->fmt == GKO_COO || m->fmt == GKO_HYBRID) {
     GKO_TRY(d2h(coo_row, m->coo_row, sizeof(int32_t) * m->coo_nnz));

@@ -10,6 +10,7 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
       if (A->plan.kind == 2) return at * 2 * (size_t)((A->n_rows + A->nnz + 2047) / 2048 + 1);
       return at * (size_t)A->plan.n_chunks;
     case GKO_ELL:
+    case GKO_SELLP:
       return 0;
     case GKO_COO:
       if (A->plan.kind == 1) return 0;
@@ -21,7 +22,7 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
 }
 
 bool spmv_fuses_dot(const gko_matrix_s* A) {
-  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL ||
+  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL || A->fmt == GKO_SELLP ||
          (A->fmt == GKO_COO && A->plan.kind == 1 && A->coo_nnz > 0);
 }
 

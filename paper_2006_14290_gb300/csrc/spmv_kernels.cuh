@@ -39,6 +39,10 @@ __device__ __forceinline__ void dot_accum(const DotSpec& d, int64_t i, XT v, dou
   if (d.want_yy) yy = __fma_rn(yv, yv, yy);
 }
 
+// Blocks that prefetch slices of x into L2 at the start of the gather-heavy
+// kernels (COO, merge path): about the first wave of blocks.
+constexpr unsigned kXPrefetchBlocks = 512;
+
 // ------------------------------------------------------------------- CSR --
 
 template <typename VT, typename XT>
@@ -56,6 +60,7 @@ struct CsrArgs {
   // every row block (rb_ptr[b] = first k with row[k] >= b*RB)
   const int32_t* row = nullptr;
   const int32_t* rb_ptr = nullptr;
+  int64_t n_cols = 0;  // length of x
 };
 
 // Subwarp-per-row CSR (irregular matrices): a subwarp of S lanes owns R
@@ -477,6 +482,7 @@ __global__ void __launch_bounds__(256, 5) csr_merge_kernel(CsrArgs<VT, XT> a, in
   __shared__ AT s_tail[256];
   __shared__ int s_end[256];
   if (gated(gate)) return;
+  prefetch_slice_l2(a.x, sizeof(XT) * (size_t)a.n_cols, kXPrefetchBlocks);
   const int t = threadIdx.x;
   const int64_t total = a.n + nnz;
   const int64_t tile = blockIdx.x;
@@ -717,12 +723,19 @@ struct EllArgs {
   XT* y;
   acc_t<VT> alpha, beta;
   bool plain;
+  // SELL-P: slice height and slice offsets (sets[s]: first column of slice s)
+  int32_t C = 0;
+  const int32_t* sets = nullptr;
 };
 
 // Column-major ELL: each thread owns RPT consecutive rows and reads slot k of
 // all of them with one 128-bit (or 64-bit) load per array; padding slots
 // (col = -1) never touch x.
-template <int RPT, typename VT, typename XT, bool DOT>
+// SELL (SELL-P): the same walk inside the thread's slice, whose own width and
+// first column come from sets[]; slot k of row i is at (sets[s] + k) * C +
+// i % C.  Slices of 64 rows are one warp's rows in FP64 (2 per thread), so a
+// warp's trip count is its slice width.
+template <int RPT, typename VT, typename XT, bool DOT, bool SELL>
 __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, int expected, const int* gate) {
   using AT = acc_t<VT>;
   constexpr int U = 4;
@@ -731,16 +744,25 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
   double dwy = 0.0, dyy = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i0 = g * RPT;
+    int32_t width = a.K;
+    int64_t first = i0, step = a.stride;
+    if (SELL) {
+      const int64_t sl = i0 / a.C;
+      const int32_t b = __ldg(a.sets + sl);
+      width = __ldg(a.sets + sl + 1) - b;
+      first = (int64_t)b * a.C + (i0 - sl * a.C);
+      step = a.C;
+    }
     AT sum[RPT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) sum[r] = AT(0);
-    for (int32_t k = 0; k < a.K; k += U) {
+    for (int32_t k = 0; k < width; k += U) {
       int32_t c[U][RPT];
       VT v[U][RPT];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (k + u < a.K) {
-          const int64_t off = (int64_t)(k + u) * a.stride + i0;
+        if (k + u < width) {
+          const int64_t off = (int64_t)(k + u) * step + first;
           ell_cols<RPT>(a.col + off, c[u]);
           EllVec<VT, RPT>::load(a.val + off, v[u]);
         } else {
@@ -771,7 +793,7 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
 
 template <typename VT, typename XT>
 struct CooArgs {
-  int64_t n_rows, nnz;
+  int64_t n_rows, n_cols, nnz;
   const int32_t* row;
   const int32_t* col;
   const VT* val;
@@ -882,6 +904,7 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
   __shared__ int s_end[kCooThreads];
   __shared__ int32_t s_prev_row;
   if (gated(gate)) return;
+  prefetch_slice_l2(a.x, sizeof(XT) * (size_t)a.n_cols, kXPrefetchBlocks);
   const int t = threadIdx.x;
   const int64_t tile = blockIdx.x;
   const int64_t base = tile * kTile;
@@ -1029,8 +1052,10 @@ struct SpmvImpl {
   using AT = acc_t<VT>;
 
   static CsrArgs<VT, XT> csr_args(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta) {
-    return CsrArgs<VT, XT>{A->n_rows, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val), x, y,
-                           alpha, beta, A->plan.long_thr, alpha == AT(1) && beta == AT(0)};
+    CsrArgs<VT, XT> a{A->n_rows, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val), x, y,
+                      alpha, beta, A->plan.long_thr, alpha == AT(1) && beta == AT(0)};
+    a.n_cols = A->n_cols;
+    return a;
   }
 
   template <int S, int R, bool DOT>
@@ -1164,11 +1189,11 @@ struct SpmvImpl {
 
   static constexpr int ell_rpt() { return sizeof(VT) == 8 ? 2 : 4; }
 
-  template <bool DOT>
+  template <bool DOT, bool SELL = false>
   static int ell_launch(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s,
                         const DotSpec& d, const int* gate) {
     constexpr int RPT = ell_rpt();
-    auto kern = ell_kernel<RPT, VT, XT, DOT>;
+    auto kern = ell_kernel<RPT, VT, XT, DOT, SELL>;
     static int per_sm = resident_blocks(kern, 256);
     const int64_t groups = (A->n_rows + RPT - 1) / RPT;
     int64_t g = (groups + 255) / 256;
@@ -1178,6 +1203,12 @@ struct SpmvImpl {
     if (g < 1) g = 1;
     EllArgs<VT, XT> a{A->n_rows, A->K, A->stride, ptr<int32_t>(A->ell_col), ptr<VT>(A->ell_val), x, y, alpha, beta,
                       alpha == AT(1) && beta == AT(0)};
+    if (SELL) {
+      a.col = ptr<int32_t>(A->sellp_col);
+      a.val = ptr<VT>(A->sellp_val);
+      a.C = A->slice;
+      a.sets = ptr<int32_t>(A->sellp_sets);
+    }
     kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g, gate);
     GKO_TRY_CUDA(cudaGetLastError());
     return GKO_OK;
@@ -1195,8 +1226,8 @@ struct SpmvImpl {
       return GKO_OK;
     }
     AT* carry = static_cast<AT*>(scratch);
-    CooArgs<VT, XT> a{A->n_rows, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col), ptr<VT>(A->coo_val),
-                      x, y, alpha, beta, alpha == AT(1) && beta == AT(0)};
+    CooArgs<VT, XT> a{A->n_rows, A->n_cols, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col),
+                      ptr<VT>(A->coo_val), x, y, alpha, beta, alpha == AT(1) && beta == AT(0)};
     constexpr int kMinB = coo_min_blocks<VT>();
     const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
     const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
@@ -1231,6 +1262,9 @@ struct SpmvImpl {
           return GKO_OK;
         }
         return coo_part(A, x, y, alpha, beta, s, scratch, false, gate);
+      case GKO_SELLP:
+        return dot ? ell_launch<true, true>(A, x, y, alpha, beta, s, d, gate)
+                   : ell_launch<false, true>(A, x, y, alpha, beta, s, d, gate);
       case GKO_HYBRID:
         GKO_TRY(ell_launch<false>(A, x, y, alpha, beta, s, d, gate));
         return coo_part(A, x, y, alpha, beta, s, scratch, true, gate);

@@ -80,4 +80,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for).
+// src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// The first `parts` blocks of a grid each prefetch one 16-byte-aligned slice
+// of the `bytes` at `src` into L2 (thread 0 only), so that gathers from a
+// vector read in random order hit L2 instead of waiting on DRAM.
+__device__ __forceinline__ void prefetch_slice_l2(const void* src, size_t bytes, unsigned parts) {
+  if (threadIdx.x != 0 || blockIdx.x >= parts || bytes < 16) return;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+  if (hi <= lo) return;
+  const uintptr_t span = hi - lo;
+  const uintptr_t slice = ((span + parts - 1) / parts + 15) & ~uintptr_t(15);
+  const uintptr_t s0 = lo + (uintptr_t)blockIdx.x * slice;
+  if (s0 >= hi) return;
+  const uintptr_t s1 = s0 + slice < hi ? s0 + slice : hi;
+  bulk_prefetch_l2(reinterpret_cast<const void*>(s0), (unsigned)(s1 - s0));
+}
+
 }  // namespace gko

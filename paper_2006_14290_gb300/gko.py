@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libgko_gb300.so")
 OK, INVALID_ARG, OUT_OF_MEMORY, FORMAT_UNSUITABLE, NOT_CONVERGED, BREAKDOWN, TIMEOUT, CUDA_ERROR, \
     BUDGET_EXCEEDED, NOT_SUPPORTED = range(10)
 F64, F32, BF16 = 0, 1, 2
-CSR, ELL, COO, HYBRID = 0, 1, 2, 3
+CSR, ELL, COO, HYBRID, SELLP = 0, 1, 2, 3, 4
 PRECISION_F64, PRECISION_MIXED_F32, PRECISION_MIXED_BF16 = 0, 1, 2
 
 _lib = None
@@ -66,6 +66,7 @@ SIGNATURES = {
     "gko_matrix_convert_to_ell": (C.c_int, [_P, _D, _P, C.POINTER(_P)]),
     "gko_matrix_convert_to_coo": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "gko_matrix_convert_to_hybrid": (C.c_int, [_P, _I32, _P, C.POINTER(_P)]),
+    "gko_matrix_convert_to_sellp": (C.c_int, [_P, _I32, _D, _P, C.POINTER(_P)]),
     "gko_matrix_convert_values": (C.c_int, [_P, C.c_int, _P, C.POINTER(_P)]),
     "gko_matrix_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _PI64, _PI64, _PI64, _PI32,
                                   _PI64, _PI64, _PI64]),
@@ -217,6 +218,13 @@ class Matrix:
             out["ell_col"] = np.empty(slots, np.int32)
             out["ell_val"] = np.empty(slots, vdt)
             args[3:5] = [out["ell_col"], out["ell_val"]]
+        if inf["format"] == SELLP:  # slice offsets in row_ptr, slots in ell_*
+            n_slices = (inf["n_rows"] + inf["ell_stride"] - 1) // inf["ell_stride"]
+            out["sets"] = np.empty(n_slices + 1, np.int32)
+            out["ell_col"] = np.empty(inf["coo_nnz"], np.int32)
+            out["ell_val"] = np.empty(inf["coo_nnz"], vdt)
+            args[0] = out["sets"]
+            args[3:5] = [out["ell_col"], out["ell_val"]]
         if inf["format"] in (COO, HYBRID):
             out["coo_row"] = np.empty(inf["coo_nnz"], np.int32)
             out["coo_col"] = np.empty(inf["coo_nnz"], np.int32)
@@ -269,6 +277,11 @@ def gko_matrix_convert_to_coo(A: Matrix, stream=None) -> Matrix:
 
 def gko_matrix_convert_to_hybrid(A: Matrix, ell_width: int = -1, stream=None) -> Matrix:
     return _convert(lib().gko_matrix_convert_to_hybrid, "convert_to_hybrid", A.handle, ell_width, stream=stream)
+
+
+def gko_matrix_convert_to_sellp(A: Matrix, slice_size: int = 0, max_fill: float = 0.0, stream=None) -> Matrix:
+    return _convert(lib().gko_matrix_convert_to_sellp, "convert_to_sellp", A.handle, slice_size, max_fill,
+                    stream=stream)
 
 
 def gko_matrix_convert_values(A: Matrix, to: int, stream=None) -> Matrix:

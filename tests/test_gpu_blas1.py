@@ -47,7 +47,7 @@ def test_multi_dot_and_multi_axpy_norm(gko, n, k):
     assert abs(nr - nro) <= 1e-13 * nro
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid", "sellp"])
 def test_spmv_dot(gko, fmt):
     G = gko
     A = I.stencil3d_7pt(20) if fmt != "csr" else I.powerlaw(40000, seed=4)
@@ -58,6 +58,8 @@ def test_spmv_dot(gko, fmt):
         M = G.gko_matrix_convert_to_coo(M)
     elif fmt == "hybrid":
         M = G.gko_matrix_convert_to_hybrid(M)
+    elif fmt == "sellp":
+        M = G.gko_matrix_convert_to_sellp(M)
     x = np.random.default_rng(3).uniform(-1, 1, A.n_cols)
     yd = dev(np.zeros(A.n_rows))
     d = G.gko_spmv_dot(M, dev(x), yd)

@@ -62,7 +62,7 @@ def test_cg_laplace2d_64_matches_oracle(gko):
     assert np.linalg.norm(xg12 - xo12) <= 1e-8 * np.linalg.norm(xo12)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid", "sellp"])
 @pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
 def test_solvers_all_formats(gko, fmt, name):
     G = gko
@@ -74,6 +74,8 @@ def test_solvers_all_formats(gko, fmt, name):
         M = G.gko_matrix_convert_to_coo(M)
     elif fmt == "hybrid":
         M = G.gko_matrix_convert_to_hybrid(M, 3)
+    elif fmt == "sellp":
+        M = G.gko_matrix_convert_to_sellp(M, 32)
     xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=4000)
     xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=4000)
     assert res.status == G.OK and ro.status == 0, (res, ro)

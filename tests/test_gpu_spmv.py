@@ -9,7 +9,7 @@ from paper_2006_14290_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-FORMATS = ["csr", "ell", "coo", "hybrid"]
+FORMATS = ["csr", "ell", "coo", "hybrid", "sellp"]
 
 
 def small_cases():
@@ -40,6 +40,8 @@ def make(G, A, fmt, dtype):
         M = G.gko_matrix_convert_to_coo(M)
     elif fmt == "hybrid":
         M = G.gko_matrix_convert_to_hybrid(M, -1)
+    elif fmt == "sellp":
+        M = G.gko_matrix_convert_to_sellp(M, 64, max_fill=1e9)
     return M
 
 
@@ -105,6 +107,14 @@ def test_conversions_bit_exact(gko, name, A):
         np.testing.assert_array_equal(H["coo_col"], Ho.coo.col)
         assert H["coo_val"].tobytes() == Ho.coo.val.tobytes()
 
+    for C in (32, 64, 128, 256):
+        S = G.gko_matrix_convert_to_sellp(M, C, max_fill=1e9).export()
+        So = O.csr_to_sellp(A, C=C)
+        assert S["ell_stride"] == C and S["coo_nnz"] == So.sets[-1] * C
+        np.testing.assert_array_equal(S["sets"], So.sets)
+        np.testing.assert_array_equal(S["ell_col"], So.col)
+        assert S["ell_val"].tobytes() == So.val.tobytes()
+
 
 def test_value_conversions_round_to_nearest(gko):
     G = gko
@@ -167,6 +177,46 @@ def test_every_plan_matches_oracle(gko, kernel, S, R, cap, mat):
     yd = dev(y0)
     G.gko_spmv(2.0, M, dev(x), -1.0, yd)
     check_spmv_f64(host(yd), A, x, 2.0, -1.0, y0)
+
+
+@pytest.mark.parametrize("C", [32, 128, 256])
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+def test_sellp_slice_sizes(gko, C, dt):
+    """SELL-P at every slice height; ragged last slice, empty rows."""
+    G = gko
+    rng = np.random.default_rng(21)
+    L = rng.integers(0, 30, 5003)
+    L[700:1100] = 0
+    A = I.rows_csr(L, 4000, rng)
+    dtype = {"f64": G.F64, "f32": G.F32, "bf16": G.BF16}[dt]
+    M = G.from_csr(A, G.F64 if dtype in (G.F64, G.BF16) else G.F32)
+    if dtype == G.BF16:
+        M = G.gko_matrix_convert_values(M, G.BF16)
+    S = G.gko_matrix_convert_to_sellp(M, C)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    if dtype == G.F64:
+        yd = dev(y0)
+        G.gko_spmv(0.5, S, dev(x), 2.0, yd)
+        check_spmv_f64(host(yd), A, x, 0.5, 2.0, y0)
+    else:
+        x32 = x.astype(np.float32)
+        yd = dev(y0, np.float32)
+        G.gko_spmv(0.5, S, dev(x32), 2.0, yd)
+        check_spmv_f32(host(yd), A, x32.astype(np.float64), 0.5, 2.0, y0.astype(np.float32).astype(np.float64),
+                       values_for(G, A, dtype))
+
+
+def test_sellp_rejects_bad_slice_and_padding(gko):
+    G = gko
+    M = G.from_csr(I.powerlaw(20000, seed=1))
+    with pytest.raises(G.GkoError) as e:
+        G.gko_matrix_convert_to_sellp(M)  # slices of 64 random power-law rows: padding over 8x nnz
+    assert e.value.status == G.FORMAT_UNSUITABLE
+    for bad in (16, 48, 512):
+        with pytest.raises(G.GkoError) as e:
+            G.gko_matrix_convert_to_sellp(M, bad, max_fill=1e9)
+        assert e.value.status == G.INVALID_ARG
 
 
 def test_coo_plan_defaults(gko):
@@ -341,6 +391,7 @@ def test_full_size_sampled(gko, name):
     formats = [("csr", M64), ("coo", G.gko_matrix_convert_to_coo(M64)), ("hybrid", G.gko_matrix_convert_to_hybrid(M64))]
     if name != "powerlaw_1m":
         formats.append(("ell", G.gko_matrix_convert_to_ell(M64)))
+        formats.append(("sellp", G.gko_matrix_convert_to_sellp(M64)))
     xd = dev(x)
     for fmt, M in formats:
         yd = dev(np.zeros(A.n_rows))
