@@ -723,8 +723,9 @@ struct EllArgs {
   XT* y;
   acc_t<VT> alpha, beta;
   bool plain;
-  // SELL-P: slice height and slice offsets (sets[s]: first column of slice s)
-  int32_t C = 0;
+  // SELL-P: slice height C = 2^cshift and slice offsets (sets[s]: first
+  // column of slice s)
+  int32_t C = 0, cshift = 0;
   const int32_t* sets = nullptr;
 };
 
@@ -747,10 +748,10 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
     int32_t width = a.K;
     int64_t first = i0, step = a.stride;
     if (SELL) {
-      const int64_t sl = i0 / a.C;
+      const int64_t sl = i0 >> a.cshift;
       const int32_t b = __ldg(a.sets + sl);
       width = __ldg(a.sets + sl + 1) - b;
-      first = (int64_t)b * a.C + (i0 - sl * a.C);
+      first = ((int64_t)b << a.cshift) + (i0 & (a.C - 1));
       step = a.C;
     }
     AT sum[RPT];
@@ -1207,6 +1208,7 @@ struct SpmvImpl {
       a.col = ptr<int32_t>(A->sellp_col);
       a.val = ptr<VT>(A->sellp_val);
       a.C = A->slice;
+      while ((1 << a.cshift) < a.C) ++a.cshift;
       a.sets = ptr<int32_t>(A->sellp_sets);
     }
     kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g, gate);
