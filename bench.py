@@ -366,6 +366,45 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
     return out
 
 
+# ------------------------------------------------------ cuSPARSE context --
+
+def cusparse_context(mats, dev, stream, flush, steps, peak):
+    """cuSPARSE CSR SpMV (torch.sparse CSR @ x, int32 indices) on the sweep
+    matrices, timed like the sweep (L2 flushed, CUDA events): an outside
+    reference point on the same GPU, not an oracle and not part of `value`."""
+    import torch
+
+    out = {}
+    for name, A in mats:
+        crow = torch.from_numpy(A.row_ptr.astype(np.int32)).to(dev)
+        col = torch.from_numpy(A.col.astype(np.int32)).to(dev)
+        for dt, tdt, sv in (("f64", torch.float64, 8), ("f32", torch.float32, 4)):
+            try:
+                val = torch.from_numpy(A.val).to(dev, tdt)
+                M = torch.sparse_csr_tensor(crow, col, val, (A.n_rows, A.n_cols))
+                x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, A.n_cols)).to(dev, tdt)
+                for _ in range(3):
+                    y = M @ x
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                for k in range(steps):
+                    flush.fill_(float(k))
+                    ev[k][0].record(stream)
+                    y = M @ x
+                    ev[k][1].record(stream)
+                torch.cuda.synchronize()
+                ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+                nb = spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, sv, sv, sv)
+                out[f"{name}/csr/{dt}"] = {"ms": round(ms, 4), "GB_s": round(nb / (ms * 1e-3) / 1e9, 1),
+                                           "frac": round(nb / (ms * 1e-3) / 1e9 / peak, 4)}
+                del M, val, x, y
+            except (RuntimeError, TypeError) as e:
+                out[f"{name}/csr/{dt}"] = {"unavailable": str(e).splitlines()[0][:160]}
+        del crow, col
+    return {"library": "cuSPARSE CSR SpMV through torch.sparse_csr_tensor @ x (torch " + torch.__version__ + ")",
+            "cases": out}
+
+
 # --------------------------------------------------------------- reference --
 
 def run_reference(args):
@@ -658,6 +697,8 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": int(sum(c["launches"] for c in cases) * args.steps),
         }
+        if not args.no_context:
+            result["cusparse_context"] = cusparse_context(mats, dev, stream, flush, min(args.steps, 10), peak)
         if not args.no_solvers:
             result["solvers"] = solver_suite(G, dev, stream)
         if not args.no_serving:
@@ -679,6 +720,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-context", action="store_true", help="skip the cuSPARSE context leg")
     ap.add_argument("--profile-cases", action="store_true",
                     help="run each SpMV case once (for ncu) and print the case order")
     ap.add_argument("--small", action="store_true", help="with --profile-cases: 27-point stencil at 96^3")
