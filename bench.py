@@ -366,6 +366,41 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
     return out
 
 
+# ------------------------------------------------ subwarp microbenchmark --
+
+def subwarp_microbench(G, dev, stream):
+    """Section 3.3 method: time of 1000 subwarp reductions = t(2000 inner
+    loops) - t(1000), median of 5, for the library primitive, CUDA
+    cooperative groups and the full-warp shuffle, subwarp sizes 4..32, on
+    4 blocks of 256 threads per SM; ratio S=4 / S=32 against log2(4)/log2(32)."""
+    import torch
+
+    props = torch.cuda.get_device_properties(dev)
+    n = 256 * 4 * props.multi_processor_count
+    out = {"threads": n, "theory_ratio_4_over_32": round(2 / 5, 3)}
+    for dt in (torch.float32, torch.float64):
+        data = torch.zeros(n, dtype=dt, device=dev)
+        for impl, iname in ((0, "library"), (1, "cooperative_groups"), (2, "legacy_shfl")):
+            per = {}
+            for S in (4, 8, 16, 32):
+                diffs = []
+                for _ in range(5):
+                    t = []
+                    for loops in (1000, 2000):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        G.gko_bench_subwarp_reduce(S, impl, data, loops, stream=stream)
+                        b.record(stream)
+                        torch.cuda.synchronize()
+                        t.append(a.elapsed_time(b))
+                    diffs.append(t[1] - t[0])
+                per[S] = statistics.median(diffs) * 1e3  # us per 1000 reductions
+            out[f"{'f32' if dt == torch.float32 else 'f64'}/{iname}"] = {
+                "us_per_1000": {str(k): round(v, 2) for k, v in per.items()},
+                "ratio_4_over_32": round(per[4] / per[32], 3) if per[32] > 0 else None}
+    return out
+
+
 # ------------------------------------------------------ cuSPARSE context --
 
 def cusparse_context(mats, dev, stream, flush, steps, peak):
@@ -699,6 +734,7 @@ def run_ours(args):
         }
         if not args.no_context:
             result["cusparse_context"] = cusparse_context(mats, dev, stream, flush, min(args.steps, 10), peak)
+            result["subwarp_reduce"] = subwarp_microbench(G, dev, stream)
         if not args.no_solvers:
             result["solvers"] = solver_suite(G, dev, stream)
         if not args.no_serving:

@@ -383,6 +383,21 @@ GKO_API int gko_server_stats(gko_server S, int64_t *completed, double *p50_ms, d
 /* Stop the workers (requests still queued are dropped) and free the server. */
 GKO_API int gko_server_destroy(gko_server S);
 
+/* --------------------------------------------------- diagnostics -- */
+
+/* Subwarp reduction microbenchmark (paper, Section 3.3: the reduce listing
+ * and its inner-loop difference method).  data: `n` device values of
+ * `dtype` (F64 or F32), n a positive multiple of 256; each value is one
+ * thread's input and receives its output.  Every thread runs `inner_loops`
+ * butterfly reductions over subwarps of `subwarp` consecutive lanes (1, 2,
+ * 4, 8, 16 or 32): in each of log2(subwarp) steps a lane adds the value of
+ * the lane whose index differs in one bit.  impl 0: the library's subwarp
+ * primitive; 1: CUDA cooperative groups tiled_partition; 2: the full-warp
+ * xor shuffle.  Stream-ordered; time two calls (e.g. 2000 and 1000 loops)
+ * and subtract.  GKO_INVALID_ARG on bad sizes. */
+GKO_API int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dtype, int32_t inner_loops,
+                                     void *data, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ _SIGS = {
     "or_sellp_sets": (_I64, [_I64, _P, _I32, _P]),
     "or_csr_to_sellp": (None, [_I64, _P, _P, _P, _I32, _P, _P, _P]),
     "or_spmv_sellp": (None, [_I64, _I32, _P, _P, _P, _P, _D, _D, _P]),
+    "or_subwarp_reduce": (None, [_I64, _I32, _I32, _P]),
     "or_csr_to_coo": (None, [_I64, _P, _P, _P, _P, _P, _P]),
     "or_spmv_coo": (C.c_int, [_I64, _I64, _P, _P, _P, _P, _D, _D, _P]),
     "or_hybrid_width": (_I32, [_I64, _P]),
@@ -191,6 +192,14 @@ def spmv_ell(E: Ell, x, alpha=1.0, beta=0.0, y=None):
     out = _y0(E.n_rows, y, beta)
     lib().or_spmv_ell(E.n_rows, E.K, E.stride, _p(E.col), _p(E.val), _p(x), alpha, beta, _p(out))
     return out
+
+
+def subwarp_reduce(data, S: int, loops: int):
+    """Section 3.3 reduce benchmark: `loops` butterfly reductions over
+    subwarps of S consecutive lanes; returns the lanes' final values."""
+    d = _f64(data).copy()
+    lib().or_subwarp_reduce(d.size, S, loops, _p(d))
+    return d
 
 
 @dataclass

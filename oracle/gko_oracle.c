@@ -217,6 +217,23 @@ void or_spmv_sellp(int64_t n, int32_t C, const int64_t *sets, const int32_t *sco
   }
 }
 
+/* Subwarp butterfly reduction of the paper's Section 3.3 benchmark (the
+ * reduce listing): lanes are grouped into subwarps of S consecutive lanes
+ * (S divides 32); each of `loops` rounds runs log2(S) steps in which every
+ * lane adds the value of the lane whose index differs in bit `bitmask`
+ * (bitmask = 1, 2, ..., S/2), all lanes of a step reading the values of the
+ * previous step.  n must be a multiple of S. */
+void or_subwarp_reduce(int64_t n, int32_t S, int32_t loops, double *data) {
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1));
+  for (int64_t g = 0; g + S <= n; g += S)
+    for (int32_t it = 0; it < loops; ++it)
+      for (int32_t bitmask = 1; bitmask < S; bitmask <<= 1) {
+        for (int32_t l = 0; l < S; ++l) tmp[l] = data[g + l] + data[g + (l ^ bitmask)];
+        for (int32_t l = 0; l < S; ++l) data[g + l] = tmp[l];
+      }
+  free(tmp);
+}
+
 /* COO: row-major expansion of CSR in storage order. */
 void or_csr_to_coo(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                    int32_t *crow, int32_t *ccol, double *cval) {

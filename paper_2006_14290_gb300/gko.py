@@ -76,6 +76,7 @@ SIGNATURES = {
     "gko_matrix_destroy": (C.c_int, [_P]),
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
     "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
+    "gko_bench_subwarp_reduce": (C.c_int, [_I32, _I32, C.c_int, _I32, _P, C.c_int64, _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
     "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
     "gko_axpy": (C.c_int, [_I64, _D, _P, _P, _P]),
@@ -307,6 +308,20 @@ def gko_spmv_coo_noalloc(alpha: float, A: Matrix, x, beta: float, y, stream=None
     _check(lib().gko_spmv_coo_noalloc(C.byref(a), A.handle, _dptr(x), C.byref(b), _dptr(y), _stream(stream)),
            "gko_spmv_coo_noalloc")
     return y
+
+
+SUBWARP_LIBRARY, SUBWARP_COOPERATIVE_GROUPS, SUBWARP_LEGACY = 0, 1, 2
+
+
+def gko_bench_subwarp_reduce(subwarp: int, impl: int, data, inner_loops: int, stream=None):
+    """Section 3.3 subwarp reduction benchmark on a float64/float32 CUDA
+    tensor (length a multiple of 256), in place."""
+    import torch
+
+    dt = F64 if data.dtype == torch.float64 else F32
+    _check(lib().gko_bench_subwarp_reduce(subwarp, impl, dt, inner_loops, _dptr(data), data.numel(),
+                                          _stream(stream)), "gko_bench_subwarp_reduce")
+    return data
 
 
 def gko_dot(x, y, stream=None) -> float:

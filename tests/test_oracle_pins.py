@@ -257,6 +257,18 @@ def test_sellp_padding_never_reads_x():
     assert np.all(np.isfinite(O.spmv_sellp(S, x)))
 
 
+@pytest.mark.parametrize("S", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("loops", [1, 2, 3])
+def test_subwarp_reduce_closed_form(S, loops):
+    """After one butterfly round every lane of a subwarp holds the subwarp
+    sum; each further round multiplies it by S (integer data, exact)."""
+    rng = np.random.default_rng(S * 10 + loops)
+    d = rng.integers(-9, 10, 128).astype(float)
+    out = O.subwarp_reduce(d, S, loops)
+    sums = d.reshape(-1, S).sum(axis=1)
+    np.testing.assert_array_equal(out.reshape(-1, S), np.repeat((sums * S ** (loops - 1))[:, None], S, axis=1))
+
+
 def test_coo_round_trip_and_dense():
     rng = np.random.default_rng(4)
     A = I.random_csr(50, 50, 0.1, rng, integer_values=True, empty_rows=0.3, sort_cols=False)
