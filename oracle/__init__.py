@@ -77,6 +77,10 @@ _SIGS = {
                            C.POINTER(_Result)]),
     "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
                               C.POINTER(_Result)]),
+    "or_jacobi_inv": (None, [_I64, _P, _P, _P, _P]),
+    "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
+    "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32,
+                                 C.POINTER(_Result)]),
 }
 
 
@@ -357,12 +361,38 @@ def gmres(A, b, **kw):
 
 
 def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
-             inner_maxit=1000, restart=30):
-    """Mixed-precision iterative refinement (FP32-stored inner solve, FP64 outer)."""
+             inner_maxit=1000, restart=30, jacobi=False):
+    """Mixed-precision iterative refinement (FP32-stored inner solve, FP64
+    outer); jacobi: the inner CG / BiCGSTAB is Jacobi preconditioned."""
     rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
     val32 = val.astype(np.float32)
     x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     res = _Result()
-    lib().or_solve_ir(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(b), _p(x), tol,
-                      max_outer, inner_tol, inner_maxit, restart, C.byref(res))
+    if jacobi:
+        minv = jacobi_inv(A)
+        lib().or_solve_ir_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(minv), _p(b), _p(x),
+                             tol, max_outer, inner_tol, inner_maxit, C.byref(res))
+    else:
+        lib().or_solve_ir(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(b), _p(x), tol,
+                          max_outer, inner_tol, inner_maxit, restart, C.byref(res))
+    return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
+
+
+def jacobi_inv(A):
+    """Inverse diagonal (diagonal entries of a row summed; zero -> 1)."""
+    rp, col, val = _i32(A.row_ptr), _i32(A.col), _f64(A.val)
+    out = np.empty(A.n_rows)
+    lib().or_jacobi_inv(A.n_rows, _p(rp), _p(col), _p(val), _p(out))
+    return out
+
+
+def solve_jacobi(solver: int, A, b, x0=None, tol=1e-10, maxit=1000):
+    """Jacobi-preconditioned FP64 CG (Saad Alg. 9.1) or right-preconditioned
+    BiCGSTAB.  Returns (x, SolveResult)."""
+    rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
+    minv = jacobi_inv(A)
+    x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    res = _Result()
+    lib().or_solve_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(minv), _p(b), _p(x), tol, maxit,
+                      C.byref(res))
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)

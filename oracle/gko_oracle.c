@@ -407,19 +407,41 @@ typedef struct {
   int true_check;
   double *hist;
   int32_t hist_len;
+  const double *minv; /* Jacobi preconditioner: inverse diagonal, or NULL */
 } or_ctx;
+
+/* z = M^-1 r for the Jacobi preconditioner M = diag(A) (Saad, Sec. 10.2);
+ * the identity without one. */
+static void precond(const or_ctx *c, const double *r, double *z) {
+  for (int64_t i = 0; i < c->A->n; ++i) z[i] = c->minv ? st(c->f32, c->minv[i] * r[i]) : r[i];
+}
+
+/* Inverse diagonal of a CSR matrix: diagonal entries of a row summed in
+ * storage order (duplicates add up as in the SpMV); a zero or missing
+ * diagonal gives 1 (that row is left unscaled). */
+void or_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const double *val, double *minv) {
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] == i) d += val[k];
+    minv[i] = d != 0.0 ? 1.0 / d : 1.0;
+  }
+}
 
 static void hist_put(const or_ctx *c, int32_t it, double v) {
   if (c->hist && it >= 1 && it <= c->hist_len) c->hist[it - 1] = v;
 }
 
-/* CG (Saad Alg. 6.18), x holds x0 on entry and the iterate on exit. */
+/* CG (Saad Alg. 6.18), or preconditioned CG with z = M^-1 r (Saad Alg.
+ * 9.1) when c->minv is set; convergence is always judged on ||r||.  x holds
+ * x0 on entry and the iterate on exit. */
 static or_result cg_core(const or_ctx *c, const double *b, double *x, double tol, int32_t maxit) {
   const or_op *A = c->A;
   int64_t n = A->n;
   or_result res = {OR_OK, 0, 0, 0, 0.0};
   double *r = calloc((size_t)n + 1, sizeof(double)), *p = calloc((size_t)n + 1, sizeof(double));
   double *q = calloc((size_t)n + 1, sizeof(double)), *t = calloc((size_t)n + 1, sizeof(double));
+  double *z = calloc((size_t)n + 1, sizeof(double));
   double nb = nrm2(n, b);
   if (nb == 0.0) {
     for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
@@ -427,9 +449,10 @@ static or_result cg_core(const or_ctx *c, const double *b, double *x, double tol
   }
   residual(A, b, x, r, t);
   for (int64_t i = 0; i < n; ++i) r[i] = st(c->f32, r[i]);
-  for (int64_t i = 0; i < n; ++i) p[i] = r[i];
-  double rho = dot(n, r, r);
-  int converged = sqrt(rho) <= tol * nb;
+  precond(c, r, z);
+  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  double rho = dot(n, r, z);
+  int converged = nrm2(n, r) <= tol * nb;
   int32_t it = 0;
   while (!converged && it < maxit) {
     op_apply(A, p, q);
@@ -444,10 +467,10 @@ static or_result cg_core(const or_ctx *c, const double *b, double *x, double tol
       x[i] = st(c->f32, x[i] + alpha * p[i]);
       r[i] = st(c->f32, r[i] - alpha * q[i]);
     }
-    double rho_new = dot(n, r, r);
+    double nr = nrm2(n, r);
     ++it;
-    hist_put(c, it, sqrt(rho_new) / nb);
-    if (sqrt(rho_new) <= tol * nb) {
+    hist_put(c, it, nr / nb);
+    if (nr <= tol * nb) {
       if (!c->true_check) {
         converged = 1;
         break;
@@ -458,10 +481,11 @@ static or_result cg_core(const or_ctx *c, const double *b, double *x, double tol
         break;
       }
       for (int64_t i = 0; i < n; ++i) r[i] = t[i]; /* residual replacement */
-      rho_new = dot(n, r, r);
     }
+    precond(c, r, z);
+    double rho_new = dot(n, r, z);
     double beta = rho_new / rho;
-    for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, r[i] + beta * p[i]);
+    for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, z[i] + beta * p[i]);
     rho = rho_new;
   }
   res.iterations = it;
@@ -477,10 +501,13 @@ done:
   free(p);
   free(q);
   free(t);
+  free(z);
   return res;
 }
 
-/* BiCGSTAB (van der Vorst 1992; Saad Alg. 7.7). */
+/* BiCGSTAB (van der Vorst 1992; Saad Alg. 7.7); with c->minv the right
+ * preconditioned form: the products are A (M^-1 p) and A (M^-1 s), and x
+ * moves along M^-1 p and M^-1 s. */
 static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, double tol,
                                int32_t maxit) {
   const or_op *A = c->A;
@@ -489,6 +516,7 @@ static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, doub
   size_t sz = (size_t)n + 1;
   double *r = calloc(sz, 8), *rh = calloc(sz, 8), *p = calloc(sz, 8), *v = calloc(sz, 8);
   double *s = calloc(sz, 8), *t = calloc(sz, 8), *w = calloc(sz, 8);
+  double *ph = calloc(sz, 8), *sh = calloc(sz, 8);
   double nb = nrm2(n, b);
   int converged = 0;
   int32_t it = 0;
@@ -508,7 +536,8 @@ static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, doub
     }
     double beta = (rho_new / rho) * (alpha / omega);
     for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, r[i] + beta * (p[i] - omega * v[i]));
-    op_apply(A, p, v);
+    precond(c, p, ph);
+    op_apply(A, ph, v);
     for (int64_t i = 0; i < n; ++i) v[i] = st(c->f32, v[i]);
     double rv = dot(n, rh, v);
     if (rv == 0.0) {
@@ -520,7 +549,7 @@ static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, doub
     ++it;
     int restart = 0;
     if (nrm2(n, s) <= tol * nb) {
-      for (int64_t i = 0; i < n; ++i) x[i] = st(c->f32, x[i] + alpha * p[i]);
+      for (int64_t i = 0; i < n; ++i) x[i] = st(c->f32, x[i] + alpha * ph[i]);
       hist_put(c, it, nrm2(n, s) / nb);
       if (!c->true_check) {
         converged = 1;
@@ -533,7 +562,8 @@ static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, doub
       }
       restart = 1;
     } else {
-      op_apply(A, s, t);
+      precond(c, s, sh);
+      op_apply(A, sh, t);
       for (int64_t i = 0; i < n; ++i) t[i] = st(c->f32, t[i]);
       double tt = dot(n, t, t);
       if (tt == 0.0) {
@@ -542,7 +572,7 @@ static or_result bicgstab_core(const or_ctx *c, const double *b, double *x, doub
       }
       omega = dot(n, t, s) / tt;
       for (int64_t i = 0; i < n; ++i) {
-        x[i] = st(c->f32, x[i] + alpha * p[i] + omega * s[i]);
+        x[i] = st(c->f32, x[i] + alpha * ph[i] + omega * sh[i]);
         r[i] = st(c->f32, s[i] - omega * t[i]);
       }
       rho = rho_new;
@@ -588,6 +618,8 @@ done:
   free(s);
   free(t);
   free(w);
+  free(ph);
+  free(sh);
   return res;
 }
 
@@ -722,8 +754,23 @@ int or_solve(int solver, int64_t n, const int32_t *rp, const int32_t *col, const
              const double *b, double *x, double tol, int32_t maxit, int32_t restart,
              double *hist, int32_t hist_len, or_result *out) {
   or_op A = {n, rp, col, val, NULL};
-  or_ctx c = {&A, 0, 1, hist, hist_len};
+  or_ctx c = {&A, 0, 1, hist, hist_len, NULL};
   *out = run_solver(&c, solver, b, x, tol, maxit, restart);
+  return out->status;
+}
+
+/* Jacobi-preconditioned FP64 CG / BiCGSTAB (minv: the inverse diagonal from
+ * or_jacobi_inv).  GMRES is not offered with a preconditioner (OR_INVALID). */
+int or_solve_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                const double *minv, const double *b, double *x, double tol, int32_t maxit, or_result *out) {
+  or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+  if (solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) {
+    *out = bad;
+    return OR_INVALID;
+  }
+  or_op A = {n, rp, col, val, NULL};
+  or_ctx c = {&A, 0, 1, NULL, 0, minv};
+  *out = run_solver(&c, solver, b, x, tol, maxit, 0);
   return out->status;
 }
 
@@ -732,14 +779,43 @@ int or_solve(int solver, int64_t n, const int32_t *rp, const int32_t *col, const
  * and vectors (FP32 SpMV accumulation, FP64 dots and scalars) to
  * ||r_inner|| <= max(inner_tol, min(0.5, 0.5 tol ||b|| / ||r||)) ||r||;
  * x += d in FP64 }. */
+static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                    const float *val32, const double *minv, const double *b, double *x, double tol,
+                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out);
+
 int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                 const float *val32, const double *b, double *x, double tol, int32_t max_outer,
                 double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
+  return solve_ir(solver, n, rp, col, val, val32, NULL, b, x, tol, max_outer, inner_tol, inner_maxit, restart, out);
+}
+
+/* Mixed-precision refinement whose inner CG / BiCGSTAB is Jacobi
+ * preconditioned with the FP64 inverse diagonal rounded to FP32 (the inner
+ * solve stores everything in FP32). */
+int or_solve_ir_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   const float *val32, const double *minv, const double *b, double *x, double tol,
+                   int32_t max_outer, double inner_tol, int32_t inner_maxit, or_result *out) {
+  if (solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) {
+    or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+    *out = bad;
+    return OR_INVALID;
+  }
+  return solve_ir(solver, n, rp, col, val, val32, minv, b, x, tol, max_outer, inner_tol, inner_maxit, 0, out);
+}
+
+static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                    const float *val32, const double *minv, const double *b, double *x, double tol,
+                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
   or_op A64 = {n, rp, col, val, NULL};
   or_op A32 = {n, rp, col, NULL, val32};
-  or_ctx inner = {&A32, 1, 0, NULL, 0};
-  or_result res = {OR_OK, 0, 0, 0, 0.0};
   size_t sz = (size_t)n + 1;
+  double *minv32 = NULL;
+  if (minv) {
+    minv32 = calloc(sz, 8);
+    for (int64_t i = 0; i < n; ++i) minv32[i] = (double)(float)minv[i];
+  }
+  or_ctx inner = {&A32, 1, 0, NULL, 0, minv32};
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
   double *r = calloc(sz, 8), *d = calloc(sz, 8), *tmp = calloc(sz, 8);
   double nb = nrm2(n, b);
   int converged = 0;
@@ -776,6 +852,7 @@ int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, co
   free(r);
   free(d);
   free(tmp);
+  free(minv32);
   *out = res;
   return res.status;
 }

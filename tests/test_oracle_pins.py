@@ -501,3 +501,67 @@ def test_blas1_exact_on_integers_and_rationals():
     ex = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(xf, yf))
     bound = 50 * U64 * float(sum(abs(Fraction(float(a)) * Fraction(float(b))) for a, b in zip(xf, yf)))
     assert abs(O.dot(xf, yf) - float(ex)) <= bound
+
+
+# -------------------------------------------------------------- Jacobi --
+
+def test_jacobi_inv_sums_diagonal_duplicates_and_guards_zero():
+    A = I.Csr(3, 3, np.array([0, 3, 3, 5], np.int32), np.array([0, 1, 0, 2, 2], np.int32),
+              np.array([2.0, 7.0, 2.0, 1.0, 3.0]))
+    np.testing.assert_array_equal(O.jacobi_inv(A), [0.25, 1.0, 0.25])
+
+
+def test_pcg_on_diagonal_matrix_is_exact_in_one_step():
+    d = np.array([1.0, 4.0, 0.5, 8.0, 2.0])
+    A = I.rows_csr([1] * 5, 5, np.random.default_rng(0))
+    A.col[:] = np.arange(5)
+    A.val[:] = d
+    b = np.array([3.0, 1.0, -2.0, 4.0, 0.5])
+    x, r = O.solve_jacobi(O.CG, A, b, tol=1e-14, maxit=10)
+    assert r.status == 0 and r.iterations == 1
+    np.testing.assert_allclose(x, b / d, rtol=1e-15)
+
+
+def test_pcg_equals_cg_for_constant_diagonal():
+    """M = 6 I: z = r/6 is a uniform rescaling, so PCG runs CG's iterates."""
+    A = I.stencil3d_7pt(6)
+    b = dense(A) @ np.ones(A.n_rows)
+    x1, r1 = O.cg(A, b, tol=1e-12, maxit=500)
+    x2, r2 = O.solve_jacobi(O.CG, A, b, tol=1e-12, maxit=500)
+    assert r1.iterations == r2.iterations
+    np.testing.assert_allclose(x2, x1, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_jacobi_solves_badly_scaled_systems(solver):
+    """D A D with a wide diagonal scaling D: the Jacobi-preconditioned solve
+    matches a dense solve and needs far fewer iterations than without."""
+    rng = np.random.default_rng(3)
+    A = I.laplace2d_5pt(12) if solver == "cg" else I.convdiff3d_7pt(5, 2.0)
+    n = A.n_rows
+    s = np.exp(rng.uniform(-3, 3, n))
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    A.val[:] = A.val * s[rows] * s[A.col]
+    b = rng.uniform(-1, 1, n)
+    xd = np.linalg.solve(dense(A), b)
+    which = O.CG if solver == "cg" else O.BICGSTAB
+    x0, r0 = O.solve(which, A, b, tol=1e-10, maxit=20000)
+    x1, r1 = O.solve_jacobi(which, A, b, tol=1e-10, maxit=20000)
+    assert r1.status == 0 and r1.rel_residual <= 1e-10
+    assert np.linalg.norm(x1 - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert r1.iterations < 0.5 * r0.iterations, (r1.iterations, r0.iterations)
+
+
+def test_jacobi_ir_reaches_fp64_tolerance():
+    rng = np.random.default_rng(5)
+    A = I.varcoef3d_7pt(8, rng)
+    b = dense(A) @ np.ones(A.n_rows)
+    x, r = O.solve_ir(O.CG, A, b, tol=1e-10, inner_tol=1e-5, jacobi=True)
+    assert r.status == 0 and r.rel_residual <= 1e-10 and r.outer_iterations >= 2
+    np.testing.assert_allclose(x, np.ones(A.n_rows), rtol=1e-7)
+
+
+def test_jacobi_gmres_refused():
+    A = I.laplace2d_5pt(4)
+    x, r = O.solve_jacobi(O.GMRES, A, np.ones(16))
+    assert r.status == 1
