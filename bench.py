@@ -175,11 +175,11 @@ def solver_suite(G, dev, stream):
 
     out = {}
 
-    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30):
+    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0):
         fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
         if solver == "bicgstab":
             maxit = 2000
-        opts = G.opts(precision=prec, restart=restart, inner_maxit=2000, max_outer=12)
+        opts = G.opts(precision=prec, restart=restart, inner_maxit=2000, max_outer=12, preconditioner=pc)
         if tag == "bicgstab_convdiff128_mixed_f32":  # known not to converge: keep it short
             opts = G.opts(precision=prec, inner_maxit=500, max_outer=3)
         xd = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -196,7 +196,7 @@ def solver_suite(G, dev, stream):
         ms = e0.elapsed_time(e1)
         sv = 8 if prec == G.PRECISION_F64 else (4 if prec == G.PRECISION_MIXED_F32 else 2)
         vb = 8 if prec == G.PRECISION_F64 else 4
-        per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver]
+        per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver] + (2 if pc else 0)
         spmvs = {"cg": 1, "bicgstab": 2, "gmres": 1}[solver]
         it_bytes = spmvs * (nnz * (sv + 4) + 4 * (n + 1) + 2 * vb * n) + per_vec_passes * vb * n
         out[tag] = {"status": int(res.status), "iterations": int(res.iterations),
@@ -249,6 +249,21 @@ def solver_suite(G, dev, stream):
     t64 = run("bicgstab_convdiff128_P1_f64", "bicgstab", M, bd, n, nnz, G.PRECISION_F64)
     t32 = run("bicgstab_convdiff128_P1_mixed_f32", "bicgstab", M, bd, n, nnz, G.PRECISION_MIXED_F32)
     out["bicgstab_convdiff128_P1_mixed_f32_speedup"] = round(t64 / t32, 3)
+    del M, ones, bd
+    # Jacobi preconditioning on the variable-coefficient Poisson problem 128^3
+    # (coefficients exp(N(0,1)) per cell, default_rng(0); b = A*1)
+    A = I.varcoef3d_7pt(128, np.random.default_rng(0))
+    M = G.from_csr(A)
+    n, nnz = A.n_rows, A.nnz
+    del A
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
+    t0 = run("cg_varcoef128_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
+    tj = run("cg_varcoef128_jacobi_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_JACOBI)
+    tm = run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
+    out["cg_varcoef128_jacobi_speedup"] = round(t0 / tj, 3)
+    out["cg_varcoef128_jacobi_mixed_f32_speedup"] = round(t0 / tm, 3)
     del M, ones, bd
     out["batched_cg"] = batched_suite(G, dev, stream)
     return out

@@ -245,6 +245,17 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
 #define GKO_PRECISION_MIXED_F32 1  /* FP32 inner solve + FP64 refinement         */
 #define GKO_PRECISION_MIXED_BF16 2 /* BF16-valued inner SpMV + FP64 refinement   */
 
+/* Preconditioners (paper, Section 1 lists them beside the solvers; M =
+ * diag(A), Saad, Iterative Methods for Sparse Linear Systems, Sec. 10.2).
+ * JACOBI: CG becomes preconditioned CG (Saad Alg. 9.1) and BiCGSTAB is
+ * right preconditioned; convergence is still judged on the unpreconditioned
+ * residual ||b - A x||.  The inverse diagonal is built per solve from the FP64
+ * matrix (diagonal duplicates summed, a zero diagonal taken as 1) and, for
+ * mixed precision, rounded to FP32 for the inner solve.  GMRES with a
+ * preconditioner returns GKO_NOT_SUPPORTED. */
+#define GKO_PRECOND_NONE 0
+#define GKO_PRECOND_JACOBI 1
+
 typedef struct {
   int32_t restart;      /* GMRES restart length m (<= 0: 30; at most 128)        */
   int32_t precision;    /* GKO_PRECISION_*                                       */
@@ -252,7 +263,7 @@ typedef struct {
   int32_t max_outer;    /* mixed: refinement steps (<= 0: 30)                    */
   int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters) */
   int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */
-  int32_t reserved;
+  int32_t preconditioner; /* GKO_PRECOND_NONE or GKO_PRECOND_JACOBI (CG, BiCGSTAB) */
 } gko_solve_opts;
 
 typedef struct {
@@ -263,7 +274,7 @@ typedef struct {
   double rel_residual;      /* true ||b - A x||_2 / ||b||_2, computed in FP64      */
 } gko_solve_result;
 
-/* Solve A x = b with unpreconditioned Krylov methods (paper, Section 1:
+/* Solve A x = b with Krylov methods (paper, Section 1:
  * CG, BiCG(STAB), GMRES; Section 4: CG timed on GPUs).
  *   A: square FP64 matrix of any format (for mixed precision an FP32 or
  *      BF16 copy is made once and cached on the handle);

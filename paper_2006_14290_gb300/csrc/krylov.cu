@@ -141,7 +141,8 @@ struct InitOp {
   Ctl* c;
   double rel_tol;
   int kind;  // 0 CG, 1 BiCGSTAB, 2 GMRES (GMRES runs its own restart step)
-  __device__ void operator()(const double (&t)[2]) const {
+  // t[0] = b.b, t[1] = r.r, t[2] = r.z (z = M^-1 r with a preconditioner, else r)
+  __device__ void operator()(const double (&t)[3]) const {
     c->nb = sqrt(t[0]);
     c->tol_abs = rel_tol * c->nb;
     c->rr = t[1];
@@ -162,7 +163,7 @@ struct InitOp {
     c->status = kRun;
     c->done = 0;
     if (kind == 0) {
-      c->rho = t[1];
+      c->rho = t[2];
     } else if (kind == 1) {
       c->rho = c->alpha = c->omega = 1.0;
       c->rho_new = t[1];  // rhat = r
@@ -171,29 +172,35 @@ struct InitOp {
   }
 };
 
+// c1 receives z = d * r when the Jacobi inverse diagonal d is given (CG's
+// first direction), else a copy of r.
 template <typename T>
 __global__ void __launch_bounds__(256) init_residual_kernel(int64_t n, const double* __restrict__ b,
                                                             const T* __restrict__ q, T* __restrict__ r, T* c1, T* c2,
-                                                            T* z1, T* z2, RedWs ws, InitOp op) {
-  double acc[2] = {0.0, 0.0};
+                                                            T* z1, T* z2, RedWs ws, InitOp op,
+                                                            const T* __restrict__ d = nullptr) {
+  double acc[3] = {0.0, 0.0, 0.0};
   GKO_GRID_LOOP(i, n) {
     const double bi = b[i];
     const T ri = (T)(q ? bi - wd(q[i]) : bi);
+    const T zi = d ? d[i] * ri : ri;
     r[i] = ri;
-    if (c1) c1[i] = ri;
+    if (c1) c1[i] = zi;
     if (c2) c2[i] = ri;
     if (z1) z1[i] = T(0);
     if (z2) z2[i] = T(0);
     acc[0] += bi * bi;
     acc[1] += wd(ri) * wd(ri);
+    acc[2] += wd(ri) * wd(zi);
   }
-  reduce_op<2>(acc, ws, op);
+  reduce_op<3>(acc, ws, op);
 }
 
 // t = b - q stored into q; ||t||^2 decides: converged, or replace r by t.
+// t[0] = ||t||^2, t[1] = t.(d t) (= t[0] without a preconditioner)
 struct TrueResOp {
   Ctl* c;
-  __device__ void operator()(const double (&t)[1]) const {
+  __device__ void operator()(const double (&t)[2]) const {
     if (sqrt(t[0]) <= c->tol_abs) {
       c->status = kConverged;
       c->done = 1;
@@ -201,7 +208,7 @@ struct TrueResOp {
       c->status = kRun;
       c->done = 0;
       c->replace = 1;
-      c->rho_new = t[0];
+      c->rho_new = t[1];
       c->phase = 0;
     }
   }
@@ -209,14 +216,15 @@ struct TrueResOp {
 
 template <typename T>
 __global__ void __launch_bounds__(256) true_res_kernel(int64_t n, const double* __restrict__ b, T* __restrict__ q,
-                                                       RedWs ws, TrueResOp op) {
-  double acc[1] = {0.0};
+                                                       RedWs ws, TrueResOp op, const T* __restrict__ d = nullptr) {
+  double acc[2] = {0.0, 0.0};
   GKO_GRID_LOOP(i, n) {
     const T t = (T)(b[i] - wd(q[i]));
     q[i] = t;
     acc[0] += wd(t) * wd(t);
+    acc[1] += wd(t) * wd(d ? d[i] * t : t);
   }
-  reduce_op<1>(acc, ws, op);
+  reduce_op<2>(acc, ws, op);
 }
 
 // red[0] = w.y, red[1] = y.y (formats whose SpMV cannot fuse the dot).
@@ -243,19 +251,21 @@ __global__ void __launch_bounds__(256) dot2_kernel(int64_t n, const T* __restric
 
 // ------------------------------------------------------------------- CG --
 
+// t[0] = r.r (convergence); with a preconditioner t[1] = r.z (the new rho)
+template <int NV>
 struct CgUpdateOp {
   Ctl* c;
-  __device__ void operator()(const double (&t)[1]) const {
+  __device__ void operator()(const double (&t)[NV]) const {
     const double pq = c->red[0];
     if (!(pq > 0.0)) {
       c->status = kBreakdown;
       c->done = 1;
       return;
     }
-    const double rho_new = t[0];
+    const double rho_new = t[NV - 1];
     c->iter += 1;
     c->rho_new = rho_new;
-    if (sqrt(rho_new) <= c->tol_abs) {
+    if (sqrt(t[0]) <= c->tol_abs) {
       c->status = c->check_true ? kCheck : kConverged;
       c->done = 1;
       return;
@@ -270,28 +280,32 @@ struct CgUpdateOp {
   }
 };
 
-// alpha = rho / (p.q); x += alpha p; r -= alpha q; reduces r.r
-template <typename T>
+// alpha = rho / (p.q); x += alpha p; r -= alpha q; reduces r.r and, with
+// the Jacobi inverse diagonal d (PC), r.z for z = d r.
+template <typename T, bool PC>
 __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
                                                         const T* __restrict__ p, const T* __restrict__ q, Ctl* c,
-                                                        RedWs ws) {
+                                                        RedWs ws, const T* __restrict__ d) {
+  constexpr int NV = PC ? 2 : 1;
   if (gated(&c->done)) return;
   const double pq = c->red[0];
   const bool ok = pq > 0.0;
   const double alpha = ok ? c->rho / pq : 0.0;
-  double acc[1] = {0.0};
+  double acc[NV] = {};
   if (ok) {
     const Lin<T> ax(alpha), ar(-alpha);
-    const bool aligned = al16(x) && al16(r) && al16(p) && al16(q);
+    const bool aligned = al16(x) && al16(r) && al16(p) && al16(q) && (!PC || al16(d));
     vec_loop<T>(n, aligned, [&](int64_t i0) {
-          Vec16<T> xv = vload(x + i0), rv = vload(r + i0);
+          Vec16<T> xv = vload(x + i0), rv = vload(r + i0), dv;
           const Vec16<T> pv = vload(p + i0), qv = vload(q + i0);
+          if (PC) dv = vload(d + i0);
 #pragma unroll
           for (int k = 0; k < Vec16<T>::N; ++k) {
             xv.v[k] = ax(pv.v[k], xv.v[k]);
             rv.v[k] = ar(qv.v[k], rv.v[k]);
             const double rw = wd(rv.v[k]);
             acc[0] = __fma_rn(rw, rw, acc[0]);
+            if (PC) acc[NV - 1] = __fma_rn(rw, wd(dv.v[k] * rv.v[k]), acc[NV - 1]);
           }
           vstore(x + i0, xv);
           vstore(r + i0, rv);
@@ -301,23 +315,28 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
           r[i] = ri;
           const double rw = wd(ri);
           acc[0] = __fma_rn(rw, rw, acc[0]);
+          if (PC) acc[NV - 1] = __fma_rn(rw, wd(d[i] * ri), acc[NV - 1]);
         });
   }
-  reduce_op<1>(acc, ws, CgUpdateOp{c});
+  reduce_op<NV>(acc, ws, CgUpdateOp<NV>{c});
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c) {
+// p = z + beta p, z = d r with the Jacobi inverse diagonal (PC), else r
+template <typename T, bool PC>
+__global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c,
+                                                   const T* __restrict__ d) {
   if (gated(&c->done)) return;
   const Lin<T> bp(c->beta);
-  const bool aligned = al16(r) && al16(p);
+  const bool aligned = al16(r) && al16(p) && (!PC || al16(d));
   vec_loop<T>(n, aligned, [&](int64_t i0) {
         Vec16<T> pv = vload(p + i0);
         const Vec16<T> rv = vload(r + i0);
+        Vec16<T> dv;
+        if (PC) dv = vload(d + i0);
 #pragma unroll
-        for (int k = 0; k < Vec16<T>::N; ++k) pv.v[k] = bp(pv.v[k], rv.v[k]);
+        for (int k = 0; k < Vec16<T>::N; ++k) pv.v[k] = bp(pv.v[k], PC ? dv.v[k] * rv.v[k] : rv.v[k]);
         vstore(p + i0, pv);
-      }, [&](int64_t i) { p[i] = bp(p[i], r[i]); });
+      }, [&](int64_t i) { p[i] = bp(p[i], PC ? d[i] * r[i] : r[i]); });
 }
 
 // after a failed true-residual check: r = t, beta = rho_new/rho, p = r + beta p
@@ -331,26 +350,37 @@ struct CgReplaceOp {
 
 template <typename T>
 __global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
-                                                         const T* __restrict__ t, Ctl* c, RedWs ws) {
+                                                         const T* __restrict__ t, Ctl* c, RedWs ws,
+                                                         const T* __restrict__ d = nullptr) {
   if (!*(volatile int*)&c->replace) return;
   const Lin<T> bp(c->rho_new / c->rho);
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
     const T ri = t[i];
     r[i] = ri;
-    p[i] = bp(p[i], ri);
+    p[i] = bp(p[i], d ? d[i] * ri : ri);
   }
   reduce_op<1>(acc, ws, CgReplaceOp{c});
 }
 
 // ------------------------------------------------------------- BiCGSTAB --
 
-// p = r + beta (p - omega v)
+// p = r + beta (p - omega v); with the Jacobi inverse diagonal d also the
+// preconditioned direction ph = d p (right preconditioning)
 template <typename T>
 __global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
-                                                     const T* __restrict__ v, Ctl* c) {
+                                                     const T* __restrict__ v, Ctl* c, const T* __restrict__ d = nullptr,
+                                                     T* __restrict__ ph = nullptr) {
   if (gated(&c->done)) return;
   const Lin<T> bp(c->beta), wv(-c->omega);
+  if (d) {
+    GKO_GRID_LOOP(i, n) {
+      const T pi = bp(wv(v[i], p[i]), r[i]);
+      p[i] = pi;
+      ph[i] = d[i] * pi;
+    }
+    return;
+  }
   const bool aligned = al16(r) && al16(p) && al16(v);
   vec_loop<T>(n, aligned, [&](int64_t i0) {
         Vec16<T> pv = vload(p + i0);
@@ -379,12 +409,22 @@ struct BicgSOp {
 // alpha = rho_new / (rhat.v); s = r - alpha v; reduces s.s
 template <typename T>
 __global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ v,
-                                                     T* __restrict__ s, Ctl* c, RedWs ws) {
+                                                     T* __restrict__ s, Ctl* c, RedWs ws,
+                                                     const T* __restrict__ d = nullptr, T* __restrict__ sh = nullptr) {
   if (gated(&c->done)) return;
   const double rv = c->red[0];
   const double alpha = rv != 0.0 ? c->rho_new / rv : 0.0;
   double acc[1] = {0.0};
-  if (rv != 0.0) {
+  if (rv != 0.0 && d) {  // right preconditioning: also sh = d s
+    const Lin<T> av(-alpha);
+    GKO_GRID_LOOP(i, n) {
+      const T si = av(v[i], r[i]);
+      s[i] = si;
+      sh[i] = d[i] * si;
+      const double sw = wd(si);
+      acc[0] = __fma_rn(sw, sw, acc[0]);
+    }
+  } else if (rv != 0.0) {
     const Lin<T> av(-alpha);
     const bool aligned = al16(r) && al16(v) && al16(s);
     vec_loop<T>(n, aligned, [&](int64_t i0) {
@@ -446,17 +486,35 @@ struct BicgXOp {
 };
 
 // omega = t.s / t.t; x += alpha p + omega s; r = s - omega t; reduces r.r and
-// rhat.r.  In the half step only x += alpha p.
+// rhat.r.  In the half step only x += alpha p.  Right preconditioning: x
+// moves along ph = d p and sh = d s instead.
 template <typename T>
 __global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ x, const T* __restrict__ p,
                                                      const T* __restrict__ s, const T* __restrict__ t,
-                                                     T* __restrict__ r, const T* __restrict__ rh, Ctl* c, RedWs ws) {
+                                                     T* __restrict__ r, const T* __restrict__ rh, Ctl* c, RedWs ws,
+                                                     const T* __restrict__ ph = nullptr,
+                                                     const T* __restrict__ sh = nullptr) {
   if (gated(&c->done)) return;
   const double alpha = c->alpha;
   double acc[2] = {0.0, 0.0};
   const Lin<T> ap(alpha);
   if (*(volatile int*)&c->phase) {
-    GKO_GRID_LOOP(i, n) x[i] = ap(p[i], x[i]);
+    const T* xp = ph ? ph : p;
+    GKO_GRID_LOOP(i, n) x[i] = ap(xp[i], x[i]);
+  } else if (ph) {
+    const double tt = c->red[1];
+    if (tt != 0.0) {
+      const double omega = c->red[0] / tt;
+      const Lin<T> os(omega), ot(-omega);
+      GKO_GRID_LOOP(i, n) {
+        x[i] = os(sh[i], ap(ph[i], x[i]));
+        const T ri = ot(t[i], s[i]);
+        r[i] = ri;
+        const double rw = wd(ri);
+        acc[0] = __fma_rn(rw, rw, acc[0]);
+        acc[1] = __fma_rn(wd(rh[i]), rw, acc[1]);
+      }
+    }
   } else {
     const double tt = c->red[1];
     if (tt != 0.0) {
@@ -821,6 +879,7 @@ struct SolveSpec {
   int restart;
   int check_true;
   int check_every;
+  const void* minv = nullptr;  // Jacobi inverse diagonal (vector of T), or none
 };
 
 struct SolveOut {
@@ -837,9 +896,10 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
                        cudaStream_t s, SolveOut* out) {
   const int64_t n = A->n_rows;
   const int m = std::max(1, sp.restart);
-  const int nvec = sp.solver == 0 ? 3 : sp.solver == 1 ? 7 : (m + 2);
+  const int nvec = sp.solver == 0 ? 3 : sp.solver == 1 ? 9 : (m + 2);
+  const T* dinv = static_cast<const T*>(sp.minv);
   const size_t spmv_sb = spmv_scratch_bytes(A);
-  const size_t bytes = 256 * 16 + sizeof(Ctl) + sizeof(double) * 2 * kDotSlots + 512 +
+  const size_t bytes = 256 * 16 + sizeof(Ctl) + sizeof(double) * 3 * kDotSlots + 512 +
                        (size_t)nvec * (sizeof(T) * ((size_t)n + 64) + 320) + spmv_sb + 320 +
                        sizeof(double) * ((size_t)(m + 1) * m + 6 * (m + 2) + (size_t)(m + 1) * kMultiSlots) + 4096;
   Scratch mem;
@@ -847,7 +907,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   Carve cv{static_cast<char*>(mem.data())};
   Ctl* c = cv.take<Ctl>(1);
   unsigned* counter = cv.take<unsigned>(4);
-  double* partials = cv.take<double>(2 * kDotSlots);
+  double* partials = cv.take<double>(3 * kDotSlots);  // up to 3 sums per block
   void* spmv_scratch = spmv_sb ? cv.take<char>(spmv_sb) : nullptr;
   RedWs ws{partials, counter};
   GKO_TRY_CUDA(cudaMemsetAsync(counter, 0, 16, s));
@@ -882,17 +942,21 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
     T* r = cv.take<T>(n);
     T* p = cv.take<T>(n);
     T* q = cv.take<T>(n);
-    T *rh = nullptr, *v = nullptr, *sv = nullptr, *tv = nullptr;
+    T *rh = nullptr, *v = nullptr, *sv = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
     if (sp.solver == 1) {
       rh = cv.take<T>(n);
       v = cv.take<T>(n);
       sv = cv.take<T>(n);
       tv = cv.take<T>(n);
+      if (dinv) {
+        ph = cv.take<T>(n);
+        sh = cv.take<T>(n);
+      }
     }
     if (!x_zero) GKO_TRY(spmv(x, q, nullptr, nullptr));
     if (sp.solver == 0)
       init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, p, nullptr, nullptr, nullptr, ws,
-                                                 InitOp{c, sp.rel_tol, 0});
+                                                 InitOp{c, sp.rel_tol, 0}, dinv);
     else
       init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, rh, nullptr, p, v, ws,
                                                  InitOp{c, sp.rel_tol, 1});
@@ -909,14 +973,19 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       for (int it = 0; it < batch; ++it) {
         if (sp.solver == 0) {
           GKO_TRY(spmv(p, q, p, &c->done));
-          cg_update_kernel<T><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws);
-          cg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, c);
+          if (dinv) {
+            cg_update_kernel<T, true><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws, dinv);
+            cg_p_kernel<T, true><<<vg, 256, 0, s>>>(n, r, p, c, dinv);
+          } else {
+            cg_update_kernel<T, false><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws, nullptr);
+            cg_p_kernel<T, false><<<vg, 256, 0, s>>>(n, r, p, c, nullptr);
+          }
         } else {
-          bicg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, v, c);
-          GKO_TRY(spmv(p, v, rh, &c->done));
-          bicg_s_kernel<T><<<rg, 256, 0, s>>>(n, r, v, sv, c, ws);
-          GKO_TRY(spmv(sv, tv, sv, &c->phase, true));
-          bicg_x_kernel<T><<<rg, 256, 0, s>>>(n, x, p, sv, tv, r, rh, c, ws);
+          bicg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, v, c, dinv, ph);
+          GKO_TRY(spmv(dinv ? ph : p, v, rh, &c->done));
+          bicg_s_kernel<T><<<rg, 256, 0, s>>>(n, r, v, sv, c, ws, dinv, sh);
+          GKO_TRY(spmv(dinv ? sh : sv, tv, sv, &c->phase, true));
+          bicg_x_kernel<T><<<rg, 256, 0, s>>>(n, x, p, sv, tv, r, rh, c, ws, ph, sh);
         }
         GKO_TRY_CUDA(cudaGetLastError());
       }
@@ -924,9 +993,9 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       if (sp.check_every <= 0) batch = std::min(batch * 2, 64);
       if (hc->status == kCheck) {  // verify with the true residual
         GKO_TRY(spmv(x, q, nullptr, nullptr));
-        true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c});
+        true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c}, sp.solver == 0 ? dinv : nullptr);
         if (sp.solver == 0)
-          cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws);
+          cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
         else
           bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
         GKO_TRY_CUDA(cudaGetLastError());
@@ -1086,8 +1155,20 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   if (sp.restart > kMaxRestart) return fail(GKO_INVALID_ARG, "GMRES restart length is limited to 128");
   sp.check_true = 1;
   sp.check_every = o.check_every;
+  if (o.preconditioner != GKO_PRECOND_NONE && o.preconditioner != GKO_PRECOND_JACOBI)
+    return fail(GKO_INVALID_ARG, "unknown preconditioner");
+  const bool jacobi = o.preconditioner == GKO_PRECOND_JACOBI;
+  if (jacobi && solver == 2) return fail(GKO_NOT_SUPPORTED, "GMRES takes no preconditioner");
   double nb = 0.0;
   GKO_TRY(norm2_host(b, n, &nb, s));
+  Scratch pc_mem;  // Jacobi inverse diagonal: FP64, and its FP32 rounding for inner solves
+  double* d64 = nullptr;
+  if (jacobi) {
+    GKO_TRY(pc_mem.get(sizeof(double) * n + sizeof(float) * n + 512, s));
+    d64 = pc_mem.as<double>();
+    GKO_TRY(jacobi_inverse(A, d64, s));
+    sp.minv = d64;
+  }
 
   if (o.precision == GKO_PRECISION_F64) {
     SolveOut so{};
@@ -1104,6 +1185,11 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   GKO_TRY(lowp_copy(A, o.precision == GKO_PRECISION_MIXED_F32 ? GKO_F32 : GKO_BF16, s, &A32));
   // mixed-precision iterative refinement: FP64 residual, FP32-stored inner solve
   SolveSpec in = sp;
+  if (jacobi) {
+    float* d32 = pc_mem.as<float>(((sizeof(double) * (size_t)n + 255) / 256) * 256);
+    GKO_TRY(narrow_to_f32(d64, d32, n, s));
+    in.minv = d32;
+  }
   in.rel_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
   in.maxit = o.inner_maxit > 0 ? o.inner_maxit : max_iters;
   in.check_true = 0;

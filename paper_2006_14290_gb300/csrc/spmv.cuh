@@ -41,6 +41,11 @@ int spmv_run_f32(const gko_matrix_s* A, const float* x, float* y, double alpha, 
 int spmv_run_bf16(const gko_matrix_s* A, const float* x, float* y, double alpha, double beta, cudaStream_t s,
                   void* scratch, const DotSpec* dot, const int* gate);
 
+// Jacobi preconditioner: d = inverse diagonal of the FP64 matrix A (any
+// format; zero diagonal -> 1), and its FP32 rounding for inner solves.
+int jacobi_inverse(const gko_matrix_s* A, double* d, cudaStream_t s);
+int narrow_to_f32(const double* d, float* f, int64_t n, cudaStream_t s);
+
 constexpr int kCooThreads = 256;
 constexpr int kCooItems = 8;
 constexpr int kCooTile = kCooThreads * kCooItems;

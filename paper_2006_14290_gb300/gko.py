@@ -42,7 +42,7 @@ class GkoError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("precision", C.c_int32), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int32), ("inner_maxit", C.c_int32), ("check_every", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("preconditioner", C.c_int32)]
 
 
 class SolveResult(C.Structure):
@@ -390,8 +390,12 @@ def gko_solve_gmres(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=N
     return _solve("gko_solve_gmres", A, b, x, rel_tol, max_iters, opts, stream)
 
 
-def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0):
-    return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, 0)
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+
+
+def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0,
+         preconditioner=PRECOND_NONE):
+    return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, preconditioner)
 
 
 def gko_device_status(stream=None):
