@@ -319,7 +319,8 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
     sides rint(n^(1/3)) for n log-uniform in [1e3, 4e6], all from
     default_rng(0), uploaded before the window.  Requests: 70% CG / 30%
     BiCGSTAB on a uniformly chosen pool matrix, b = A*1, tolerance 1e-8
-    (iteration caps CG 5000, BiCGSTAB 500), admitted by a 150 GB budget over
+    (iteration caps CG 5000, BiCGSTAB 500; CG Jacobi-preconditioned, as the
+    variable coefficients call for), admitted by a 150 GB budget over
     `slots` concurrent solves.  Each arrival window runs FP64 and mixed FP32.
     """
     import torch
@@ -357,6 +358,7 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
             S = G.Server(slots=slots, budget_bytes=budget_bytes)
             ids = [S.add_matrix(p[1]) for p in pool]
             opts = G.opts(precision=prec, inner_maxit=1000)
+            opts_cg = G.opts(precision=prec, inner_maxit=1000, preconditioner=G.PRECOND_JACOBI)
             t0 = time.perf_counter()
             rids = []
             for at, m in zip(times, picks):
@@ -365,7 +367,7 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
                     time.sleep(at - now)
                 kind = pool[m][0]
                 rids.append(S.submit(ids[m], 0 if kind == "cg" else 1, pool[m][2], 1e-8,
-                                     5000 if kind == "cg" else 500, opts))
+                                     5000 if kind == "cg" else 500, opts_cg if kind == "cg" else opts))
             results = [S.result(r) for r in rids]
             wall = time.perf_counter() - t0
             st = S.stats()
