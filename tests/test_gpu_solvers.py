@@ -172,3 +172,36 @@ def test_cg_poisson_256_full_size(gko):
         x = host(xd)
         assert true_rel_res(A, x, b) <= 1.01e-8
         assert abs(res.rel_residual - true_rel_res(A, x, b)) <= 1e-11
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", ["bicgstab_P1", "gmres30_P10", "cg_jacobi_varcoef"])
+def test_solver_workloads_full_size(gko, case):
+    """The other solver workloads of the benchmark at full size (128^3), FP64
+    and mixed FP32, in the benchmark's options: converged, the reported
+    residual equals the true one recomputed with the oracle's SpMV, and the
+    iterate is close to the exact solution 1 (b = A*1)."""
+    import torch
+
+    G = gko
+    if case == "cg_jacobi_varcoef":
+        A = I.varcoef3d_7pt(128, np.random.default_rng(0))
+    else:
+        A = I.convdiff3d_7pt(128, 1.0 if case == "bicgstab_P1" else 10.0)
+    M = G.from_csr(A)
+    ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+    bd = torch.zeros_like(ones)
+    G.gko_spmv(1.0, M, ones, 0.0, bd)
+    b = host(bd)
+    fn = {"bicgstab_P1": G.gko_solve_bicgstab, "gmres30_P10": G.gko_solve_gmres,
+          "cg_jacobi_varcoef": G.gko_solve_cg}[case]
+    pc = G.PRECOND_JACOBI if case == "cg_jacobi_varcoef" else G.PRECOND_NONE
+    for prec in (G.PRECISION_F64, G.PRECISION_MIXED_F32):
+        xd = torch.zeros_like(ones)
+        res = fn(M, bd, xd, 1e-8, 20000, G.opts(precision=prec, restart=30, inner_maxit=2000, max_outer=12,
+                                                 preconditioner=pc))
+        assert res.status == G.OK, (case, prec, res)
+        x = host(xd)
+        tr = true_rel_res(A, x, b)
+        assert tr <= 1.01e-8 and abs(res.rel_residual - tr) <= 1e-11
+        assert np.linalg.norm(x - 1.0) <= 1e-4 * np.sqrt(A.n_rows)
