@@ -409,6 +409,14 @@ GKO_API int gko_server_destroy(gko_server S);
 GKO_API int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dtype, int32_t inner_loops,
                                      void *data, int64_t n, void *stream);
 
+/* Failure-detection check (no counterpart in the paper): one warp waits on a
+ * shared-memory barrier that nothing completes, through the bounded wait the
+ * bulk-copy SpMV kernels use, for at most `cycles` clock cycles (1 .. 2^32).
+ * The wait gives up, the kernel records GKO_TIMEOUT in the device error word
+ * (read and cleared by gko_device_status) and returns; *timed_out = 1.
+ * Synchronises `stream`; the context stays usable. */
+GKO_API int gko_diag_bounded_wait(int64_t cycles, int32_t *timed_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -65,10 +66,43 @@ int launch_typed(int32_t S, int32_t impl, T* data, int64_t n, int32_t loops, cud
   return launch_impl<T, 2>(S, data, n, loops, s);
 }
 
+// Failure-detection check of the bounded waits: one warp waits on an
+// mbarrier that nothing ever completes, through the same bounded wait the
+// bulk-copy pipelines use, but with a caller-given cycle limit.  The wait
+// gives up, records GKO_TIMEOUT in the device error word and the kernel
+// returns normally; no copy is in flight, so the block may leave.
+__global__ void bounded_wait_kernel(long long limit, int* err, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_for(&bar, 0u, err, limit);
+  if (threadIdx.x == 0) *out = ok ? 0 : 1;
+}
+
 }  // namespace
 }  // namespace gko
 
 using namespace gko;
+
+extern "C" int gko_diag_bounded_wait(int64_t cycles, int32_t* timed_out, void* stream) {
+  if (!timed_out || cycles <= 0 || cycles > kWaitCycles)
+    return fail(GKO_INVALID_ARG, "cycles must be in 1 .. 2^32 and timed_out non-null");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = device_error_word();
+  if (!err) return fail(GKO_CUDA_ERROR, "device error word unavailable");
+  Scratch sc;
+  GKO_TRY(sc.get(sizeof(int), s));
+  bounded_wait_kernel<<<1, 32, 0, s>>>((long long)cycles, err, sc.as<int>());
+  GKO_TRY_CUDA(cudaGetLastError());
+  int v = 0;
+  GKO_TRY_CUDA(cudaMemcpyAsync(&v, sc.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  *timed_out = v;
+  return GKO_OK;
+}
 
 extern "C" int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dtype, int32_t inner_loops,
                                         void* data, int64_t n, void* stream) {

@@ -57,17 +57,23 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the barrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+// Wait for the barrier phase with the given parity for at most `limit`
+// clock cycles; on time-out record GKO_TIMEOUT in *err and return false.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, unsigned parity, int* err, long long limit) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       if (err) atomicOr(err, 1 << GKO_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+
+// Bounded wait of the copy pipelines (~2 s).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+  return mbar_wait_for(bar, parity, err, kWaitCycles);
 }
 
 // Global -> shared bulk copy completing on `bar`.  dst/src 16-byte aligned,

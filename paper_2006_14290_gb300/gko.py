@@ -77,6 +77,7 @@ SIGNATURES = {
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
     "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
     "gko_bench_subwarp_reduce": (C.c_int, [_I32, _I32, C.c_int, _I32, _P, C.c_int64, _P]),
+    "gko_diag_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
     "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
     "gko_axpy": (C.c_int, [_I64, _D, _P, _P, _P]),
@@ -322,6 +323,13 @@ def gko_bench_subwarp_reduce(subwarp: int, impl: int, data, inner_loops: int, st
     _check(lib().gko_bench_subwarp_reduce(subwarp, impl, dt, inner_loops, _dptr(data), data.numel(),
                                           _stream(stream)), "gko_bench_subwarp_reduce")
     return data
+
+
+def gko_diag_bounded_wait(cycles: int, stream=None) -> bool:
+    """Run the bounded-wait failure check; True when the wait gave up."""
+    t = C.c_int32()
+    _check(lib().gko_diag_bounded_wait(cycles, C.byref(t), _stream(stream)), "gko_diag_bounded_wait")
+    return bool(t.value)
 
 
 def gko_dot(x, y, stream=None) -> float:
