@@ -632,12 +632,16 @@ def run_ours(args):
             if events is not None:
                 events[i][1].record(stream)
 
+    # end to end: every SpMV through the host-buffer C ABI call (x copied in
+    # from pinned host memory, y copied back), cases rotating over three
+    # streams so one case's copies overlap another's SpMV.  No L2 flush here:
+    # a case's matrix was last touched 21 SpMVs (gigabytes) earlier and x
+    # arrives by copy anyway.
+    e2e_streams = [stream, torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+
     def e2e_step():
         for i, c in enumerate(cases):
-            flush.fill_(float(i))
-            c["x"].copy_(c["xh"], non_blocking=True)
-            G.gko_spmv(1.0, c["M"], c["x"], 0.0, c["y"], stream=stream)
-            c["yh"].copy_(c["y"], non_blocking=True)
+            G.gko_spmv_host(1.0, c["M"], c["xh"], 0.0, c["yh"], c["x"], c["y"], stream=e2e_streams[i % 3])
 
     def barrier():
         if world > 1:
@@ -677,21 +681,15 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    for st in e2e_streams[1:]:
+        st.wait_event(e0)
     for _ in range(args.steps):
         e2e_step()
+    for st in e2e_streams[1:]:
+        stream.wait_stream(st)
     e1.record(stream)
     barrier()
-    e2e_ms_step = e0.elapsed_time(e1) / args.steps
-    flush_ms = 0.0
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for i in range(len(cases)):
-        flush.fill_(float(i))
-    f1.record(stream)
-    torch.cuda.synchronize()
-    flush_ms = f0.elapsed_time(f1)
-    e2e_ms = max(e2e_ms_step - flush_ms, 1e-9)
+    e2e_ms = e0.elapsed_time(e1) / args.steps
 
     kernel_ms, e2e_ms = ranks_max([kernel_ms, e2e_ms], dev)
 

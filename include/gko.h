@@ -203,6 +203,17 @@ GKO_API int gko_matrix_destroy(gko_matrix m);
 GKO_API int gko_spmv(const double *alpha, gko_matrix A, const void *x, const double *beta, void *y,
              gko_dtype vec_dtype, void *stream);
 
+/* gko_spmv on HOST vectors: copies x_host (n_cols elements of vec_dtype) to
+ * the caller's device buffer x_dev, and y_host to y_dev when beta != 0,
+ * runs gko_spmv, and copies y_dev back to y_host, all in stream order on
+ * `stream` (returns once enqueued; host buffers must stay valid until the
+ * stream reaches the last copy, and should be page-locked for the copies to
+ * be asynchronous).  Calls on different streams overlap one call's copies
+ * with another's SpMV.  Errors as gko_spmv; null host or device buffers ->
+ * GKO_INVALID_ARG. */
+GKO_API int gko_spmv_host(const double *alpha, gko_matrix A, const void *x_host, const double *beta,
+                          void *y_host, gko_dtype vec_dtype, void *x_dev, void *y_dev, void *stream);
+
 /* y = alpha * A * x + beta * y for an F64 COO handle, allocating nothing.
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory at the time they multiply (their memory is owned by

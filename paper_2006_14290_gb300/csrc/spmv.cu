@@ -58,3 +58,22 @@ extern "C" int gko_spmv(const double* alpha, gko_matrix A, const void* x, const 
   if (sb) GKO_TRY(scratch.get(sb, s));
   return spmv_run(A, x, y, *alpha, *beta, s, scratch.data(), nullptr);
 }
+
+// SpMV on host vectors: stream-ordered copies around gko_spmv (see gko.h).
+extern "C" int gko_spmv_host(const double* alpha, gko_matrix A, const void* x_host, const double* beta,
+                             void* y_host, gko_dtype vec_dtype, void* x_dev, void* y_dev, void* stream) {
+  if (!A || !alpha || !beta) return fail(GKO_INVALID_ARG, "null matrix or scalar");
+  if (A->n_rows > 0 && (!y_host || !y_dev)) return fail(GKO_INVALID_ARG, "null y");
+  if (A->n_cols > 0 && (!x_host || !x_dev)) return fail(GKO_INVALID_ARG, "null x");
+  const size_t es = vec_dtype == GKO_F64 ? sizeof(double) : sizeof(float);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (A->n_cols > 0)
+    GKO_TRY_CUDA(cudaMemcpyAsync(x_dev, x_host, es * (size_t)A->n_cols, cudaMemcpyHostToDevice, s));
+  if (A->n_rows > 0 && *beta != 0.0)
+    GKO_TRY_CUDA(cudaMemcpyAsync(y_dev, y_host, es * (size_t)A->n_rows, cudaMemcpyHostToDevice, s));
+  GKO_TRY(gko_spmv(alpha, A, x_dev, beta, y_dev, vec_dtype, stream));
+  if (A->n_rows > 0)
+    GKO_TRY_CUDA(cudaMemcpyAsync(y_host, y_dev, es * (size_t)A->n_rows, cudaMemcpyDeviceToHost, s));
+  return GKO_OK;
+}
+

@@ -76,6 +76,7 @@ SIGNATURES = {
     "gko_matrix_destroy": (C.c_int, [_P]),
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
     "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
+    "gko_spmv_host": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P, _P, _P]),
     "gko_bench_subwarp_reduce": (C.c_int, [_I32, _I32, C.c_int, _I32, _P, C.c_int64, _P]),
     "gko_diag_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
@@ -301,6 +302,19 @@ def gko_spmv(alpha: float, A: Matrix, x, beta: float, y, vec_dtype=None, stream=
     _check(lib().gko_spmv(C.byref(a), A.handle, _dptr(x), C.byref(b), _dptr(y), vec_dtype, _stream(stream)),
            "gko_spmv")
     return y
+
+
+def gko_spmv_host(alpha: float, A: Matrix, x_host, beta: float, y_host, x_dev, y_dev, stream=None):
+    """y_host = alpha*A*x_host + beta*y_host through device buffers x_dev /
+    y_dev (torch tensors; host ones pinned), stream-ordered, asynchronous."""
+    import torch
+
+    vdt = F64 if x_dev.dtype == torch.float64 else F32
+    a, b = C.c_double(alpha), C.c_double(beta)
+    _check(lib().gko_spmv_host(C.byref(a), A.handle, C.c_void_p(x_host.data_ptr()), C.byref(b),
+                               C.c_void_p(y_host.data_ptr()), vdt, _dptr(x_dev), _dptr(y_dev), _stream(stream)),
+           "gko_spmv_host")
+    return y_host
 
 
 def gko_spmv_coo_noalloc(alpha: float, A: Matrix, x, beta: float, y, stream=None):

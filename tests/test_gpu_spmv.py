@@ -420,3 +420,25 @@ def test_memory_budget_refuses_and_recovers(gko):
     M = G.from_csr(A)
     assert G.memory_in_use() > used
     del M
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo"])
+def test_spmv_host_buffers(gko, fmt):
+    """gko_spmv_host: host x and y (pinned), copies in stream order; equals
+    the oracle for beta = 0 and beta != 0."""
+    import torch
+
+    G = gko
+    A = I.banded(3000, 12, 0.4, seed=4)
+    M = make(G, A, fmt, G.F64)
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    xh = torch.from_numpy(x).pin_memory()
+    xd = torch.empty(A.n_cols, dtype=torch.float64, device="cuda")
+    yd = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    for alpha, beta in [(1.0, 0.0), (-2.0, 0.5)]:
+        yh = torch.from_numpy(y0.copy()).pin_memory()
+        G.gko_spmv_host(alpha, M, xh, beta, yh, xd, yd)
+        torch.cuda.synchronize()
+        check_spmv_f64(yh.numpy(), A, x, alpha, beta, y0)
