@@ -75,6 +75,33 @@ struct Lin<float> {
 
 __device__ __forceinline__ double dsq(double a) { return a * a; }
 
+template <typename T>
+struct LinPair {
+  Lin<T> a, b;
+};
+template <typename T>
+struct LinTriple {
+  Lin<T> a, b, c;
+};
+
+// One value per block: thread 0 evaluates f() and the block reads it from
+// shared memory.  The step scalars need an FP64 division and, for FP32
+// vectors, a float-pair split; both run on GB300's narrow FP64/conversion
+// path, so doing them once per block instead of once per thread removes a
+// fixed cost of several microseconds per launch.  Call from block-uniform
+// control flow (it synchronises the block), at most once per call site.
+template <typename V, typename F>
+__device__ __forceinline__ V block_bcast(F f) {
+  __shared__ __align__(16) unsigned char buf[sizeof(V)];
+  if (threadIdx.x == 0) {
+    const V v = f();
+    memcpy(buf, &v, sizeof(V));
+  }
+  __syncthreads();
+  V out = *reinterpret_cast<const V*>(buf);
+  return out;
+}
+
 // 16-byte vectors of T for the streaming solver kernels: VN elements per
 // load/store (2 doubles or 4 floats).  The vector path runs when every
 // pointer of the kernel is 16-byte aligned; the last n % VN elements and
@@ -119,7 +146,15 @@ __device__ __forceinline__ void vec_loop(int64_t n, bool aligned, VF vf, SF sf) 
   int64_t done = 0;
   if (aligned) {
     const int64_t nv = n / VN;
-    for (int64_t iv = tid; iv < nv; iv += nth) vf(iv * VN);
+    int64_t iv = tid;
+    // four vectors per trip keep several 16-byte loads in flight per thread
+    for (; iv + 3 * nth < nv; iv += 4 * nth) {
+      vf(iv * VN);
+      vf((iv + nth) * VN);
+      vf((iv + 2 * nth) * VN);
+      vf((iv + 3 * nth) * VN);
+    }
+    for (; iv < nv; iv += nth) vf(iv * VN);
     done = nv * VN;
   }
   for (int64_t i = done + tid; i < n; i += nth) sf(i);
@@ -288,12 +323,14 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
                                                         RedWs ws, const T* __restrict__ d) {
   constexpr int NV = PC ? 2 : 1;
   if (gated(&c->done)) return;
-  const double pq = c->red[0];
-  const bool ok = pq > 0.0;
-  const double alpha = ok ? c->rho / pq : 0.0;
+  const bool ok = c->red[0] > 0.0;
+  const LinPair<T> L = block_bcast<LinPair<T>>([&] {
+    const double alpha = ok ? c->rho / c->red[0] : 0.0;
+    return LinPair<T>{Lin<T>(alpha), Lin<T>(-alpha)};
+  });
   double acc[NV] = {};
   if (ok) {
-    const Lin<T> ax(alpha), ar(-alpha);
+    const Lin<T> ax = L.a, ar = L.b;
     const bool aligned = al16(x) && al16(r) && al16(p) && al16(q) && (!PC || al16(d));
     vec_loop<T>(n, aligned, [&](int64_t i0) {
           Vec16<T> xv = vload(x + i0), rv = vload(r + i0), dv;
@@ -326,7 +363,7 @@ template <typename T, bool PC>
 __global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c,
                                                    const T* __restrict__ d) {
   if (gated(&c->done)) return;
-  const Lin<T> bp(c->beta);
+  const Lin<T> bp = block_bcast<Lin<T>>([&] { return Lin<T>(c->beta); });
   const bool aligned = al16(r) && al16(p) && (!PC || al16(d));
   vec_loop<T>(n, aligned, [&](int64_t i0) {
         Vec16<T> pv = vload(p + i0);
@@ -353,7 +390,7 @@ __global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restric
                                                          const T* __restrict__ t, Ctl* c, RedWs ws,
                                                          const T* __restrict__ d = nullptr) {
   if (!*(volatile int*)&c->replace) return;
-  const Lin<T> bp(c->rho_new / c->rho);
+  const Lin<T> bp = block_bcast<Lin<T>>([&] { return Lin<T>(c->rho_new / c->rho); });
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
     const T ri = t[i];
@@ -372,7 +409,8 @@ __global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restr
                                                      const T* __restrict__ v, Ctl* c, const T* __restrict__ d = nullptr,
                                                      T* __restrict__ ph = nullptr) {
   if (gated(&c->done)) return;
-  const Lin<T> bp(c->beta), wv(-c->omega);
+  const LinPair<T> L = block_bcast<LinPair<T>>([&] { return LinPair<T>{Lin<T>(c->beta), Lin<T>(-c->omega)}; });
+  const Lin<T> bp = L.a, wv = L.b;
   if (d) {
     GKO_GRID_LOOP(i, n) {
       const T pi = bp(wv(v[i], p[i]), r[i]);
@@ -413,10 +451,9 @@ __global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restr
                                                      const T* __restrict__ d = nullptr, T* __restrict__ sh = nullptr) {
   if (gated(&c->done)) return;
   const double rv = c->red[0];
-  const double alpha = rv != 0.0 ? c->rho_new / rv : 0.0;
+  const Lin<T> av = block_bcast<Lin<T>>([&] { return Lin<T>(rv != 0.0 ? -(c->rho_new / rv) : 0.0); });
   double acc[1] = {0.0};
   if (rv != 0.0 && d) {  // right preconditioning: also sh = d s
-    const Lin<T> av(-alpha);
     GKO_GRID_LOOP(i, n) {
       const T si = av(v[i], r[i]);
       s[i] = si;
@@ -425,7 +462,6 @@ __global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restr
       acc[0] = __fma_rn(sw, sw, acc[0]);
     }
   } else if (rv != 0.0) {
-    const Lin<T> av(-alpha);
     const bool aligned = al16(r) && al16(v) && al16(s);
     vec_loop<T>(n, aligned, [&](int64_t i0) {
           const Vec16<T> vv = vload(v + i0), rr = vload(r + i0);
@@ -495,17 +531,20 @@ __global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ 
                                                      const T* __restrict__ ph = nullptr,
                                                      const T* __restrict__ sh = nullptr) {
   if (gated(&c->done)) return;
-  const double alpha = c->alpha;
   double acc[2] = {0.0, 0.0};
-  const Lin<T> ap(alpha);
+  const LinTriple<T> L = block_bcast<LinTriple<T>>([&] {
+    const double tt = c->red[1];
+    const double omega = tt != 0.0 ? c->red[0] / tt : 0.0;
+    return LinTriple<T>{Lin<T>(c->alpha), Lin<T>(omega), Lin<T>(-omega)};
+  });
+  const Lin<T> ap = L.a;
   if (*(volatile int*)&c->phase) {
     const T* xp = ph ? ph : p;
     GKO_GRID_LOOP(i, n) x[i] = ap(xp[i], x[i]);
   } else if (ph) {
     const double tt = c->red[1];
     if (tt != 0.0) {
-      const double omega = c->red[0] / tt;
-      const Lin<T> os(omega), ot(-omega);
+      const Lin<T> os = L.b, ot = L.c;
       GKO_GRID_LOOP(i, n) {
         x[i] = os(sh[i], ap(ph[i], x[i]));
         const T ri = ot(t[i], s[i]);
@@ -518,8 +557,7 @@ __global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ 
   } else {
     const double tt = c->red[1];
     if (tt != 0.0) {
-      const double omega = c->red[0] / tt;
-      const Lin<T> os(omega), ot(-omega);
+      const Lin<T> os = L.b, ot = L.c;
       const bool aligned = al16(x) && al16(p) && al16(s) && al16(t) && al16(r) && al16(rh);
       vec_loop<T>(n, aligned, [&](int64_t i0) {
             Vec16<T> xv = vload(x + i0), rv;
@@ -628,7 +666,7 @@ __global__ void __launch_bounds__(256) gm_start_kernel(int64_t n, const double* 
 template <typename T>
 __global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict__ v, const double* den, Ctl* c) {
   if (gated(&c->phase)) return;
-  const Lin<T> sc(1.0 / *den);
+  const Lin<T> sc = block_bcast<Lin<T>>([&] { return Lin<T>(1.0 / *den); });
   GKO_GRID_LOOP(i, n) v[i] = sc.scale(v[i]);
 }
 
@@ -756,7 +794,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
                                                       Ctl* c) {
   if (gated(&c->phase)) return;
-  const Lin<T> sc(1.0 / c->rho);
+  const Lin<T> sc = block_bcast<Lin<T>>([&] { return Lin<T>(1.0 / c->rho); });
   GKO_GRID_LOOP(i, n) vn[i] = sc.scale(w[i]);
 }
 

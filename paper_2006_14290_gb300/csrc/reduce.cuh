@@ -63,6 +63,7 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < expected; i += THREADS)
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (int64_t)i * NV + k);
