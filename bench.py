@@ -10,6 +10,8 @@ matrix is rejected by the padding limit and is not part of the step.
 SELL-P (slices of 64 rows) is timed the same way after the step and reported
 under `extra_formats`, outside `value` (the sweep's formats are CSR, ELL, COO
 and hybrid); on the power-law matrix it is rejected by the padding limit too.
+CSR and COO plans are chosen by the library's plan autotuner (gko_matrix_tune)
+at setup, untimed; the chosen plans are listed in config.tuned_plans.
 value = algorithmic bytes of all SpMVs / their summed device time (GB/s);
 L2 is flushed (256 MB write) before every SpMV.  Matrices stay resident in
 HBM; `e2e` repeats the step through the same C ABI calls with x copied in
@@ -544,7 +546,7 @@ def whole_job_gbs(world, bytes_per_rank, ms):
 
 # ---------------------------------------------------------------- our path --
 
-def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid")):
+def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid"), tune=True):
     """Every (matrix, format, value type) SpMV case of the sweep, resident on
     the device, with its algorithmic bytes and the number of kernel launches
     one gko_spmv call makes for it."""
@@ -555,7 +557,6 @@ def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid")):
     cases, skipped = [], []
     for name, A in mats:
         M64 = G.from_csr(A)
-        plan = M64.plan()
         base = {"csr": M64} if "csr" in formats else {}
         for fmt in formats:
             if fmt == "csr":
@@ -575,15 +576,20 @@ def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid")):
                 sv = 8 if dt == "f64" else 4
                 ell_nnz = inf["nnz"] - inf["coo_nnz"] if fmt == "hybrid" else 0
                 nb = spmv_bytes(fmt, A.n_rows, A.n_cols, A.nnz, ell_nnz, inf["coo_nnz"], sv, sv, sv)
+                x = x64 if dt == "f64" else x32
+                y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
+                plan = None
+                if tune and fmt in ("csr", "coo"):  # setup step: the plan autotuner, untimed
+                    k, S, R, cap, _ = H.tune(x, y, reps=2)
+                    plan = {"kernel": k, "subwarp": S, "rows_per_subwarp": R, "stage_cap": cap}
                 coo_launches = 2 if inf["coo_nnz"] > 0 and fmt in ("coo", "hybrid") else 0
-                csr_launches = 2 if plan["kernel"] == 2 else 1 + (2 if plan["n_long_rows"] > 0 else 0)
-                if fmt == "coo" and M.plan()["kernel"] == 1:
+                hp = H.plan() if fmt in ("csr", "coo") else None
+                csr_launches = 2 if hp and hp["kernel"] == 2 else 1 + (2 if hp and hp["n_long_rows"] > 0 else 0)
+                if fmt == "coo" and hp["kernel"] == 1:
                     coo_launches = 1  # row-block COO: one launch, no tile fix-up
                 launches = {"csr": csr_launches, "ell": 1, "sellp": 1,
                             "coo": coo_launches if coo_launches else 1, "hybrid": 1 + coo_launches}[fmt]
-                x = x64 if dt == "f64" else x32
-                y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
-                cases.append({"label": f"{name}/{fmt}/{dt}", "M": H, "x": x, "y": y, "bytes": nb,
+                cases.append({"label": f"{name}/{fmt}/{dt}", "M": H, "x": x, "y": y, "bytes": nb, "plan": plan,
                               "launches": launches, "nnz": int(A.nnz), "xh": x.cpu().pin_memory(),
                               "yh": torch.empty(A.n_rows, dtype=x.dtype).pin_memory()})
         del A
@@ -733,6 +739,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "l2": "flushed before every SpMV (256 MB write, excluded from time)",
                        "matrices": {n: {"n": int(A.n_rows), "nnz": int(A.nnz)} for n, A in mats},
                        "skipped": skipped, "frac_of_peak_value": round(value / world / peak, 4),
+                       "tuned_plans": {c["label"]: c["plan"] for c in cases if c["plan"]},
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom_case["label"], "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),

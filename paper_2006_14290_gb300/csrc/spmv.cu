@@ -1,4 +1,6 @@
 // SpMV dispatch over value types and the gko_spmv entry point.
+#include <vector>
+
 #include "spmv.cuh"
 
 namespace gko {
@@ -74,6 +76,80 @@ extern "C" int gko_spmv_host(const double* alpha, gko_matrix A, const void* x_ho
   GKO_TRY(gko_spmv(alpha, A, x_dev, beta, y_dev, vec_dtype, stream));
   if (A->n_rows > 0)
     GKO_TRY_CUDA(cudaMemcpyAsync(y_host, y_dev, es * (size_t)A->n_rows, cudaMemcpyDeviceToHost, s));
+  return GKO_OK;
+}
+
+// Autotuner of the SpMV plan (see gko.h): times each candidate plan on the
+// caller's vectors with L2 flushed before every timed SpMV, keeps the best.
+extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t reps, int32_t* kernel, int32_t* S,
+                               int32_t* R, int32_t* cap, float* best_ms, void* stream) {
+  if (!m || reps < 1 || reps > 100) return fail(GKO_INVALID_ARG, "bad tune arguments (reps 1..100)");
+  if (m->fmt != GKO_CSR && m->fmt != GKO_COO) return fail(GKO_NOT_SUPPORTED, "tuning covers CSR and COO plans");
+  if (m->n_rows > 0 && (!x || !y)) return fail(GKO_INVALID_ARG, "null x or y");
+  cudaStream_t s = (cudaStream_t)stream;
+  struct Cand {
+    int32_t k, S, R, cap;
+  };
+  std::vector<Cand> cands;
+  for (int32_t ss : {1, 2, 4, 8})
+    for (int32_t rr : {1, 2, 4})
+      for (int32_t cc : {512, 1024, 2048}) cands.push_back({1, ss, rr, cc});
+  if (m->fmt == GKO_CSR) {
+    cands.push_back({2, 1, 1, 1024});  // merge path
+    for (int32_t ss : {4, 8, 16, 32}) cands.push_back({0, ss, 2, 1024});
+  } else {
+    cands.push_back({0, 1, 1, 1024});  // segmented reduction
+  }
+  const Cand start{m->plan.kind, m->plan.S, m->plan.R, m->plan.cap};
+  if (m->n_rows == 0) {
+    if (kernel) *kernel = start.k;
+    if (S) *S = start.S;
+    if (R) *R = start.R;
+    if (cap) *cap = start.cap;
+    if (best_ms) *best_ms = 0.f;
+    return GKO_OK;
+  }
+  const size_t flush_bytes = 256u << 20;  // larger than the 129 MB L2
+  Scratch flush;
+  GKO_TRY(flush.get(flush_bytes, s));
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  GKO_TRY_CUDA(cudaEventCreate(&ev.a));
+  GKO_TRY_CUDA(cudaEventCreate(&ev.b));
+  const double one = 1.0, zero = 0.0;
+  const gko_dtype vdt = m->dtype == GKO_F64 ? GKO_F64 : GKO_F32;
+  float best = 1e30f;
+  Cand best_c = start;
+  for (const Cand& c : cands) {
+    if (gko_matrix_set_plan(m, c.k, c.S, c.R, c.cap, stream) != GKO_OK) continue;  // not applicable here
+    GKO_TRY(gko_spmv(&one, m, x, &zero, y, vdt, stream));  // first use of this configuration
+    float t = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      GKO_TRY_CUDA(cudaMemsetAsync(flush.data(), r & 0xff, flush_bytes, s));
+      GKO_TRY_CUDA(cudaEventRecord(ev.a, s));
+      GKO_TRY(gko_spmv(&one, m, x, &zero, y, vdt, stream));
+      GKO_TRY_CUDA(cudaEventRecord(ev.b, s));
+      GKO_TRY_CUDA(cudaEventSynchronize(ev.b));
+      float ms = 0.f;
+      GKO_TRY_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+      t = std::min(t, ms);
+    }
+    if (t < best) {
+      best = t;
+      best_c = c;
+    }
+  }
+  GKO_TRY(gko_matrix_set_plan(m, best_c.k, best_c.S, best_c.R, best_c.cap, stream));
+  if (kernel) *kernel = best_c.k;
+  if (S) *S = best_c.S;
+  if (R) *R = best_c.R;
+  if (cap) *cap = best_c.cap;
+  if (best_ms) *best_ms = best;
   return GKO_OK;
 }
 

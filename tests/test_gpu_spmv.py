@@ -442,3 +442,41 @@ def test_spmv_host_buffers(gko, fmt):
         G.gko_spmv_host(alpha, M, xh, beta, yh, xd, yd)
         torch.cuda.synchronize()
         check_spmv_f64(yh.numpy(), A, x, alpha, beta, y0)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo"])
+@pytest.mark.parametrize("mat", ["banded", "powerlaw"])
+def test_tune_sets_a_valid_plan(gko, fmt, mat):
+    """The plan autotuner leaves the handle on the plan it reports, and SpMV
+    on that plan matches the oracle (FP64 and an FP32 copy)."""
+    import torch
+
+    G = gko
+    A = I.banded(30000, 24, 0.5, seed=6) if mat == "banded" else I.powerlaw(30000, seed=7)
+    M = make(G, A, fmt, G.F64)
+    x = np.random.default_rng(2).uniform(-1, 1, A.n_cols)
+    xd, yd = dev(x), torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    k, S, R, cap, ms = M.tune(xd, yd, reps=1)
+    p = M.plan()
+    assert p["kernel"] == k and ms > 0
+    if k == 1:
+        assert (p["subwarp"], p["rows_per_subwarp"], p["stage_cap"]) == (S, R, cap)
+    yd = dev(np.zeros(A.n_rows))
+    G.gko_spmv(1.0, M, xd, 0.0, yd)
+    check_spmv_f64(host(yd), A, x, 1.0, 0.0, None)
+    M32 = G.gko_matrix_convert_values(M, G.F32)
+    x32 = x.astype(np.float32)
+    M32.tune(dev(x32), torch.empty(A.n_rows, dtype=torch.float32, device="cuda"), reps=1)
+    yd = dev(np.zeros(A.n_rows), np.float32)
+    G.gko_spmv(1.0, M32, dev(x32), 0.0, yd)
+    check_spmv_f32(host(yd), A, x32.astype(np.float64), 1.0, 0.0, None, A.val.astype(np.float32).astype(np.float64))
+
+
+def test_tune_refuses_other_formats(gko):
+    G = gko
+    A = I.laplace2d_5pt(8)
+    E = G.gko_matrix_convert_to_ell(G.from_csr(A))
+    import torch
+    with pytest.raises(G.GkoError) as e:
+        E.tune(dev(np.ones(64)), torch.empty(64, dtype=torch.float64, device="cuda"))
+    assert e.value.status == G.NOT_SUPPORTED
