@@ -48,22 +48,27 @@ struct BatchArgs {
   unsigned* queue;
 };
 
-template <typename VT>
-__device__ __forceinline__ double ldv(const VT* v, int64_t k) {
-  return (double)v[k];
-}
+// Stored value widened to FP64: FP32 storage goes through the exact integer
+// widening (GB300 runs the F2F conversion on its narrow path).
+__device__ __forceinline__ double ldv(const double* v, int64_t k) { return v[k]; }
+__device__ __forceinline__ double ldv(const float* v, int64_t k) { return widen(v[k]); }
 
-// sum over the block, result in every thread
+// sum over the block, result in every thread: warps reduce by shuffles, warp
+// 0 adds the eight warp sums (not every thread) and shares the total
 __device__ __forceinline__ double block_allsum(double v, double* red) {
+  constexpr int NW = kBatchThreads / kWarp;
   v = subwarp_sum<32>(v, 0xffffffffu);
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[w] = v;
+  if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < kBatchThreads / kWarp; ++i) s += red[i];
-  return s;
+  if (w == 0) {
+    double t = lane < NW ? red[lane] : 0.0;
+    t = subwarp_sum<NW>(t, 0xffffffffu);
+    if (lane == 0) red[NW] = t;
+  }
+  __syncthreads();
+  return red[NW];
 }
 
 // One CG solve by a group of G threads (G = 256: a block; G = 32: a warp).
@@ -189,7 +194,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
 template <typename VT>
 __global__ void __launch_bounds__(kBatchThreads) batch_cg_kernel(BatchArgs a, int block_rows) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ double red[kBatchThreads / kWarp];
+  __shared__ double red[kBatchThreads / kWarp + 1];  // warp sums + the block total
   __shared__ int item_s;
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(a.queue, 1u);
