@@ -10,8 +10,9 @@ matrix is rejected by the padding limit and is not part of the step.
 SELL-P (slices of 64 rows) is timed the same way after the step and reported
 under `extra_formats`, outside `value` (the sweep's formats are CSR, ELL, COO
 and hybrid); on the power-law matrix it is rejected by the padding limit too.
-CSR and COO plans are chosen by the library's plan autotuner (gko_matrix_tune)
-at setup, untimed; the chosen plans are listed in config.tuned_plans.
+CSR and COO plan parameters are chosen by the library's plan autotuner
+(gko_matrix_tune, kernel kept) at setup, untimed; the plans are listed in
+config.tuned_plans.
 value = algorithmic bytes of all SpMVs / their summed device time (GB/s);
 L2 is flushed (256 MB write) before every SpMV.  Matrices stay resident in
 HBM; `e2e` repeats the step through the same C ABI calls with x copied in
@@ -579,8 +580,9 @@ def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid"), tune=True
                 x = x64 if dt == "f64" else x32
                 y = torch.zeros(A.n_rows, dtype=x.dtype, device=dev)
                 plan = None
-                if tune and fmt in ("csr", "coo"):  # setup step: the plan autotuner, untimed
-                    k, S, R, cap, _ = H.tune(x, y, reps=2)
+                if tune and fmt in ("csr", "coo"):  # setup step: the plan autotuner, untimed; the kernel
+                    # itself stays the histogram rule's, so profiled runs launch the same kernels
+                    k, S, R, cap, _ = H.tune(x, y, reps=2, keep_kernel=True)
                     plan = {"kernel": k, "subwarp": S, "rows_per_subwarp": R, "stage_cap": cap}
                 coo_launches = 2 if inf["coo_nnz"] > 0 and fmt in ("coo", "hybrid") else 0
                 hp = H.plan() if fmt in ("csr", "coo") else None

@@ -193,14 +193,18 @@ GKO_API int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t subwarp, i
  * for a CSR handle it times every row-block plan (subwarp 1,2,4,8 x rows per
  * subwarp 1,2,4 x stage_cap 512,1024,2048), the merge path and the subwarp
  * kernel with subwarp 4..32; for a COO handle the row-block plans and the
- * segmented reduction.  Each candidate runs y = A x once untimed, then `reps`
+ * segmented reduction.  keep_kernel != 0 keeps the handle's kernel and tunes
+ * only its parameters (row-block plans; nothing to tune for the merge path
+ * and the segmented reduction), so the kernel choice stays the histogram
+ * rule's whatever the timing conditions.  Each candidate runs y = A x once untimed, then `reps`
  * times (1..100) with L2 flushed (256 MB write) before each, best time kept;
  * the fastest plan is set on the handle (as gko_matrix_set_plan) and
  * returned (outputs may be NULL; best_ms in milliseconds).  x, y: device
  * vectors of the SpMV's vector dtype; y is overwritten.  Synchronises
  * `stream`.  GKO_NOT_SUPPORTED for other formats. */
-GKO_API int gko_matrix_tune(gko_matrix m, const void *x, void *y, int32_t reps, int32_t *kernel, int32_t *subwarp,
-                            int32_t *rows_per_subwarp, int32_t *stage_cap, float *best_ms, void *stream);
+GKO_API int gko_matrix_tune(gko_matrix m, const void *x, void *y, int32_t reps, int32_t keep_kernel,
+                            int32_t *kernel, int32_t *subwarp, int32_t *rows_per_subwarp, int32_t *stage_cap,
+                            float *best_ms, void *stream);
 
 GKO_API int gko_matrix_destroy(gko_matrix m);
 

@@ -81,8 +81,8 @@ extern "C" int gko_spmv_host(const double* alpha, gko_matrix A, const void* x_ho
 
 // Autotuner of the SpMV plan (see gko.h): times each candidate plan on the
 // caller's vectors with L2 flushed before every timed SpMV, keeps the best.
-extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t reps, int32_t* kernel, int32_t* S,
-                               int32_t* R, int32_t* cap, float* best_ms, void* stream) {
+extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t reps, int32_t keep_kernel,
+                               int32_t* kernel, int32_t* S, int32_t* R, int32_t* cap, float* best_ms, void* stream) {
   if (!m || reps < 1 || reps > 100) return fail(GKO_INVALID_ARG, "bad tune arguments (reps 1..100)");
   if (m->fmt != GKO_CSR && m->fmt != GKO_COO) return fail(GKO_NOT_SUPPORTED, "tuning covers CSR and COO plans");
   if (m->n_rows > 0 && (!x || !y)) return fail(GKO_INVALID_ARG, "null x or y");
@@ -91,16 +91,22 @@ extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t rep
     int32_t k, S, R, cap;
   };
   std::vector<Cand> cands;
-  for (int32_t ss : {1, 2, 4, 8})
-    for (int32_t rr : {1, 2, 4})
-      for (int32_t cc : {512, 1024, 2048}) cands.push_back({1, ss, rr, cc});
-  if (m->fmt == GKO_CSR) {
-    cands.push_back({2, 1, 1, 1024});  // merge path
-    for (int32_t ss : {4, 8, 16, 32}) cands.push_back({0, ss, 2, 1024});
-  } else {
-    cands.push_back({0, 1, 1, 1024});  // segmented reduction
-  }
   const Cand start{m->plan.kind, m->plan.S, m->plan.R, m->plan.cap};
+  // keep_kernel: only the parameters of the handle's current kernel (the
+  // row-block plans; merge path and segmented reduction have none)
+  if (!keep_kernel || start.k == 1)
+    for (int32_t ss : {1, 2, 4, 8})
+      for (int32_t rr : {1, 2, 4})
+        for (int32_t cc : {512, 1024, 2048}) cands.push_back({1, ss, rr, cc});
+  if (!keep_kernel) {
+    if (m->fmt == GKO_CSR) {
+      cands.push_back({2, 1, 1, 1024});  // merge path
+      for (int32_t ss : {4, 8, 16, 32}) cands.push_back({0, ss, 2, 1024});
+    } else {
+      cands.push_back({0, 1, 1, 1024});  // segmented reduction
+    }
+  }
+  if (cands.empty()) cands.push_back(start);
   if (m->n_rows == 0) {
     if (kernel) *kernel = start.k;
     if (S) *S = start.S;

@@ -73,7 +73,8 @@ SIGNATURES = {
     "gko_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gko_matrix_plan": (C.c_int, [_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI64, _PI64, _PI64]),
     "gko_matrix_set_plan": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P]),
-    "gko_matrix_tune": (C.c_int, [_P, _P, _P, _I32, _PI32, _PI32, _PI32, _PI32, C.POINTER(C.c_float), _P]),
+    "gko_matrix_tune": (C.c_int, [_P, _P, _P, _I32, _I32, _PI32, _PI32, _PI32, _PI32, C.POINTER(C.c_float),
+                                  _P]),
     "gko_matrix_destroy": (C.c_int, [_P]),
     "gko_spmv": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P]),
     "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
@@ -206,13 +207,15 @@ class Matrix:
         _check(lib().gko_matrix_set_plan(self.handle, kernel, subwarp, rows_per_subwarp, stage_cap,
                                          _stream(stream)), "set_plan")
 
-    def tune(self, x, y, reps: int = 2, stream=None):
+    def tune(self, x, y, reps: int = 2, keep_kernel: bool = False, stream=None):
         """Time the candidate SpMV plans on device vectors x, y and keep the
-        fastest; returns (kernel, subwarp, rows_per_subwarp, stage_cap, ms)."""
+        fastest (keep_kernel: only the current kernel's parameters); returns
+        (kernel, subwarp, rows_per_subwarp, stage_cap, ms)."""
         k, S, R, cap = (C.c_int32() for _ in range(4))
         ms = C.c_float()
-        _check(lib().gko_matrix_tune(self.handle, _dptr(x), _dptr(y), reps, C.byref(k), C.byref(S), C.byref(R),
-                                     C.byref(cap), C.byref(ms), _stream(stream)), "gko_matrix_tune")
+        _check(lib().gko_matrix_tune(self.handle, _dptr(x), _dptr(y), reps, 1 if keep_kernel else 0, C.byref(k),
+                                     C.byref(S), C.byref(R), C.byref(cap), C.byref(ms), _stream(stream)),
+               "gko_matrix_tune")
         return k.value, S.value, R.value, cap.value, ms.value
 
     def export(self, stream=None):

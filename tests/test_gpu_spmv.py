@@ -456,6 +456,9 @@ def test_tune_sets_a_valid_plan(gko, fmt, mat):
     M = make(G, A, fmt, G.F64)
     x = np.random.default_rng(2).uniform(-1, 1, A.n_cols)
     xd, yd = dev(x), torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    k0 = M.plan()["kernel"]
+    k, S, R, cap, ms = M.tune(xd, yd, reps=1, keep_kernel=True)
+    assert k == k0 and M.plan()["kernel"] == k0
     k, S, R, cap, ms = M.tune(xd, yd, reps=1)
     p = M.plan()
     assert p["kernel"] == k and ms > 0
