@@ -237,7 +237,7 @@ GKO_API int gko_spmv_host(const double *alpha, gko_matrix A, const void *x_host,
  * allocate device memory at the time they multiply (their memory is owned by
  * another allocator, or an allocation's possible implicit synchronisation is
  * not acceptable in their loop).  Same kernels and results as gko_spmv on the
- * handle, but the per-tile carries live in a fixed 1 MiB device array inside
+ * handle, but the per-tile carries live in a fixed 2 MiB device array inside
  * the library (held on every GPU that loads the library until exit) instead
  * of pool scratch.  At most 134,217,728 COO entries; larger handles are
  * rejected with GKO_INVALID_ARG.  The first call on a device looks up the

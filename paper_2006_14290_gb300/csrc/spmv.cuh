@@ -46,7 +46,7 @@ int spmv_run_bf16(const gko_matrix_s* A, const float* x, float* y, double alpha,
 int jacobi_inverse(const gko_matrix_s* A, double* d, cudaStream_t s);
 int narrow_to_f32(const double* d, float* f, int64_t n, cudaStream_t s);
 
-constexpr int kCooThreads = 256;
+constexpr int kCooThreads = 128;
 constexpr int kCooItems = 8;
 constexpr int kCooTile = kCooThreads * kCooItems;
 

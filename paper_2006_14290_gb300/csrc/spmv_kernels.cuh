@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
 
 // ------------------------------------------------- segmented tile carries --
 //
-// Carries of a 256-thread segmented pass (COO and merge-path kernels).  Each
+// Carries of an NT-thread segmented pass (COO and merge-path kernels).  Each
 // thread publishes `tail` (its sum after its last row end, or all of its sum
 // without one) and whether it ended a row.  A thread that ended a row gets
 // `in`, the sum of the tails of the preceding threads back to the nearest one
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
 // through shared memory, about one FP64 add per thread in total.  A warp
 // without a row end (a row longer than a warp's entries) would make some
 // walk long and serial, so the whole block then takes a log-step segmented
-// scan instead: 5 shuffle steps per warp, then a walk over at most 7 warp
-// totals.  The choice depends only on the sparsity pattern, so results stay
+// scan instead: 5 shuffle steps per warp, then a walk over at most NT/32 - 1
+// warp totals.  The choice depends only on the sparsity pattern, so results stay
 // reproducible.
 template <typename AT, int NT>
 __device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, int* s_end, AT* carry, int64_t tile,
@@ -879,16 +879,18 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
   for (int64_t r = r0; r < r1; ++r) y[r] = beta == AT(0) ? XT(0) : (XT)(beta * to_acc(y[r]));
 }
 
-// Resident blocks per SM the COO kernel's register budget is held to: 5 for
-// FP64 values (48 registers), 6 for FP32/BF16 (40).  Measured 5-10% faster
-// than the unconstrained 63/48 registers at 4/5 blocks.
+// Resident 128-thread blocks per SM the COO kernel's register budget is held
+// to: 9 for FP64 values (56 registers, the most blocks without spills), 11
+// for FP32/BF16 (40 registers; at 48 without spills it ran 6-8% slower).
+// FP64 against 256-thread blocks at 5 per SM (48 registers, with spills):
+// 5-8% faster, a tile's two barriers waiting on 4 warps instead of 8.
 template <typename VT>
 constexpr int coo_min_blocks() {
-  return std::is_same<VT, double>::value ? 5 : 6;
+  return std::is_same<VT, double>::value ? 9 : 11;
 }
 
-// Tiled segmented reduction over row-sorted COO.  Each 256-thread block owns
-// a tile of 256*kCooItems entries; each thread owns kCooItems consecutive
+// Tiled segmented reduction over row-sorted COO.  Each block of kCooThreads
+// threads owns a tile of kCooTile entries; each thread owns kCooItems consecutive
 // entries (vector loads) and folds them with one FMA per entry, finishing
 // the rows that start and end inside its entries on the spot.  The running
 // sum entering a thread's first row is the sum of the trailing partials of
