@@ -360,9 +360,12 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
 // Carries of an NT-thread segmented pass (COO and merge-path kernels).  Each
 // thread publishes `tail` (its sum after its last row end, or all of its sum
 // without one) and whether it ended a row.  A thread that ended a row gets
-// `in`, the sum of the tails of the preceding threads back to the nearest one
-// that ended a row, and `from_before` (no such thread: the row began before
-// the tile).  The tile's last-segment sum goes to carry[2*tile+1], and also
+// `total`, its first row's sum: `head` (its own entries of that row) plus the
+// tails of the preceding threads back to the nearest one that ended a row,
+// and `from_before` (no such thread: the row began before the tile).  The
+// walk starts from `head` rather than from zero: 0 + t is a real FP64 add
+// (signed zeros keep the compiler from folding it), and FP64 instructions
+// co-limit these kernels.  The tile's last-segment sum goes to carry[2*tile+1], and also
 // to carry[2*tile] when no thread ended a row.
 // Every warp holding a row end (short rows): each ending thread walks back
 // through shared memory, about one FP64 add per thread in total.  A warp
@@ -372,8 +375,8 @@ __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT
 // warp totals.  The choice depends only on the sparsity pattern, so results stay
 // reproducible.
 template <typename AT, int NT>
-__device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, int* s_end, AT* carry, int64_t tile,
-                                             AT& in, bool& from_before) {
+__device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT head, AT* s_tail, int* s_end, AT* carry,
+                                             int64_t tile, AT& total, bool& from_before) {
   constexpr int NW = NT / 32;
   __shared__ AT s_wv[NW];
   __shared__ int s_wf[NW];
@@ -382,12 +385,12 @@ __device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, 
   s_end[t] = has_end;
   const unsigned ends = __ballot_sync(0xffffffffu, has_end);
   const bool scan = __syncthreads_or(ends == 0u);
-  in = AT(0);
+  total = head;
   from_before = true;
   if (!scan) {
     if (has_end) {
       for (int u = t - 1; u >= 0; --u) {
-        in += s_tail[u];
+        total = s_tail[u] + total;
         if (s_end[u]) {
           from_before = false;
           break;
@@ -395,14 +398,11 @@ __device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, 
       }
     }
     if (t == 0) {
-      AT tv = AT(0);
-      bool any_end = false;
-      for (int u = NT - 1; u >= 0; --u) {
-        tv += s_tail[u];
-        if (s_end[u]) {
-          any_end = true;
-          break;
-        }
+      AT tv = s_tail[NT - 1];
+      bool any_end = s_end[NT - 1] != 0;
+      for (int u = NT - 2; u >= 0 && !any_end; --u) {
+        tv = s_tail[u] + tv;
+        any_end = s_end[u] != 0;
       }
       if (!any_end) carry[2 * tile] = tv;
       carry[2 * tile + 1] = tv;
@@ -446,7 +446,7 @@ __device__ __forceinline__ void tile_carries(AT tail, bool has_end, AT* s_tail, 
     fe = cf;
   }
   if (has_end) {
-    in = ve;
+    total = ve + head;
     from_before = !fe;
   }
   if (t == NT - 1) {
@@ -564,11 +564,10 @@ __global__ void __launch_bounds__(256, 5) csr_merge_kernel(CsrArgs<VT, XT> a, in
     }
   }
   while (items > 0) end_row();
-  AT in;
+  AT tot;
   bool from_before_tile;
-  tile_carries<AT, 256>(run, nends > 0, s_tail, s_end, carry, tile, in, from_before_tile);
+  tile_carries<AT, 256>(run, nends > 0, first_sum, s_tail, s_end, carry, tile, tot, from_before_tile);
   if (nends > 0) {
-    const AT tot = in + first_sum;
     if (from_before_tile && first_open)
       carry[2 * tile] = tot;
     else
@@ -991,11 +990,10 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
       if (r != nr && r + 1 < gap_end) coo_empty_rows(a.y, (int64_t)r + 1, (int64_t)gap_end, a.beta);
     }
   }
-  AT in;
+  AT total;
   bool from_before_tile;
-  tile_carries<AT, kCooThreads>(run, nends > 0, s_tail, s_end, carry, tile, in, from_before_tile);
+  tile_carries<AT, kCooThreads>(run, nends > 0, first_sum, s_tail, s_end, carry, tile, total, from_before_tile);
   if (nends > 0) {
-    const AT total = in + first_sum;
     if (from_before_tile && first_open)
       carry[2 * tile] = total;  // the tile's first row began in an earlier tile
     else
