@@ -882,7 +882,7 @@ __device__ __forceinline__ void coo_empty_rows(XT* y, int64_t r0, int64_t r1, AT
 // to: 9 for FP64 values (56 registers, the most blocks without spills), 11
 // for FP32/BF16 (40 registers; at 48 without spills it ran 6-8% slower).
 // FP64 against 256-thread blocks at 5 per SM (48 registers, with spills):
-// 5-8% faster, a tile's two barriers waiting on 4 warps instead of 8.
+// 5-8% faster, a tile's block barriers waiting on 4 warps instead of 8.
 template <typename VT>
 constexpr int coo_min_blocks() {
   return std::is_same<VT, double>::value ? 9 : 11;
@@ -903,10 +903,8 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
                                                                 const int* gate) {
   using AT = acc_t<VT>;
   constexpr int kTile = kCooThreads * IPT;
-  __shared__ int32_t s_first[kCooThreads + 1];
   __shared__ AT s_tail[kCooThreads];
   __shared__ int s_end[kCooThreads];
-  __shared__ int32_t s_prev_row;
   if (gated(gate)) return;
   prefetch_slice_l2(a.x, sizeof(XT) * (size_t)a.n_cols, kXPrefetchBlocks);
   const int t = threadIdx.x;
@@ -941,14 +939,16 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
       }
     }
   }
-  s_first[t] = my > 0 ? rows[0] : INT_MAX;
-  if (t == 0) {
-    s_first[kCooThreads] = (base + cnt < a.nnz) ? a.row[base + cnt] : -1;
-    s_prev_row = base > 0 ? a.row[base - 1] : -1;
-  }
-  __syncthreads();
-  const int32_t next_row = (j0 + IPT < cnt) ? s_first[t + 1] : s_first[kCooThreads];
-  const bool first_open = base > 0 && s_prev_row == s_first[0];
+  // Row of the entry after this thread's last one (-1 after the matrix's
+  // last entry): the next lane's first row by a shuffle; lane 31 and the
+  // tile's last thread load it.  No block barrier here (exchanging it
+  // through shared memory cost 4-5% on FP64).
+  const int32_t nb = __shfl_down_sync(0xffffffffu, my > 0 ? rows[0] : INT_MAX, 1);
+  int32_t next_row;
+  if (j0 + IPT < cnt)
+    next_row = (t & 31) != 31 ? nb : a.row[base + j0 + IPT];
+  else
+    next_row = (base + cnt < a.nnz) ? a.row[base + cnt] : -1;
   // rows before the first entry of the matrix have no entries
   if (!ACCUM && base == 0 && t == 0 && my > 0) coo_empty_rows(a.y, 0, (int64_t)rows[0], a.beta);
 
@@ -994,8 +994,10 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
   bool from_before_tile;
   tile_carries<AT, kCooThreads>(run, nends > 0, first_sum, s_tail, s_end, carry, tile, total, from_before_tile);
   if (nends > 0) {
-    if (from_before_tile && first_open)
-      carry[2 * tile] = total;  // the tile's first row began in an earlier tile
+    // the tile's first row began in an earlier tile: its sum so far is a carry
+    const bool first_open = from_before_tile && base > 0 && a.row[base - 1] == a.row[base];
+    if (first_open)
+      carry[2 * tile] = total;
     else
       coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM, a.plain);
   }
