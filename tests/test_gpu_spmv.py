@@ -24,6 +24,14 @@ def small_cases():
     yield "powerlaw_20k", I.powerlaw(20000, seed=1)
     yield "banded_5k", I.banded(5000, 16, 0.3, seed=2)
     yield "n1", I.rows_csr([3], 5, rng)
+    # Segmented-reduction boundaries (8 entries per thread, 256 per warp, 1024
+    # per COO tile): every thread ending a row on its last entry; rows ending
+    # on warp and tile edges; empty rows right after a tile edge.
+    yield "rows_of_8", I.rows_csr([8] * 4099, 3000, rng)
+    # row ends at entries 256, 512, ..., 2048, 3072, 5120, ... (5 on tile edges, 16 on warp edges)
+    yield "warp_tile_edges", I.rows_csr([256] * 4 + [1024, 1, 1023, 1025, 1023, 0, 255, 1, 0, 257, 255, 0, 512, 511, 1,
+                                         2047, 1] + [8] * 32 + [7, 9] * 16 + [3, 253, 1024, 0, 0, 1], 4000, rng)
+    yield "empty_after_tile_edge", I.rows_csr([1024, 0, 0, 1024, 0, 512, 512, 0, 3, 1021, 0] * 5, 2000, rng)
 
 
 CASES = list(small_cases())
