@@ -208,6 +208,41 @@ __device__ __forceinline__ T subwarp_sum(T v, unsigned mask) {
   return v;
 }
 
+// Reduce-scatter over a subwarp of S lanes that each hold R partial sums (R
+// rows).  The xor steps run S/2, ..., 1 as in subwarp_sum, so each row's sum
+// is the same tree of lane partials as R separate butterflies and the result
+// is bit-identical to them.  While a lane holds more than one value, a step
+// halves them: the lane keeps the half that its rank bit selects and adds
+// the partner's copy of that half.  Once one value is left, the steps are
+// plain butterflies.  Adds per lane: R/2 + R/4 + ... down to one value, then
+// one per remaining step, against R*log2(S) for separate butterflies (R = 4,
+// S = 4: 3 instead of 8).  Returns the index of the first row whose complete
+// sum this lane holds in v[0 .. max(1, R/S)).  The lanes whose low
+// log2(S / min(R, S)) rank bits are zero hold distinct rows.
+template <int S, int R, typename T>
+__device__ __forceinline__ int subwarp_reduce_scatter(T (&v)[R], int rank) {
+  int first = 0;
+  int cnt = R;
+#pragma unroll
+  for (int m = S / 2; m > 0; m >>= 1) {
+    if (cnt > 1) {
+      const bool hi = (rank & m) != 0;
+      const int h = cnt / 2;
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const T keep = hi ? v[h + j] : v[j];
+        const T give = hi ? v[j] : v[h + j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, give, m);
+      }
+      if (hi) first += h;
+      cnt = h;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+    }
+  }
+  return first;
+}
+
 // Exact float -> double widening with integer operations (GB300 runs the
 // F2F conversion instruction on its narrow FP64/conversion path).  Normal
 // numbers, zeros, infinities and NaNs convert exactly; FP32 subnormals

@@ -320,20 +320,27 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
     }
     const bool last = c.j + 1 >= c.nch;
     if (last) {
+      // Every lane of the block is here (block-uniform control flow), so the
+      // full-warp mask is valid (partial-mask shuffles measured ~3x slower in
+      // FP32, subwarp reduction benchmark, S = 4).  The R row sums are
+      // reduce-scattered: min(R, S) lanes of the subwarp each finish
+      // max(1, R/S) rows, with fewer FP64 adds than one butterfly per row.
+      constexpr int W = S < R ? S : R;   // lanes holding distinct rows
+      constexpr int NC = R > S ? R / S : 1;  // rows per such lane
+      const int first = S > 1 ? subwarp_reduce_scatter<S, R>(sum, rank) : 0;
+      if ((rank & (S / W - 1)) == 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        // every lane of the block is here (block-uniform control flow), so
-        // the full-warp mask is valid: partial-mask shuffles measured ~3x
-        // slower in FP32 (subwarp reduction benchmark, S = 4)
-        if (S > 1) sum[r] = subwarp_sum<S>(sum[r], 0xffffffffu);
-        const int64_t i = c.b * RB + sg + (int64_t)r * G;
-        if (rank == 0 && i < a.n) {
-          const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
-          a.y[i] = v;
-          if (DOT) dot_accum(d, i, v, dwy, dyy);
+        for (int j = 0; j < NC; ++j) {
+          const int64_t i = c.b * RB + sg + (int64_t)(first + j) * G;
+          if (i < a.n) {
+            const XT v = (XT)finish_row(a.y, i, sum[j], a.alpha, a.beta, a.plain);
+            a.y[i] = v;
+            if (DOT) dot_accum(d, i, v, dwy, dyy);
+          }
         }
-        sum[r] = AT(0);
       }
+#pragma unroll
+      for (int r = 0; r < R; ++r) sum[r] = AT(0);
     }
     if (!advance(c)) break;
     if (last) row_bounds(c.b);
