@@ -895,6 +895,37 @@ constexpr int coo_min_blocks() {
   return std::is_same<VT, double>::value ? 9 : 11;
 }
 
+// One thread's pass over its entries: an FMA per entry; rows that start and
+// end here are stored now.  FULL: all IPT entries are present (every thread
+// of every tile but the last), so the entry guards and the next-row choice
+// are compile-time.
+template <bool FULL, bool ACCUM, bool PLAIN, int IPT, typename VT, typename XT, typename AT>
+__device__ __forceinline__ void coo_thread_pass(const CooArgs<VT, XT>& a, const int32_t (&rows)[IPT],
+                                                const int32_t (&cols)[IPT], const VT (&vals)[IPT], int my,
+                                                int32_t next_row, AT& run, AT& first_sum, int32_t& first_row,
+                                                int& nends, bool& gap) {
+  const int32_t n_rows32 = (int32_t)a.n_rows;
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    if (FULL || u < my) {
+      const int32_t r = rows[u];
+      run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
+      const int32_t nr = FULL ? (u + 1 < IPT ? rows[u + 1] : next_row) : (u + 1 < my ? rows[u + 1] : next_row);
+      if (r != nr) {
+        if (nends == 0) {
+          first_sum = run;
+          first_row = r;
+        } else {
+          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM, PLAIN);
+        }
+        if (!ACCUM) gap |= r + 1 < (nr < 0 ? n_rows32 : nr);
+        ++nends;
+        run = AT(0);
+      }
+    }
+  }
+}
+
 // Tiled segmented reduction over row-sorted COO.  Each block of kCooThreads
 // threads owns a tile of kCooTile entries; each thread owns kCooItems consecutive
 // entries (vector loads) and folds them with one FMA per entry, finishing
@@ -905,7 +936,9 @@ constexpr int coo_min_blocks() {
 // carry[2*tile] / carry[2*tile+1] for coo_fixup_kernel.
 // ACCUM: y[r] += alpha*sum (hybrid tail); otherwise rows absent from the COO
 // arrays are scaled by beta here too.
-template <typename VT, typename XT, bool ACCUM, int IPT = kCooItems, int MINB = 1>
+// PLAIN: alpha == 1 and beta == 0, the store is a plain write (coo_launch
+// picks the instantiation from a.plain).
+template <typename VT, typename XT, bool ACCUM, int IPT = kCooItems, int MINB = 1, bool PLAIN = false>
 __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> a, acc_t<VT>* __restrict__ carry,
                                                                 const int* gate) {
   using AT = acc_t<VT>;
@@ -959,34 +992,18 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
   // rows before the first entry of the matrix have no entries
   if (!ACCUM && base == 0 && t == 0 && my > 0) coo_empty_rows(a.y, 0, (int64_t)rows[0], a.beta);
 
-  // one pass: FMA per entry; rows that start and end here are finished now.
   // Rows without entries lie between a row's end and the next entry's row;
-  // the thread that owns that row end scales them by beta (rare: flagged
-  // here, done after the pass from the row indices in memory).
+  // the thread that owns that row end scales them by beta (rare: flagged in
+  // the pass, done after it from the row indices in memory).
   AT run = AT(0), first_sum = AT(0);
   int32_t first_row = -1;
   int nends = 0;
   bool gap = false;
   const int32_t n_rows32 = (int32_t)a.n_rows;
-#pragma unroll
-  for (int u = 0; u < IPT; ++u) {
-    if (u < my) {
-      const int32_t r = rows[u];
-      run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
-      const int32_t nr = (u + 1 < my) ? rows[u + 1] : next_row;  // -1 after the last entry
-      if (r != nr) {
-        if (nends == 0) {
-          first_sum = run;
-          first_row = r;
-        } else {
-          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM, a.plain);
-        }
-        if (!ACCUM) gap |= r + 1 < (nr < 0 ? n_rows32 : nr);
-        ++nends;
-        run = AT(0);
-      }
-    }
-  }
+  if (my == IPT)
+    coo_thread_pass<true, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends, gap);
+  else
+    coo_thread_pass<false, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends, gap);
   if (!ACCUM && gap) {
 #pragma unroll 1
     for (int u = 0; u < my; ++u) {
@@ -1006,9 +1023,14 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
     if (first_open)
       carry[2 * tile] = total;
     else
-      coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM, a.plain);
+      coo_store(a.y, first_row, total, a.alpha, a.beta, ACCUM, PLAIN);
   }
 }
+
+// Segmented-reduction COO pass (kernel + fix-up) on stream s, with the
+// instantiation for a.plain (the hybrid tail always accumulates).
+template <typename VT, typename XT, bool ACCUM>
+inline void coo_launch(const CooArgs<VT, XT>& a, acc_t<VT>* carry, const int* gate, cudaStream_t s);
 
 // Complete rows that span tiles: the tile where such a row starts adds its
 // last-segment partial and the first-segment partials of the following
@@ -1036,6 +1058,23 @@ __global__ void __launch_bounds__(256)
     }
     coo_store(y, r, s, alpha, beta, ACCUM, alpha == acc_t<VT>(1) && beta == acc_t<VT>(0));
   }
+}
+
+template <typename VT, typename XT, bool ACCUM>
+inline void coo_launch(const CooArgs<VT, XT>& a, acc_t<VT>* carry, const int* gate, cudaStream_t s) {
+  constexpr int kMinB = coo_min_blocks<VT>();
+  const int64_t tiles = (a.nnz + kCooTile - 1) / kCooTile;
+  const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
+  if constexpr (!ACCUM) {
+    if (a.plain) {
+      coo_kernel<VT, XT, false, kCooItems, kMinB, true><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+    } else {
+      coo_kernel<VT, XT, false, kCooItems, kMinB, false><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+    }
+  } else {
+    coo_kernel<VT, XT, true, kCooItems, kMinB, false><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
+  }
+  coo_fixup_kernel<VT, XT, ACCUM><<<fg, 256, 0, s>>>(a.nnz, tiles, a.row, carry, a.y, a.alpha, a.beta, gate);
 }
 
 template <typename XT, typename AT>
@@ -1241,16 +1280,10 @@ struct SpmvImpl {
     AT* carry = static_cast<AT*>(scratch);
     CooArgs<VT, XT> a{A->n_rows, A->n_cols, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col),
                       ptr<VT>(A->coo_val), x, y, alpha, beta, alpha == AT(1) && beta == AT(0)};
-    constexpr int kMinB = coo_min_blocks<VT>();
-    const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
-    const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
-    if (accum) {
-      coo_kernel<VT, XT, true, kCooItems, kMinB><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
-      coo_fixup_kernel<VT, XT, true><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
-    } else {
-      coo_kernel<VT, XT, false, kCooItems, kMinB><<<(unsigned)tiles, kCooThreads, 0, s>>>(a, carry, gate);
-      coo_fixup_kernel<VT, XT, false><<<fg, 256, 0, s>>>(nnz, tiles, a.row, carry, y, alpha, beta, gate);
-    }
+    if (accum)
+      coo_launch<VT, XT, true>(a, carry, gate, s);
+    else
+      coo_launch<VT, XT, false>(a, carry, gate, s);
     GKO_TRY_CUDA(cudaGetLastError());
     return GKO_OK;
   }

@@ -75,13 +75,9 @@ extern "C" int gko_spmv_coo_noalloc(const double* alpha, gko_matrix A, const dou
   // Every carry slot the fix-up reads is written earlier in the same call, so
   // nothing needs clearing; calls that overlap on the GPU share the array
   // and race.
-  const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
   CooArgs<double, double> args{A->n_rows, A->n_cols, nnz, ptr<int32_t>(A->coo_row), ptr<int32_t>(A->coo_col),
                                ptr<double>(A->coo_val), x, y, a, b, a == 1.0 && b == 0.0};
-  const unsigned fg = (unsigned)std::min<int64_t>((tiles + 255) / 256, 4096);
-  coo_kernel<double, double, false, kCooItems, coo_min_blocks<double>()>
-      <<<(unsigned)tiles, kCooThreads, 0, s>>>(args, carry, nullptr);
-  coo_fixup_kernel<double, double, false><<<fg, 256, 0, s>>>(nnz, tiles, args.row, carry, y, a, b, nullptr);
+  coo_launch<double, double, false>(args, carry, nullptr, s);
   GKO_TRY_CUDA(cudaGetLastError());
   return GKO_OK;
 }
