@@ -214,6 +214,13 @@ def solver_suite(G, dev, stream):
                     "GB_s_per_iteration": round(it_bytes * max(res.iterations, 1) / (ms * 1e-3) / 1e9, 1)}
         return ms
 
+    def speedup(base, other):
+        """Time ratio of two runs, only when both converged (a ratio against
+        a breakdown or a stalled run says nothing)."""
+        if out[base]["status"] != G.OK or out[other]["status"] != G.OK:
+            return None
+        return round(out[base]["time_ms"] / out[other]["time_ms"], 3)
+
     A = I.stencil3d_7pt(256)
     M = G.from_csr(A)
     n, nnz = A.n_rows, A.nnz
@@ -221,10 +228,10 @@ def solver_suite(G, dev, stream):
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     bd = torch.zeros_like(ones)
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
-    t64 = run("cg_poisson256_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
-    t32 = run("cg_poisson256_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32)
+    run("cg_poisson256_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
+    run("cg_poisson256_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32)
     run("cg_poisson256_mixed_bf16", "cg", M, bd, n, nnz, G.PRECISION_MIXED_BF16)
-    out["cg_poisson256_mixed_f32_speedup"] = round(t64 / t32, 3)
+    out["cg_poisson256_mixed_f32_speedup"] = speedup("cg_poisson256_f64", "cg_poisson256_mixed_f32")
     # fixed work: 1,000 iterations (tolerance 0 never stops early)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
@@ -243,9 +250,9 @@ def solver_suite(G, dev, stream):
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
     for solver in ("bicgstab", "gmres"):
         tag = "bicgstab" if solver == "bicgstab" else "gmres30"
-        t64 = run(f"{tag}_convdiff128_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
-        t32 = run(f"{tag}_convdiff128_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
-        out[f"{tag}_convdiff128_mixed_f32_speedup"] = round(t64 / t32, 3)
+        run(f"{tag}_convdiff128_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
+        run(f"{tag}_convdiff128_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
+        out[f"{tag}_convdiff128_mixed_f32_speedup"] = speedup(f"{tag}_convdiff128_f64", f"{tag}_convdiff128_mixed_f32")
     del M, ones, bd
     # unpreconditioned BiCGSTAB does not converge at cell Peclet 10 on 128^3
     # (the oracle diverges too); Peclet 1 is the converging companion case
@@ -255,9 +262,10 @@ def solver_suite(G, dev, stream):
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     bd = torch.zeros_like(ones)
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
-    t64 = run("bicgstab_convdiff128_P1_f64", "bicgstab", M, bd, n, nnz, G.PRECISION_F64)
-    t32 = run("bicgstab_convdiff128_P1_mixed_f32", "bicgstab", M, bd, n, nnz, G.PRECISION_MIXED_F32)
-    out["bicgstab_convdiff128_P1_mixed_f32_speedup"] = round(t64 / t32, 3)
+    run("bicgstab_convdiff128_P1_f64", "bicgstab", M, bd, n, nnz, G.PRECISION_F64)
+    run("bicgstab_convdiff128_P1_mixed_f32", "bicgstab", M, bd, n, nnz, G.PRECISION_MIXED_F32)
+    out["bicgstab_convdiff128_P1_mixed_f32_speedup"] = speedup("bicgstab_convdiff128_P1_f64",
+                                                               "bicgstab_convdiff128_P1_mixed_f32")
     del M, ones, bd
     # Jacobi preconditioning on the variable-coefficient Poisson problem 128^3
     # (coefficients exp(N(0,1)) per cell, default_rng(0); b = A*1)
@@ -268,11 +276,11 @@ def solver_suite(G, dev, stream):
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     bd = torch.zeros_like(ones)
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
-    t0 = run("cg_varcoef128_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
-    tj = run("cg_varcoef128_jacobi_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_JACOBI)
-    tm = run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
-    out["cg_varcoef128_jacobi_speedup"] = round(t0 / tj, 3)
-    out["cg_varcoef128_jacobi_mixed_f32_speedup"] = round(t0 / tm, 3)
+    run("cg_varcoef128_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
+    run("cg_varcoef128_jacobi_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_JACOBI)
+    run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
+    out["cg_varcoef128_jacobi_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_f64")
+    out["cg_varcoef128_jacobi_mixed_f32_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_mixed_f32")
     del M, ones, bd
     out["batched_cg"] = batched_suite(G, dev, stream)
     return out
