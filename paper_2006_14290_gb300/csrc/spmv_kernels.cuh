@@ -898,30 +898,26 @@ constexpr int coo_min_blocks() {
 // One thread's pass over its entries: an FMA per entry; rows that start and
 // end here are stored now.  FULL: all IPT entries are present (every thread
 // of every tile but the last), so the entry guards and the next-row choice
-// are compile-time.
+// are compile-time.  The row-end bookkeeping is written as selects around a
+// predicated store (measured the same as the branchy form).
 template <bool FULL, bool ACCUM, bool PLAIN, int IPT, typename VT, typename XT, typename AT>
 __device__ __forceinline__ void coo_thread_pass(const CooArgs<VT, XT>& a, const int32_t (&rows)[IPT],
                                                 const int32_t (&cols)[IPT], const VT (&vals)[IPT], int my,
                                                 int32_t next_row, AT& run, AT& first_sum, int32_t& first_row,
-                                                int& nends, bool& gap) {
-  const int32_t n_rows32 = (int32_t)a.n_rows;
+                                                int& nends) {
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     if (FULL || u < my) {
       const int32_t r = rows[u];
       run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
       const int32_t nr = FULL ? (u + 1 < IPT ? rows[u + 1] : next_row) : (u + 1 < my ? rows[u + 1] : next_row);
-      if (r != nr) {
-        if (nends == 0) {
-          first_sum = run;
-          first_row = r;
-        } else {
-          coo_store(a.y, r, run, a.alpha, a.beta, ACCUM, PLAIN);
-        }
-        if (!ACCUM) gap |= r + 1 < (nr < 0 ? n_rows32 : nr);
-        ++nends;
-        run = AT(0);
-      }
+      const bool e = r != nr;
+      if (e && nends > 0) coo_store(a.y, r, run, a.alpha, a.beta, ACCUM, PLAIN);
+      const bool f = e && nends == 0;
+      first_sum = f ? run : first_sum;
+      first_row = f ? r : first_row;
+      nends += e ? 1 : 0;
+      run = e ? AT(0) : run;
     }
   }
 }
@@ -992,18 +988,20 @@ __global__ void __launch_bounds__(kCooThreads, MINB) coo_kernel(CooArgs<VT, XT> 
   // rows before the first entry of the matrix have no entries
   if (!ACCUM && base == 0 && t == 0 && my > 0) coo_empty_rows(a.y, 0, (int64_t)rows[0], a.beta);
 
-  // Rows without entries lie between a row's end and the next entry's row;
-  // the thread that owns that row end scales them by beta (rare: flagged in
-  // the pass, done after it from the row indices in memory).
   AT run = AT(0), first_sum = AT(0);
   int32_t first_row = -1;
   int nends = 0;
-  bool gap = false;
-  const int32_t n_rows32 = (int32_t)a.n_rows;
   if (my == IPT)
-    coo_thread_pass<true, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends, gap);
+    coo_thread_pass<true, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends);
   else
-    coo_thread_pass<false, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends, gap);
+    coo_thread_pass<false, ACCUM, PLAIN>(a, rows, cols, vals, my, next_row, run, first_sum, first_row, nends);
+  // Rows without entries lie between a row's end and the next entry's row;
+  // the thread that owns that row end scales them by beta.  Rows are sorted,
+  // so rows[0] .. stop-1 (stop: the next entry's row, or n) are all present
+  // exactly when there are as many of them as row ends here; otherwise
+  // (rare) the gaps are found from the row indices in memory.
+  const int32_t n_rows32 = (int32_t)a.n_rows;
+  const bool gap = !ACCUM && my > 0 && (next_row < 0 ? n_rows32 : next_row) - rows[0] > nends;
   if (!ACCUM && gap) {
 #pragma unroll 1
     for (int u = 0; u < my; ++u) {
