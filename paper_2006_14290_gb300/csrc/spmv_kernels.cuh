@@ -739,7 +739,8 @@ struct EllArgs {
 
 // Column-major ELL: each thread owns RPT consecutive rows and reads slot k of
 // all of them with one 128-bit (or 64-bit) load per array; padding slots
-// (col = -1) never touch x.
+// (col = -1) never touch x, and a thread stops at the first 4-slot chunk that
+// ends in padding for all its rows.
 // SELL (SELL-P): the same walk inside the thread's slice, whose own width and
 // first column come from sets[]; slot k of row i is at (sets[s] + k) * C +
 // i % C.  Slices of 64 rows are one warp's rows in FP64 (2 per thread), so a
@@ -784,6 +785,13 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
           if (c[u][r] >= 0) sum[r] = madd(to_acc(v[u][r]), to_acc(ld_vec(a.x + c[u][r])), sum[r]);
+      // Padding is trailing in every row: once the chunk's last slot is
+      // padding in all of this thread's rows, so is the rest, and the thread
+      // stops loading (its lanes' sectors drop out of the warp's loads).
+      bool done = true;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) done = done && c[U - 1][r] < 0;
+      if (done) break;
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
