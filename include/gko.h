@@ -196,9 +196,11 @@ GKO_API int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t subwarp, i
  * segmented reduction.  keep_kernel != 0 keeps the handle's kernel and tunes
  * only its parameters (row-block plans; nothing to tune for the merge path
  * and the segmented reduction), so the kernel choice stays the histogram
- * rule's whatever the timing conditions.  Each candidate runs y = A x once untimed, then `reps`
- * times (1..100) with L2 flushed (256 MB write) before each, best time kept;
- * the fastest plan is set on the handle (as gko_matrix_set_plan) and
+ * rule's whatever the timing conditions.  Each candidate runs y = A x once
+ * untimed, then `reps` times (1..100) with L2 flushed (256 MB write) before
+ * each, best time kept; the three fastest are timed again the same way with
+ * 3*reps runs, and the fastest of those is set on the handle (as
+ * gko_matrix_set_plan) and
  * returned (outputs may be NULL; best_ms in milliseconds).  x, y: device
  * vectors of the SpMV's vector dtype; y is overwritten.  Synchronises
  * `stream`.  GKO_NOT_SUPPORTED for other formats. */

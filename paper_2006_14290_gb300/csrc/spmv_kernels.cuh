@@ -309,7 +309,17 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
         acc = madd(to_acc(v2), to_acc(x2), acc);
         acc = madd(to_acc(v3), to_acc(x3), acc);
       }
-      for (; k < hi; k += S) acc = madd(to_acc(sv[k]), to_acc(ld_vec(a.x + sc[k])), acc);
+      // At most 3 entries remain.  One row per subwarp: three predicated
+      // steps, no loop (27-pt FP64, S = 4: 0.165 -> 0.156 ms).  With R > 1
+      // the R copies of those steps cost more than the loop (banded FP64,
+      // S = 4, R = 4: 0.144 -> 0.19 ms), so they keep the loop.
+      if constexpr (R == 1) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (k + u * S < hi) acc = madd(to_acc(sv[k + u * S]), to_acc(ld_vec(a.x + sc[k + u * S])), acc);
+      } else {
+        for (; k < hi; k += S) acc = madd(to_acc(sv[k]), to_acc(ld_vec(a.x + sc[k])), acc);
+      }
       sum[r] = acc;
     }
     __syncthreads();  // stage consumed by everyone
