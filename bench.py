@@ -594,7 +594,7 @@ def build_cases(G, mats, dev, formats=("csr", "ell", "coo", "hybrid"), tune=True
                     plan = {"kernel": k, "subwarp": S, "rows_per_subwarp": R, "stage_cap": cap}
                 coo_launches = 2 if inf["coo_nnz"] > 0 and fmt in ("coo", "hybrid") else 0
                 hp = H.plan() if fmt in ("csr", "coo") else None
-                csr_launches = 2 if hp and hp["kernel"] == 2 else 1 + (2 if hp and hp["n_long_rows"] > 0 else 0)
+                csr_launches = 2 if hp and hp["kernel"] in (2, 3) else 1 + (2 if hp and hp["n_long_rows"] > 0 else 0)
                 if fmt == "coo" and hp["kernel"] == 1:
                     coo_launches = 1  # row-block COO: one launch, no tile fix-up
                 launches = {"csr": csr_launches, "ell": 1, "sellp": 1,

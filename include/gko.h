@@ -160,9 +160,14 @@ GKO_API int gko_matrix_export(gko_matrix m, int32_t *row_ptr, int32_t *col, void
  * rows_per_subwarp interleaved rows of a block of 128 threads.
  * Handles with FP32 or BF16 values use a quarter of the FP64 lanes per row
  * (at least 1) and, when that changes the width, two rows per subwarp.
- * CSR kernel 2, the merge-path kernel (skewed matrices, the default there):
- * the merged sequence of row ends and nonzeros is split into equal shares
- * per thread, so long rows spread over many threads and tiles.
+ * CSR kernel 2, the merge-path kernel: the merged sequence of row ends and
+ * nonzeros is split into equal shares per thread, so long rows spread over
+ * many threads and tiles.
+ * CSR kernel 3, the nonzero split (skewed matrices, the default there): the
+ * nonzeros are cut into equal tiles of
+ * 1024, 8 consecutive ones per thread; each tile finds its rows in a staged
+ * slice of row_ptr (one row index per tile is precomputed), and rows that
+ * cross threads or tiles are completed from carries in a fixed order.
  * CSR kernel 0, the subwarp kernel: `subwarp` lanes per row,
  * rows_per_subwarp rows per pass, and rows longer than long_threshold split
  * into fixed-size nonzero chunks (n_long_rows rows, n_long_chunks chunks).
@@ -180,8 +185,8 @@ GKO_API int gko_matrix_plan(gko_matrix m, int32_t *kernel, int32_t *subwarp, int
 /* Override the plan (the autotuner's knob).  CSR kernel 0: subwarp S in
  * 1,2,4,8,16,32, R in 1,2,4, long-row threshold 32*S; CSR kernel 1:
  * row-block, S in 1,2,4,8, R in 1,2,4, stage_cap a power of two in
- * 512..8192 (ignored otherwise); CSR kernel 2: merge path (S, R still
- * validated, unused).  COO kernel 1: row-block, S in 1,2,4,8, R in 1,2,4,
+ * 512..8192 (ignored otherwise); CSR kernel 2: merge path, kernel 3: nonzero
+ * split (S, R still validated, unused).  COO kernel 1: row-block, S in 1,2,4,8, R in 1,2,4,
  * stage_cap a power of two in 512..4096; COO kernel 0 or 2: segmented
  * reduction.  The solvers' cached low-precision copies follow; handles made by
  * gko_matrix_convert_values keep their own plan.  Synchronises `stream`. */
@@ -191,8 +196,8 @@ GKO_API int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t subwarp, i
 /* SpMV plan autotuner (the project's tuner for lanes per row, rows per
  * subwarp, stage capacity and kernel; the paper tunes nothing at run time):
  * for a CSR handle it times every row-block plan (subwarp 1,2,4,8 x rows per
- * subwarp 1,2,4 x stage_cap 512,1024,2048), the merge path and the subwarp
- * kernel with subwarp 4..32; for a COO handle the row-block plans and the
+ * subwarp 1,2,4 x stage_cap 512,1024,2048), the merge path, the nonzero split
+ * and the subwarp kernel with subwarp 4..32; for a COO handle the row-block plans and the
  * segmented reduction.  keep_kernel != 0 keeps the handle's kernel and tunes
  * only its parameters (row-block plans; nothing to tune for the merge path
  * and the segmented reduction), so the kernel choice stays the histogram

@@ -99,7 +99,7 @@ inline size_t rb_smem_need(int cap, size_t value_bytes, bool coo) {
 
 // Load-balancing plan of the CSR SpMV, built from the row-length histogram.
 struct CsrPlan {
-  int32_t kind = 0;         // 0: subwarp kernel, 1: TMA row-block kernel
+  int32_t kind = 0;         // 0: subwarp, 1: TMA row-block, 2: merge path, 3: nonzero split
   int32_t S = 32;           // subwarp width for ordinary rows
   int32_t R = 4;            // rows per subwarp pass (row-block: rows per subwarp)
   int32_t cap = 2048;       // row-block kernel: nonzeros per shared-memory stage
@@ -114,6 +114,8 @@ struct CsrPlan {
   Buf chunk_start;     // int32[n_chunks]   first nonzero of each chunk
   Buf merge_x;         // int32[tiles+1]    merge-path row coordinate of each tile corner
   int64_t merge_tiles = 0;
+  Buf seg_row;         // int32[tiles+1]    nonzero split: row of the first nonzero of each tile
+  int64_t seg_tiles = 0;
   // COO handles: kind 1 runs the row-block kernel over the COO arrays, any
   // other kind the tiled segmented reduction.
   Buf coo_rb;          // int32[n_rb+1]     first COO entry of each row block of (128/S)*R rows

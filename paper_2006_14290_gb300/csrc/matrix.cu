@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "scan.cuh"
+#include "spmv.cuh"
 
 gko_matrix_s::~gko_matrix_s() {
   for (auto& kv : lowp) delete kv.second;
@@ -205,11 +206,13 @@ static unsigned grid_for(int64_t work, int threads = 256) {
 //    (interleaved rows per subwarp) the largest power of two <= 4 with
 //    (128/S)*R*m <= cap, so one row block fills about a stage.
 //    No row is split.
-//  * Skewed matrices use the merge-path kernel (equal shares of row ends plus
-//    nonzeros per thread).  The subwarp kernel with a nonzero split of long
-//    rows stays available through gko_matrix_set_plan (kernel 0): S = the
-//    smallest power of two (<= 32) not below the mean length of rows shorter
-//    than 1024, R = 2 rows per pass, rows longer than 32*S split.
+//  * Skewed matrices use the nonzero split (kernel 3: equal tiles of
+//    nonzeros, 8 per thread; on the power-law matrix 26% faster than the
+//    merge path in FP64).  The merge path (kernel 2) and the subwarp kernel
+//    with a nonzero split of long rows (kernel 0) stay available through
+//    gko_matrix_set_plan; for kernel 0, S = the smallest power of two
+//    (<= 32) not below the mean length of rows shorter than 1024, R = 2 rows
+//    per pass, rows longer than 32*S split.
 // Narrower values (FP32, BF16) halve or quarter the bytes a lane streams per
 // entry while the x gather stays, so the row-block kernel runs best with a
 // quarter of the FP64 lanes per row and two interleaved rows per subwarp
@@ -248,10 +251,10 @@ static void choose_plan(CsrPlan& p, int64_t n) {
   const double mean = rows ? (double)nz / (double)rows : 1.0;
   int32_t S = 1;
   while (S < 32 && (double)S < mean) S *= 2;
-  p.kind = 2;
+  p.kind = 3;
   p.S = S;
   p.R = 2;
-  p.long_thr = INT32_MAX;  // merge path needs no long-row split
+  p.long_thr = INT32_MAX;  // the nonzero split needs no long-row split
 }
 
 // Row coordinate of every merge-path tile corner (diagonal t * tile, t =
@@ -288,6 +291,43 @@ static int build_merge_corners(gko_matrix m, cudaStream_t s) {
   GKO_TRY_CUDA(cudaGetLastError());
   GKO_TRY_CUDA(cudaStreamSynchronize(s));
   p.merge_tiles = tiles;
+  return GKO_OK;
+}
+
+// Nonzero-split tiles: row of nonzero t * tile for t < tiles (the last row
+// whose pointer is <= it, which has nonzeros), and n - 1 for t = tiles.
+__global__ void seg_rows_kernel(int64_t n, int64_t tiles, int64_t tile, const int32_t* __restrict__ rp,
+                                int32_t* __restrict__ sr) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t == tiles) {
+      sr[t] = (int32_t)(n - 1);
+      continue;
+    }
+    const int64_t k = t * tile;
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo + 1) / 2;
+      if ((int64_t)rp[mid] <= k)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    sr[t] = (int32_t)lo;
+  }
+}
+
+static int build_seg_rows(gko_matrix m, cudaStream_t s) {
+  CsrPlan& p = m->plan;
+  p.seg_row.reset();
+  p.seg_tiles = 0;
+  if (p.kind != 3 || m->nnz == 0) return GKO_OK;
+  const int64_t tiles = (m->nnz + kCooTile - 1) / kCooTile;
+  GKO_TRY(alloc(sizeof(int32_t) * (tiles + 1), &p.seg_row));
+  seg_rows_kernel<<<grid_for(tiles + 1), 256, 0, s>>>(m->n_rows, tiles, kCooTile, ptr<int32_t>(m->row_ptr),
+                                                      ptr<int32_t>(p.seg_row));
+  GKO_TRY_CUDA(cudaGetLastError());
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  p.seg_tiles = tiles;
   return GKO_OK;
 }
 
@@ -386,6 +426,7 @@ static int build_plan(gko_matrix m, cudaStream_t s) {
   choose_plan(p, n);
   if (m->dtype != GKO_F64) narrow_plan(p);
   GKO_TRY(build_merge_corners(m, s));
+  GKO_TRY(build_seg_rows(m, s));
   return build_long_split(m, s);
 }
 
@@ -565,11 +606,11 @@ int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int3
   }
   if (!m || m->fmt != GKO_CSR) return fail(GKO_INVALID_ARG, "plan needs a CSR or COO handle");
   const bool rb = kernel == 1;
-  if ((kernel < 0 || kernel > 2) || !valid_S(S) || !valid_R(R) || (rb && S > 8) ||
+  if ((kernel < 0 || kernel > 3) || !valid_S(S) || !valid_R(R) || (rb && S > 8) ||
       (rb && (cap < 512 || cap > 8192 || (cap & (cap - 1)))))
     return fail(GKO_INVALID_ARG,
-                "kernel 0 (subwarp: S 1..32, R 1,2,4), 1 (row-block: S 1..8, R 1,2,4, cap 512..8192, powers of 2) "
-                "or 2 (merge path)");
+                "kernel 0 (subwarp: S 1..32, R 1,2,4), 1 (row-block: S 1..8, R 1,2,4, cap 512..8192, powers of 2), "
+                "2 (merge path) or 3 (nonzero split)");
   std::lock_guard<std::mutex> lk(m->mu);
   m->plan.kind = kernel;
   m->plan.S = S;
@@ -577,6 +618,7 @@ int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int3
   if (rb) m->plan.cap = cap;
   m->plan.long_thr = kernel == 0 ? 32 * S : INT32_MAX;
   GKO_TRY(build_merge_corners(m, (cudaStream_t)stream));
+  GKO_TRY(build_seg_rows(m, (cudaStream_t)stream));
   GKO_TRY(build_long_split(m, (cudaStream_t)stream));
   for (auto& kv : m->lowp) {  // low-precision copies share the pattern
     if (kv.second->fmt == GKO_CSR) {
@@ -594,6 +636,8 @@ int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t S, int32_t R, int3
       q.chunk_start = m->plan.chunk_start;
       q.merge_x = m->plan.merge_x;
       q.merge_tiles = m->plan.merge_tiles;
+      q.seg_row = m->plan.seg_row;
+      q.seg_tiles = m->plan.seg_tiles;
     }
   }
   return GKO_OK;
@@ -813,6 +857,8 @@ int gko_matrix_convert_values(gko_matrix src, gko_dtype to, void* stream, gko_ma
   m->plan.chunk_start = src->plan.chunk_start;
   m->plan.merge_x = src->plan.merge_x;
   m->plan.merge_tiles = src->plan.merge_tiles;
+  m->plan.seg_row = src->plan.seg_row;
+  m->plan.seg_tiles = src->plan.seg_tiles;
   m->plan.coo_rb = src->plan.coo_rb;
   m->plan.coo_rb_n = src->plan.coo_rb_n;
   m->K = src->K;
@@ -865,7 +911,7 @@ int gko_matrix_info(gko_matrix m, gko_format* format, gko_dtype* dtype, int64_t*
     int64_t b = 0;
     for (const Buf* x : {&m->row_ptr, &m->col, &m->val, &m->ell_col, &m->ell_val, &m->coo_row, &m->coo_col,
                          &m->coo_val, &m->plan.long_rows, &m->plan.long_chunk_ptr, &m->plan.chunk_row,
-                         &m->plan.chunk_start, &m->plan.merge_x, &m->plan.coo_rb, &m->sellp_sets,
+                         &m->plan.chunk_start, &m->plan.merge_x, &m->plan.seg_row, &m->plan.coo_rb, &m->sellp_sets,
                          &m->sellp_col, &m->sellp_val})
       if (*x) b += (int64_t)(*x)->bytes;
     *bytes = b;

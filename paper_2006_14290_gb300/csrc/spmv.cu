@@ -12,6 +12,7 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
   switch (A->fmt) {
     case GKO_CSR:
       if (A->plan.kind == 2) return at * 2 * (size_t)((A->n_rows + A->nnz + 2047) / 2048 + 1);
+      if (A->plan.kind == 3) return at * 2 * (size_t)((A->nnz + kCooTile - 1) / kCooTile + 1);
       return at * (size_t)A->plan.n_chunks;
     case GKO_ELL:
     case GKO_SELLP:
@@ -26,7 +27,7 @@ size_t spmv_scratch_bytes(const gko_matrix_s* A) {
 }
 
 bool spmv_fuses_dot(const gko_matrix_s* A) {
-  return (A->fmt == GKO_CSR && A->plan.kind != 2) || A->fmt == GKO_ELL || A->fmt == GKO_SELLP ||
+  return (A->fmt == GKO_CSR && A->plan.kind != 2 && A->plan.kind != 3) || A->fmt == GKO_ELL || A->fmt == GKO_SELLP ||
          (A->fmt == GKO_COO && A->plan.kind == 1 && A->coo_nnz > 0);
 }
 
@@ -103,6 +104,7 @@ extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t rep
   if (!keep_kernel) {
     if (m->fmt == GKO_CSR) {
       cands.push_back({2, 1, 1, 1024});  // merge path
+      cands.push_back({3, 1, 1, 1024});  // nonzero split
       for (int32_t ss : {4, 8, 16, 32}) cands.push_back({0, ss, 2, 1024});
     } else {
       cands.push_back({0, 1, 1, 1024});  // segmented reduction

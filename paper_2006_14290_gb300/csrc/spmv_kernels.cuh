@@ -1093,6 +1093,147 @@ inline void coo_launch(const CooArgs<VT, XT>& a, acc_t<VT>* carry, const int* ga
   coo_fixup_kernel<VT, XT, ACCUM><<<fg, 256, 0, s>>>(a.nnz, tiles, a.row, carry, a.y, a.alpha, a.beta, gate);
 }
 
+// ------------------------------------------------- nonzero-split CSR --
+//
+// Nonzero-split CSR (skewed matrices): the nonzeros are cut into tiles of
+// kCooTile, kCooItems consecutive ones per thread loaded with 16-byte loads,
+// as in the COO kernel, but no row index is read: a row ends where the next
+// row pointer lies.  The plan holds seg_row[t], the row of nonzero
+// t*kCooTile (t < tiles), and seg_row[tiles] = n - 1.  A tile stages
+// row_ptr[seg_row[t] .. seg_row[t+1] + 1] in shared memory (reads it from
+// global memory instead when that slice is longer than kSegRpCap, i.e. the
+// tile spans thousands of empty rows); each thread finds the row of its first
+// nonzero by binary search there and walks its entries.  Carries as in the
+// COO kernel; rows that cross tiles are finished by csr_seg_fixup_kernel.
+// Rows without nonzeros are written by the thread that ends the row before
+// them (those before the first nonzero by tile 0's first thread).
+constexpr int kSegRpCap = 2048;
+
+template <bool FULL, bool PLAIN, typename VT, typename XT, typename AT, typename RPV>
+__device__ __forceinline__ void csr_seg_pass(const CsrArgs<VT, XT>& a, const int32_t (&cols)[kCooItems],
+                                             const VT (&vals)[kCooItems], int my, int32_t k0, const RPV& rpv,
+                                             int32_t r, AT& run, AT& first_sum, int32_t& first_row, int& nends) {
+  const int32_t n32 = (int32_t)a.n;
+  int32_t nb = rpv(r + 1);  // one past the last nonzero of row r
+#pragma unroll
+  for (int u = 0; u < kCooItems; ++u) {
+    if (FULL || u < my) {
+      run = madd(to_acc(vals[u]), to_acc(ld_vec(a.x + cols[u])), run);
+      const int32_t k1 = k0 + u + 1;
+      if (k1 == nb) {  // row r ends at this entry
+        if (nends == 0) {
+          first_sum = run;
+          first_row = r;
+        } else {
+          coo_store(a.y, r, run, a.alpha, a.beta, false, PLAIN);
+        }
+        ++nends;
+        run = AT(0);
+        // on to the next row with nonzeros; the rows skipped have none
+        ++r;
+        nb = r < n32 ? rpv(r + 1) : INT_MAX;
+        while (nb == k1) {
+          coo_empty_rows(a.y, (int64_t)r, (int64_t)r + 1, a.beta);
+          ++r;
+          nb = r < n32 ? rpv(r + 1) : INT_MAX;
+        }
+      }
+    }
+  }
+}
+
+template <typename VT, typename XT, bool PLAIN>
+__global__ void __launch_bounds__(kCooThreads, coo_min_blocks<VT>())
+    csr_seg_kernel(CsrArgs<VT, XT> a, int64_t nnz, const int32_t* __restrict__ seg_row,
+                   acc_t<VT>* __restrict__ carry, const int* gate) {
+  using AT = acc_t<VT>;
+  __shared__ int32_t s_rp[kSegRpCap + 2];
+  __shared__ AT s_tail[kCooThreads];
+  __shared__ int s_end[kCooThreads];
+  if (gated(gate)) return;
+  prefetch_slice_l2(a.x, sizeof(XT) * (size_t)a.n_cols, kXPrefetchBlocks);
+  const int t = threadIdx.x;
+  const int64_t tile = blockIdx.x;
+  const int64_t base = tile * kCooTile;
+  const int cnt = (int)min((int64_t)kCooTile, nnz - base);
+  const int j0 = t * kCooItems;
+  const int my = max(0, min(kCooItems, cnt - j0));
+  int32_t cols[kCooItems];
+  VT vals[kCooItems];
+  if (my == kCooItems) {
+    load8_i32(a.col + base + j0, cols);
+    Load8<VT>::run(a.val + base + j0, vals);
+  } else {
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) {
+      cols[u] = u < my ? a.col[base + j0 + u] : 0;
+      vals[u] = u < my ? a.val[base + j0 + u] : VT(0);
+    }
+  }
+  const int32_t ra = __ldg(seg_row + tile), rb = __ldg(seg_row + tile + 1);
+  const int span = rb - ra + 2;  // row pointers ra .. rb + 1
+  const bool staged = span <= kSegRpCap + 2;
+  if (staged)
+    for (int i = t; i < span; i += kCooThreads) s_rp[i] = __ldg(a.rp + ra + i);
+  __syncthreads();
+  const auto rpv = [&](int32_t r) -> int32_t { return staged ? s_rp[r - ra] : __ldg(a.rp + r); };
+  // rows before the first nonzero of the matrix have none
+  if (base == 0 && t == 0) coo_empty_rows(a.y, 0, (int64_t)ra, a.beta);
+
+  const int32_t k0 = (int32_t)(base + j0);
+  AT run = AT(0), first_sum = AT(0);
+  int32_t first_row = -1;
+  int nends = 0;
+  if (my > 0) {
+    int32_t lo = ra, hi = rb;  // the last row starting at or before k0 holds it
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if (rpv(mid) <= k0)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (my == kCooItems)
+      csr_seg_pass<true, PLAIN>(a, cols, vals, my, k0, rpv, lo, run, first_sum, first_row, nends);
+    else
+      csr_seg_pass<false, PLAIN>(a, cols, vals, my, k0, rpv, lo, run, first_sum, first_row, nends);
+  }
+  AT total;
+  bool from_before_tile;
+  tile_carries<AT, kCooThreads>(run, nends > 0, first_sum, s_tail, s_end, carry, tile, total, from_before_tile);
+  if (nends > 0) {
+    // the tile's first row began in an earlier tile: its sum so far is a carry
+    const bool first_open = from_before_tile && rpv(first_row) < base;
+    if (first_open)
+      carry[2 * tile] = total;
+    else
+      coo_store(a.y, first_row, total, a.alpha, a.beta, false, PLAIN);
+  }
+}
+
+// Rows that cross tiles: the tile where such a row begins adds its last
+// segment and the first segments of the following tiles, in tile order.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256)
+    csr_seg_fixup_kernel(CsrArgs<VT, XT> a, int64_t tiles, const int32_t* __restrict__ seg_row,
+                         const acc_t<VT>* __restrict__ carry, const int* gate) {
+  using AT = acc_t<VT>;
+  if (gated(gate)) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t + 1 < tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = seg_row[t + 1];  // row of the next tile's first nonzero
+    const int64_t rs = a.rp[r];
+    if (rs >= (t + 1) * kCooTile) continue;  // it starts there: nothing crosses
+    if (rs < t * kCooTile) continue;         // it began before this tile
+    AT s = carry[2 * t + 1];
+    for (int64_t u = t + 1; u < tiles; ++u) {
+      s += carry[2 * u];
+      if (!(u + 1 < tiles && seg_row[u + 1] == r)) break;  // row r ends in tile u
+    }
+    a.y[r] = (XT)finish_row(a.y, r, s, a.alpha, a.beta, a.plain);
+  }
+}
+
 template <typename XT, typename AT>
 __global__ void scale_kernel(int64_t n, XT* __restrict__ y, AT beta, const int* gate) {
   if (gated(gate)) return;
@@ -1208,6 +1349,26 @@ struct SpmvImpl {
 
   static int csr(const gko_matrix_s* A, const XT* x, XT* y, AT alpha, AT beta, cudaStream_t s, void* scratch,
                  const DotSpec* dot, const int* gate) {
+    if (A->plan.kind == 3) {  // nonzero split (no fused dot)
+      if (A->nnz == 0) {
+        scale_kernel<XT, AT><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((A->n_rows + 255) / 256, 4096)),
+                               256, 0, s>>>(A->n_rows, y, beta, gate);
+        GKO_TRY_CUDA(cudaGetLastError());
+        return GKO_OK;
+      }
+      const int64_t tiles = (A->nnz + kCooTile - 1) / kCooTile;
+      AT* carry = static_cast<AT*>(scratch);
+      const CsrArgs<VT, XT> ca = csr_args(A, x, y, alpha, beta);
+      const int32_t* sr = ptr<int32_t>(A->plan.seg_row);
+      if (ca.plain)
+        csr_seg_kernel<VT, XT, true><<<(unsigned)tiles, kCooThreads, 0, s>>>(ca, A->nnz, sr, carry, gate);
+      else
+        csr_seg_kernel<VT, XT, false><<<(unsigned)tiles, kCooThreads, 0, s>>>(ca, A->nnz, sr, carry, gate);
+      const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tiles + 255) / 256, 4096));
+      csr_seg_fixup_kernel<VT, XT><<<fg, 256, 0, s>>>(ca, tiles, sr, carry, gate);
+      GKO_TRY_CUDA(cudaGetLastError());
+      return GKO_OK;
+    }
     if (A->plan.kind == 2) {  // merge path (no fused dot)
       const int64_t total = A->n_rows + A->nnz;
       const int64_t tiles = (total + kMergeTile - 1) / kMergeTile;

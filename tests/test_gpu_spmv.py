@@ -153,7 +153,7 @@ def test_plan_histogram_and_split(gko):
             assert (p["kernel"], p["subwarp"], p["rows_per_subwarp"], p["stage_cap"], p["n_long_rows"]) == \
                 (1, S, R, 1024, 0)
             continue
-        assert p["kernel"] == 2 and p["n_long_rows"] == 0  # skewed: merge path
+        assert p["kernel"] == 3 and p["n_long_rows"] == 0  # skewed: nonzero split
         M = G.from_csr(A)
         M.set_plan(0, 8, 2)
         p = M.plan()
@@ -165,7 +165,7 @@ def test_plan_histogram_and_split(gko):
 
 PLANS = ([(0, S, R, 2048) for S in (1, 2, 4, 8, 16, 32) for R in (1, 2, 4)]
          + [(1, S, R, cap) for S in (1, 2, 4, 8) for R in (1, 2, 4) for cap in (512, 2048)]
-         + [(1, 1, 4, 8192), (1, 2, 1, 1024), (2, 1, 1, 2048)])
+         + [(1, 1, 4, 8192), (1, 2, 1, 1024), (2, 1, 1, 2048), (3, 1, 1, 1024)])
 
 
 @pytest.mark.parametrize("kernel,S,R,cap", PLANS)
@@ -185,6 +185,45 @@ def test_every_plan_matches_oracle(gko, kernel, S, R, cap, mat):
     yd = dev(y0)
     G.gko_spmv(2.0, M, dev(x), -1.0, yd)
     check_spmv_f64(host(yd), A, x, 2.0, -1.0, y0)
+
+
+def empty_run_cases():
+    rng = np.random.default_rng(31)
+    # tiles spanning thousands of empty rows (row pointers read from global
+    # memory), empty rows before the first and after the last nonzero
+    yield "empty_runs", I.rows_csr([0] * 700 + [3] + [0] * 5000 + [2] * 10 + [0] * 3000 + [1500, 1] + [0] * 2600
+                                   + [7] * 300 + [0] * 9000, 3000, rng)
+    yield "one_row", I.rows_csr([5000], 7000, rng)
+    yield "all_single", I.rows_csr([1] * 5000, 5000, rng)
+
+
+SEG_CASES = CASES + list(empty_run_cases())
+
+
+@pytest.mark.parametrize("name,A", SEG_CASES, ids=[c[0] for c in SEG_CASES])
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+def test_nonzero_split_plan(gko, name, A, dt):
+    """CSR kernel 3 (nonzero split) on every case matrix, both alpha/beta
+    settings, all value types."""
+    G = gko
+    dtype = {"f64": G.F64, "f32": G.F32, "bf16": G.BF16}[dt]
+    M = make(G, A, "csr", dtype)
+    M.set_plan(3, 1, 1, 1024)
+    assert M.plan()["kernel"] == 3
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-1, 1, A.n_cols)
+    y0 = rng.uniform(-1, 1, A.n_rows)
+    for alpha, beta in [(1.0, 0.0), (-0.75, 1.5)]:
+        if dtype == G.F64:
+            yd = dev(y0)
+            G.gko_spmv(alpha, M, dev(x), beta, yd)
+            check_spmv_f64(host(yd), A, x, alpha, beta, y0)
+        else:
+            x32 = x.astype(np.float32)
+            yd = dev(y0, np.float32)
+            G.gko_spmv(alpha, M, dev(x32), beta, yd)
+            check_spmv_f32(host(yd), A, x32.astype(np.float64), alpha, beta, y0.astype(np.float32).astype(np.float64),
+                           values_for(G, A, dtype))
 
 
 @pytest.mark.parametrize("C", [32, 128, 256])
