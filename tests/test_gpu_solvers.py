@@ -88,6 +88,28 @@ def test_solvers_all_formats(gko, fmt, name):
         assert iters_close(res.iterations, ro.iterations) or abs(res.outer_iterations - ro.outer_iterations) <= 1
 
 
+@pytest.mark.parametrize("plan", [(0, 4, 2), (2, 1, 1), (3, 1, 1)], ids=["subwarp", "merge", "nzsplit"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
+def test_solvers_every_csr_plan(gko, plan, precision, name):
+    """The solvers on CSR plans whose SpMV does not fuse the dot product
+    (subwarp, merge path, nonzero split); mixed precision runs the plan on the
+    solver's cached FP32 copy."""
+    G = gko
+    A, b = spd_problem() if name == "cg" else nonsym_problem()
+    M = G.from_csr(A)
+    M.set_plan(*plan, 1024)
+    assert M.plan()["kernel"] == plan[0]
+    opt = {} if precision == "f64" else {"precision": G.PRECISION_MIXED_F32}
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=4000, **opt)
+    xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=4000)
+    assert res.status == G.OK and ro.status == 0, (res, ro)
+    assert true_rel_res(A, xg, b) <= 1.01e-12
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    if precision == "f64" and name != "gmres":
+        assert iters_close(res.iterations, ro.iterations), (res.iterations, ro.iterations)
+
+
 @pytest.mark.parametrize("restart", [5, 30])
 def test_gmres_restart_lengths(gko, restart):
     G = gko
