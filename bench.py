@@ -188,7 +188,8 @@ def solver_suite(G, dev, stream):
         fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
         if solver == "bicgstab":
             maxit = 2000
-        opts = G.opts(precision=prec, restart=restart, inner_maxit=2000, max_outer=12, preconditioner=pc)
+        # the library's refinement defaults (GMRES: one restart cycle per step)
+        opts = G.opts(precision=prec, restart=restart, preconditioner=pc)
         if tag == "bicgstab_convdiff128_mixed_f32":  # known not to converge: keep it short
             opts = G.opts(precision=prec, inner_maxit=500, max_outer=3)
         xd = torch.zeros(n, dtype=torch.float64, device=dev)

@@ -296,8 +296,10 @@ typedef struct {
   int32_t restart;      /* GMRES restart length m (<= 0: 30; at most 128)        */
   int32_t precision;    /* GKO_PRECISION_*                                       */
   double inner_tol;     /* mixed: inner relative tolerance (<= 0: 1e-5)          */
-  int32_t max_outer;    /* mixed: refinement steps (<= 0: 30)                    */
-  int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters) */
+  int32_t max_outer;    /* mixed: refinement steps (<= 0: 30; GMRES: the larger of
+                           30 and ceil(max_iters / (4 restart)))                */
+  int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters;
+                           GMRES: 4 restart cycles per step)                    */
   int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */
   int32_t preconditioner; /* GKO_PRECOND_NONE or GKO_PRECOND_JACOBI (CG, BiCGSTAB) */
 } gko_solve_opts;

@@ -136,7 +136,11 @@ def test_mixed_precision_refinement(gko, precision, name):
     xo, _ = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=4000)
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
     if precision == "f32":
-        xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, inner_maxit=2000)
+        # the library's default inner limits: GMRES 4 restart cycles per
+        # refinement step (outer steps up to max(30, ceil(maxit / 120))), the
+        # others the whole iteration budget
+        inner = dict(inner_maxit=120, max_outer=30) if name == "gmres" else dict(inner_maxit=2000)
+        xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, **inner)
         assert ri.status == 0 and abs(res.outer_iterations - ri.outer_iterations) <= 2, (res, ri)
 
 
