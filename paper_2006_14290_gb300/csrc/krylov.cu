@@ -1136,6 +1136,15 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       if (!(first && x_zero)) GKO_TRY(spmv(x, w, nullptr, &c->done));
       gm_start_kernel<T><<<rg, 256, 0, s>>>(n, b, (first && x_zero) ? nullptr : w, V, c, ws, GmStartOp{c, g, m});
       first = false;
+      if (hc->iter >= sp.maxit) {
+        // iteration cap reached: this start only decides the final status
+        // (converged or not) and always ends the solve, so the cycle's
+        // Arnoldi steps are not launched (gated, they still cost about 270
+        // launches: 2.5 ms per call at n = 2.1M)
+        GKO_TRY_CUDA(cudaGetLastError());
+        GKO_TRY(read_ctl(c, hc, s));
+        continue;
+      }
       gm_scale_kernel<T><<<vg, 256, 0, s>>>(n, V, &c->beta, c);
       for (int j = 0; j < m; ++j) {
         T* vj = V + (int64_t)j * ld;
@@ -1294,10 +1303,9 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   // GMRES: at most 4 restart cycles per refinement step by default.  An
   // inner FP32 GMRES left to restart on its own FP32 residual until the
   // inner tolerance needed a third more iterations on 128^3 convection-
-  // diffusion (863 vs 645 in FP64); with 1, 2 or 4 cycles per step it took
-  // 653, and each step costs about 2.6 ms besides its iterations (281 / 252 /
-  // 239 ms against 273 ms in FP64), hence 4.  Up to max_iters inner
-  // iterations in all.
+  // diffusion (863 vs 645 in FP64); with 1, 2 or 4 cycles per step it takes
+  // 653 (227 ms against 273 ms in FP64 whichever), and 4 needs the fewest
+  // FP64 residuals.  Up to max_iters inner iterations in all.
   const bool gmres = solver == 2;
   const int gmres_inner = 4 * sp.restart;
   in.maxit = o.inner_maxit > 0 ? o.inner_maxit : (gmres ? gmres_inner : max_iters);
