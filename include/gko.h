@@ -199,9 +199,9 @@ GKO_API int gko_matrix_set_plan(gko_matrix m, int32_t kernel, int32_t subwarp, i
  * subwarp 1,2,4 x stage_cap 512,1024,2048), the merge path, the nonzero split
  * and the subwarp kernel with subwarp 4..32; for a COO handle the row-block plans and the
  * segmented reduction.  keep_kernel != 0 keeps the handle's kernel and tunes
- * only its parameters (row-block plans; nothing to tune for the merge path
- * and the segmented reduction), so the kernel choice stays the histogram
- * rule's whatever the timing conditions.  Each candidate runs y = A x once
+ * only its parameters (row-block plans; nothing to tune for the nonzero
+ * split, the merge path and the segmented reduction), so the kernel choice
+ * stays the histogram rule's whatever the timing conditions.  Each candidate runs y = A x once
  * untimed, then `reps` times (1..100) with L2 flushed (256 MB write) before
  * each, best time kept; the three fastest are timed again the same way with
  * 3*reps runs, and the fastest of those is set on the handle (as
