@@ -96,8 +96,7 @@ extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t rep
   std::vector<Cand> cands;
   const Cand start{m->plan.kind, m->plan.S, m->plan.R, m->plan.cap};
   // keep_kernel: only the parameters of the handle's current kernel (the
-  // row-block plans; the nonzero split, the merge path and the segmented
-  // reduction have none)
+  // row-block plans; merge path and segmented reduction have none)
   if (!keep_kernel || start.k == 1)
     for (int32_t ss : {1, 2, 4, 8})
       for (int32_t rr : {1, 2, 4})
