@@ -150,8 +150,8 @@ extern "C" int gko_matrix_tune(gko_matrix m, const void* x, void* y, int32_t rep
     }
     return GKO_OK;
   };
-  // Round 1: every candidate, `reps` runs.  Round 2: the three fastest again
-  // with 3*reps runs, so a single lucky run cannot pick the plan.
+  // First pass: every candidate, `reps` runs.  Second pass: the three fastest
+  // again with 3*reps runs, so a single lucky run cannot pick the plan.
   std::vector<std::pair<float, size_t>> t1;
   for (size_t i = 0; i < cands.size(); ++i) {
     float t = 1e30f;
