@@ -54,12 +54,15 @@ __device__ __forceinline__ double ldv(const double* v, int64_t k) { return v[k];
 __device__ __forceinline__ double ldv(const float* v, int64_t k) { return widen(v[k]); }
 
 // sum over the block, result in every thread: warps reduce by shuffles, warp
-// 0 adds the eight warp sums (not every thread) and shares the total
+// 0 adds the eight warp sums (not every thread) and shares the total.  Two
+// barriers: a call's warp sums are written after every thread has passed the
+// previous call's last barrier (so warp 0 has read the old ones), and the new
+// total is written after this call's first barrier (so every thread has read
+// the old total).
 __device__ __forceinline__ double block_allsum(double v, double* red) {
   constexpr int NW = kBatchThreads / kWarp;
   v = subwarp_sum<32>(v, 0xffffffffu);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
