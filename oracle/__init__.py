@@ -78,6 +78,7 @@ _SIGS = {
     "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
                               C.POINTER(_Result)]),
     "or_jacobi_inv": (None, [_I64, _P, _P, _P, _P]),
+    "or_batch_cg": (None, [_I32, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _P, _P, _P]),
     "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
     "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32,
                                  C.POINTER(_Result)]),
@@ -396,3 +397,25 @@ def solve_jacobi(solver: int, A, b, x0=None, tol=1e-10, maxit=1000):
     lib().or_solve_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(minv), _p(b), _p(x), tol, maxit,
                       C.byref(res))
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
+
+
+def batch_cg(systems, bs, x0=None, tol=1e-10, maxit=10000):
+    """The single-system CG on every system of a batch (OpenMP over systems).
+    systems: list of host CSR objects; bs: right-hand sides.  Returns
+    (x per system, iterations, true relative residuals, statuses)."""
+    count = len(systems)
+    rows = np.array([S.n_rows for S in systems], np.int64)
+    nnzs = np.array([int(S.row_ptr[-1]) for S in systems], np.int64)
+    row_off = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
+    nnz_off = np.concatenate([[0], np.cumsum(nnzs)]).astype(np.int64)
+    rp = np.concatenate([_i32(S.row_ptr) for S in systems])
+    col = np.concatenate([_i32(S.col) for S in systems])
+    val = np.concatenate([_f64(S.val) for S in systems])
+    b = np.concatenate([_f64(v) for v in bs])
+    x = np.zeros(b.size) if x0 is None else np.concatenate([_f64(v) for v in x0])
+    it = np.zeros(count, np.int32)
+    rr = np.zeros(count, np.float64)
+    st = np.zeros(count, np.int32)
+    lib().or_batch_cg(count, _p(row_off), _p(nnz_off), _p(rp), _p(col), _p(val), _p(b), _p(x), tol, maxit,
+                      _p(it), _p(rr), _p(st))
+    return [x[row_off[i]:row_off[i + 1]] for i in range(count)], it, rr, st

@@ -364,11 +364,9 @@ static void op_apply(const or_op *A, const double *x, double *y) {
     free(xs);
     free(ys);
   } else {
-    for (int64_t i = 0; i < A->n; ++i) {
-      double s = 0.0;
-      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) s += A->val[k] * x[A->col[k]];
-      y[i] = s;
-    }
+    /* the plain CSR SpMV above (rows over the OpenMP threads, each row summed
+     * in storage order; alpha = 1 gives y = s exactly) */
+    or_spmv_csr(A->n, A->rp, A->col, A->val, x, 1.0, 0.0, y);
   }
 }
 
@@ -772,6 +770,29 @@ int or_solve_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col, co
   or_ctx c = {&A, 0, 1, NULL, 0, minv};
   *out = run_solver(&c, solver, b, x, tol, maxit, 0);
   return out->status;
+}
+
+/* Batched CG (the single-system CG above applied to each system on its own):
+ * system i has rows [row_off[i], row_off[i+1]) of b and x, local row
+ * pointers starting at rp[row_off[i] + i] and entries [nnz_off[i],
+ * nnz_off[i+1]) of col/val.  Systems are spread over the OpenMP threads;
+ * each system's solve is sequential, so results do not depend on the
+ * thread count.  iters, relres, status: per system. */
+void or_batch_cg(int32_t count, const int64_t *row_off, const int64_t *nnz_off, const int32_t *rp,
+                 const int32_t *col, const double *val, const double *b, double *x, double tol, int32_t maxit,
+                 int32_t *iters, double *relres, int32_t *status) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+#endif
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t r0 = row_off[i], k0 = nnz_off[i];
+    or_op A = {row_off[i + 1] - r0, rp + r0 + i, col + k0, val + k0, NULL};
+    or_ctx c = {&A, 0, 1, NULL, 0, NULL};
+    const or_result res = cg_core(&c, b + r0, x + r0, tol, maxit);
+    iters[i] = res.iterations;
+    relres[i] = res.rel_residual;
+    status[i] = res.status;
+  }
 }
 
 /* Mixed-precision iterative refinement: x = x0; repeat { r = b - A64 x in

@@ -565,3 +565,35 @@ def test_jacobi_gmres_refused():
     A = I.laplace2d_5pt(4)
     x, r = O.solve_jacobi(O.GMRES, A, np.ones(16))
     assert r.status == 1
+
+
+def test_batch_cg_is_the_single_system_cg_per_system():
+    """The batched oracle (c8: CG applied to each system on its own) equals
+    the single-system CG bit for bit, whatever the thread count, and its
+    solutions agree with dense solves."""
+    sides = [5, 8, 3, 11, 6]
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, sd)
+        systems.append(A)
+        bs.append(b)
+    bs[2] = np.zeros_like(bs[2])
+    outs = []
+    for threads in (1, 4):
+        O.set_threads(threads)
+        outs.append(O.batch_cg(systems, bs, tol=1e-12, maxit=5000))
+    O.set_threads(1)
+    (x1, it1, rr1, st1), (x4, it4, rr4, st4) = outs
+    for i, (A, b) in enumerate(zip(systems, bs)):
+        xs, rs = O.cg(A, b, tol=1e-12, maxit=5000)
+        assert x1[i].tobytes() == xs.tobytes() == x4[i].tobytes()
+        assert it1[i] == rs.iterations == it4[i] and st1[i] == rs.status == 0
+        assert rr1[i] == rs.rel_residual
+        if i != 2:
+            D = np.zeros((A.n_rows, A.n_rows))
+            for r in range(A.n_rows):
+                D[r, A.col[A.row_ptr[r]:A.row_ptr[r + 1]]] += A.val[A.row_ptr[r]:A.row_ptr[r + 1]]
+            xd = np.linalg.solve(D, b)
+            assert np.linalg.norm(xs - xd) <= 1e-9 * np.linalg.norm(xd)
+        else:
+            assert np.all(x1[i] == 0) and it1[i] == 0
