@@ -24,6 +24,8 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   int64_t id = 0;
   int32_t matrix = 0;
+  gko_matrix A = nullptr;  // the resident matrix and its size, copied at submission under the lock
+  int64_t n = 0;
   int32_t solver = 0;
   double tol = 1e-8;
   int32_t maxit = 1000;
@@ -103,8 +105,7 @@ void worker_loop(gko_server S) {
       S->peak_active = std::max(S->peak_active, S->active);
     }
     r->t_start = Clock::now();
-    const Resident& M = S->matrices[r->matrix];
-    const int64_t n = M.n;
+    const int64_t n = r->n;
     int code = GKO_OK;
     gko::Scratch dev;
     if ((size_t)n > pin_n) {
@@ -118,12 +119,14 @@ void worker_loop(gko_server S) {
       double* db = dev.as<double>();
       double* dx = dev.as<double>(((sizeof(double) * (size_t)n + 255) / 256) * 256);
       std::copy(r->b.begin(), r->b.end(), pin);
-      cudaMemcpyAsync(db, pin, sizeof(double) * n, cudaMemcpyHostToDevice, s);
-      cudaMemsetAsync(dx, 0, sizeof(double) * n, s);
       const gko_solve_opts* o = r->has_opts ? &r->opts : nullptr;
-      if (r->solver == 0) code = gko_solve_cg(M.A, db, dx, r->tol, r->maxit, o, &r->res, s);
-      else if (r->solver == 1) code = gko_solve_bicgstab(M.A, db, dx, r->tol, r->maxit, o, &r->res, s);
-      else code = gko_solve_gmres(M.A, db, dx, r->tol, r->maxit, o, &r->res, s);
+      if (cudaMemcpyAsync(db, pin, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaMemsetAsync(dx, 0, sizeof(double) * n, s) != cudaSuccess) {
+        cudaGetLastError();
+        code = GKO_CUDA_ERROR;
+      } else if (r->solver == 0) code = gko_solve_cg(r->A, db, dx, r->tol, r->maxit, o, &r->res, s);
+      else if (r->solver == 1) code = gko_solve_bicgstab(r->A, db, dx, r->tol, r->maxit, o, &r->res, s);
+      else code = gko_solve_gmres(r->A, db, dx, r->tol, r->maxit, o, &r->res, s);
       if (code == GKO_OK || code == GKO_NOT_CONVERGED || code == GKO_BREAKDOWN) {
         if (cudaMemcpyAsync(pin, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
@@ -189,13 +192,17 @@ int gko_server_submit(gko_server S, int32_t matrix_id, int32_t solver, const dou
   if (!S || !b || !request_id) return fail(GKO_INVALID_ARG, "null argument");
   auto r = std::make_shared<Request>();
   r->t_submit = Clock::now();
+  if (solver < 0 || solver > 2 || !(rel_tol >= 0.0) || max_iters < 0) return fail(GKO_INVALID_ARG, "bad request");
   {
+    // the request keeps its own copy of the handle and size: add_matrix may
+    // grow the matrix table while solves run
     std::lock_guard<std::mutex> lk(S->mu);
     if (matrix_id < 0 || matrix_id >= (int32_t)S->matrices.size())
       return fail(GKO_INVALID_ARG, "unknown matrix id");
+    r->A = S->matrices[matrix_id].A;
+    r->n = S->matrices[matrix_id].n;
   }
-  if (solver < 0 || solver > 2 || !(rel_tol >= 0.0) || max_iters < 0) return fail(GKO_INVALID_ARG, "bad request");
-  const int64_t n = S->matrices[matrix_id].n;
+  const int64_t n = r->n;
   r->matrix = matrix_id;
   r->solver = solver;
   r->tol = rel_tol;

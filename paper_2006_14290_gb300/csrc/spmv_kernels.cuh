@@ -1289,22 +1289,42 @@ struct SpmvImpl {
     auto kern = COO ? coo_rowblock_kernel<S, R, VT, XT, DOT> : csr_rowblock_kernel<S, R, VT, XT, DOT>;
     const int cap = A->plan.cap;
     const size_t smem = rb_smem_bytes<VT>(cap, COO);
-    static int per_sm_cache[8] = {};                    // by log2(cap / 512)
-    static size_t smem_allowed = 48 * 1024;             // this kernel's dynamic shared memory limit
+    // Per device: this kernel's dynamic shared memory limit and its resident
+    // blocks per SM by stage size (slot = log2(cap / 512)).  Solves on
+    // several host threads (the serving workers) launch concurrently, so the
+    // attribute update and the caches change together under one lock.
+    struct LaunchCache {
+      std::mutex mu;
+      size_t smem_allowed[64];
+      int per_sm[64][8];
+    };
+    static LaunchCache lc{};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+      cudaGetLastError();
+      fail(GKO_CUDA_ERROR, "row-block kernel: no current device");
+      return kLaunchCudaError;
+    }
     int slot = 0;
     while ((512 << slot) < cap && slot < 7) ++slot;
-    if (smem > smem_allowed) {
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        fail(GKO_CUDA_ERROR, "row-block kernel: shared memory request refused");
-        return kLaunchCudaError;
+    int per_sm = 0;
+    {
+      std::lock_guard<std::mutex> lk(lc.mu);
+      if (lc.smem_allowed[dev] < 48 * 1024) lc.smem_allowed[dev] = 48 * 1024;
+      if (smem > lc.smem_allowed[dev]) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+          cudaGetLastError();
+          fail(GKO_CUDA_ERROR, "row-block kernel: shared memory request refused");
+          return kLaunchCudaError;
+        }
+        lc.smem_allowed[dev] = smem;
       }
-      smem_allowed = smem;
+      if (!lc.per_sm[dev][slot]) lc.per_sm[dev][slot] = resident_blocks(kern, kRbThreads, smem);
+      per_sm = lc.per_sm[dev][slot];
     }
-    if (!per_sm_cache[slot]) per_sm_cache[slot] = resident_blocks(kern, kRbThreads, smem);
     constexpr int RB = (kRbThreads / S) * R;
     int64_t g = (A->n_rows + RB - 1) / RB;
-    int64_t cap_g = (int64_t)per_sm_cache[slot] * sm_count();
+    int64_t cap_g = (int64_t)per_sm * sm_count();
     if (DOT && cap_g > kDotSlots - extra) cap_g = kDotSlots - extra;
     if (g > cap_g) g = cap_g;
     if (g < 1) g = 1;
