@@ -243,15 +243,21 @@ GKO_API int gko_spmv_host(const double *alpha, gko_matrix A, const void *x_host,
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory at the time they multiply (their memory is owned by
  * another allocator, or an allocation's possible implicit synchronisation is
- * not acceptable in their loop).  Same kernels and results as gko_spmv on the
- * handle, but the per-tile carries live in a fixed 2 MiB device array inside
- * the library (held on every GPU that loads the library until exit) instead
- * of pool scratch.  At most 134,217,728 COO entries; larger handles are
- * rejected with GKO_INVALID_ARG.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current).
- * Every call shares the one array: calls that overlap on the GPU (other
- * streams, or other threads) race and give wrong results; serialise them.
- * Asynchronous on `stream`. */
+ * not acceptable in their loop).  It always runs the tiled segmented-reduction
+ * kernels, whatever plan the handle carries, so its y equals gko_spmv's
+ * within the SpMV tolerance (bit-identical under the default plan; a handle
+ * set to the row-block COO plan sums in another order).  The per-tile
+ * carries live in a fixed 2 MiB device array inside the library instead of
+ * pool scratch.  At most 134,217,728 COO entries; larger handles are
+ * rejected with GKO_INVALID_ARG.  CUDA loads this entry point's device code,
+ * and with it the array, lazily: the first call on a device (which also
+ * looks up the array's device address with cudaGetSymbolAddress, that
+ * device current) allocates that module's memory once and may synchronise,
+ * so make the first call on each device during set-up, before any stream
+ * capture; from then on the array stays on that device until the process
+ * exits and calls touch no allocator.  Every call shares the one array:
+ * calls that overlap on the GPU (other streams, or other threads) race and
+ * give wrong results; serialise them.  Asynchronous on `stream`. */
 GKO_API int gko_spmv_coo_noalloc(const double *alpha, gko_matrix A, const double *x, const double *beta,
                                  double *y, void *stream);
 
@@ -356,13 +362,31 @@ GKO_API int gko_solve_gmres(gko_matrix A, const double *b, double *x, double rel
  * [nnz_off[i], nnz_off[i+1]); its local row pointers (n_i + 1 entries, from
  * 0 to nnz_i) start at row_ptr[row_off[i] + i]; col holds local column
  * indices (0 <= col < n_i).  All arrays are HOST arrays, copied and checked
- * at creation (bad input -> GKO_INVALID_ARG); values are F64, or F32 for
- * FP32 storage (the F32 batch solves the FP32-rounded systems; arithmetic and
- * vectors stay FP64).  Systems may have up to 8192 rows. */
+ * at creation (bad input -> GKO_INVALID_ARG); values are always FP64.
+ * `storage` GKO_F64 keeps them; GKO_F32 rounds them to nearest FP32 on the
+ * device (the same rounding as gko_matrix_convert_values), and the batch
+ * then solves the FP32-rounded systems with FP64 arithmetic and vectors.
+ * Systems may have up to 8192 rows.  Synchronises `stream`. */
 typedef struct gko_batch_s *gko_batch;
 GKO_API int gko_batch_create(int32_t count, const int64_t *row_off, const int64_t *nnz_off,
-                             const int32_t *row_ptr, const int32_t *col, const void *values,
+                             const int32_t *row_ptr, const int32_t *col, const double *values,
                              gko_dtype storage, void *stream, gko_batch *out);
+
+/* The same from one CSR per system: system i has n_rows[i] rows, HOST arrays
+ * row_ptrs[i] (n_rows[i] + 1 entries from 0), cols[i] and values[i] (FP64,
+ * row_ptrs[i][n_rows[i]] entries each).  The library concatenates them and
+ * builds the offsets; checks, storage and rounding as gko_batch_create. */
+GKO_API int gko_batch_create_systems(int32_t count, const int32_t *n_rows, const int32_t *const *row_ptrs,
+                                     const int32_t *const *cols, const double *const *values, gko_dtype storage,
+                                     void *stream, gko_batch *out);
+
+/* Copy the stored batch to HOST arrays in gko_batch_create's layout (any
+ * pointer may be NULL to skip that array): row_off and nnz_off (count + 1),
+ * row_ptr (total_rows + count), col (total_nnz) and values (total_nnz
+ * elements of the storage type: double for F64, float for F32).
+ * Synchronises `stream`. */
+GKO_API int gko_batch_export(gko_batch B, int64_t *row_off, int64_t *nnz_off, int32_t *row_ptr, int32_t *col,
+                             void *values, void *stream);
 
 /* Solve every system: b, x are DEVICE FP64 vectors laid out like the rows
  * (x: x0 in, solution out).  Per system: stop when ||r_k|| <= rel_tol ||b_i||

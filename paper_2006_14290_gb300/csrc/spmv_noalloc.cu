@@ -19,8 +19,9 @@ namespace gko {
 constexpr int64_t kNoAllocMaxNnz = (int64_t)1 << 27;  // 134,217,728 entries
 constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxNnz / kCooTile;
 
-// Two FP64 carries per tile (2 MiB).  Every GPU that loads the library holds
-// this array until the process exits.
+// Two FP64 carries per tile (2 MiB).  CUDA loads this file's device code,
+// and the array with it, lazily: on a device's first call (or first symbol
+// lookup); from then on that device holds the array until the process exits.
 static __device__ __align__(256) double g_noalloc_carry[2 * kNoAllocMaxTiles];
 
 static std::mutex g_noalloc_mu;

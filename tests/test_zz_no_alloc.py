@@ -21,17 +21,22 @@ def _coo(G, A):
     return G.gko_matrix_convert_to_coo(G.from_csr(A))
 
 
-@pytest.mark.parametrize("name", ["powerlaw", "stencil", "empty_rows"])
+@pytest.mark.parametrize("name", ["powerlaw", "stencil", "empty_rows", "stencil_rowblock_plan"])
 def test_noalloc_matches_spmv_twice(gko, name):
     G = gko
     rng = np.random.default_rng(3)
     if name == "powerlaw":
         A = I.powerlaw(60000, seed=2)  # long rows spanning several tiles
-    elif name == "stencil":
+    elif name.startswith("stencil"):
         A = I.stencil3d_27pt(24)
     else:
         A = I.random_csr(5000, 4000, 0.003, rng, empty_rows=0.4, sort_cols=False)
     M = _coo(G, A)
+    if name == "stencil_rowblock_plan":
+        # gko_spmv then runs the row-block COO kernel (another summation
+        # order); the allocation-free call keeps the segmented reduction
+        M.set_plan(1, 4, 1, 1024)
+        assert M.plan()["kernel"] == 1
     for call, (alpha, beta) in enumerate([(1.0, 0.0), (-0.5, 2.0)]):
         x = rng.uniform(-1, 1, A.n_cols)
         y0 = rng.uniform(-1, 1, A.n_rows)
