@@ -222,6 +222,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_cg_kernel(BatchArgs a, in
   }
 }
 
+// FP64 -> FP32 rounding (to nearest even) of the systems' values for FP32
+// storage; the same rounding as gko_matrix_convert_values.
+__global__ void round_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
 }  // namespace gko
 
 using namespace gko;
@@ -364,7 +371,7 @@ static int batch_run(gko_batch B, const double* b, double* x, double tol, int ma
 extern "C" {
 
 int gko_batch_create(int32_t count, const int64_t* row_off, const int64_t* nnz_off, const int32_t* row_ptr,
-                     const int32_t* col, const void* values, gko_dtype storage, void* stream, gko_batch* out) {
+                     const int32_t* col, const double* values, gko_dtype storage, void* stream, gko_batch* out) {
   if (!out) return fail(GKO_INVALID_ARG, "null out");
   *out = nullptr;
   if (count <= 0 || !row_off || !nnz_off || !row_ptr || !col || !values)
@@ -412,10 +419,72 @@ int gko_batch_create(int32_t count, const int64_t* row_off, const int64_t* nnz_o
   GKO_TRY_CUDA(cudaMemcpyAsync(B->nnz_off->ptr, nnz_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
   GKO_TRY_CUDA(cudaMemcpyAsync(B->rp->ptr, row_ptr, sizeof(int32_t) * nrp, cudaMemcpyHostToDevice, s));
   GKO_TRY_CUDA(cudaMemcpyAsync(B->col->ptr, col, sizeof(int32_t) * B->total_nnz, cudaMemcpyHostToDevice, s));
-  GKO_TRY_CUDA(cudaMemcpyAsync(B->val->ptr, values, vs * B->total_nnz, cudaMemcpyHostToDevice, s));
+  if (storage == GKO_F64) {
+    GKO_TRY_CUDA(cudaMemcpyAsync(B->val->ptr, values, sizeof(double) * B->total_nnz, cudaMemcpyHostToDevice, s));
+  } else if (B->total_nnz > 0) {
+    // FP32 storage: the FP64 values are rounded to nearest on the device
+    Scratch v64;
+    GKO_TRY(v64.get(sizeof(double) * B->total_nnz, s));
+    GKO_TRY_CUDA(cudaMemcpyAsync(v64.data(), values, sizeof(double) * B->total_nnz, cudaMemcpyHostToDevice, s));
+    round_f32_kernel<<<(unsigned)std::min<int64_t>((B->total_nnz + 255) / 256, (int64_t)sm_count() * 16), 256, 0,
+                       s>>>(B->total_nnz, v64.as<double>(), ptr<float>(B->val));
+    GKO_TRY_CUDA(cudaGetLastError());
+    GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  }
   GKO_TRY_CUDA(cudaMemcpyAsync(B->order->ptr, B->h_order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
   GKO_TRY(build_items(B.get(), 144, s));
   *out = B.release();
+  return GKO_OK;
+}
+
+int gko_batch_create_systems(int32_t count, const int32_t* n_rows, const int32_t* const* row_ptrs,
+                             const int32_t* const* cols, const double* const* values, gko_dtype storage, void* stream,
+                             gko_batch* out) {
+  if (!out) return fail(GKO_INVALID_ARG, "null out");
+  *out = nullptr;
+  if (count <= 0 || !n_rows || !row_ptrs || !cols || !values) return fail(GKO_INVALID_ARG, "bad batch arguments");
+  // offsets from the systems' sizes, then the concatenated arrays (checked
+  // in full by gko_batch_create)
+  std::vector<int64_t> row_off((size_t)count + 1, 0), nnz_off((size_t)count + 1, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    if (n_rows[i] <= 0 || !row_ptrs[i]) return fail(GKO_INVALID_ARG, "every system needs rows and row pointers");
+    const int64_t z = row_ptrs[i][n_rows[i]];
+    if (z < 0 || (z > 0 && (!cols[i] || !values[i]))) return fail(GKO_INVALID_ARG, "bad system arrays");
+    row_off[i + 1] = row_off[i] + n_rows[i];
+    nnz_off[i + 1] = nnz_off[i] + z;
+    if (nnz_off[i + 1] >= INT32_MAX) return fail(GKO_INVALID_ARG, "the batch's nonzeros must fit int32");
+  }
+  std::vector<int32_t> rp((size_t)(row_off[count] + count)), col((size_t)nnz_off[count]);
+  std::vector<double> val((size_t)nnz_off[count]);
+  for (int32_t i = 0; i < count; ++i) {
+    std::copy(row_ptrs[i], row_ptrs[i] + n_rows[i] + 1, rp.begin() + (row_off[i] + i));
+    const int64_t z = nnz_off[i + 1] - nnz_off[i];
+    if (z > 0) {
+      std::copy(cols[i], cols[i] + z, col.begin() + nnz_off[i]);
+      std::copy(values[i], values[i] + z, val.begin() + nnz_off[i]);
+    }
+  }
+  const int st = gko_batch_create(count, row_off.data(), nnz_off.data(), rp.data(), col.data(), val.data(), storage,
+                                  stream, out);
+  // the pageable sources above must outlive the copies gko_batch_create enqueued
+  if (st == GKO_OK) GKO_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return st;
+}
+
+int gko_batch_export(gko_batch B, int64_t* row_off, int64_t* nnz_off, int32_t* row_ptr, int32_t* col, void* values,
+                     void* stream) {
+  if (!B) return fail(GKO_INVALID_ARG, "null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto get = [&](void* dst, const Buf& b, size_t bytes) -> int {
+    if (dst && b && bytes) GKO_TRY_CUDA(cudaMemcpyAsync(dst, b->ptr, bytes, cudaMemcpyDeviceToHost, s));
+    return GKO_OK;
+  };
+  GKO_TRY(get(row_off, B->row_off, sizeof(int64_t) * (B->count + 1)));
+  GKO_TRY(get(nnz_off, B->nnz_off, sizeof(int64_t) * (B->count + 1)));
+  GKO_TRY(get(row_ptr, B->rp, sizeof(int32_t) * (B->total_rows + B->count)));
+  GKO_TRY(get(col, B->col, sizeof(int32_t) * B->total_nnz));
+  GKO_TRY(get(values, B->val, dtype_size(B->dtype) * B->total_nnz));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
   return GKO_OK;
 }
 

@@ -93,6 +93,8 @@ SIGNATURES = {
 }
 SIGNATURES.update({
     "gko_batch_create": (C.c_int, [_I32, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)]),
+    "gko_batch_create_systems": (C.c_int, [_I32, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)]),
+    "gko_batch_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "gko_batch_cg": (C.c_int, [_P, _P, _P, _D, _I32, _P, _P, _P, _P]),
     "gko_batch_tune": (C.c_int, [_P, _P, _P, _D, _I32, _PI32, C.POINTER(C.c_float), _P]),
     "gko_batch_set_threshold": (C.c_int, [_P, _I32, _P]),
@@ -442,24 +444,45 @@ class Batch:
     """Owning wrapper of a gko_batch handle (batched CG)."""
 
     def __init__(self, systems, storage=F64, stream=None):
-        """systems: list of objects with n_rows, row_ptr, col, val (host CSR)."""
+        """systems: list of objects with n_rows, row_ptr, col, val (host CSR,
+        FP64 values); the library concatenates them and, for F32 storage,
+        rounds the values on the device."""
         count = len(systems)
-        rows = np.array([S.n_rows for S in systems], np.int64)
-        nnzs = np.array([int(S.row_ptr[-1]) for S in systems], np.int64)
-        self.row_off = np.zeros(count + 1, np.int64)
-        np.cumsum(rows, out=self.row_off[1:])
-        self.nnz_off = np.zeros(count + 1, np.int64)
-        np.cumsum(nnzs, out=self.nnz_off[1:])
-        rp = np.concatenate([np.asarray(S.row_ptr, np.int32) for S in systems])
-        col = np.concatenate([np.asarray(S.col, np.int32) for S in systems])
-        vdt = np.float64 if storage == F64 else np.float32
-        val = np.concatenate([np.asarray(S.val, np.float64) for S in systems]).astype(vdt)
+        keep = [(np.ascontiguousarray(S.row_ptr, np.int32), np.ascontiguousarray(S.col, np.int32),
+                 np.ascontiguousarray(S.val, np.float64)) for S in systems]
+        n_rows = np.array([S.n_rows for S in systems], np.int32)
+        rps = (C.c_void_p * count)(*[a[0].ctypes.data for a in keep])
+        cols = (C.c_void_p * count)(*[a[1].ctypes.data for a in keep])
+        vals = (C.c_void_p * count)(*[a[2].ctypes.data for a in keep])
         h = C.c_void_p()
-        _check(lib().gko_batch_create(count, _hptr(self.row_off), _hptr(self.nnz_off), _hptr(rp), _hptr(col),
-                                      _hptr(val), storage, _stream(stream), C.byref(h)), "gko_batch_create")
+        _check(lib().gko_batch_create_systems(count, _hptr(n_rows), rps, cols, vals, storage, _stream(stream),
+                                              C.byref(h)), "gko_batch_create_systems")
         self.handle = h
         self.count = count
-        self.total_rows = int(self.row_off[-1])
+        self.storage = storage
+        inf = self.info()
+        self.total_rows = inf["total_rows"]
+        self.total_nnz = inf["total_nnz"]
+        self.row_off, self.nnz_off = self.offsets(stream)
+
+    def offsets(self, stream=None):
+        """The library's row and nonzero offsets of the systems (host arrays)."""
+        ro = np.empty(self.count + 1, np.int64)
+        no = np.empty(self.count + 1, np.int64)
+        _check(lib().gko_batch_export(self.handle, _hptr(ro), _hptr(no), None, None, None, _stream(stream)),
+               "gko_batch_export")
+        return ro, no
+
+    def export(self, stream=None):
+        """The stored arrays (row_off, nnz_off, row_ptr, col, values) on the host."""
+        ro = np.empty(self.count + 1, np.int64)
+        no = np.empty(self.count + 1, np.int64)
+        rp = np.empty(self.total_rows + self.count, np.int32)
+        col = np.empty(self.total_nnz, np.int32)
+        val = np.empty(self.total_nnz, np.float64 if self.storage == F64 else np.float32)
+        _check(lib().gko_batch_export(self.handle, _hptr(ro), _hptr(no), _hptr(rp), _hptr(col), _hptr(val),
+                                      _stream(stream)), "gko_batch_export")
+        return ro, no, rp, col, val
 
     def __del__(self):
         try:

@@ -85,6 +85,27 @@ def test_batch_fp32_storage_and_caps(gko):
     assert code == G.NOT_CONVERGED and np.all(it == 3) and np.all(st == G.NOT_CONVERGED)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_batch_stores_the_systems_it_was_given(gko, storage):
+    """gko_batch_create_systems packs per-system CSR arrays itself: the
+    exported offsets, row pointers and columns equal the concatenation, and
+    the values equal the FP64 input (F64) or its round-to-nearest FP32
+    rounding (F32 storage, rounded on the device) byte for byte."""
+    G = gko
+    systems, _ = batch_problem(50, seed=6)
+    B = G.Batch(systems, storage=G.F64 if storage == "f64" else G.F32)
+    ro, no, rp, col, val = B.export()
+    rows = [S.n_rows for S in systems]
+    nnzs = [int(S.row_ptr[-1]) for S in systems]
+    assert ro.tolist() == [sum(rows[:i]) for i in range(len(rows) + 1)]
+    assert no.tolist() == [sum(nnzs[:i]) for i in range(len(nnzs) + 1)]
+    assert rp.tobytes() == np.concatenate([np.asarray(S.row_ptr, np.int32) for S in systems]).tobytes()
+    assert col.tobytes() == np.concatenate([np.asarray(S.col, np.int32) for S in systems]).tobytes()
+    v64 = np.concatenate([np.asarray(S.val, np.float64) for S in systems])
+    want = v64 if storage == "f64" else v64.astype(np.float32)
+    assert val.dtype == want.dtype and val.tobytes() == want.tobytes()
+
+
 def test_batch_tuner_and_invalid_input(gko):
     G = gko
     systems, bs = batch_problem(200, seed=5)
