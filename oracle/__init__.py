@@ -75,12 +75,12 @@ _SIGS = {
     "or_multi_axpy_norm": (_D, [_I64, _I32, _P, _P, _I64, _P]),
     "or_solve": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _D, _I32, _I32, _P, _I32,
                            C.POINTER(_Result)]),
-    "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
+    "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32, _I32,
                               C.POINTER(_Result)]),
     "or_jacobi_inv": (None, [_I64, _P, _P, _P, _P]),
     "or_batch_cg": (None, [_I32, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _P, _P, _P]),
     "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
-    "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32,
+    "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
                                  C.POINTER(_Result)]),
 }
 
@@ -362,9 +362,11 @@ def gmres(A, b, **kw):
 
 
 def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
-             inner_maxit=1000, restart=30, jacobi=False):
+             inner_maxit=1000, restart=30, jacobi=False, adaptive=False):
     """Mixed-precision iterative refinement (FP32-stored inner solve, FP64
-    outer); jacobi: the inner CG / BiCGSTAB is Jacobi preconditioned."""
+    outer); each inner solve reduces the residual by inner_tol (adaptive: by
+    max(inner_tol, min(0.5, 0.5 tol ||b|| / ||r||)), the library's tunable);
+    jacobi: the inner CG / BiCGSTAB is Jacobi preconditioned."""
     rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
     val32 = val.astype(np.float32)
     x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
@@ -372,10 +374,10 @@ def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
     if jacobi:
         minv = jacobi_inv(A)
         lib().or_solve_ir_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(minv), _p(b), _p(x),
-                             tol, max_outer, inner_tol, inner_maxit, C.byref(res))
+                             tol, max_outer, inner_tol, inner_maxit, int(adaptive), C.byref(res))
     else:
         lib().or_solve_ir(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(b), _p(x), tol,
-                          max_outer, inner_tol, inner_maxit, restart, C.byref(res))
+                          max_outer, inner_tol, inner_maxit, restart, int(adaptive), C.byref(res))
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
 
 

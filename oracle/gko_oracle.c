@@ -798,16 +798,19 @@ void or_batch_cg(int32_t count, const int64_t *row_off, const int64_t *nnz_off, 
 /* Mixed-precision iterative refinement: x = x0; repeat { r = b - A64 x in
  * FP64; stop if ||r|| <= tol ||b||; solve A32 d = r with FP32-stored values
  * and vectors (FP32 SpMV accumulation, FP64 dots and scalars) to
- * ||r_inner|| <= max(inner_tol, min(0.5, 0.5 tol ||b|| / ||r||)) ||r||;
- * x += d in FP64 }. */
+ * ||r_inner|| <= inner_tol ||r|| (adaptive != 0: to max(inner_tol, min(0.5,
+ * 0.5 tol ||b|| / ||r||)) ||r||, the library's adaptive tunable); x += d in
+ * FP64 }. */
 static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                     const float *val32, const double *minv, const double *b, double *x, double tol,
-                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out);
+                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, int adaptive,
+                    or_result *out);
 
 int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                 const float *val32, const double *b, double *x, double tol, int32_t max_outer,
-                double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
-  return solve_ir(solver, n, rp, col, val, val32, NULL, b, x, tol, max_outer, inner_tol, inner_maxit, restart, out);
+                double inner_tol, int32_t inner_maxit, int32_t restart, int32_t adaptive, or_result *out) {
+  return solve_ir(solver, n, rp, col, val, val32, NULL, b, x, tol, max_outer, inner_tol, inner_maxit, restart,
+                  adaptive, out);
 }
 
 /* Mixed-precision refinement whose inner CG / BiCGSTAB is Jacobi
@@ -815,18 +818,20 @@ int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, co
  * solve stores everything in FP32). */
 int or_solve_ir_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                    const float *val32, const double *minv, const double *b, double *x, double tol,
-                   int32_t max_outer, double inner_tol, int32_t inner_maxit, or_result *out) {
+                   int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t adaptive, or_result *out) {
   if (solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) {
     or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
     *out = bad;
     return OR_INVALID;
   }
-  return solve_ir(solver, n, rp, col, val, val32, minv, b, x, tol, max_outer, inner_tol, inner_maxit, 0, out);
+  return solve_ir(solver, n, rp, col, val, val32, minv, b, x, tol, max_outer, inner_tol, inner_maxit, 0, adaptive,
+                  out);
 }
 
 static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                     const float *val32, const double *minv, const double *b, double *x, double tol,
-                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, or_result *out) {
+                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, int adaptive,
+                    or_result *out) {
   or_op A64 = {n, rp, col, val, NULL};
   or_op A32 = {n, rp, col, NULL, val32};
   size_t sz = (size_t)n + 1;
@@ -853,11 +858,17 @@ static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col
     }
     if (res.outer_iterations >= max_outer) break;
     for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
-    /* the inner solve is asked only for the reduction still needed, with a
-     * factor-2 margin: max(inner_tol, min(0.5, 0.5 * tol * ||b|| / ||r||)) */
-    double need = 0.5 * tol * nb / nr;
-    if (need > 0.5) need = 0.5;
-    const double itol = need > inner_tol ? need : inner_tol;
+    /* the inner solve reduces the residual by the fixed factor inner_tol
+     * (refinement with an inner solver of fixed relative accuracy, as in
+     * Carson & Higham 2018).  adaptive: the library's tunable instead, which
+     * asks only for the reduction still needed, with a factor-2 margin:
+     * max(inner_tol, min(0.5, 0.5 * tol * ||b|| / ||r||)). */
+    double itol = inner_tol;
+    if (adaptive) {
+      double need = 0.5 * tol * nb / nr;
+      if (need > 0.5) need = 0.5;
+      itol = need > inner_tol ? need : inner_tol;
+    }
     or_result in = run_solver(&inner, solver, r, d, itol, inner_maxit, restart);
     res.iterations += in.iterations;
     res.outer_iterations += 1;

@@ -69,7 +69,7 @@ def test_jacobi_mixed_precision_matches_oracle(gko, name):
     b = O.spmv_csr(A, np.ones(A.n_rows))
     M = G.from_csr(A)
     which = O.CG if name == "cg" else O.BICGSTAB
-    xo, ro = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, inner_maxit=5000, jacobi=True)
+    xo, ro = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, inner_maxit=5000, jacobi=True, adaptive=True)
     xg, rg = solve(G, name, M, b, 1e-10, 5000, precision=G.PRECISION_MIXED_F32, inner_tol=1e-5,
                    inner_maxit=5000, preconditioner=G.PRECOND_JACOBI)
     assert ro.status == 0 and rg.status == G.OK, (ro, rg)

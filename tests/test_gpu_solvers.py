@@ -110,6 +110,32 @@ def test_solvers_every_csr_plan(gko, plan, precision, name):
         assert iters_close(res.iterations, ro.iterations), (res.iterations, ro.iterations)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["cg", "bicgstab", "gmres"])
+def test_solvers_mid_size_match_oracle(gko, name, precision):
+    """Solution parity on a grid-sized launch (n = 48^3 = 110,592: many full
+    waves of every vector kernel and of the SpMV): 7-point Poisson (CG, b
+    uniform in [-1, 1]) and upwind convection-diffusion at cell Peclet 1
+    (BiCGSTAB, GMRES(30), b = A*1), both sides to 1e-12, FP64 and mixed FP32."""
+    G = gko
+    if name == "cg":
+        A = I.stencil3d_7pt(48)
+        b = np.random.default_rng(11).uniform(-1, 1, A.n_rows)
+    else:
+        A = I.convdiff3d_7pt(48, 1.0)
+        b = O.spmv_csr(A, np.ones(A.n_rows))
+    M = G.from_csr(A)
+    opt = {} if precision == "f64" else {"precision": G.PRECISION_MIXED_F32}
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=6000, **opt)
+    xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=6000)
+    assert res.status == G.OK and ro.status == 0, (res, ro)
+    assert true_rel_res(A, xg, b) <= 1.01e-12
+    assert abs(res.rel_residual - true_rel_res(A, xg, b)) <= 1e-13
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    if precision == "f64" and name != "gmres":
+        assert iters_close(res.iterations, ro.iterations), (res.iterations, ro.iterations)
+
+
 @pytest.mark.parametrize("restart", [5, 30])
 def test_gmres_restart_lengths(gko, restart):
     G = gko
@@ -140,7 +166,7 @@ def test_mixed_precision_refinement(gko, precision, name):
         # refinement step (outer steps up to max(30, ceil(maxit / 120))), the
         # others the whole iteration budget
         inner = dict(inner_maxit=120, max_outer=30) if name == "gmres" else dict(inner_maxit=2000)
-        xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, **inner)
+        xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, adaptive=True, **inner)
         assert ri.status == 0 and abs(res.outer_iterations - ri.outer_iterations) <= 2, (res, ri)
 
 

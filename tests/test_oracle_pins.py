@@ -597,3 +597,19 @@ def test_batch_cg_is_the_single_system_cg_per_system():
             assert np.linalg.norm(xs - xd) <= 1e-9 * np.linalg.norm(xd)
         else:
             assert np.all(x1[i] == 0) and it1[i] == 0
+
+
+def test_ir_fixed_inner_tolerance_contracts_by_inner_tol():
+    """With the inner solve held to a fixed relative tolerance, each
+    refinement step reduces the true residual by about inner_tol (the FP32
+    storage floor is far below 1e-4 here): 1e-12 takes exactly 3 steps at
+    inner_tol 1e-4 and 4 at 1e-3 (reductions compound as inner_tol^k).  The
+    library's adaptive tunable needs no more steps."""
+    A = I.laplace2d_5pt(24)
+    b = dense(A) @ np.ones(A.n_rows)
+    _, r4 = O.solve_ir(O.CG, A, b, tol=1e-12, inner_tol=1e-4, inner_maxit=2000)
+    _, r3 = O.solve_ir(O.CG, A, b, tol=1e-12, inner_tol=1e-3, inner_maxit=2000)
+    _, ra = O.solve_ir(O.CG, A, b, tol=1e-12, inner_tol=1e-4, inner_maxit=2000, adaptive=True)
+    assert r4.status == r3.status == ra.status == 0
+    assert r4.outer_iterations == 3 and r3.outer_iterations == 4, (r4, r3)
+    assert ra.outer_iterations <= r4.outer_iterations
