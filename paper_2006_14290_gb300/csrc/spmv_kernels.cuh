@@ -322,7 +322,14 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
       }
       sum[r] = acc;
     }
-    __syncthreads();  // stage consumed by everyone
+    // Stage consumed by everyone.  The refill below writes this buffer
+    // through the async proxy (bulk copy), which the block barrier alone
+    // does not order after the generic-proxy shared-memory loads above: each
+    // thread first orders its own loads before later async-proxy accesses
+    // (without this fence, blocks that reuse a buffer under load summed
+    // entries of the next stage; seen with many row blocks per block).
+    fence_proxy_async_shared();
+    __syncthreads();
     if (tid == 0 && p_ok) {
       issue(p, stage);
       ++issued;

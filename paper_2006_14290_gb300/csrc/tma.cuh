@@ -76,6 +76,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* e
   return mbar_wait_for(bar, parity, err, kWaitCycles);
 }
 
+// Order this thread's earlier generic-proxy accesses to shared memory before
+// its later async-proxy ones (a bulk copy that overwrites a buffer these
+// threads have read): every thread that read the buffer runs it, then a
+// block barrier, then the thread that issues the copy.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Global -> shared bulk copy completing on `bar`.  dst/src 16-byte aligned,
 // bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {

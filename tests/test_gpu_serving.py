@@ -100,3 +100,53 @@ def test_nonblocking_poll(gko):
     final = first if first is not None else S.result(rid, wait=True)
     assert final[0] == G.OK and final[3] > 0
     S.close()
+
+
+def test_bench_scale_mix_bitwise_alone(gko):
+    """The serving benchmark's kind of load: 8 slots over resident matrices
+    of sides 19..81 (Jacobi CG on variable-coefficient Poisson, BiCGSTAB on
+    convection-diffusion), FP64 and mixed FP32, 160 requests queued at once.
+    Every request must return GKO_OK with x bitwise equal to the same request
+    solved alone on a one-slot server.  (Concurrent solves once summed stale
+    bulk-copied SpMV stages here: 15-20% of the side-81 BiCGSTAB solves
+    differed and some CG solves failed.)"""
+    G = gko
+    rng = np.random.default_rng(12)
+    mats = [("cg", I.varcoef3d_7pt(side, rng)) for side in (72, 58, 35)]
+    mats += [("bicgstab", I.convdiff3d_7pt(side, P)) for side, P in ((81, 8.0), (41, 3.0), (19, 12.0))]
+    handles = [G.from_csr(A) for _, A in mats]
+    bs = [O.spmv_csr(A, np.random.default_rng([3, m]).uniform(0.5, 1.5, A.n_rows)) for m, (_, A) in enumerate(mats)]
+    arr = np.random.default_rng(13)
+    reqs = [(int(arr.integers(0, 3)) if arr.random() < 0.7 else 3 + int(arr.integers(0, 3)),
+             G.PRECISION_F64 if k % 2 == 0 else G.PRECISION_MIXED_F32) for k in range(160)]
+
+    def opts(m, prec):
+        if mats[m][0] == "cg":
+            return G.opts(precision=prec, inner_maxit=1000, preconditioner=G.PRECOND_JACOBI)
+        return G.opts(precision=prec, inner_maxit=1000)
+
+    def submit(S, ids, m, prec):
+        cg = mats[m][0] == "cg"
+        return S.submit(ids[m], 0 if cg else 1, bs[m], 1e-8, 5000 if cg else 500, opts(m, prec))
+
+    S = G.Server(slots=1)
+    ids = [S.add_matrix(H) for H in handles]
+    alone = {}
+    for key in sorted(set(reqs)):
+        alone[key] = S.result(submit(S, ids, *key))
+    S.close()
+    S = G.Server(slots=8, budget_bytes=150 << 30)
+    ids = [S.add_matrix(H) for H in handles]
+    rids = [submit(S, ids, m, prec) for m, prec in reqs]
+    mixed = [S.result(r) for r in rids]
+    st = S.stats()
+    S.close()
+    assert st["peak_active"] == 8
+    bad = []
+    for k, ((m, prec), (code, res, x, _)) in enumerate(zip(reqs, mixed)):
+        c0, r0, x0, _ = alone[(m, prec)]
+        assert c0 == G.OK, (m, prec, r0)
+        if code != G.OK or x.tobytes() != x0.tobytes() or res.iterations != r0.iterations:
+            bad.append((k, m, prec, code, res.iterations, r0.iterations))
+    assert not bad, bad
+    G.gko_device_status()
