@@ -2,11 +2,13 @@
 """Benchmark of the sparse hot path on one node; prints ONE JSON line.
 
 Step = one SpMV y = A x in every format (CSR, ELL, COO, hybrid) and value
-type (FP64, FP32 values+vectors) on the three synthetic matrices of the SpMV
+type (FP64, FP32 values+vectors) on the four synthetic matrices of the SpMV
 sweep: 3D 27-point stencil 128^3 (n = 2,097,152, nnz = 55,742,968), the
-power-law matrix n = 10^6 (Zipf(2) row lengths clipped to [1, 10^4]) and the
-banded matrix n = 10^6 (half-bandwidth 64, fill 0.3).  ELL on the power-law
-matrix is rejected by the padding limit and is not part of the step.
+power-law matrix n = 10^6 (Zipf(2) row lengths clipped to [1, 10^4]), its
+mean-16 variant (row lengths clip(ceil(2.65 Z), 1, 10^4), nnz 16,016,318)
+and the banded matrix n = 10^6 (half-bandwidth 64, fill 0.3).  ELL on the
+power-law matrices is rejected by the padding limit and is not part of the
+step.
 SELL-P (slices of 64 rows) is timed the same way after the step and reported
 under `extra_formats`, outside `value` (the sweep's formats are CSR, ELL, COO
 and hybrid); on the power-law matrix it is rejected by the padding limit too.
@@ -42,8 +44,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SpMV GB/s (% HBM peak) per format; solves/s + p99 latency at 1e-8 residual, mixed vs FP64"
+# power-law "mean ~16" variant: row lengths clip(ceil(lambda * Zipf(2)), 1, 1e4); lambda = 2.65 gives mean
+# 16.02 (nnz 16,016,318) at seed 0
+POWERLAW16_LAMBDA = 2.65
 WORKLOAD = ("SpMV format sweep: CSR/ELL/COO/hybrid x FP64/FP32 (int32 indices) on 27-pt stencil 128^3, "
-            "power-law n=1e6 (Zipf s=2, clip [1,1e4], seed 0), banded n=1e6 (hb 64, fill 0.3, seed 0)")
+            "power-law n=1e6 (Zipf s=2, clip [1,1e4], seed 0), power-law-16 n=1e6 (lambda 2.65, mean 16.0), "
+            "banded n=1e6 (hb 64, fill 0.3, seed 0)")
 FALLBACK_HBM_GBS = 6800.0
 SWEEP_FORMATS = ("csr", "ell", "coo", "hybrid")
 EXTRA_FORMATS = ("sellp",)  # timed the same way, reported beside the sweep, not part of `value`
@@ -67,7 +73,9 @@ def workload_matrices(small=False):
     from paper_2006_14290_gb300 import inputs as I
 
     st = ("stencil27_96", I.stencil3d_27pt(96)) if small else ("stencil27_128", I.stencil3d_27pt(128))
-    return [st, ("powerlaw_1m", I.powerlaw(1_000_000, seed=0)), ("banded_1m", I.banded(1_000_000, 64, 0.3, seed=0))]
+    return [st, ("powerlaw_1m", I.powerlaw(1_000_000, seed=0)),
+            ("powerlaw16_1m", I.powerlaw(1_000_000, seed=0, lam=POWERLAW16_LAMBDA)),
+            ("banded_1m", I.banded(1_000_000, 64, 0.3, seed=0))]
 
 
 def spmv_bytes(fmt, n_rows, n_cols, nnz, ell_nnz, tail_nnz, sv, sx, sy):
@@ -174,15 +182,106 @@ def traffic_record():
 
 # ----------------------------------------------------------------- solvers --
 
-def solver_suite(G, dev, stream):
+def oracle_solver_sample(solver, A, b, iters, pc=False):
+    """The oracle's FP64 solve (as it stands: OpenMP over rows in its SpMV,
+    vector operations sequential) run for a bounded number of iterations
+    (tolerance 0 never stops early): ms per iteration on the host cores."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    if pc:
+        _, r = O.solve_jacobi(solver, A, b, tol=0.0, maxit=iters)
+    else:
+        _, r = O.solve(solver, A, b, tol=0.0, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt * 1e3 / max(r.iterations, 1), int(r.iterations)
+
+
+def cfg1_suite(G, dev, stream, flush, cores):
+    """The 2D 5-point Laplacian 64^2 (n = 4,096, nnz = 20,224) with x and b
+    uniform in [-1, 1] from default_rng(0) (x first): CSR FP64 SpMV (median of
+    20, L2 flushed before each) and CG to 1e-10 (median of 10 solves), with the
+    oracle's SpMV and CG timed beside them on 1 core and on all cores."""
+    import torch
+    import oracle as O
+    from paper_2006_14290_gb300 import inputs as I
+
+    A, x, b = I.laplace2d_problem(64)
+    M = G.from_csr(A)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.zeros(A.n_rows, dtype=torch.float64, device=dev)
+    bd = torch.from_numpy(b).to(dev)
+    for _ in range(3):
+        G.gko_spmv(1.0, M, xd, 0.0, yd, stream=stream)
+    ts = []
+    for k in range(20):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.gko_spmv(1.0, M, xd, 0.0, yd, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    spmv_ms = float(np.median(ts))
+    nb = spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, 8, 8, 8)
+    for _ in range(3):
+        xs = torch.zeros_like(bd)
+        G.gko_solve_cg(M, bd, xs, 1e-10, 5000, stream=stream)
+    cg_ms, res = [], None
+    for _ in range(10):
+        xs = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = G.gko_solve_cg(M, bd, xs, 1e-10, 5000, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cg_ms.append(e0.elapsed_time(e1))
+    out = {"n": int(A.n_rows), "nnz": int(A.nnz),
+           "spmv_us": round(spmv_ms * 1e3, 2), "spmv_GB_s": round(nb / (spmv_ms * 1e-3) / 1e9, 1),
+           "cg_status": int(res.status), "cg_iterations": int(res.iterations),
+           "cg_rel_residual": float(res.rel_residual), "cg_ms": round(float(np.median(cg_ms)), 3),
+           "cg_solves_per_s": round(1e3 / float(np.median(cg_ms)), 1)}
+    orc = {}
+    for tag, t in (("cores_1", 1), ("cores_all", cores)):
+        used = O.set_threads(t)
+        reps, t0 = 0, time.perf_counter()
+        while reps < 2000 and time.perf_counter() - t0 < 1.0:
+            O.spmv_csr(A, x)
+            reps += 1
+        sp = (time.perf_counter() - t0) / reps
+        creps, t0 = 0, time.perf_counter()
+        while creps < 50 and time.perf_counter() - t0 < 2.0:
+            _, ro = O.cg(A, b, tol=1e-10, maxit=5000)
+            creps += 1
+        cg = (time.perf_counter() - t0) / creps
+        orc[tag] = {"threads": used, "spmv_us": round(sp * 1e6, 2), "spmv_GB_s": round(nb / sp / 1e9, 2),
+                    "cg_ms": round(cg * 1e3, 3), "cg_iterations": int(ro.iterations),
+                    "cg_solves_per_s": round(1.0 / cg, 2)}
+    O.set_threads(cores)
+    out["oracle"] = orc
+    return out
+
+
+def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     """Krylov solves to 1e-8 relative residual, FP64 vs mixed precision:
     CG on the 7-point Poisson problem 256^3 (b = A*1) and BiCGSTAB / GMRES(30)
     on 7-point upwind convection-diffusion 128^3 (cell Peclet 10, b = A*1);
-    plus 1,000 CG iterations of fixed work (the paper's CG experiment)."""
+    plus 1,000 CG iterations of fixed work (the paper's CG experiment), the
+    2D 5-point 64^2 CG configuration, and the batched CG.  With oracle_cores
+    > 0 every solve has the oracle's FP64 solve of the same problem timed
+    beside it on a bounded sample of iterations (oracle_ms = its ms per
+    iteration x the GPU's FP64 iteration count)."""
     import torch
+    import oracle as O
     from paper_2006_14290_gb300 import inputs as I
 
     out = {}
+    if oracle_cores:
+        O.lib()
+        O.set_threads(oracle_cores)
+    if flush is not None:
+        out["cfg1_laplace64"] = cfg1_suite(G, dev, stream, flush, oracle_cores or (os.cpu_count() or 1))
 
     def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0):
         fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
@@ -215,6 +314,20 @@ def solver_suite(G, dev, stream):
                     "GB_s_per_iteration": round(it_bytes * max(res.iterations, 1) / (ms * 1e-3) / 1e9, 1)}
         return ms
 
+    def oracle_beside(tags, solver, A, b, sample_iters, pc=False, fp64_tag=None):
+        """Oracle FP64 solve of the same problem on a bounded sample; each tag
+        gets oracle_ms = ms per iteration x the FP64 GPU run's iterations."""
+        if not oracle_cores:
+            return
+        sid = {"cg": O.CG, "bicgstab": O.BICGSTAB, "gmres": O.GMRES}[solver]
+        per_it, done = oracle_solver_sample(sid, A, b, sample_iters, pc=pc)
+        its = out[fp64_tag or tags[0]]["iterations"]
+        for t in tags:
+            out[t]["oracle_ms"] = round(per_it * its, 1)
+            out[t]["oracle_sample"] = (f"oracle FP64 {solver}{' + Jacobi' if pc else ''}: {done} iterations timed "
+                                       f"({per_it:.2f} ms each, {oracle_cores} threads in its SpMV), "
+                                       f"x {its} iterations of the GPU FP64 run")
+
     def speedup(base, other):
         """Time ratio of two runs, only when both converged (a ratio against
         a breakdown or a stalled run says nothing)."""
@@ -225,7 +338,6 @@ def solver_suite(G, dev, stream):
     A = I.stencil3d_7pt(256)
     M = G.from_csr(A)
     n, nnz = A.n_rows, A.nnz
-    del A
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     bd = torch.zeros_like(ones)
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
@@ -241,39 +353,37 @@ def solver_suite(G, dev, stream):
     dt = time.perf_counter() - t0
     out["cg_poisson256_1000_iterations"] = {"iterations": int(res.iterations), "time_ms": round(dt * 1e3, 3),
                                             "iterations_per_s": round(res.iterations / dt, 1)}
-    del M, ones, bd, xd
-    A = I.convdiff3d_7pt(128, 10.0)
-    M = G.from_csr(A)
-    n, nnz = A.n_rows, A.nnz
-    del A
-    ones = torch.ones(n, dtype=torch.float64, device=dev)
-    bd = torch.zeros_like(ones)
-    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
-    for solver in ("bicgstab", "gmres"):
-        tag = "bicgstab" if solver == "bicgstab" else "gmres30"
-        run(f"{tag}_convdiff128_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
-        run(f"{tag}_convdiff128_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
-        out[f"{tag}_convdiff128_mixed_f32_speedup"] = speedup(f"{tag}_convdiff128_f64", f"{tag}_convdiff128_mixed_f32")
-    del M, ones, bd
-    # unpreconditioned BiCGSTAB does not converge at cell Peclet 10 on 128^3
-    # (the oracle diverges too); Peclet 1 is the converging companion case
-    A = I.convdiff3d_7pt(128, 1.0)
-    M = G.from_csr(A)
-    del A
-    ones = torch.ones(n, dtype=torch.float64, device=dev)
-    bd = torch.zeros_like(ones)
-    G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
-    run("bicgstab_convdiff128_P1_f64", "bicgstab", M, bd, n, nnz, G.PRECISION_F64)
-    run("bicgstab_convdiff128_P1_mixed_f32", "bicgstab", M, bd, n, nnz, G.PRECISION_MIXED_F32)
-    out["bicgstab_convdiff128_P1_mixed_f32_speedup"] = speedup("bicgstab_convdiff128_P1_f64",
-                                                               "bicgstab_convdiff128_P1_mixed_f32")
-    del M, ones, bd
+    if oracle_cores:
+        b_host = bd.cpu().numpy()
+        oracle_beside(["cg_poisson256_f64", "cg_poisson256_mixed_f32", "cg_poisson256_mixed_bf16"], "cg", A,
+                      b_host, 8)
+        per_it = out["cg_poisson256_f64"]["oracle_ms"] / max(out["cg_poisson256_f64"]["iterations"], 1)
+        out["cg_poisson256_1000_iterations"]["oracle_ms"] = round(per_it * 1000, 1)
+        del b_host
+    del A, M, ones, bd, xd
+    for P, sfx in ((10.0, ""), (1.0, "_P1")):
+        A = I.convdiff3d_7pt(128, P)
+        M = G.from_csr(A)
+        n, nnz = A.n_rows, A.nnz
+        ones = torch.ones(n, dtype=torch.float64, device=dev)
+        bd = torch.zeros_like(ones)
+        G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
+        b_host = bd.cpu().numpy()
+        # unpreconditioned BiCGSTAB does not converge at cell Peclet 10 on 128^3
+        # (the oracle diverges too); Peclet 1 is the converging companion case
+        solvers = ("bicgstab", "gmres") if P == 10.0 else ("bicgstab",)
+        for solver in solvers:
+            tag = ("bicgstab" if solver == "bicgstab" else "gmres30") + "_convdiff128" + sfx
+            run(f"{tag}_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
+            run(f"{tag}_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
+            out[f"{tag}_mixed_f32_speedup"] = speedup(f"{tag}_f64", f"{tag}_mixed_f32")
+            oracle_beside([f"{tag}_f64", f"{tag}_mixed_f32"], solver, A, b_host, 30 if solver == "gmres" else 12)
+        del A, M, ones, bd, b_host
     # Jacobi preconditioning on the variable-coefficient Poisson problem 128^3
     # (coefficients exp(N(0,1)) per cell, default_rng(0); b = A*1)
     A = I.varcoef3d_7pt(128, np.random.default_rng(0))
     M = G.from_csr(A)
     n, nnz = A.n_rows, A.nnz
-    del A
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     bd = torch.zeros_like(ones)
     G.gko_spmv(1.0, M, ones, 0.0, bd, stream=stream)
@@ -282,15 +392,28 @@ def solver_suite(G, dev, stream):
     run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
     out["cg_varcoef128_jacobi_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_f64")
     out["cg_varcoef128_jacobi_mixed_f32_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_mixed_f32")
-    del M, ones, bd
-    out["batched_cg"] = batched_suite(G, dev, stream)
+    if oracle_cores:
+        b_host = bd.cpu().numpy()
+        oracle_beside(["cg_varcoef128_f64"], "cg", A, b_host, 12)
+        oracle_beside(["cg_varcoef128_jacobi_f64", "cg_varcoef128_jacobi_mixed_f32"], "cg", A, b_host, 12, pc=True)
+        del b_host
+    del A, M, ones, bd
+    out["batched_cg"] = batched_suite(G, dev, stream, oracle_cores)
     return out
 
 
-def batched_suite(G, dev, stream):
+# nominal FP64 rate of the part (2 FMA per SM per clock, 152 SMs, 2.07 GHz)
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def batched_suite(G, dev, stream, oracle_cores=0):
     """4096 variable-coefficient 2D 5-point systems (sides log-uniform in
     [8, 64]) solved by batched CG to 1e-10 in one persistent graph-captured
-    launch; FP64 and FP32 storage; warp/block threshold from the autotuner."""
+    launch; FP64 and FP32 storage; schedule from the autotuner.  Work per
+    batch: global bytes = sum over systems of iterations x (values, columns
+    and row pointers of the system's matrix + x read and written; r, p, q live
+    in shared memory), FP64 FMAs = sum of iterations x (nnz + 5 n).  The
+    oracle's batched CG (OpenMP over systems) is timed beside it."""
     import torch
     from paper_2006_14290_gb300 import inputs as I
 
@@ -301,11 +424,14 @@ def batched_suite(G, dev, stream):
         systems.append(A)
         bs.append(b)
     b = torch.from_numpy(np.concatenate(bs)).to(dev)
-    res = {"systems": 4096, "rows": int(sum(S.n_rows for S in systems)), "nnz": int(sum(S.nnz for S in systems))}
+    rows = np.array([S.n_rows for S in systems], np.int64)
+    nnzs = np.array([S.nnz for S in systems], np.int64)
+    res = {"systems": 4096, "rows": int(rows.sum()), "nnz": int(nnzs.sum())}
+    peak_hbm, _ = measured_peaks()
     for storage, tag in ((G.F64, "f64"), (G.F32, "f32_storage")):
         B = G.Batch(systems, storage=storage)
         x0 = torch.zeros(B.total_rows, dtype=torch.float64, device=dev)
-        chosen, tune_ms = B.tune(b, x0, 1e-10, 20000, stream=stream)
+        tuned = B.tune(b, x0, 1e-10, 20000, stream=stream)
         x = torch.zeros_like(x0)
         B.cg(b, x, 1e-10, 20000, stream=stream)  # capture the graph
         times = []
@@ -319,27 +445,56 @@ def batched_suite(G, dev, stream):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
+        sv = 8 if storage == G.F64 else 4
+        itd = it.astype(np.float64)
+        nbytes = float(np.sum(itd * (nnzs * (sv + 4) + 4 * (rows + 1) + 16 * rows)))
+        fmas = float(np.sum(itd * (nnzs + 5 * rows)))
+        fp64_frac = 2 * fmas / (ms * 1e-3) / (FP64_TFLOPS_NOMINAL * 1e12)
         res[tag] = {"status": int(code), "time_ms": round(ms, 3), "systems_per_s": round(4096 / (ms * 1e-3), 1),
-                    "warp_rows_threshold": int(chosen), "tuned_ms": round(float(tune_ms), 3),
+                    "schedule": tuned, "tuned_over": "warp rows {0,64,144,256} x threads {256,512,1024} x CSR/ELL",
                     "iterations_total": int(it.sum()), "iterations_max": int(it.max()),
-                    "max_rel_residual": float(rr.max())}
+                    "max_rel_residual": float(rr.max()), "bytes": nbytes, "fp64_fmas": fmas,
+                    "GB_s": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                    "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
+                    "frac_fp64": round(fp64_frac, 4),
+                    "fp64_peak": f"{FP64_TFLOPS_NOMINAL} TFLOP/s nominal (2 FMA/SM/clock x 152 SMs x 2.07 GHz)"}
         del B
+    if oracle_cores:
+        import oracle as O
+
+        O.set_threads(oracle_cores)
+        t0 = time.perf_counter()
+        _, oit, orr, ost = O.batch_cg(systems, bs, tol=1e-10, maxit=20000)
+        dt = time.perf_counter() - t0
+        res["oracle"] = {"ms": round(dt * 1e3, 1), "systems_per_s": round(4096 / dt, 1), "threads": oracle_cores,
+                         "converged": int(np.sum(ost == 0)), "iterations_total": int(oit.sum()),
+                         "sample": "the full batch: the oracle's FP64 CG per system, OpenMP over systems"}
+        res["f64"]["oracle_ms"] = res["oracle"]["ms"]
+        res["f32_storage"]["oracle_ms"] = res["oracle"]["ms"]
     return res
 
 
 # ----------------------------------------------------------------- serving --
 
-def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_bytes=150 << 30):
+SERVING_RATES = (100.0, 250.0, 500.0, 1000.0, 2000.0)
+
+
+def serving_suite(G, rates=SERVING_RATES, per_type=64, slots=8, budget_bytes=150 << 30, max_requests=500):
     """Poisson arrivals of sparse solves against resident matrices.
 
-    Pool: 8 variable-coefficient 7-point Poisson matrices (CG) and 8 upwind
-    convection-diffusion matrices with cell Peclet ~ U[1, 20] (BiCGSTAB), cube
-    sides rint(n^(1/3)) for n log-uniform in [1e3, 4e6], all from
-    default_rng(0), uploaded before the window.  Requests: 70% CG / 30%
-    BiCGSTAB on a uniformly chosen pool matrix, b = A*1, tolerance 1e-8
-    (iteration caps CG 5000, BiCGSTAB 500; CG Jacobi-preconditioned, as the
-    variable coefficients call for), admitted by a 150 GB budget over
-    `slots` concurrent solves.  Each arrival window runs FP64 and mixed FP32.
+    Pool: `per_type` variable-coefficient 7-point Poisson matrices (CG, Jacobi
+    preconditioned, as the variable coefficients call for) and `per_type`
+    upwind convection-diffusion matrices with cell Peclet ~ U[1, 20]
+    (BiCGSTAB), cube sides rint(n^(1/3)) for n log-uniform in [1e3, 4e6], all
+    from default_rng(0), uploaded before any window.  Requests: one Poisson
+    stream from default_rng(1) (70% CG / 30% BiCGSTAB, uniformly chosen pool
+    matrix), each with its own right-hand side b = A v, v uniform in [0.5,
+    1.5] from default_rng([2, request]); tolerance 1e-8, iteration caps CG
+    5000, BiCGSTAB 500; admitted by a 150 GB budget over `slots` concurrent
+    solves.  Every rate replays the same requests with arrival times scaled
+    to it (window: the first min(max_requests, rate) arrivals, at most 1 s),
+    FP64 and mixed FP32.  Every request that does not return GKO_OK is listed
+    with its status, solver, matrix, size, iterations and residual.
     """
     import torch
     from paper_2006_14290_gb300 import inputs as I
@@ -347,31 +502,34 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
     rng = np.random.default_rng(0)
     pool = []
     for kind in ("cg", "bicgstab"):
-        for _ in range(8):
+        for _ in range(per_type):
             n = float(np.exp(rng.uniform(np.log(1e3), np.log(4e6))))
             side = max(4, int(np.rint(n ** (1.0 / 3.0))))
             if kind == "cg":
                 A = I.varcoef3d_7pt(side, rng)
             else:
                 A = I.convdiff3d_7pt(side, float(rng.uniform(1.0, 20.0)))
-            M = G.from_csr(A)
-            ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
-            bd = torch.zeros_like(ones)
-            G.gko_spmv(1.0, M, ones, 0.0, bd)
-            pool.append((kind, M, bd.cpu().numpy(), A.n_rows))
+            pool.append([kind, G.from_csr(A), int(A.n_rows), side])
             del A
-    out = {"pool_rows": [p[3] for p in pool], "slots": slots, "budget_GB": budget_bytes / 2**30}
-    for rate, window in windows:
-        arr = np.random.default_rng(1)
-        times, picks = [], []
-        t = 0.0
-        while True:
-            t += arr.exponential(1.0 / rate)
-            if t > window:
-                break
-            times.append(t)
-            k = 0 if arr.random() < 0.7 else 1
-            picks.append(int(arr.integers(0, 8)) + 8 * k)
+    arr = np.random.default_rng(1)
+    unit_times = np.cumsum(arr.exponential(1.0, max_requests))  # arrivals at rate 1
+    picks = []
+    for _ in range(max_requests):
+        k = 0 if arr.random() < 0.7 else 1
+        picks.append(int(arr.integers(0, per_type)) + per_type * k)
+    bs = []
+    for r, m in enumerate(picks):
+        n = pool[m][2]
+        v = torch.from_numpy(np.random.default_rng([2, r]).uniform(0.5, 1.5, n)).cuda()
+        bd = torch.zeros_like(v)
+        G.gko_spmv(1.0, pool[m][1], v, 0.0, bd)
+        bs.append(bd.cpu().numpy())
+        del v, bd
+    out = {"pool_matrices": len(pool), "pool_rows_total": int(sum(p[2] for p in pool)), "slots": slots,
+           "budget_GB": budget_bytes / 2**30, "rates": list(rates)}
+    for rate in rates:
+        count = int(min(max_requests, np.searchsorted(unit_times / rate, 1.0, side="right")))
+        times = unit_times[:count] / rate
         for prec_name, prec in (("f64", G.PRECISION_F64), ("mixed_f32", G.PRECISION_MIXED_F32)):
             S = G.Server(slots=slots, budget_bytes=budget_bytes)
             ids = [S.add_matrix(p[1]) for p in pool]
@@ -379,25 +537,33 @@ def serving_suite(G, windows=((2000.0, 0.25), (100.0, 1.0)), slots=8, budget_byt
             opts_cg = G.opts(precision=prec, inner_maxit=1000, preconditioner=G.PRECOND_JACOBI)
             t0 = time.perf_counter()
             rids = []
-            for at, m in zip(times, picks):
+            for r in range(count):
                 now = time.perf_counter() - t0
-                if at > now:
-                    time.sleep(at - now)
-                kind = pool[m][0]
-                rids.append(S.submit(ids[m], 0 if kind == "cg" else 1, pool[m][2], 1e-8,
-                                     5000 if kind == "cg" else 500, opts_cg if kind == "cg" else opts))
-            results = [S.result(r) for r in rids]
+                if times[r] > now:
+                    time.sleep(times[r] - now)
+                m = picks[r]
+                cg = pool[m][0] == "cg"
+                rids.append(S.submit(ids[m], 0 if cg else 1, bs[r], 1e-8, 5000 if cg else 500,
+                                     opts_cg if cg else opts))
+            results = [S.result(q) for q in rids]
             wall = time.perf_counter() - t0
             st = S.stats()
             S.close()
-            ok = sum(1 for r in results if r[0] == G.OK)
-            cg_ok = sum(1 for r, m in zip(results, picks) if r[0] == G.OK and pool[m][0] == "cg")
+            failed = []
+            for r, (code, res, _, lat) in enumerate(results):
+                if code != G.OK:
+                    m = picks[r]
+                    failed.append({"request": r, "status": int(code), "solver": pool[m][0], "matrix": m,
+                                   "n": pool[m][2], "iterations": int(res.iterations),
+                                   "rel_residual": float(res.rel_residual)})
+            cg_req = sum(1 for r in range(count) if pool[picks[r]][0] == "cg")
             out[f"rate{int(rate)}_{prec_name}"] = {
-                "requests": len(rids), "window_s": window, "converged": ok,
-                "cg_converged": cg_ok, "cg_requests": sum(1 for m in picks if pool[m][0] == "cg"),
+                "requests": count, "window_s": round(float(times[-1]), 3) if count else 0.0,
+                "converged": count - len(failed), "cg_requests": cg_req,
+                "cg_converged": cg_req - sum(1 for f in failed if f["solver"] == "cg"),
                 "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                 "solves_per_s": round(st["solves_per_s"], 2), "drain_s": round(wall, 3),
-                "peak_concurrent": st["peak_active"]}
+                "peak_concurrent": st["peak_active"], "failed": failed}
     return out
 
 
@@ -502,7 +668,7 @@ def run_reference(args):
         one_step()
     dt = time.perf_counter() - t0
     gbs = step_bytes * args.steps / dt / 1e9
-    sample = (f"oracle FP64 CSR SpMV on the three sweep matrices per step ({args.steps} steps after "
+    sample = (f"oracle FP64 CSR SpMV on the {len(mats)} sweep matrices per step ({args.steps} steps after "
               f"{args.warmup} warm-up), OpenMP over rows on {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
@@ -515,23 +681,31 @@ def run_reference(args):
 
 
 def cpu_baseline(mats, budget_s=12.0):
-    """The oracle as it stands on the host cores, on a bounded sample."""
+    """The oracle as it stands on the host cores, on a bounded sample: FP64
+    CSR SpMV over the sweep matrices, on all cores (OpenMP over rows) and on
+    one core."""
     import oracle as O
 
     O.lib()
-    cores = O.set_threads(os.cpu_count() or 1)
     xs = {name: np.random.default_rng(0).uniform(-1, 1, A.n_cols) for name, A in mats}
-    nbytes = 0
-    reps = 0
-    t0 = time.perf_counter()
-    while reps < 20 and (time.perf_counter() - t0) < budget_s:
-        for name, A in mats:
-            O.spmv_csr(A, xs[name])
-            nbytes += spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, 8, 8, 8)
-        reps += 1
-    dt = time.perf_counter() - t0
-    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 CSR SpMV on the three sweep matrices, {reps} passes ({dt:.1f} s), OpenMP over rows"}
+    out = {}
+    for tag, threads, budget in (("cores_all", os.cpu_count() or 1, budget_s), ("cores_1", 1, budget_s / 2)):
+        cores = O.set_threads(threads)
+        nbytes, reps = 0, 0
+        t0 = time.perf_counter()
+        while reps < 20 and (time.perf_counter() - t0) < budget:
+            for name, A in mats:
+                O.spmv_csr(A, xs[name])
+                nbytes += spmv_bytes("csr", A.n_rows, A.n_cols, A.nnz, 0, 0, 8, 8, 8)
+            reps += 1
+        dt = time.perf_counter() - t0
+        out[tag] = {"value": round(nbytes / dt / 1e9, 3), "cores": cores, "passes": reps, "s": round(dt, 2)}
+    O.set_threads(os.cpu_count() or 1)
+    allc = out["cores_all"]
+    return {"value": allc["value"], "unit": "GB/s", "cores": allc["cores"], "kind": "oracle",
+            "sample": (f"FP64 CSR SpMV on the {len(mats)} sweep matrices, {allc['passes']} passes "
+                       f"({allc['s']:.1f} s) with OpenMP over rows; one-core figure in cores_1"),
+            "cores_all": out["cores_all"], "cores_1": out["cores_1"]}
 
 
 # ------------------------------------------------------------ multi-rank --
@@ -777,7 +951,8 @@ def run_ours(args):
             result["cusparse_context"] = cusparse_context(mats, dev, stream, flush, min(args.steps, 10), peak)
             result["subwarp_reduce"] = subwarp_microbench(G, dev, stream)
         if not args.no_solvers:
-            result["solvers"] = solver_suite(G, dev, stream)
+            oc = 0 if args.no_cpu_baseline else (os.cpu_count() or 1)
+            result["solvers"] = solver_suite(G, dev, stream, flush, oracle_cores=oc)
         if not args.no_serving:
             result["serving"] = serving_suite(G)
         if world == 1 and not args.no_cpu_baseline:

@@ -1123,10 +1123,11 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
     if (hc->nb == 0.0) {
       zero_kernel<T><<<vg, 256, 0, s>>>(n, x);
     } else {
-      // the initial residual decides afresh in the first cycle start
-      const int zero = 0, run = kRun;
-      GKO_TRY_CUDA(cudaMemcpyAsync(&c->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-      GKO_TRY_CUDA(cudaMemcpyAsync(&c->status, &run, sizeof(int), cudaMemcpyHostToDevice, s));
+      // the initial residual decides afresh in the first cycle start (done =
+      // 0, status = kRun = 0; set on the device, no host source to outlive)
+      static_assert(kRun == 0, "kRun is written as a zero word");
+      GKO_TRY_CUDA(cudaMemsetAsync(&c->done, 0, sizeof(int), s));
+      GKO_TRY_CUDA(cudaMemsetAsync(&c->status, 0, sizeof(int), s));
       hc->done = 0;
     }
     int64_t mg = std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, kMultiSlots));
