@@ -391,28 +391,39 @@ GKO_API int gko_batch_export(gko_batch B, int64_t *row_off, int64_t *nnz_off, in
 /* Solve every system: b, x are DEVICE FP64 vectors laid out like the rows
  * (x: x0 in, solution out).  Per system: stop when ||r_k|| <= rel_tol ||b_i||
  * and the true residual confirms (else it replaces r), or after max_iters.
- * Systems with at most the batch's warp-mode threshold rows are solved by one
- * warp each, larger ones by a 256-thread block; the launch is captured once
- * into a CUDA graph per (b, x, rel_tol, max_iters, stream) and replayed.
- * iterations / rel_residuals (true residuals) / statuses: optional HOST
- * arrays of `count` entries.  Returns GKO_OK when every system converged,
- * else GKO_BREAKDOWN or GKO_NOT_CONVERGED.  Synchronises `stream`. */
+ * The batch's schedule decides how: systems with at most warp_rows rows are
+ * solved by one warp each, larger ones by a block of `threads` threads, from
+ * the CSR arrays or from the batch's per-system ELL copy (both sum every row
+ * in storage order, so the results are identical).  The launch is captured
+ * once into a CUDA graph per (b, x, rel_tol, max_iters, stream, schedule) and
+ * replayed.  iterations / rel_residuals (true residuals) / statuses: optional
+ * HOST arrays of `count` entries.  Returns GKO_OK when every system
+ * converged, else GKO_BREAKDOWN or GKO_NOT_CONVERGED.  Synchronises
+ * `stream`. */
 GKO_API int gko_batch_cg(gko_batch B, const double *b, double *x, double rel_tol, int32_t max_iters,
                          int32_t *iterations, double *rel_residuals, int32_t *statuses, void *stream);
 
-/* Autotuner: times the whole batch for warp-mode thresholds 0, 64, 100, 144,
- * 196 and 256 rows (solving from a scratch copy of x0; x0 is not changed)
- * and keeps the fastest.  *chosen and *best_ms (either may be NULL) report
- * the choice.  Synchronises `stream`. */
-GKO_API int gko_batch_tune(gko_batch B, const double *b, const double *x0, double rel_tol, int32_t max_iters,
-                           int32_t *chosen, float *best_ms, void *stream);
+#define GKO_BATCH_CSR 0 /* the concatenated CSR arrays                       */
+#define GKO_BATCH_ELL 1 /* per-system column-major ELL (longest row's slots) */
 
-/* Set the warp-mode threshold directly (rows; 0 = block mode only; capped at
- * 256). */
+/* Autotuner (the project's; the paper tunes nothing at run time): times the
+ * whole batch for every schedule, warp_rows in {0, 64, 144, 256} x threads
+ * per block in {256, 512, 1024} x storage CSR or ELL (solving from a scratch
+ * copy of x0; x0 is not changed), keeps the fastest and reports it (outputs
+ * may be NULL; best_ms in milliseconds).  Synchronises `stream`. */
+GKO_API int gko_batch_tune(gko_batch B, const double *b, const double *x0, double rel_tol, int32_t max_iters,
+                           int32_t *warp_rows, int32_t *threads, int32_t *storage, float *best_ms, void *stream);
+
+/* Set the schedule directly: warp_rows >= 0 (0 = block mode only; capped at
+ * 256), threads 256, 512 or 1024, storage GKO_BATCH_CSR or GKO_BATCH_ELL;
+ * anything else -> GKO_INVALID_ARG.  gko_batch_set_threshold changes
+ * warp_rows only.  The default: 144 rows, 256 threads, CSR. */
+GKO_API int gko_batch_set_schedule(gko_batch B, int32_t warp_rows, int32_t threads, int32_t storage, void *stream);
 GKO_API int gko_batch_set_threshold(gko_batch B, int32_t warp_rows, void *stream);
 
+/* The batch's sizes and schedule (outputs may be NULL). */
 GKO_API int gko_batch_info(gko_batch B, int32_t *count, int64_t *total_rows, int64_t *total_nnz,
-                           int32_t *warp_rows, int32_t *n_items);
+                           int32_t *warp_rows, int32_t *n_items, int32_t *threads, int32_t *storage);
 GKO_API int gko_batch_destroy(gko_batch B);
 
 /* --------------------------------------------------------------- serving -- */

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -23,9 +24,7 @@
 
 namespace gko {
 
-constexpr int kBatchThreads = 256;
-constexpr int kWarpItemSystems = kBatchThreads / kWarp;  // 8
-constexpr int kWarpMaxRows = 256;                         // warp mode: rows per system
+constexpr int kWarpMaxRows = 256;  // warp mode: rows per system
 
 enum : int { kBRun = 0, kBOk = 1, kBBreak = 2, kBNotConv = 3 };
 
@@ -38,6 +37,13 @@ struct BatchArgs {
   const int32_t* rp;        // concatenated local row pointers (n_i + 1 each)
   const int32_t* col;
   const void* val;
+  // ELL storage: system i holds ell_k[i] slots per row, slot k of local row r
+  // at ell_off[i] + k * n_i + r (column-major within the system), padding
+  // column -1
+  const int64_t* ell_off;
+  const int32_t* ell_k;
+  const int32_t* ell_col;
+  const void* ell_val;
   const double* b;
   double* x;
   double rel_tol;
@@ -53,14 +59,15 @@ struct BatchArgs {
 __device__ __forceinline__ double ldv(const double* v, int64_t k) { return v[k]; }
 __device__ __forceinline__ double ldv(const float* v, int64_t k) { return widen(v[k]); }
 
-// sum over the block, result in every thread: warps reduce by shuffles, warp
-// 0 adds the eight warp sums (not every thread) and shares the total.  Two
-// barriers: a call's warp sums are written after every thread has passed the
-// previous call's last barrier (so warp 0 has read the old ones), and the new
-// total is written after this call's first barrier (so every thread has read
-// the old total).
+// Sum over a block of THREADS threads, result in every thread: warps reduce
+// by shuffles, warp 0 adds the warp sums (not every thread) and shares the
+// total.  Two barriers: a call's warp sums are written after every thread
+// has passed the previous call's last barrier (so warp 0 has read the old
+// ones), and the new total is written after this call's first barrier (so
+// every thread has read the old total).
+template <int THREADS>
 __device__ __forceinline__ double block_allsum(double v, double* red) {
-  constexpr int NW = kBatchThreads / kWarp;
+  constexpr int NW = THREADS / kWarp;
   v = subwarp_sum<32>(v, 0xffffffffu);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[w] = v;
@@ -74,23 +81,26 @@ __device__ __forceinline__ double block_allsum(double v, double* red) {
   return red[NW];
 }
 
-// One CG solve by a group of G threads (G = 256: a block; G = 32: a warp).
-// r, p, q: the group's shared-memory vectors.  Follows the single-system
-// solver: recurrence residual test, then the true residual; a failed true
-// check replaces r and continues.
-template <int G, typename VT>
+// One CG solve by a group of G threads (G = THREADS: a block; G = 32: a
+// warp).  r, p, q: the group's shared-memory vectors.  Follows the
+// single-system solver: recurrence residual test, then the true residual; a
+// failed true check replaces r and continues.  ELL: the system's entries
+// come from its column-major ELL slots (every row's slots in storage order,
+// so each row sum is the same sequence of FMAs as from CSR).
+template <int G, int THREADS, typename VT, bool ELL>
 __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, double* q, double* red, int lane) {
   const int64_t r0 = a.row_off[sys];
   const int n = (int)(a.row_off[sys + 1] - r0);
   const int32_t* rp = a.rp + r0 + sys;
-  const int64_t k0 = a.nnz_off[sys];
-  const int32_t* col = a.col + k0;
-  const VT* val = static_cast<const VT*>(a.val) + k0;
+  const int64_t k0 = ELL ? a.ell_off[sys] : a.nnz_off[sys];
+  const int32_t* col = (ELL ? a.ell_col : a.col) + k0;
+  const VT* val = static_cast<const VT*>(ELL ? a.ell_val : a.val) + k0;
+  const int K = ELL ? a.ell_k[sys] : 0;
   const double* b = a.b + r0;
   double* x = a.x + r0;
   auto gsum = [&](double v) -> double {
     if (G == kWarp) return subwarp_sum<32>(v, 0xffffffffu);
-    return block_allsum(v, red);
+    return block_allsum<THREADS>(v, red);
   };
   auto gsync = [&]() {
     if (G == kWarp) __syncwarp();
@@ -98,7 +108,15 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   };
   auto row_dot = [&](int i, const double* v) -> double {
     double s = 0.0;
-    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fma_rn(ldv(val, k), v[col[k]], s);
+    if (ELL) {
+      for (int k = 0; k < K; ++k) {
+        const int64_t q = (int64_t)k * n + i;
+        const int32_t c = col[q];
+        if (c >= 0) s = __fma_rn(ldv(val, q), v[c], s);
+      }
+    } else {
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fma_rn(ldv(val, k), v[col[k]], s);
+    }
     return s;
   };
   // r = b - A x0, p = r (x0 staged through q)
@@ -194,10 +212,13 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   gsync();
 }
 
-template <typename VT>
-__global__ void __launch_bounds__(kBatchThreads) batch_cg_kernel(BatchArgs a, int block_rows) {
+// Persistent batched CG: blocks of THREADS threads take work items from an
+// atomic queue, largest systems first; a block item is one system solved by
+// the whole block, a warp item THREADS/32 systems, one per warp.
+template <int THREADS, typename VT, bool ELL>
+__global__ void __launch_bounds__(THREADS) batch_cg_kernel(BatchArgs a, int block_rows) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ double red[kBatchThreads / kWarp + 1];  // warp sums + the block total
+  __shared__ double red[THREADS / kWarp + 1];  // warp sums + the block total
   __shared__ int item_s;
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(a.queue, 1u);
@@ -211,12 +232,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_cg_kernel(BatchArgs a, in
       double* r = sm;
       double* p = sm + block_rows;
       double* q = sm + 2 * block_rows;
-      cg_group<kBatchThreads, VT>(a, a.order[first], r, p, q, red, threadIdx.x);
+      cg_group<THREADS, THREADS, VT, ELL>(a, a.order[first], r, p, q, red, threadIdx.x);
     } else {
       const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
       double* base = sm + (size_t)w * 3 * kWarpMaxRows;
-      if (w < it.y) cg_group<kWarp, VT>(a, a.order[first + w], base, base + kWarpMaxRows, base + 2 * kWarpMaxRows,
-                                        red, lane);
+      if (w < it.y)
+        cg_group<kWarp, THREADS, VT, ELL>(a, a.order[first + w], base, base + kWarpMaxRows, base + 2 * kWarpMaxRows,
+                                          red, lane);
       __syncthreads();
     }
   }
@@ -239,9 +261,13 @@ struct gko_batch_s {
   int64_t total_rows = 0, total_nnz = 0;
   int32_t max_rows = 0;
   Buf row_off, nnz_off, rp, col, val, order, items, iters, relres, status, queue;
+  Buf ell_off, ell_k, ell_col, ell_val;  // the same systems in per-system column-major ELL
+  int64_t ell_slots = 0;
   std::vector<int64_t> h_rows;   // rows per system
   std::vector<int32_t> h_order;  // largest first
   int32_t threshold = 0;         // warp mode for systems with <= threshold rows
+  int32_t threads = 256;         // threads per block (a block item's group size)
+  int32_t ell = 0;               // 1: solve from the ELL arrays
   int n_items = 0;
   int block_rows = 0;
   // cached graph of (queue reset + kernel)
@@ -269,8 +295,9 @@ static int build_items(gko_batch B, int32_t threshold, cudaStream_t s) {
     items.push_back(make_int2((int)(i << 1) | 0, 1));
     ++i;
   }
+  const size_t per_item = (size_t)B->threads / kWarp;
   while (i < n) {
-    const int cnt = (int)std::min<size_t>(kWarpItemSystems, n - i);
+    const int cnt = (int)std::min<size_t>(per_item, n - i);
     items.push_back(make_int2((int)(i << 1) | 1, cnt));
     i += cnt;
   }
@@ -290,8 +317,20 @@ static int build_items(gko_batch B, int32_t threshold, cudaStream_t s) {
 
 static size_t batch_smem(const gko_batch_s* B) {
   const size_t blk = (size_t)3 * B->block_rows * sizeof(double);
-  const size_t wrp = B->threshold > 0 ? (size_t)kWarpItemSystems * 3 * kWarpMaxRows * sizeof(double) : 0;
+  const size_t wrp = B->threshold > 0 ? (size_t)(B->threads / kWarp) * 3 * kWarpMaxRows * sizeof(double) : 0;
   return std::max<size_t>(std::max(blk, wrp), 16);
+}
+
+template <int T, typename VT, bool E>
+static int batch_launch_t(const BatchArgs& a, int n_items, int block_rows, size_t smem, cudaStream_t s) {
+  auto kern = batch_cg_kernel<T, VT, E>;
+  GKO_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
+  const int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * sm_count()));
+  kern<<<grid, T, smem, s>>>(a, block_rows);
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
 }
 
 static int batch_launch(gko_batch B, const double* b, double* x, double tol, int maxit, cudaStream_t s) {
@@ -312,23 +351,25 @@ static int batch_launch(gko_batch B, const double* b, double* x, double tol, int
   a.relres = ptr<double>(B->relres);
   a.status = ptr<int32_t>(B->status);
   a.queue = ptr<unsigned>(B->queue);
+  a.ell_off = ptr<int64_t>(B->ell_off);
+  a.ell_k = ptr<int32_t>(B->ell_k);
+  a.ell_col = ptr<int32_t>(B->ell_col);
+  a.ell_val = B->ell_val ? B->ell_val->ptr : nullptr;
   const size_t smem = batch_smem(B);
-  int per_sm = 1;
-  if (B->dtype == GKO_F64) {
-    GKO_TRY_CUDA(cudaFuncSetAttribute(batch_cg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cg_kernel<double>, kBatchThreads, smem));
-  } else {
-    GKO_TRY_CUDA(cudaFuncSetAttribute(batch_cg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cg_kernel<float>, kBatchThreads, smem));
-  }
-  const int grid = std::max(1, std::min(B->n_items, std::max(1, per_sm) * sm_count()));
   GKO_TRY_CUDA(cudaMemsetAsync(B->queue->ptr, 0, sizeof(unsigned), s));
-  if (B->dtype == GKO_F64)
-    batch_cg_kernel<double><<<grid, kBatchThreads, smem, s>>>(a, B->block_rows);
-  else
-    batch_cg_kernel<float><<<grid, kBatchThreads, smem, s>>>(a, B->block_rows);
-  GKO_TRY_CUDA(cudaGetLastError());
-  return GKO_OK;
+  const bool f64 = B->dtype == GKO_F64;
+  switch (B->threads * 4 + (f64 ? 2 : 0) + (B->ell ? 1 : 0)) {
+#define GKO_BATCH_CASE(T, VT, E) \
+  case T * 4 + (std::is_same<VT, double>::value ? 2 : 0) + (E ? 1 : 0): \
+    return batch_launch_t<T, VT, E>(a, B->n_items, B->block_rows, smem, s);
+#define GKO_BATCH_T(T) \
+  GKO_BATCH_CASE(T, double, false) GKO_BATCH_CASE(T, double, true) GKO_BATCH_CASE(T, float, false) \
+  GKO_BATCH_CASE(T, float, true)
+    GKO_BATCH_T(256) GKO_BATCH_T(512) GKO_BATCH_T(1024)
+#undef GKO_BATCH_T
+#undef GKO_BATCH_CASE
+  }
+  return fail(GKO_INVALID_ARG, "unsupported batch schedule");
 }
 
 // Capture (queue reset + kernel) once per (b, x, tol, maxit, stream) and
@@ -363,6 +404,64 @@ static int batch_run(gko_batch B, const double* b, double* x, double tol, int ma
     B->g_stream = s;
   }
   GKO_TRY_CUDA(cudaGraphLaunch(B->exec, s));
+  return GKO_OK;
+}
+
+// The systems in per-system column-major ELL (the batch's ELL storage):
+// system i keeps K_i = its longest row slots per row, slot k of local row r
+// at ell_off[i] + k * n_i + r, filled from the CSR rows in storage order,
+// padding column -1 and value 0.  Values FP64, rounded to FP32 on the device
+// for FP32 storage (the rounding of gko_batch_create).
+static int build_ell(gko_batch B, const int64_t* row_off, const int64_t* nnz_off, const int32_t* row_ptr,
+                     const int32_t* col, const double* values, cudaStream_t s) {
+  const int32_t count = B->count;
+  std::vector<int64_t> off((size_t)count + 1, 0);
+  std::vector<int32_t> kk((size_t)count, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t n = row_off[i + 1] - row_off[i];
+    const int32_t* rp = row_ptr + row_off[i] + i;
+    int32_t k = 0;
+    for (int64_t r = 0; r < n; ++r) k = std::max(k, rp[r + 1] - rp[r]);
+    kk[(size_t)i] = k;
+    off[(size_t)i + 1] = off[(size_t)i] + (int64_t)k * n;
+  }
+  const int64_t slots = off[(size_t)count];
+  std::vector<int32_t> ecol((size_t)std::max<int64_t>(slots, 1), -1);
+  std::vector<double> eval((size_t)std::max<int64_t>(slots, 1), 0.0);
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t n = row_off[i + 1] - row_off[i];
+    const int32_t* rp = row_ptr + row_off[i] + i;
+    const int64_t k0 = nnz_off[i];
+    for (int64_t r = 0; r < n; ++r)
+      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+        const int64_t q = off[(size_t)i] + (int64_t)(k - rp[r]) * n + r;
+        ecol[(size_t)q] = col[k0 + k];
+        eval[(size_t)q] = values[k0 + k];
+      }
+  }
+  const size_t vs = dtype_size(B->dtype);
+  GKO_TRY(alloc(sizeof(int64_t) * (count + 1), &B->ell_off));
+  GKO_TRY(alloc(sizeof(int32_t) * count, &B->ell_k));
+  GKO_TRY(alloc(sizeof(int32_t) * std::max<int64_t>(slots, 1), &B->ell_col));
+  GKO_TRY(alloc(vs * std::max<int64_t>(slots, 1), &B->ell_val));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->ell_off->ptr, off.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  GKO_TRY_CUDA(cudaMemcpyAsync(B->ell_k->ptr, kk.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+  if (slots > 0) {
+    GKO_TRY_CUDA(cudaMemcpyAsync(B->ell_col->ptr, ecol.data(), sizeof(int32_t) * slots, cudaMemcpyHostToDevice, s));
+    if (B->dtype == GKO_F64) {
+      GKO_TRY_CUDA(cudaMemcpyAsync(B->ell_val->ptr, eval.data(), sizeof(double) * slots, cudaMemcpyHostToDevice, s));
+    } else {
+      Scratch v64;
+      GKO_TRY(v64.get(sizeof(double) * slots, s));
+      GKO_TRY_CUDA(cudaMemcpyAsync(v64.data(), eval.data(), sizeof(double) * slots, cudaMemcpyHostToDevice, s));
+      round_f32_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, (int64_t)sm_count() * 16), 256, 0, s>>>(
+          slots, v64.as<double>(), ptr<float>(B->ell_val));
+      GKO_TRY_CUDA(cudaGetLastError());
+      GKO_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));  // the host arrays above go out of scope
+  B->ell_slots = slots;
   return GKO_OK;
 }
 
@@ -432,6 +531,7 @@ int gko_batch_create(int32_t count, const int64_t* row_off, const int64_t* nnz_o
     GKO_TRY_CUDA(cudaStreamSynchronize(s));
   }
   GKO_TRY_CUDA(cudaMemcpyAsync(B->order->ptr, B->h_order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+  GKO_TRY(build_ell(B.get(), row_off, nnz_off, row_ptr, col, values, s));
   GKO_TRY(build_items(B.get(), 144, s));
   *out = B.release();
   return GKO_OK;
@@ -493,14 +593,25 @@ int gko_batch_set_threshold(gko_batch B, int32_t warp_rows, void* stream) {
   return build_items(B, warp_rows, (cudaStream_t)stream);
 }
 
+int gko_batch_set_schedule(gko_batch B, int32_t warp_rows, int32_t threads, int32_t storage, void* stream) {
+  if (!B || warp_rows < 0 || (threads != 256 && threads != 512 && threads != 1024) ||
+      (storage != GKO_BATCH_CSR && storage != GKO_BATCH_ELL))
+    return fail(GKO_INVALID_ARG, "batch schedule: warp_rows >= 0, threads 256/512/1024, storage CSR or ELL");
+  B->threads = threads;
+  B->ell = storage == GKO_BATCH_ELL ? 1 : 0;
+  return build_items(B, warp_rows, (cudaStream_t)stream);
+}
+
 int gko_batch_info(gko_batch B, int32_t* count, int64_t* total_rows, int64_t* total_nnz, int32_t* warp_rows,
-                   int32_t* n_items) {
+                   int32_t* n_items, int32_t* threads, int32_t* storage) {
   if (!B) return fail(GKO_INVALID_ARG, "null batch");
   if (count) *count = B->count;
   if (total_rows) *total_rows = B->total_rows;
   if (total_nnz) *total_nnz = B->total_nnz;
   if (warp_rows) *warp_rows = B->threshold;
   if (n_items) *n_items = B->n_items;
+  if (threads) *threads = B->threads;
+  if (storage) *storage = B->ell ? GKO_BATCH_ELL : GKO_BATCH_CSR;
   return GKO_OK;
 }
 
@@ -526,40 +637,49 @@ int gko_batch_cg(gko_batch B, const double* b, double* x, double rel_tol, int32_
   return worst;
 }
 
-// Autotuner: time the whole batch for each candidate warp-mode threshold
-// (on a scratch copy of x0) and keep the fastest.
+// Autotuner: time the whole batch for every schedule (warp-mode threshold x
+// threads per block x storage) on a scratch copy of x0 and keep the fastest.
 int gko_batch_tune(gko_batch B, const double* b, const double* x0, double rel_tol, int32_t max_iters,
-                   int32_t* chosen, float* best_ms, void* stream) {
+                   int32_t* warp_rows, int32_t* threads, int32_t* storage, float* best_ms, void* stream) {
   if (!B || !b || !x0) return fail(GKO_INVALID_ARG, "bad tune arguments");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch xs;
   GKO_TRY(xs.get(sizeof(double) * B->total_rows, s));
-  const int32_t cands[] = {0, 64, 100, 144, 196, 256};
-  cudaEvent_t e0, e1;
-  GKO_TRY_CUDA(cudaEventCreate(&e0));
-  GKO_TRY_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int32_t best_t = B->threshold;
-  for (int32_t t : cands) {
-    GKO_TRY(build_items(B, t, s));
-    for (int rep = 0; rep < 2; ++rep) {
-      GKO_TRY_CUDA(cudaMemcpyAsync(xs.data(), x0, sizeof(double) * B->total_rows, cudaMemcpyDeviceToDevice, s));
-      GKO_TRY_CUDA(cudaEventRecord(e0, s));
-      GKO_TRY(batch_run(B, b, xs.as<double>(), rel_tol, max_iters, s));
-      GKO_TRY_CUDA(cudaEventRecord(e1, s));
-      GKO_TRY_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      GKO_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep == 1 && ms < best) {
-        best = ms;
-        best_t = t;
-      }
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
     }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  GKO_TRY(build_items(B, best_t, s));
-  if (chosen) *chosen = best_t;
+  } ev;
+  GKO_TRY_CUDA(cudaEventCreate(&ev.a));
+  GKO_TRY_CUDA(cudaEventCreate(&ev.b));
+  float best = 1e30f;
+  int32_t best_t = B->threshold, best_th = B->threads, best_st = B->ell ? GKO_BATCH_ELL : GKO_BATCH_CSR;
+  for (int32_t st : {GKO_BATCH_CSR, GKO_BATCH_ELL})
+    for (int32_t th : {256, 512, 1024})
+      for (int32_t t : {0, 64, 144, 256}) {
+        GKO_TRY(gko_batch_set_schedule(B, t, th, st, stream));
+        for (int rep = 0; rep < 2; ++rep) {
+          GKO_TRY_CUDA(cudaMemcpyAsync(xs.data(), x0, sizeof(double) * B->total_rows, cudaMemcpyDeviceToDevice, s));
+          GKO_TRY_CUDA(cudaEventRecord(ev.a, s));
+          GKO_TRY(batch_run(B, b, xs.as<double>(), rel_tol, max_iters, s));
+          GKO_TRY_CUDA(cudaEventRecord(ev.b, s));
+          GKO_TRY_CUDA(cudaEventSynchronize(ev.b));
+          float ms = 0.f;
+          GKO_TRY_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+          if (rep == 1 && ms < best) {
+            best = ms;
+            best_t = t;
+            best_th = th;
+            best_st = st;
+          }
+        }
+      }
+  GKO_TRY(gko_batch_set_schedule(B, best_t, best_th, best_st, stream));
+  if (warp_rows) *warp_rows = best_t;
+  if (threads) *threads = best_th;
+  if (storage) *storage = best_st;
   if (best_ms) *best_ms = best;
   return GKO_OK;
 }

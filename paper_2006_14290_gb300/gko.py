@@ -96,9 +96,10 @@ SIGNATURES.update({
     "gko_batch_create_systems": (C.c_int, [_I32, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)]),
     "gko_batch_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "gko_batch_cg": (C.c_int, [_P, _P, _P, _D, _I32, _P, _P, _P, _P]),
-    "gko_batch_tune": (C.c_int, [_P, _P, _P, _D, _I32, _PI32, C.POINTER(C.c_float), _P]),
+    "gko_batch_tune": (C.c_int, [_P, _P, _P, _D, _I32, _PI32, _PI32, _PI32, C.POINTER(C.c_float), _P]),
     "gko_batch_set_threshold": (C.c_int, [_P, _I32, _P]),
-    "gko_batch_info": (C.c_int, [_P, _PI32, _PI64, _PI64, _PI32, _PI32]),
+    "gko_batch_set_schedule": (C.c_int, [_P, _I32, _I32, _I32, _P]),
+    "gko_batch_info": (C.c_int, [_P, _PI32, _PI64, _PI64, _PI32, _PI32, _PI32, _PI32]),
     "gko_batch_destroy": (C.c_int, [_P]),
 })
 SIGNATURES.update({
@@ -428,6 +429,7 @@ def gko_solve_gmres(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=N
 
 
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
+BATCH_CSR, BATCH_ELL = 0, 1
 
 
 def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0,
@@ -503,21 +505,29 @@ class Batch:
         return code, it, rr, st
 
     def tune(self, b, x0, rel_tol=1e-10, max_iters=10000, stream=None):
-        ch = C.c_int32()
+        """The autotuner: returns dict(warp_rows, threads, storage, ms)."""
+        wr, th, st = C.c_int32(), C.c_int32(), C.c_int32()
         ms = C.c_float()
-        _check(lib().gko_batch_tune(self.handle, _dptr(b), _dptr(x0), rel_tol, max_iters, C.byref(ch), C.byref(ms),
-                                    _stream(stream)), "gko_batch_tune")
-        return ch.value, ms.value
+        _check(lib().gko_batch_tune(self.handle, _dptr(b), _dptr(x0), rel_tol, max_iters, C.byref(wr), C.byref(th),
+                                    C.byref(st), C.byref(ms), _stream(stream)), "gko_batch_tune")
+        return dict(warp_rows=wr.value, threads=th.value, storage="ell" if st.value == BATCH_ELL else "csr",
+                    ms=round(ms.value, 3))
 
     def set_threshold(self, warp_rows, stream=None):
         _check(lib().gko_batch_set_threshold(self.handle, warp_rows, _stream(stream)), "gko_batch_set_threshold")
 
+    def set_schedule(self, warp_rows, threads=256, storage=None, stream=None):
+        st = BATCH_CSR if storage is None else storage
+        _check(lib().gko_batch_set_schedule(self.handle, warp_rows, threads, st, _stream(stream)),
+               "gko_batch_set_schedule")
+
     def info(self):
-        c, wr, ni = C.c_int32(), C.c_int32(), C.c_int32()
+        c, wr, ni, th, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         tr, tn = C.c_int64(), C.c_int64()
-        _check(lib().gko_batch_info(self.handle, C.byref(c), C.byref(tr), C.byref(tn), C.byref(wr), C.byref(ni)),
-               "gko_batch_info")
-        return dict(count=c.value, total_rows=tr.value, total_nnz=tn.value, warp_rows=wr.value, n_items=ni.value)
+        _check(lib().gko_batch_info(self.handle, C.byref(c), C.byref(tr), C.byref(tn), C.byref(wr), C.byref(ni),
+                                    C.byref(th), C.byref(st)), "gko_batch_info")
+        return dict(count=c.value, total_rows=tr.value, total_nnz=tn.value, warp_rows=wr.value, n_items=ni.value,
+                    threads=th.value, storage="ell" if st.value == BATCH_ELL else "csr")
 
 
 class Server:

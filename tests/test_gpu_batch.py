@@ -23,13 +23,17 @@ def concat(v):
     return np.concatenate([np.asarray(a, np.float64) for a in v])
 
 
+@pytest.mark.parametrize("storage", ["csr", "ell"])
+@pytest.mark.parametrize("threads", [256, 512, 1024])
 @pytest.mark.parametrize("threshold", [0, 64, 144, 256])
-def test_batch_cg_matches_oracle(gko, threshold):
+def test_batch_cg_matches_oracle(gko, threshold, threads, storage):
+    """Every schedule (warp threshold x threads per block x CSR or ELL
+    storage) against the per-system oracle CG."""
     G = gko
     systems, bs = batch_problem(120)
     bs[5] = np.zeros_like(bs[5])  # a zero right-hand side
     B = G.Batch(systems)
-    B.set_threshold(threshold)
+    B.set_schedule(threshold, threads, G.BATCH_ELL if storage == "ell" else G.BATCH_CSR)
     b = concat(bs)
     xd = dev(np.zeros(b.size))
     code, it, rr, st = B.cg(dev(b), xd, 1e-12, 20000)
@@ -112,9 +116,10 @@ def test_batch_tuner_and_invalid_input(gko):
     B = G.Batch(systems)
     b = dev(concat(bs))
     x0 = dev(np.zeros(B.total_rows))
-    chosen, ms = B.tune(b, x0, 1e-10, 20000)
-    assert chosen in (0, 64, 100, 144, 196, 256) and ms > 0
-    assert B.info()["warp_rows"] == chosen
+    t = B.tune(b, x0, 1e-10, 20000)
+    assert t["warp_rows"] in (0, 64, 144, 256) and t["threads"] in (256, 512, 1024) and t["ms"] > 0
+    inf = B.info()
+    assert (inf["warp_rows"], inf["threads"], inf["storage"]) == (t["warp_rows"], t["threads"], t["storage"])
     assert np.all(host(x0) == 0)
     bad = I.laplace2d_5pt(4)
     bad.col = bad.col.copy()
@@ -147,3 +152,23 @@ def test_batch_full_size_4096(gko):
         assert true <= 1.01e-10
         xo, ro = O.cg(A, bs[i], tol=1e-10, maxit=20000)
         assert abs(int(it[i]) - ro.iterations) <= max(2, 0.1 * ro.iterations)
+
+
+def test_batch_storages_give_identical_results(gko):
+    """ELL storage keeps every row's entries in storage order, so the batch
+    solved from it is bit-identical to the CSR run, at every group size."""
+    G = gko
+    # 5-point systems: boundary rows are shorter, so ELL pads them
+    systems, bs = batch_problem(80, seed=7, extra_sides=(64, 8, 9, 33))
+    B = G.Batch(systems)
+    b = dev(concat(bs))
+    outs = {}
+    for threads in (256, 1024):
+        for st in (G.BATCH_CSR, G.BATCH_ELL):
+            B.set_schedule(64, threads, st)
+            xd = dev(np.zeros(B.total_rows))
+            code, it, rr, stt = B.cg(b, xd, 1e-11, 20000)
+            assert code == G.OK
+            outs[(threads, st)] = (host(xd).tobytes(), it.tobytes())
+    for threads in (256, 1024):
+        assert outs[(threads, G.BATCH_CSR)] == outs[(threads, G.BATCH_ELL)]
