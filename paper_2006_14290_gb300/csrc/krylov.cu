@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "blas1.cuh"
 #include "reduce.cuh"
@@ -972,12 +973,407 @@ struct SolveOut {
   int cycles;
 };
 
+// ------------------------------------------------ single-launch small CG --
+//
+// Small systems are bound by kernel launch latency, not bandwidth: three
+// dependent launches per CG iteration take about 24 us whatever n.  For a
+// CSR handle with the row-block plan (regular rows) and n <= kSmallRows, the
+// whole CG (Saad Alg. 6.18, Jacobi-preconditioned as Alg. 9.1 when a
+// diagonal is given, with the multi-kernel path's true-residual check,
+// residual replacement, breakdown and iteration-cap rules) runs in one
+// cooperative launch of G blocks.  Thread t of block g owns RPT rows (g *
+// 256 * RPT + t + j * 256) and keeps their x, r, p, b and Jacobi entries in
+// registers; the block stages its rows' matrix entries in shared memory once
+// (when they fit), so an iteration reads only the gathered p values from
+// L2.  p is published to global memory after each update, x only for the
+// true-residual check and at the end.  Each iteration is the SpMV and two
+// grid reductions separated by three grid barriers.  Reductions are
+// deterministic: every block adds the G block partials in index order, so
+// all blocks hold the same scalars and take the same decisions.  Values
+// written by other blocks (the gathered p and x, the partials) are read with
+// ld.global.cg: inside one launch L1 is not coherent across SMs.  Every
+// barrier wait is bounded (~1 s); a block that gives up records GKO_TIMEOUT
+// and the solve returns it.
+constexpr int kSmallThreads = 256;
+constexpr int64_t kSmallRows = 1 << 18;
+constexpr long long kSmallWait = 1ll << 31;
+constexpr size_t kSmallSmemMax = 96 * 1024;  // staged matrix entries per block
+
+template <typename T, typename VT>
+struct SmallArgs {
+  int64_t n;
+  const int32_t* rp;
+  const int32_t* col;
+  const VT* val;
+  const double* b;  // FP64 right-hand side
+  T* x;
+  T* p;
+  const T* d;  // Jacobi inverse diagonal, or null
+  double rel_tol;
+  int maxit;
+  int check_true;
+  int x_zero;
+  int32_t block_cap;  // staged entries per block (shared memory)
+  double* part;       // 4 reduction sites x 3 values x gridDim.x
+  unsigned* bar;      // grid barrier: arrival counter (zero at launch)
+  int* err;
+  Ctl* c;             // status and iteration count on exit
+};
+
+// Grid-wide barrier of a cooperative launch (all blocks resident), bounded:
+// one monotonic arrival counter (zero at launch); barrier number k of the
+// launch waits until it reaches (k + 1) * gridDim.x.  Each block's thread 0
+// arrives with a release add and polls with acquire loads, so a barrier
+// costs about one L2 round trip after the last arrival and nothing is reset.
+// `target` is the caller's count of barriers passed times the grid size
+// (the same in every thread).
+__device__ __forceinline__ bool small_sync(unsigned* bar, unsigned& target, int* err) {
+  __shared__ int s_ok;
+  target += gridDim.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (clock64() - t0 > kSmallWait) {
+        if (err) atomicOr(err, 1 << GKO_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Grid sum of NV values: block sums to part[k * G + block], barrier, then
+// every block adds the G partials in index order (warp 0, lane-strided, then
+// a fixed butterfly): the same totals in every block.
+template <int NV>
+__device__ __forceinline__ bool small_reduce(double (&v)[NV], double* part, unsigned* bar, unsigned& target,
+                                             int* err) {
+  __shared__ double tot[NV];
+  block_sum_n<kSmallThreads, NV>(v);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[(int64_t)k * G + blockIdx.x] = v[k];
+  if (!small_sync(bar, target, err)) return false;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < G; i += 32) s += __ldcg(part + (int64_t)k * G + i);
+      s = subwarp_sum<32>(s, 0xffffffffu);
+      if (threadIdx.x == 0) tot[k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = tot[k];
+  return true;
+}
+
+template <typename T, typename VT, int RPT, bool SMEM>
+__global__ void __launch_bounds__(kSmallThreads) small_cg_kernel(SmallArgs<T, VT> a) {
+  using AT = acc_t<VT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G3 = 3 * (int)gridDim.x;
+  double* P_init = a.part;
+  double* P_pq = a.part + G3;
+  double* P_rr = a.part + 2 * G3;
+  double* P_true = a.part + 3 * G3;
+  const int64_t row0 = (int64_t)blockIdx.x * kSmallThreads * RPT;
+  const int64_t row1 = row0 + (int64_t)kSmallThreads * RPT < a.n ? row0 + (int64_t)kSmallThreads * RPT : a.n;
+  const int32_t e0 = __ldg(a.rp + row0), e1 = __ldg(a.rp + row1);
+  int32_t* scol = reinterpret_cast<int32_t*>(smem_raw);
+  VT* sval = reinterpret_cast<VT*>(smem_raw + (((size_t)a.block_cap * sizeof(int32_t) + 15) & ~(size_t)15));
+  if (SMEM) {
+    for (int32_t k = e0 + (int32_t)threadIdx.x; k < e1; k += kSmallThreads) {
+      scol[k - e0] = __ldg(a.col + k);
+      sval[k - e0] = a.val[k];
+    }
+  }
+  __syncthreads();
+  // this thread's rows
+  int32_t ks[RPT], ke[RPT];
+  bool own[RPT];
+  double bj[RPT];
+  T xj[RPT], rj[RPT], pj[RPT], dj[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    const int64_t i = row0 + threadIdx.x + (int64_t)j * kSmallThreads;
+    own[j] = i < a.n;
+    ks[j] = own[j] ? __ldg(a.rp + i) - (SMEM ? e0 : 0) : 0;
+    ke[j] = own[j] ? __ldg(a.rp + i + 1) - (SMEM ? e0 : 0) : 0;
+    bj[j] = own[j] ? a.b[i] : 0.0;
+    xj[j] = own[j] && !a.x_zero ? a.x[i] : T(0);
+    dj[j] = own[j] && a.d ? a.d[i] : T(1);
+  }
+  const bool pc = a.d != nullptr;
+  // row j of A v: staged (or global) entries in storage order, v gathered
+  // with ld.global.cg; the gathers of up to 8 entries are issued before
+  // their FMAs, so a stencil row costs one L2 round trip, not one per entry
+  auto row_dot = [&](int j, const T* v) -> T {
+    constexpr int U = 8;
+    AT s = AT(0);
+    for (int32_t k = ks[j]; k < ke[j]; k += U) {
+      VT w[U];
+      T g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = k + u < ke[j];
+        const int32_t c = in ? (SMEM ? scol[k + u] : __ldg(a.col + k + u)) : 0;
+        w[u] = in ? (SMEM ? sval[k + u] : a.val[k + u]) : VT(0);
+        g[u] = in ? __ldcg(v + c) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k + u < ke[j]) s = madd(to_acc(w[u]), to_acc(g[u]), s);
+    }
+    return (T)s;
+  };
+  auto publish = [&](T* dst, const T (&v)[RPT]) {
+#pragma unroll
+    for (int j = 0; j < RPT; ++j)
+      if (own[j]) dst[row0 + threadIdx.x + (int64_t)j * kSmallThreads] = v[j];
+  };
+  int status = kRun, it = 0;
+  unsigned tgt = 0;  // grid barriers passed x gridDim.x
+  // r = b - A x0 (x0 = 0: r = b), z = d r, p = z; ||b||^2, r.r, r.z
+  double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    if (!own[j]) continue;
+    const T ri = a.x_zero ? (T)bj[j] : (T)(bj[j] - wd(row_dot(j, a.x)));
+    const T zi = pc ? dj[j] * ri : ri;
+    rj[j] = ri;
+    pj[j] = zi;
+    v3[0] += bj[j] * bj[j];
+    v3[1] += wd(ri) * wd(ri);
+    v3[2] += wd(ri) * wd(zi);
+  }
+  publish(a.p, pj);  // published by the reduction's barrier
+  const bool ok0 = small_reduce<3>(v3, P_init, a.bar, tgt, a.err);
+  const double nb = sqrt(v3[0]), tol_abs = a.rel_tol * nb;
+  double rho = v3[2];
+  if (!ok0) {
+    status = -1;
+  } else if (v3[0] == 0.0) {  // b == 0: x = 0 after 0 iterations
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) xj[j] = T(0);
+    status = kConverged;
+  } else if (sqrt(v3[1]) <= tol_abs) {
+    status = kConverged;
+  } else if (a.maxit <= 0) {
+    status = kNotConverged;
+  }
+  while (status == kRun) {
+    // q = A p, p.q
+    T qj[RPT];
+    double v1[1] = {0.0};
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      qj[j] = own[j] ? row_dot(j, a.p) : T(0);
+      v1[0] += wd(pj[j]) * wd(qj[j]);
+    }
+    if (!small_reduce<1>(v1, P_pq, a.bar, tgt, a.err)) {
+      status = -1;
+      break;
+    }
+    const double pq = v1[0];
+    if (!(pq > 0.0)) {
+      status = kBreakdown;
+      break;
+    }
+    const double alpha = rho / pq;
+    const Lin<T> ax(alpha), ar(-alpha);
+    double v2[2] = {0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      if (!own[j]) continue;
+      xj[j] = ax(pj[j], xj[j]);
+      rj[j] = ar(qj[j], rj[j]);
+      const double rw = wd(rj[j]);
+      v2[0] = __fma_rn(rw, rw, v2[0]);
+      v2[1] = pc ? __fma_rn(rw, wd(dj[j] * rj[j]), v2[1]) : v2[0];
+    }
+    if (!small_reduce<2>(v2, P_rr, a.bar, tgt, a.err)) {
+      status = -1;
+      break;
+    }
+    ++it;
+    double rho_new = pc ? v2[1] : v2[0];
+    if (sqrt(v2[0]) <= tol_abs) {
+      if (!a.check_true) {
+        status = kConverged;
+        break;
+      }
+      // true residual t = b - A x: every block's x first
+      publish(a.x, xj);
+      if (!small_sync(a.bar, tgt, a.err)) {
+        status = -1;
+        break;
+      }
+      T tj[RPT];
+      double vt[2] = {0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        tj[j] = own[j] ? (T)(bj[j] - wd(row_dot(j, a.x))) : T(0);
+        vt[0] += wd(tj[j]) * wd(tj[j]);
+        vt[1] += wd(tj[j]) * wd(pc ? dj[j] * tj[j] : tj[j]);
+      }
+      if (!small_reduce<2>(vt, P_true, a.bar, tgt, a.err)) {
+        status = -1;
+        break;
+      }
+      if (sqrt(vt[0]) <= tol_abs) {
+        status = kConverged;
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) rj[j] = tj[j];  // residual replacement (p is kept)
+      rho_new = vt[1];
+    } else if (it >= a.maxit) {
+      status = kNotConverged;
+      break;
+    }
+    const Lin<T> bp(rho_new / rho);
+    rho = rho_new;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) pj[j] = bp(pj[j], pc ? dj[j] * rj[j] : rj[j]);
+    publish(a.p, pj);
+    if (!small_sync(a.bar, tgt, a.err)) {
+      status = -1;
+      break;
+    }
+  }
+  publish(a.x, xj);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.c->status = status < 0 ? kNotConverged : status;
+    a.c->iter = it;
+    a.c->cycles = status < 0 ? 1 : 0;  // 1: a barrier timed out
+  }
+}
+
+// Whether the single-launch CG serves this matrix (see above).
+static bool small_cg_ok(const gko_matrix_s* A, const SolveSpec& sp) {
+  if (sp.solver != 0 || A->fmt != GKO_CSR || A->plan.kind != 1 || A->n_rows <= 0 || A->n_rows > kSmallRows)
+    return false;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) !=
+                                                   cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return coop != 0;
+}
+
+// Resident blocks per SM of one instantiation at the given dynamic shared
+// memory (computed once per instantiation and size class).
+template <typename K>
+static int small_per_sm(K kern, size_t smem) {
+  int nb = 0;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                              cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kSmallThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+template <typename T, typename VT, int RPT>
+static int small_cg_launch(const gko_matrix_s* A, SmallArgs<T, VT>& a, int G, size_t smem, bool staged,
+                           cudaStream_t s) {
+  void* args[] = {&a};
+  if (staged) {
+    auto kern = small_cg_kernel<T, VT, RPT, true>;
+    if (smem > 48 * 1024)
+      GKO_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GKO_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)G), dim3(kSmallThreads), args, smem, s));
+  } else {
+    auto kern = small_cg_kernel<T, VT, RPT, false>;
+    GKO_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)G), dim3(kSmallThreads), args, 0, s));
+  }
+  return GKO_OK;
+}
+
+template <typename T, typename VT>
+static int small_cg(const gko_matrix_s* A, const double* b, T* x, bool x_zero, const SolveSpec& sp, cudaStream_t s,
+                    SolveOut* out) {
+  const int64_t n = A->n_rows;
+  // rows per thread: the fewest (1, 2, 4) whose grid fits on the GPU at once
+  int rpt = 0, G = 0;
+  size_t smem = 0;
+  bool staged = false;
+  for (int r : {1, 2, 4}) {
+    const int64_t g = (n + (int64_t)kSmallThreads * r - 1) / ((int64_t)kSmallThreads * r);
+    const size_t cap = (size_t)kSmallThreads * r * (size_t)std::max(1, A->plan.max_len);
+    const size_t bytes = ((cap * sizeof(int32_t) + 15) & ~(size_t)15) + cap * sizeof(VT);
+    const bool st = bytes <= kSmallSmemMax;
+    int per_sm = 0;
+    if (r == 1) per_sm = st ? small_per_sm(small_cg_kernel<T, VT, 1, true>, bytes) : small_per_sm(small_cg_kernel<T, VT, 1, false>, 0);
+    if (r == 2) per_sm = st ? small_per_sm(small_cg_kernel<T, VT, 2, true>, bytes) : small_per_sm(small_cg_kernel<T, VT, 2, false>, 0);
+    if (r == 4) per_sm = st ? small_per_sm(small_cg_kernel<T, VT, 4, true>, bytes) : small_per_sm(small_cg_kernel<T, VT, 4, false>, 0);
+    if (per_sm > 0 && g <= (int64_t)per_sm * sm_count()) {
+      rpt = r;
+      G = (int)g;
+      staged = st;
+      smem = st ? bytes : 0;
+      break;
+    }
+  }
+  if (!rpt) return GKO_NOT_SUPPORTED;  // the caller falls back to the multi-kernel solve
+  Scratch mem;
+  GKO_TRY(mem.get(sizeof(Ctl) + sizeof(T) * (size_t)n + sizeof(double) * 12 * (size_t)G + 2048, s));
+  Carve cv{static_cast<char*>(mem.data())};
+  Ctl* c = cv.take<Ctl>(1);
+  unsigned* bar = cv.take<unsigned>(4);
+  double* part = cv.take<double>(12 * (size_t)G);
+  T* p = cv.take<T>(n);
+  const int32_t cap32 = (int32_t)((size_t)kSmallThreads * rpt * (size_t)std::max(1, A->plan.max_len));
+  SmallArgs<T, VT> a{n,  ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val),
+                     b,  x, p, static_cast<const T*>(sp.minv), sp.rel_tol, sp.maxit, sp.check_true,
+                     x_zero ? 1 : 0, cap32, part, bar, device_error_word(), c};
+  GKO_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
+  if (rpt == 1) GKO_TRY((small_cg_launch<T, VT, 1>(A, a, G, smem, staged, s)));
+  if (rpt == 2) GKO_TRY((small_cg_launch<T, VT, 2>(A, a, G, smem, staged, s)));
+  if (rpt == 4) GKO_TRY((small_cg_launch<T, VT, 4>(A, a, G, smem, staged, s)));
+  Ctl* hc = host_ctl();
+  GKO_TRY(read_ctl(c, hc, s));
+  if (hc->cycles) return fail(GKO_TIMEOUT, "single-launch CG: a grid barrier wait timed out");
+  out->status = hc->status;
+  out->iterations = hc->iter;
+  out->cycles = 0;
+  return GKO_OK;
+}
+
 // One Krylov solve on the device.  A: matrix whose value type matches T
 // (double: F64; float: F32/BF16).  b: FP64 right-hand side; x: T vector,
 // x0 on entry (x_zero: treat x0 as zero without reading it).
 template <typename T>
 static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero, const SolveSpec& sp,
                        cudaStream_t s, SolveOut* out) {
+  if (small_cg_ok(A, sp)) {
+    int rc = GKO_NOT_SUPPORTED;
+    if constexpr (std::is_same<T, double>::value) {
+      if (A->dtype == GKO_F64) rc = small_cg<double, double>(A, b, x, x_zero, sp, s, out);
+    } else {
+      if (A->dtype == GKO_F32) rc = small_cg<float, float>(A, b, x, x_zero, sp, s, out);
+      if (A->dtype == GKO_BF16) rc = small_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
+    }
+    if (rc != GKO_NOT_SUPPORTED) return rc;
+  }
   const int64_t n = A->n_rows;
   const int m = std::max(1, sp.restart);
   const int nvec = sp.solver == 0 ? 3 : sp.solver == 1 ? 9 : (m + 2);
