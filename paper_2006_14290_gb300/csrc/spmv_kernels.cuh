@@ -247,18 +247,13 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
   bool timed_out = false;
   for (unsigned q = 0;; ++q) {
     const int stage = (int)(q % NS);
+    // Each thread waits for the stage itself; the block agrees on a time-out
+    // at the barrier that ends the stage, so a stage costs one block barrier.
     const bool ok = mbar_wait(&bar[stage], (q / NS) & 1u, err);
-    if (__syncthreads_or(!ok)) {
-      // let every copy still in flight land before the block's shared memory goes
-      if (tid == 0)
-        for (unsigned u = q; u < issued; ++u) mbar_wait(&bar[u % NS], (u / NS) & 1u, err);
-      timed_out = true;
-      break;
-    }
     const int32_t* sc = scol + (size_t)stage * cap;
     const VT* sv = sval + (size_t)stage * cap;
     const int64_t cs = c.kb + (int64_t)c.j * cap;
-    if (COO) {
+    if (COO && ok) {
       // sb[j], j = 0..RB: first staged entry whose position is >= j, where
       // an entry's position is its row minus the block's first row, -1 for
       // entries staged before the row block and RB for entries after it (or
@@ -292,10 +287,10 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
       }
       if (tid == kRbThreads - 1)
         for (int j = pp + 1; j <= RB; ++j) sb[j] = cap;  // rows that reach the end of a full stage
-      __syncthreads();
     }
+    if (COO) __syncthreads();  // sb complete (all threads reach it: block-uniform)
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < R && ok; ++r) {
       const int lo = COO ? sb[sg + r * G] : (int)(imax64(rs[r], cs) - cs);
       const int hi = COO ? sb[sg + r * G + 1] : (int)(imin64(re[r], cs + cap) - cs);
       AT acc = sum[r];
@@ -329,7 +324,14 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
     // (without this fence, blocks that reuse a buffer under load summed
     // entries of the next stage; seen with many row blocks per block).
     fence_proxy_async_shared();
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      // a wait timed out: let every copy still in flight land before the
+      // block's shared memory goes
+      if (tid == 0)
+        for (unsigned u = q; u < issued; ++u) mbar_wait(&bar[u % NS], (u / NS) & 1u, err);
+      timed_out = true;
+      break;
+    }
     if (tid == 0 && p_ok) {
       issue(p, stage);
       ++issued;
