@@ -801,6 +801,40 @@ def profile_cases(args):
     G.gko_device_status()
     print(json.dumps([[c["label"], c["launches"], int(c["bytes"]), c["nnz"]] for c in cases]))
 
+def profile_solvers(args):
+    """Short fixed-work solves for ncu launch lists: BiCGSTAB (40 iterations,
+    convection-diffusion 128^3, cell Peclet 1) and GMRES(30) (one restart
+    cycle, Peclet 10), FP64, tolerance 0; each runs once untimed, then once
+    inside the NVTX range "profile_solvers"."""
+    import torch
+    from paper_2006_14290_gb300 import gko as G
+    from paper_2006_14290_gb300 import inputs as I
+
+    G.load()
+    out = {}
+    for solver, P, iters in (("bicgstab", 1.0, 40), ("gmres", 10.0, 30)):
+        A = I.convdiff3d_7pt(128, P)
+        M = G.from_csr(A)
+        ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+        bd = torch.zeros_like(ones)
+        G.gko_spmv(1.0, M, ones, 0.0, bd)
+        fn = G.gko_solve_bicgstab if solver == "bicgstab" else G.gko_solve_gmres
+        for rep in range(2):
+            x = torch.zeros_like(ones)
+            torch.cuda.synchronize()
+            if rep == 1:
+                torch.cuda.nvtx.range_push("profile_solvers")
+            t0 = time.perf_counter()
+            r = fn(M, bd, x, 0.0, iters)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if rep == 1:
+                torch.cuda.nvtx.range_pop()
+        out[solver] = {"n": int(A.n_rows), "iterations": int(r.iterations), "ms": round(dt * 1e3, 3)}
+        del M, A, ones, bd, x
+    print(json.dumps(out))
+
+
 def run_ours(args):
     import torch
 
@@ -976,9 +1010,14 @@ def main():
     ap.add_argument("--profile-cases", action="store_true",
                     help="run each SpMV case once (for ncu) and print the case order")
     ap.add_argument("--small", action="store_true", help="with --profile-cases: 27-point stencil at 96^3")
+    ap.add_argument("--profile-solvers", action="store_true",
+                    help="short BiCGSTAB and GMRES(30) solves at 128^3 inside an NVTX range (for ncu)")
     args = ap.parse_args()
     if args.profile_cases:
         profile_cases(args)
+        return
+    if args.profile_solvers:
+        profile_solvers(args)
         return
     if args.impl == "reference":
         run_reference(args)
