@@ -802,35 +802,39 @@ def profile_cases(args):
     print(json.dumps([[c["label"], c["launches"], int(c["bytes"]), c["nnz"]] for c in cases]))
 
 def profile_solvers(args):
-    """Short fixed-work solves for ncu launch lists: BiCGSTAB (40 iterations,
-    convection-diffusion 128^3, cell Peclet 1) and GMRES(30) (one restart
-    cycle, Peclet 10), FP64, tolerance 0; each runs once untimed, then once
-    inside the NVTX range "profile_solvers"."""
+    """Short fixed-work solves for ncu launch lists, convection-diffusion
+    128^3, tolerance 0: BiCGSTAB FP64 (40 iterations, cell Peclet 1),
+    BiCGSTAB mixed FP32 (one refinement step of 40 inner iterations, Peclet 1)
+    and GMRES(30) FP64 (one restart cycle, Peclet 10); each runs once
+    untimed, then once inside the NVTX range "profile_solvers"."""
     import torch
     from paper_2006_14290_gb300 import gko as G
     from paper_2006_14290_gb300 import inputs as I
 
     G.load()
     out = {}
-    for solver, P, iters in (("bicgstab", 1.0, 40), ("gmres", 10.0, 30)):
+    runs = (("bicgstab", 1.0, 40, None), ("bicgstab_mixed_f32", 1.0, 40, G.PRECISION_MIXED_F32),
+            ("gmres", 10.0, 30, None))
+    for tag, P, iters, prec in runs:
         A = I.convdiff3d_7pt(128, P)
         M = G.from_csr(A)
         ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
         bd = torch.zeros_like(ones)
         G.gko_spmv(1.0, M, ones, 0.0, bd)
-        fn = G.gko_solve_bicgstab if solver == "bicgstab" else G.gko_solve_gmres
+        fn = G.gko_solve_gmres if tag == "gmres" else G.gko_solve_bicgstab
+        o = G.opts(precision=prec, inner_maxit=iters, max_outer=1) if prec is not None else None
         for rep in range(2):
             x = torch.zeros_like(ones)
             torch.cuda.synchronize()
             if rep == 1:
                 torch.cuda.nvtx.range_push("profile_solvers")
             t0 = time.perf_counter()
-            r = fn(M, bd, x, 0.0, iters)
+            r = fn(M, bd, x, 0.0, iters, o) if o is not None else fn(M, bd, x, 0.0, iters)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             if rep == 1:
                 torch.cuda.nvtx.range_pop()
-        out[solver] = {"n": int(A.n_rows), "iterations": int(r.iterations), "ms": round(dt * 1e3, 3)}
+        out[tag] = {"n": int(A.n_rows), "iterations": int(r.iterations), "ms": round(dt * 1e3, 3)}
         del M, A, ones, bd, x
     print(json.dumps(out))
 
