@@ -59,26 +59,29 @@ struct BatchArgs {
 __device__ __forceinline__ double ldv(const double* v, int64_t k) { return v[k]; }
 __device__ __forceinline__ double ldv(const float* v, int64_t k) { return widen(v[k]); }
 
-// Sum over a block of THREADS threads, result in every thread: warps reduce
-// by shuffles, warp 0 adds the warp sums (not every thread) and shares the
-// total.  Two barriers: a call's warp sums are written after every thread
-// has passed the previous call's last barrier (so warp 0 has read the old
-// ones), and the new total is written after this call's first barrier (so
-// every thread has read the old total).
-template <int THREADS>
-__device__ __forceinline__ double block_allsum(double v, double* red) {
-  constexpr int NW = THREADS / kWarp;
-  v = subwarp_sum<32>(v, 0xffffffffu);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[w] = v;
+// Sum over a block of THREADS threads, after which one thread derives the
+// step's scalars from the total: every thread stores its partial, warp 0
+// adds them (lane l the partials l, l + 32, ..., then a 5-step shuffle) and
+// its lane 0 runs fin(total, out), writing out[0..3] = red[THREADS ..
+// THREADS + 3], which every thread reads after the second barrier.  On
+// GB300's narrow FP64 pipe this matters: one warp adds the partials instead
+// of every warp running its own shuffle tree, and the divisions and square
+// roots of the CG step run once per block, not once per warp.  Barriers: the
+// partials are written after every thread passed the previous call's last
+// barrier (warp 0 has read the old ones and every thread the old out[]).
+template <int THREADS, typename F>
+__device__ __forceinline__ const double* block_sum_fin(double v, double* red, F fin) {
+  red[threadIdx.x] = v;
   __syncthreads();
-  if (w == 0) {
-    double t = lane < NW ? red[lane] : 0.0;
-    t = subwarp_sum<NW>(t, 0xffffffffu);
-    if (lane == 0) red[NW] = t;
+  if (threadIdx.x < kWarp) {
+    double t = red[threadIdx.x];
+#pragma unroll
+    for (int j = 1; j < THREADS / kWarp; ++j) t += red[j * kWarp + threadIdx.x];
+    t = subwarp_sum<32>(t, 0xffffffffu);
+    if (threadIdx.x == 0) fin(t, red + THREADS);
   }
   __syncthreads();
-  return red[NW];
+  return red + THREADS;
 }
 
 // One CG solve by a group of G threads (G = THREADS: a block; G = 32: a
@@ -98,9 +101,24 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   const int K = ELL ? a.ell_k[sys] : 0;
   const double* b = a.b + r0;
   double* x = a.x + r0;
+  // group sum; fin(total, out) derives the step's scalars from it (once per
+  // block for a block group, in every lane of a warp group)
+  struct Scal {
+    double o[4];
+  };
+  auto gstep = [&](double v, auto fin) -> Scal {
+    Scal sc;
+    if (G == kWarp) {
+      fin(subwarp_sum<32>(v, 0xffffffffu), sc.o);
+    } else {
+      const double* o = block_sum_fin<THREADS>(v, red, fin);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sc.o[j] = o[j];
+    }
+    return sc;
+  };
   auto gsum = [&](double v) -> double {
-    if (G == kWarp) return subwarp_sum<32>(v, 0xffffffffu);
-    return block_allsum<THREADS>(v, red);
+    return gstep(v, [](double t, double* o) { o[0] = t; }).o[0];
   };
   auto gsync = [&]() {
     if (G == kWarp) __syncwarp();
@@ -152,12 +170,15 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
       q[i] = qi;
       pq += p[i] * qi;
     }
-    pq = gsum(pq);
-    if (!(pq > 0.0)) {
+    const Scal sp = gstep(pq, [&](double t, double* o) {
+      o[0] = t > 0.0 ? 1.0 : 0.0;
+      o[1] = rho / t;
+    });
+    if (sp.o[0] == 0.0) {
       status = kBBreak;
       break;
     }
-    const double alpha = rho / pq;
+    const double alpha = sp.o[1];
     double rn = 0.0;
     for (int i = lane; i < n; i += G) {
       x[i] = __fma_rn(alpha, p[i], x[i]);
@@ -165,9 +186,15 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
       r[i] = ri;
       rn += ri * ri;
     }
-    double rho_new = gsum(rn);
+    const Scal sr = gstep(rn, [&](double t, double* o) {
+      o[0] = t;
+      o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
+      o[2] = t / rho;
+    });
+    double rho_new = sr.o[0];
+    double beta = sr.o[2];
     ++it;
-    if (sqrt(rho_new) <= tol) {
+    if (sr.o[1] != 0.0) {
       // true residual b - A x (x staged through q)
       gsync();
       for (int i = lane; i < n; i += G) q[i] = x[i];
@@ -178,15 +205,20 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
         r[i] = ti;
         tt += ti * ti;
       }
-      tt = gsum(tt);
-      res = sqrt(tt) / nb;
-      if (sqrt(tt) <= tol) {
+      const Scal st = gstep(tt, [&](double t, double* o) {
+        o[0] = sqrt(t) / nb;
+        o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
+        o[2] = t;
+        o[3] = t / rho;
+      });
+      res = st.o[0];
+      if (st.o[1] != 0.0) {
         status = kBOk;
         break;
       }
-      rho_new = tt;  // residual replacement
+      rho_new = st.o[2];  // residual replacement
+      beta = st.o[3];
     }
-    const double beta = rho_new / rho;
     rho = rho_new;
     for (int i = lane; i < n; i += G) p[i] = __fma_rn(beta, p[i], r[i]);
     gsync();
@@ -218,7 +250,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
 template <int THREADS, typename VT, bool ELL>
 __global__ void __launch_bounds__(THREADS) batch_cg_kernel(BatchArgs a, int block_rows) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ double red[THREADS / kWarp + 1];  // warp sums + the block total
+  __shared__ double red[THREADS + 4];  // partials + the step's scalars
   __shared__ int item_s;
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(a.queue, 1u);
