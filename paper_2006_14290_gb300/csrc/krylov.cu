@@ -211,7 +211,7 @@ struct InitOp {
 // c1 receives z = d * r when the Jacobi inverse diagonal d is given (CG's
 // first direction), else a copy of r.
 template <typename T>
-__global__ void __launch_bounds__(256) init_residual_kernel(int64_t n, const double* __restrict__ b,
+__global__ void __launch_bounds__(256, 4) init_residual_kernel(int64_t n, const double* __restrict__ b,
                                                             const T* __restrict__ q, T* __restrict__ r, T* c1, T* c2,
                                                             T* z1, T* z2, RedWs ws, InitOp op,
                                                             const T* __restrict__ d = nullptr) {
@@ -251,7 +251,7 @@ struct TrueResOp {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) true_res_kernel(int64_t n, const double* __restrict__ b, T* __restrict__ q,
+__global__ void __launch_bounds__(256, 4) true_res_kernel(int64_t n, const double* __restrict__ b, T* __restrict__ q,
                                                        RedWs ws, TrueResOp op, const T* __restrict__ d = nullptr) {
   double acc[2] = {0.0, 0.0};
   GKO_GRID_LOOP(i, n) {
@@ -273,7 +273,7 @@ struct Store2 {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) dot2_kernel(int64_t n, const T* __restrict__ w, const T* __restrict__ y,
+__global__ void __launch_bounds__(256, 4) dot2_kernel(int64_t n, const T* __restrict__ w, const T* __restrict__ y,
                                                    RedWs ws, double* out, const int* gate) {
   if (gated(gate)) return;
   double acc[2] = {0.0, 0.0};
@@ -319,7 +319,7 @@ struct CgUpdateOp {
 // alpha = rho / (p.q); x += alpha p; r -= alpha q; reduces r.r and, with
 // the Jacobi inverse diagonal d (PC), r.z for z = d r.
 template <typename T, bool PC>
-__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
+__global__ void __launch_bounds__(256, 4) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
                                                         const T* __restrict__ p, const T* __restrict__ q, Ctl* c,
                                                         RedWs ws, const T* __restrict__ d) {
   constexpr int NV = PC ? 2 : 1;
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict
 
 // p = z + beta p, z = d r with the Jacobi inverse diagonal (PC), else r
 template <typename T, bool PC>
-__global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c,
+__global__ void __launch_bounds__(256, 4) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c,
                                                    const T* __restrict__ d) {
   if (gated(&c->done)) return;
   const Lin<T> bp = block_bcast<Lin<T>>([&] { return Lin<T>(c->beta); });
@@ -387,7 +387,7 @@ struct CgReplaceOp {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
                                                          const T* __restrict__ t, Ctl* c, RedWs ws,
                                                          const T* __restrict__ d = nullptr) {
   if (!*(volatile int*)&c->replace) return;
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) cg_replace_kernel(int64_t n, T* __restric
 // p = r + beta (p - omega v); with the Jacobi inverse diagonal d also the
 // preconditioned direction ph = d p (right preconditioning)
 template <typename T>
-__global__ void __launch_bounds__(256) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
                                                      const T* __restrict__ v, Ctl* c, const T* __restrict__ d = nullptr,
                                                      T* __restrict__ ph = nullptr) {
   if (gated(&c->done)) return;
@@ -447,7 +447,7 @@ struct BicgSOp {
 
 // alpha = rho_new / (rhat.v); s = r - alpha v; reduces s.s
 template <typename T>
-__global__ void __launch_bounds__(256) bicg_s_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ v,
+__global__ void __launch_bounds__(256, 4) bicg_s_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ v,
                                                      T* __restrict__ s, Ctl* c, RedWs ws,
                                                      const T* __restrict__ d = nullptr, T* __restrict__ sh = nullptr) {
   if (gated(&c->done)) return;
@@ -526,7 +526,7 @@ struct BicgXOp {
 // rhat.r.  In the half step only x += alpha p.  Right preconditioning: x
 // moves along ph = d p and sh = d s instead.
 template <typename T>
-__global__ void __launch_bounds__(256) bicg_x_kernel(int64_t n, T* __restrict__ x, const T* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) bicg_x_kernel(int64_t n, T* __restrict__ x, const T* __restrict__ p,
                                                      const T* __restrict__ s, const T* __restrict__ t,
                                                      T* __restrict__ r, const T* __restrict__ rh, Ctl* c, RedWs ws,
                                                      const T* __restrict__ ph = nullptr,
@@ -606,7 +606,7 @@ struct BicgRestartOp {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) bicg_restart_kernel(int64_t n, T* __restrict__ r, const T* __restrict__ rh,
+__global__ void __launch_bounds__(256, 4) bicg_restart_kernel(int64_t n, T* __restrict__ r, const T* __restrict__ rh,
                                                            T* __restrict__ p, T* __restrict__ v,
                                                            const T* __restrict__ t, Ctl* c, RedWs ws) {
   if (!*(volatile int*)&c->replace) return;
@@ -650,7 +650,7 @@ struct GmStartOp {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) gm_start_kernel(int64_t n, const double* __restrict__ b,
+__global__ void __launch_bounds__(256, 4) gm_start_kernel(int64_t n, const double* __restrict__ b,
                                                        const T* __restrict__ q, T* __restrict__ v0, Ctl* c, RedWs ws,
                                                        GmStartOp op) {
   if (gated(&c->done)) return;
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256) gm_start_kernel(int64_t n, const double* 
 
 // v = v * (1 / *den); den = &beta for v0, &H[(j+1), j] for v_{j+1}
 template <typename T>
-__global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict__ v, const double* den, Ctl* c) {
+__global__ void __launch_bounds__(256, 4) gm_scale_kernel(int64_t n, T* __restrict__ v, const double* den, Ctl* c) {
   if (gated(&c->phase)) return;
   const Lin<T> sc = block_bcast<Lin<T>>([&] { return Lin<T>(1.0 / *den); });
   GKO_GRID_LOOP(i, n) v[i] = sc.scale(v[i]);
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(256) gm_scale_kernel(int64_t n, T* __restrict_
 
 // gated multi-dot: partial sums of V_j . w for j <= jmax (blockIdx.y = j)
 template <typename T>
-__global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(256, 4) gm_multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ldv,
                                                           const T* __restrict__ w, double* __restrict__ partials,
                                                           Ctl* c, int pass) {
   if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t n, const T* __
   if (threadIdx.x == 0) partials[(int64_t)j * kMultiSlots + blockIdx.x] = sblk;
 }
 
-__global__ void __launch_bounds__(256) gm_multidot_finish_kernel(int g, const double* __restrict__ partials,
+__global__ void __launch_bounds__(256, 4) gm_multidot_finish_kernel(int g, const double* __restrict__ partials,
                                                                  double* __restrict__ h, int accumulate, Ctl* c,
                                                                  int pass) {
   if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
@@ -733,7 +733,7 @@ __device__ __forceinline__ T lin_apply(T hi, T lo, T x, T y) {
 }
 
 template <typename T, bool NORM>
-__global__ void __launch_bounds__(256) gm_axpy_kernel(int64_t n, int jcount, const double* __restrict__ h,
+__global__ void __launch_bounds__(256, 4) gm_axpy_kernel(int64_t n, int jcount, const double* __restrict__ h,
                                                       const T* __restrict__ V, int64_t ldv, T* __restrict__ w, Ctl* c,
                                                       RedWs ws, int pass) {
   __shared__ T s_hi[kMaxRestart + 1], s_lo[kMaxRestart + 1];
@@ -792,7 +792,7 @@ __global__ void gm_givens_kernel(int j, int m, const double* __restrict__ h1, co
 
 // v_{j+1} = w / h_{j+1,j} (skipped once the cycle has ended)
 template <typename T>
-__global__ void __launch_bounds__(256) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
+__global__ void __launch_bounds__(256, 4) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
                                                       Ctl* c) {
   if (gated(&c->phase)) return;
   const Lin<T> sc = block_bcast<Lin<T>>([&] { return Lin<T>(1.0 / c->rho); });
@@ -815,7 +815,7 @@ __global__ void gm_backsolve_kernel(int m, const double* __restrict__ H, const d
 // x += V y  (= x - sum_j ny_j V_j), then close the cycle: stop on breakdown,
 // otherwise the next cycle recomputes the true residual.
 template <typename T>
-__global__ void __launch_bounds__(256) gm_update_x_kernel(int64_t n, const double* __restrict__ ny,
+__global__ void __launch_bounds__(256, 4) gm_update_x_kernel(int64_t n, const double* __restrict__ ny,
                                                           const T* __restrict__ V, int64_t ldv, T* __restrict__ x,
                                                           Ctl* c) {
   __shared__ T s_hi[kMaxRestart + 1], s_lo[kMaxRestart + 1];
@@ -852,7 +852,7 @@ struct FinalOp {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) final_res_kernel(int64_t n, const double* __restrict__ b,
+__global__ void __launch_bounds__(256, 4) final_res_kernel(int64_t n, const double* __restrict__ b,
                                                         const T* __restrict__ q, RedWs ws, Ctl* c) {
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
@@ -875,7 +875,7 @@ __global__ void add_f32_kernel(int64_t n, double* __restrict__ x, const float* _
 // ================================================================ host ====
 
 static int vec_grid(int64_t n) {
-  const int64_t g = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 4));
   return (int)g;
 }
 
