@@ -263,6 +263,31 @@ def cfg1_suite(G, dev, stream, flush, cores):
     return out
 
 
+def fma_peak(G, dev, fp64=True):
+    """FMA rate of the GPU measured with the library's probe (gko_bench_fma:
+    8 register-resident FMA chains per thread, 8 resident 256-thread blocks
+    per SM): FMAs per second from the difference of two loop counts."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n = sms * 8 * 256
+    t = torch.ones(n, dtype=torch.float64 if fp64 else torch.float32, device=dev)
+    lo, hi = (1024, 3072) if fp64 else (16384, 49152)
+    G.gko_bench_fma(t, lo)
+    best = {}
+    for loops in (lo, hi):
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.gko_bench_fma(t, loops)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        best[loops] = min(ts)
+    return 8.0 * n * (hi - lo) / ((best[hi] - best[lo]) * 1e-3)
+
+
 def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     """Krylov solves to 1e-8 relative residual, FP64 vs mixed precision:
     CG on the 7-point Poisson problem 256^3 (b = A*1) and BiCGSTAB / GMRES(30)
@@ -277,6 +302,11 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     from paper_2006_14290_gb300 import inputs as I
 
     out = {}
+    fp64_fma = fma_peak(G, dev)
+    hbm_peak, _ = measured_peaks()
+    out["fp64_fma_peak"] = {"fma_per_s": round(fp64_fma, -8), "tflops": round(2 * fp64_fma / 1e12, 3),
+                            "how": "gko_bench_fma, 8 FMA chains per thread, 8 blocks of 256 per SM, "
+                                   "difference of 3072 and 1024 loops"}
     if oracle_cores:
         O.lib()
         O.set_threads(oracle_cores)
@@ -308,10 +338,25 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
         per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver] + (2 if pc else 0)
         spmvs = {"cg": 1, "bicgstab": 2, "gmres": 1}[solver]
         it_bytes = spmvs * (nnz * (sv + 4) + 4 * (n + 1) + 2 * vb * n) + per_vec_passes * vb * n
+        its = max(res.iterations, 1)
         out[tag] = {"status": int(res.status), "iterations": int(res.iterations),
                     "outer_iterations": int(res.outer_iterations), "rel_residual": float(res.rel_residual),
                     "time_ms": round(ms, 3), "wall_ms": round(wall * 1e3, 3), "solves_per_s": round(1e3 / ms, 3),
-                    "GB_s_per_iteration": round(it_bytes * max(res.iterations, 1) / (ms * 1e-3) / 1e9, 1)}
+                    "GB_s_per_iteration": round(it_bytes * its / (ms * 1e-3) / 1e9, 1),
+                    "frac_hbm": round(it_bytes * its / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        if prec == G.PRECISION_F64:
+            # FP64 FMAs per iteration: SpMV nnz; CG x, r, p updates and the
+            # p.q and r.r dots; BiCGSTAB p (2), s, x (2), r updates and five
+            # dots; GMRES(30) both Gram-Schmidt passes (a dot and an axpy
+            # per basis vector each, mean j + 1 = 15.5) and the norm;
+            # Jacobi: z = d r and r.z
+            fma_it = {"cg": nnz + 5 * n, "bicgstab": 2 * nnz + 12 * n, "gmres": nnz + 63 * n}[solver]
+            fma_it += 2 * n if pc else 0
+            t_fp64, t_hbm = fma_it / fp64_fma, it_bytes / (hbm_peak * 1e9)
+            out[tag].update({"fp64_fmas_per_iteration": int(fma_it),
+                             "frac_fp64": round(fma_it * its / (ms * 1e-3) / fp64_fma, 4),
+                             "bound": "fp64" if t_fp64 > t_hbm else "hbm",
+                             "frac_of_bound": round(max(t_fp64, t_hbm) * its / (ms * 1e-3), 4)})
         return ms
 
     def oracle_beside(tags, solver, A, b, sample_iters, pc=False, fp64_tag=None):
@@ -398,15 +443,14 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
         oracle_beside(["cg_varcoef128_jacobi_f64", "cg_varcoef128_jacobi_mixed_f32"], "cg", A, b_host, 12, pc=True)
         del b_host
     del A, M, ones, bd
-    out["batched_cg"] = batched_suite(G, dev, stream, oracle_cores)
+    out["batched_cg"] = batched_suite(G, dev, stream, oracle_cores, fp64_fma)
     return out
 
 
 # nominal FP64 rate of the part (2 FMA per SM per clock, 152 SMs, 2.07 GHz)
-FP64_TFLOPS_NOMINAL = 1.25
 
 
-def batched_suite(G, dev, stream, oracle_cores=0):
+def batched_suite(G, dev, stream, oracle_cores=0, fp64_fma=None):
     """4096 variable-coefficient 2D 5-point systems (sides log-uniform in
     [8, 64]) solved by batched CG to 1e-10 in one persistent graph-captured
     launch; FP64 and FP32 storage; schedule from the autotuner.  Work per
@@ -449,7 +493,8 @@ def batched_suite(G, dev, stream, oracle_cores=0):
         itd = it.astype(np.float64)
         nbytes = float(np.sum(itd * (nnzs * (sv + 4) + 4 * (rows + 1) + 16 * rows)))
         fmas = float(np.sum(itd * (nnzs + 5 * rows)))
-        fp64_frac = 2 * fmas / (ms * 1e-3) / (FP64_TFLOPS_NOMINAL * 1e12)
+        fp64_fma = fp64_fma or fma_peak(G, dev)
+        fp64_frac = fmas / (ms * 1e-3) / fp64_fma
         res[tag] = {"status": int(code), "time_ms": round(ms, 3), "systems_per_s": round(4096 / (ms * 1e-3), 1),
                     "schedule": tuned, "tuned_over": "warp rows {0,64,144,256} x threads {256,512,1024} x CSR/ELL",
                     "iterations_total": int(it.sum()), "iterations_max": int(it.max()),
@@ -457,7 +502,7 @@ def batched_suite(G, dev, stream, oracle_cores=0):
                     "GB_s": round(nbytes / (ms * 1e-3) / 1e9, 1),
                     "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
                     "frac_fp64": round(fp64_frac, 4),
-                    "fp64_peak": f"{FP64_TFLOPS_NOMINAL} TFLOP/s nominal (2 FMA/SM/clock x 152 SMs x 2.07 GHz)"}
+                    "fp64_peak": f"{2 * fp64_fma / 1e12:.3f} TFLOP/s measured (gko_bench_fma)"}
         del B
     if oracle_cores:
         import oracle as O
@@ -948,6 +993,7 @@ def run_ours(args):
                 for i in range(len(extra))]
 
     peak, peak_kind = measured_peaks()
+    fp64_fma = fma_peak(G, dev)
     dom = int(np.argmax(per_case_ms))
     dom_case = cases[dom]
     achieved = dom_case["bytes"] / (per_case_ms[dom] * 1e-3) / 1e9
@@ -969,10 +1015,14 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": dom_case["label"], "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes": int(dom_case["bytes"])},
-            "per_case": {c["label"]: {"ms": round(per_case_ms[i], 4),
-                                      "GB_s": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9, 1),
-                                      "frac": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9 / peak, 4)}
+            "per_case": {c["label"]: dict({"ms": round(per_case_ms[i], 4),
+                                           "GB_s": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9, 1),
+                                           "frac": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9 / peak, 4)},
+                                          **({"frac_fp64": round(c["nnz"] / (per_case_ms[i] * 1e-3) / fp64_fma, 4)}
+                                             if c["label"].endswith("/f64") else {}))
                          for i, c in enumerate(cases)},
+            "fp64_fma_peak": {"fma_per_s": round(fp64_fma, -8), "tflops": round(2 * fp64_fma / 1e12, 3),
+                              "note": "per_case frac_fp64 = nnz FMAs per SpMV / time / this rate (FP64 cases)"},
             "e2e": {"value": round(whole_job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(sum(c["x"].numel() * c["x"].element_size() for c in cases)),
                     "d2h_bytes_per_step": int(sum(c["y"].numel() * c["y"].element_size() for c in cases))},

@@ -482,6 +482,16 @@ GKO_API int gko_server_destroy(gko_server S);
 GKO_API int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dtype, int32_t inner_loops,
                                      void *data, int64_t n, void *stream);
 
+/* FMA throughput probe (no counterpart in the paper; it measures the FP64
+ * pipe that co-limits the FP64 kernels on this GPU).  data: `n` device values
+ * of `dtype` (F64 or F32), n a positive multiple of 256; each is one
+ * thread's seed.  Every thread runs 8 independent chains v = fma(v, a, b)
+ * (a = 1 - 2^-10, b = 2^-10; chain c starts at seed + c/8) for `inner_loops`
+ * steps in registers and overwrites its value with the sum of its chains.
+ * n * 8 * inner_loops FMAs per call; time two loop counts and subtract.
+ * Stream-ordered.  GKO_INVALID_ARG on bad sizes or dtype. */
+GKO_API int gko_bench_fma(gko_dtype dtype, int32_t inner_loops, void *data, int64_t n, void *stream);
+
 /* Failure-detection check (no counterpart in the paper): one warp waits on a
  * shared-memory barrier that nothing completes, through the bounded wait the
  * bulk-copy SpMV kernels use, for at most `cycles` clock cycles (1 .. 2^32).

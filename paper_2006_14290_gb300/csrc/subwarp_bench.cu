@@ -66,6 +66,31 @@ int launch_typed(int32_t S, int32_t impl, T* data, int64_t n, int32_t loops, cud
   return launch_impl<T, 2>(S, data, n, loops, s);
 }
 
+// FMA throughput probe: every thread runs 8 independent chains
+// v = fma(v, a, b) in registers (a = 1 - 2^-10, b = 2^-10, so each chain
+// tends to 1 and stays finite) and stores the sum of its chains.  No memory
+// traffic inside the loop, so the difference of two loop counts over the
+// difference of their times is the FMA pipe's rate; used to state FP64
+// fractions next to the HBM fractions (GB300's FP64 pipe co-limits the FP64
+// kernels).
+template <typename T>
+__global__ void __launch_bounds__(kBenchThreads) fma_chain_kernel(T* __restrict__ data, int loops) {
+  const int64_t i = (int64_t)blockIdx.x * kBenchThreads + threadIdx.x;
+  const T a = (T)0.9990234375, b = (T)0.0009765625;
+  T v[8];
+  const T x0 = data[i];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = x0 + (T)c * (T)0.125;
+  for (int it = 0; it < loops; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = fma(v[c], a, b);
+  }
+  T sum = (T)0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sum += v[c];
+  data[i] = sum;
+}
+
 // Failure-detection check of the bounded waits: one warp waits on an
 // mbarrier that nothing ever completes, through the same bounded wait the
 // bulk-copy pipelines use, but with a caller-given cycle limit.  The wait
@@ -113,4 +138,20 @@ extern "C" int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype
   if (dtype == GKO_F64) return launch_typed(subwarp, impl, static_cast<double*>(data), n, inner_loops, s);
   if (dtype == GKO_F32) return launch_typed(subwarp, impl, static_cast<float*>(data), n, inner_loops, s);
   return fail(GKO_INVALID_ARG, "dtype must be F64 or F32");
+}
+
+extern "C" int gko_bench_fma(gko_dtype dtype, int32_t inner_loops, void* data, int64_t n, void* stream) {
+  if (!data || n <= 0 || n % kBenchThreads != 0 || n / kBenchThreads > INT32_MAX || inner_loops < 0)
+    return fail(GKO_INVALID_ARG, "bad FMA benchmark arguments (n a positive multiple of 256)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned blocks = (unsigned)(n / kBenchThreads);
+  if (dtype == GKO_F64) {
+    fma_chain_kernel<double><<<blocks, kBenchThreads, 0, s>>>(static_cast<double*>(data), inner_loops);
+  } else if (dtype == GKO_F32) {
+    fma_chain_kernel<float><<<blocks, kBenchThreads, 0, s>>>(static_cast<float*>(data), inner_loops);
+  } else {
+    return fail(GKO_INVALID_ARG, "dtype must be F64 or F32");
+  }
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
 }

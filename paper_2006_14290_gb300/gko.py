@@ -80,6 +80,7 @@ SIGNATURES = {
     "gko_spmv_coo_noalloc": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, _P]),
     "gko_spmv_host": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P, _P, _P]),
     "gko_bench_subwarp_reduce": (C.c_int, [_I32, _I32, C.c_int, _I32, _P, C.c_int64, _P]),
+    "gko_bench_fma": (C.c_int, [C.c_int, _I32, _P, C.c_int64, _P]),
     "gko_diag_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
     "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
@@ -352,6 +353,16 @@ def gko_bench_subwarp_reduce(subwarp: int, impl: int, data, inner_loops: int, st
     dt = F64 if data.dtype == torch.float64 else F32
     _check(lib().gko_bench_subwarp_reduce(subwarp, impl, dt, inner_loops, _dptr(data), data.numel(),
                                           _stream(stream)), "gko_bench_subwarp_reduce")
+    return data
+
+
+def gko_bench_fma(data, inner_loops: int, stream=None):
+    """FMA throughput probe on a float64/float32 CUDA tensor (length a
+    multiple of 256), in place: 8 * numel * inner_loops FMAs."""
+    import torch
+
+    dt = F64 if data.dtype == torch.float64 else F32
+    _check(lib().gko_bench_fma(dt, inner_loops, _dptr(data), data.numel(), _stream(stream)), "gko_bench_fma")
     return data
 
 

@@ -31,3 +31,31 @@ def test_subwarp_reduce_rejects_bad_arguments(gko):
             G.gko_bench_subwarp_reduce(S, impl, t, 1)
     with pytest.raises(G.GkoError):
         G.gko_bench_subwarp_reduce(4, 0, dev(np.zeros(100)), 1)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_fma_probe_runs_the_stated_recurrence(gko, dt):
+    """gko_bench_fma: 8 chains v <- v*a + b per thread (a = 1 - 2^-10,
+    b = 2^-10, chain c from seed + c/8), the sum stored; checked against
+    the same recurrence on the host (fused vs unfused rounding: a
+    tolerance of a few units in the last place per step)."""
+    G = gko
+    rng = np.random.default_rng(5)
+    seeds = rng.uniform(-4, 4, 512)
+    loops = 37
+    npt = np.float64 if dt == "f64" else np.float32
+    t = dev(seeds) if dt == "f64" else dev(seeds, np.float32)
+    G.gko_bench_fma(t, loops)
+    s0 = seeds.astype(npt)
+    a, b = npt(0.9990234375), npt(0.0009765625)
+    want = np.zeros(512, np.float64)
+    for c in range(8):
+        v = (s0 + npt(c) * npt(0.125)).astype(npt)
+        for _ in range(loops):
+            v = (v * a + b).astype(npt)
+        want += v.astype(np.float64)
+    got = host(t).astype(np.float64)
+    tol = 1e-12 if dt == "f64" else 2e-4
+    np.testing.assert_allclose(got, want, rtol=tol, atol=tol)
+    with pytest.raises(G.GkoError):
+        G.gko_bench_fma(dev(np.zeros(100)), 1)
