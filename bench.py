@@ -884,6 +884,40 @@ def profile_solvers(args):
     print(json.dumps(out))
 
 
+def profile_batch(args):
+    """The 4,096-system batched CG (FP64 storage, schedule 512 threads per
+    block, warp threshold 0, CSR: the autotuner's choice on this workload)
+    once untimed, then once inside the NVTX range "profile_batch", for ncu."""
+    import torch
+    from paper_2006_14290_gb300 import gko as G
+    from paper_2006_14290_gb300 import inputs as I
+
+    G.load()
+    sides = I.batch_sides(4096)
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, int(sd))
+        systems.append(A)
+        bs.append(b)
+    b = torch.from_numpy(np.concatenate(bs)).cuda()
+    B = G.Batch(systems, storage=G.F64)
+    B.set_schedule(0, 512, G.BATCH_CSR)
+    out = {}
+    for rep in range(2):
+        x = torch.zeros(B.total_rows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        if rep == 1:
+            torch.cuda.nvtx.range_push("profile_batch")
+        t0 = time.perf_counter()
+        code, it, rr, st = B.cg(b, x, 1e-10, 20000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if rep == 1:
+            torch.cuda.nvtx.range_pop()
+        out = {"status": int(code), "iterations_total": int(it.sum()), "ms": round(dt * 1e3, 3)}
+    print(json.dumps(out))
+
+
 def run_ours(args):
     import torch
 
@@ -1064,6 +1098,8 @@ def main():
     ap.add_argument("--profile-cases", action="store_true",
                     help="run each SpMV case once (for ncu) and print the case order")
     ap.add_argument("--small", action="store_true", help="with --profile-cases: 27-point stencil at 96^3")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run the batched CG once inside an NVTX range (for ncu)")
     ap.add_argument("--profile-solvers", action="store_true",
                     help="short BiCGSTAB and GMRES(30) solves at 128^3 inside an NVTX range (for ncu)")
     args = ap.parse_args()
@@ -1072,6 +1108,9 @@ def main():
         return
     if args.profile_solvers:
         profile_solvers(args)
+        return
+    if args.profile_batch:
+        profile_batch(args)
         return
     if args.impl == "reference":
         run_reference(args)
