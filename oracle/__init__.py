@@ -82,6 +82,8 @@ _SIGS = {
     "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
     "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
                                  C.POINTER(_Result)]),
+    "or_solve_reliable": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _I32, _P, _P, _D, _I32, _D,
+                                    C.POINTER(_Result)]),
 }
 
 
@@ -378,6 +380,25 @@ def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
     else:
         lib().or_solve_ir(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(b), _p(x), tol,
                           max_outer, inner_tol, inner_maxit, restart, int(adaptive), C.byref(res))
+    return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
+
+
+def solve_reliable(solver: int, A, b, x0=None, tol=1e-8, maxit=5000, delta=0.1, f32=True, jacobi=False):
+    """CG / BiCGSTAB with reliable updates: recurrences on FP32 values with
+    FP32-stored vectors (f32=False: the FP64 matrix and FP64 vectors), the
+    partial solution folded into the FP64 x and the recurrence residual
+    replaced by the FP64 residual b - A x whenever the recurrence residual
+    meets tol ||b|| or drops below delta times its largest value since the
+    last update.  outer_iterations counts the updates.  Returns (x,
+    SolveResult)."""
+    rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
+    val32 = val.astype(np.float32) if f32 else None
+    minv = jacobi_inv(A) if jacobi else None
+    x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    res = _Result()
+    lib().or_solve_reliable(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32) if f32 else None,
+                            _p(minv) if jacobi else None, int(bool(f32)), _p(b), _p(x), tol, maxit, delta,
+                            C.byref(res))
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
 
 

@@ -888,3 +888,223 @@ static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col
   *out = res;
   return res.status;
 }
+
+/* ------------------------------------------- reliable-update refinement -- */
+
+/* Mixed precision with reliable updates: the Krylov recurrences of CG or
+ * BiCGSTAB run on the inner operator (FP32 values with FP32 accumulation
+ * when val32 is given, else the FP64 matrix) with every vector stored in the
+ * inner precision (f32 != 0: rounded to FP32), FP64 dots and FP64 scalars;
+ * the iterate's change since the last update is kept in y.  When the
+ * recurrence residual drops to tol ||b||, or below delta times its largest
+ * value since the last update, an update folds y into the FP64 solution x
+ * (x += y, y = 0), forms the FP64 residual b - A x with the FP64 matrix and
+ * replaces the recurrence residual by it (rounded to the inner precision);
+ * the solve has converged when that FP64 residual meets tol ||b||, and
+ * otherwise the recurrences go on with their directions and scalars kept.
+ * Sources: Sleijpen & van der Vorst, "Reliable updated residuals in hybrid
+ * Bi-CG methods", Computing 56 (1996) (the delta criterion and the folding of
+ * the partial solution); van der Vorst & Ye, SIAM J. Sci. Comput. 22 (2000)
+ * (replacing the recurrence residual by the true one without restarting);
+ * Clark et al., Comput. Phys. Commun. 181 (2010) (the low precision for the
+ * recurrences, the high precision for x and the replaced residual).
+ * Readings: BiCGSTAB's half step (||s|| <= tol ||b||: y += alpha p, update)
+ * has no continuation for its s, so an unconverged half-step update restarts
+ * the recurrences (p = v = 0, rho = alpha = omega = 1) as the plain solver
+ * does; after an update BiCGSTAB takes rho from rhat and the replaced r (its
+ * next step's beta uses it), CG takes rho = r.z of the replaced r; omega == 0
+ * is a breakdown once the step's update test has passed.  outer_iterations
+ * counts the updates. */
+static void fold_and_replace(const or_op *A64, int f32, const double *b, double *x, double *y, double *w,
+                             double *tmp, double *rn) {
+  int64_t n = A64->n;
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] += y[i];
+    y[i] = 0.0;
+  }
+  residual(A64, b, x, w, tmp);
+  *rn = nrm2(n, w);
+  for (int64_t i = 0; i < n; ++i) w[i] = st(f32, w[i]);
+}
+
+static or_result reliable_core(const or_ctx *c, const or_op *A64, int solver, const double *b, double *x,
+                               double tol, int32_t maxit, double delta) {
+  const or_op *A = c->A;
+  int64_t n = A->n;
+  size_t sz = (size_t)n + 1;
+  or_result res = {OR_OK, 0, 0, 0, 0.0};
+  double *y = calloc(sz, 8), *r = calloc(sz, 8), *w = calloc(sz, 8), *tmp = calloc(sz, 8);
+  double *p = calloc(sz, 8), *q = calloc(sz, 8), *z = calloc(sz, 8);
+  double *rh = calloc(sz, 8), *s = calloc(sz, 8), *t = calloc(sz, 8), *ph = calloc(sz, 8), *sh = calloc(sz, 8);
+  double nb = nrm2(n, b), rn = 0.0;
+  int converged = 0, updates = 0;
+  int32_t it = 0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    converged = 1;
+    goto done;
+  }
+  fold_and_replace(A64, c->f32, b, x, y, w, tmp, &rn);
+  converged = rn <= tol * nb;
+  for (int64_t i = 0; i < n; ++i) r[i] = w[i];
+  double maxrr = rn;
+  if (solver == OR_SOLVER_CG) {
+    precond(c, r, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    double rho = dot(n, r, z);
+    while (!converged && it < maxit) {
+      op_apply(A, p, q);
+      for (int64_t i = 0; i < n; ++i) q[i] = st(c->f32, q[i]);
+      double pq = dot(n, p, q);
+      if (!(pq > 0.0)) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+      double alpha = rho / pq;
+      for (int64_t i = 0; i < n; ++i) {
+        y[i] = st(c->f32, y[i] + alpha * p[i]);
+        r[i] = st(c->f32, r[i] - alpha * q[i]);
+      }
+      ++it;
+      double nr = nrm2(n, r);
+      hist_put(c, it, nr / nb);
+      if (nr > maxrr) maxrr = nr;
+      if (nr <= tol * nb || nr < delta * maxrr) {
+        fold_and_replace(A64, c->f32, b, x, y, w, tmp, &rn);
+        ++updates;
+        if (rn <= tol * nb) {
+          converged = 1;
+          break;
+        }
+        for (int64_t i = 0; i < n; ++i) r[i] = w[i];
+        maxrr = rn;
+      }
+      precond(c, r, z);
+      double rho_new = dot(n, r, z);
+      double beta = rho_new / rho;
+      for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, z[i] + beta * p[i]);
+      rho = rho_new;
+    }
+  } else {
+    for (int64_t i = 0; i < n; ++i) rh[i] = r[i];
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    while (!converged && it < maxit) {
+      double rho_new = dot(n, rh, r);
+      if (rho_new == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+      double beta = (rho_new / rho) * (alpha / omega);
+      for (int64_t i = 0; i < n; ++i) p[i] = st(c->f32, r[i] + beta * (p[i] - omega * q[i]));
+      precond(c, p, ph);
+      op_apply(A, ph, q); /* q holds v = A M^-1 p */
+      for (int64_t i = 0; i < n; ++i) q[i] = st(c->f32, q[i]);
+      double rv = dot(n, rh, q);
+      if (rv == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+      alpha = rho_new / rv;
+      for (int64_t i = 0; i < n; ++i) s[i] = st(c->f32, r[i] - alpha * q[i]);
+      ++it;
+      double ns = nrm2(n, s);
+      if (ns <= tol * nb) { /* half step */
+        for (int64_t i = 0; i < n; ++i) y[i] = st(c->f32, y[i] + alpha * ph[i]);
+        hist_put(c, it, ns / nb);
+        fold_and_replace(A64, c->f32, b, x, y, w, tmp, &rn);
+        ++updates;
+        if (rn <= tol * nb) {
+          converged = 1;
+          break;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+          r[i] = w[i];
+          p[i] = q[i] = 0.0;
+        }
+        rho = alpha = omega = 1.0;
+        maxrr = rn;
+        continue;
+      }
+      precond(c, s, sh);
+      op_apply(A, sh, t);
+      for (int64_t i = 0; i < n; ++i) t[i] = st(c->f32, t[i]);
+      double tt = dot(n, t, t);
+      if (tt == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+      omega = dot(n, t, s) / tt;
+      for (int64_t i = 0; i < n; ++i) {
+        y[i] = st(c->f32, y[i] + alpha * ph[i] + omega * sh[i]);
+        r[i] = st(c->f32, s[i] - omega * t[i]);
+      }
+      rho = rho_new;
+      double nr = nrm2(n, r);
+      hist_put(c, it, nr / nb);
+      if (nr > maxrr) maxrr = nr;
+      if (nr <= tol * nb || nr < delta * maxrr) {
+        fold_and_replace(A64, c->f32, b, x, y, w, tmp, &rn);
+        ++updates;
+        if (rn <= tol * nb) {
+          converged = 1;
+          break;
+        }
+        for (int64_t i = 0; i < n; ++i) r[i] = w[i];
+        maxrr = rn;
+      }
+      if (omega == 0.0) {
+        res.status = OR_BREAKDOWN;
+        break;
+      }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) x[i] += y[i];
+  res.iterations = it;
+  res.outer_iterations = updates;
+  if (res.status == OR_OK && !converged) res.status = OR_NOT_CONVERGED;
+done:
+  if (nb == 0.0) {
+    res.rel_residual = 0.0;
+  } else {
+    residual(A64, b, x, w, tmp);
+    res.rel_residual = nrm2(n, w) / nb;
+  }
+  free(y);
+  free(r);
+  free(w);
+  free(tmp);
+  free(p);
+  free(q);
+  free(z);
+  free(rh);
+  free(s);
+  free(t);
+  free(ph);
+  free(sh);
+  return res;
+}
+
+/* CG or BiCGSTAB with reliable updates (above).  val32: FP32 values for the
+ * recurrences' operator (NULL: the FP64 matrix); f32: inner vectors stored
+ * in FP32; minv: Jacobi inverse diagonal (NULL: none), rounded to FP32 for
+ * the recurrences when f32 is set; x: x0 on entry, the solution on exit. */
+int or_solve_reliable(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                      const float *val32, const double *minv, int32_t f32, const double *b, double *x,
+                      double tol, int32_t maxit, double delta, or_result *out) {
+  if (solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) {
+    or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+    *out = bad;
+    return OR_INVALID;
+  }
+  or_op A64 = {n, rp, col, val, NULL};
+  or_op Ain = {n, rp, col, val32 ? NULL : val, val32};
+  double *m = NULL;
+  if (minv) {
+    m = calloc((size_t)n + 1, 8);
+    for (int64_t i = 0; i < n; ++i) m[i] = st(f32, minv[i]);
+  }
+  or_ctx c = {&Ain, f32 != 0, 0, NULL, 0, m};
+  *out = reliable_core(&c, &A64, solver, b, x, tol, maxit, delta);
+  free(m);
+  return out->status;
+}

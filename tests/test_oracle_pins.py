@@ -613,3 +613,76 @@ def test_ir_fixed_inner_tolerance_contracts_by_inner_tol():
     assert r4.status == r3.status == ra.status == 0
     assert r4.outer_iterations == 3 and r3.outer_iterations == 4, (r4, r3)
     assert ra.outer_iterations <= r4.outer_iterations
+
+
+# ------------------------------------------------- reliable-update solves --
+
+@pytest.mark.parametrize("solver", [O.CG, O.BICGSTAB])
+@pytest.mark.parametrize("N", [4, 8, 12])
+def test_reliable_fp64_without_updates_is_the_plain_solver(solver, N):
+    # FP64 operator and storage, delta = 0: the only update is the final check,
+    # and with x0 = 0 the folded partial solution is the plain solver's iterate,
+    # so iterations and x agree bit for bit with textbook CG / BiCGSTAB (pinned
+    # above against dense solves)
+    A = I.stencil3d_7pt(N) if solver == O.CG else I.convdiff3d_7pt(N, 3.0)
+    b = np.random.default_rng(N).uniform(-1, 1, A.n_rows)
+    x0, r0 = O.solve(solver, A, b, tol=1e-11, maxit=5000)
+    x1, r1 = O.solve_reliable(solver, A, b, tol=1e-11, maxit=5000, delta=0.0, f32=False)
+    assert r0.status == r1.status == 0
+    assert r1.iterations == r0.iterations and r1.outer_iterations == 1
+    np.testing.assert_array_equal(x1, x0)
+
+
+@pytest.mark.parametrize("solver,N,P", [(O.CG, 8, 0.0), (O.BICGSTAB, 8, 1.0), (O.BICGSTAB, 7, 10.0)])
+def test_reliable_mixed_reaches_fp64_accuracy(solver, N, P):
+    # FP32 values and vectors in the recurrences: the FP64 replacements still
+    # bring the true residual to 1e-12, and x agrees with a dense solve
+    A = I.varcoef3d_7pt(N, np.random.default_rng(2)) if solver == O.CG else I.convdiff3d_7pt(N, P)
+    b = np.random.default_rng(5).uniform(-1, 1, A.n_rows)
+    x, r = O.solve_reliable(solver, A, b, tol=1e-12, maxit=5000, delta=0.1)
+    assert r.status == 0 and r.rel_residual <= 1e-12 and r.outer_iterations >= 3
+    D = dense(A)
+    xd = np.linalg.solve(D, b)
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(x - xd) <= 10 * kappa * 1e-12 * np.linalg.norm(xd)
+
+
+def test_reliable_recurrences_are_fp32_and_updates_matter():
+    # the recurrences really run in FP32: with updates only when the FP32
+    # recurrence residual meets the tolerance (delta = 0), the true residual
+    # stalls far above 1e-12; the delta updates bring it there
+    A = I.varcoef2d_5pt(24, np.random.default_rng(3))
+    b = np.random.default_rng(4).uniform(-1, 1, A.n_rows)
+    x, r = O.solve_reliable(O.CG, A, b, tol=1e-12, maxit=3000, delta=0.0)
+    assert r.status == O.STATUS_NOT_CONVERGED and r.rel_residual > 1e-9
+    x, r = O.solve_reliable(O.CG, A, b, tol=1e-12, maxit=3000, delta=0.1)
+    assert r.status == 0 and r.rel_residual <= 1e-12 and r.outer_iterations >= 3
+    xd = np.linalg.solve(dense(A), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_reliable_jacobi_zero_rhs_and_x0():
+    A = I.varcoef3d_7pt(6, np.random.default_rng(7))
+    b = np.random.default_rng(8).uniform(-1, 1, A.n_rows)
+    xd = np.linalg.solve(dense(A), b)
+    for solver in (O.CG, O.BICGSTAB):
+        x, r = O.solve_reliable(solver, A, b, tol=1e-12, maxit=5000, delta=0.1, jacobi=True)
+        assert r.status == 0 and np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+        x, r = O.solve_reliable(solver, A, np.zeros(A.n_rows), x0=np.ones(A.n_rows))
+        assert r.status == 0 and r.iterations == 0 and np.all(x == 0)
+        x, r = O.solve_reliable(solver, A, b, x0=xd, tol=1e-8)
+        assert r.status == 0 and r.iterations == 0 and r.outer_iterations == 0
+    x, r = O.solve_reliable(O.CG, A, b, tol=1e-12, maxit=3)
+    assert r.status == O.STATUS_NOT_CONVERGED and r.iterations == 3
+
+
+@pytest.mark.parametrize("solver", [O.CG, O.BICGSTAB])
+def test_reliable_partial_solution_is_fp32_stored(solver):
+    # from x0 = 0 with no update before the iteration cap, x is the folded
+    # partial solution y, which the recurrences store in FP32
+    A = I.laplace2d_5pt(12) if solver == O.CG else I.convdiff3d_7pt(5, 5.0)
+    b = np.random.default_rng(11).uniform(-1, 1, A.n_rows)
+    x, r = O.solve_reliable(solver, A, b, tol=1e-14, maxit=4, delta=0.0)
+    assert r.status == O.STATUS_NOT_CONVERGED and r.outer_iterations == 0
+    np.testing.assert_array_equal(x.astype(np.float32).astype(np.float64), x)
+    assert np.any(x != 0)
