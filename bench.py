@@ -313,14 +313,15 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     if flush is not None:
         out["cfg1_laplace64"] = cfg1_suite(G, dev, stream, flush, oracle_cores or (os.cpu_count() or 1))
 
-    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0):
+    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0, refine=0):
         fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
         if solver == "bicgstab":
             maxit = 2000
         # the library's refinement defaults (GMRES: one restart cycle per step)
-        opts = G.opts(precision=prec, restart=restart, preconditioner=pc)
+        opts = G.opts(precision=prec, restart=restart, preconditioner=pc, refinement=refine)
         if tag == "bicgstab_convdiff128_mixed_f32":  # known not to converge: keep it short
             opts = G.opts(precision=prec, inner_maxit=500, max_outer=3)
+            maxit = 500
         xd = torch.zeros(n, dtype=torch.float64, device=dev)
         fn(M, bd, xd, tol, maxit, opts, stream=stream)  # warm-up (also builds the low-precision copy)
         xd.zero_()
@@ -389,7 +390,9 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     run("cg_poisson256_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
     run("cg_poisson256_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32)
     run("cg_poisson256_mixed_bf16", "cg", M, bd, n, nnz, G.PRECISION_MIXED_BF16)
+    run("cg_poisson256_mixed_f32_restart", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, refine=G.REFINE_RESTART)
     out["cg_poisson256_mixed_f32_speedup"] = speedup("cg_poisson256_f64", "cg_poisson256_mixed_f32")
+    out["cg_poisson256_mixed_f32_restart_speedup"] = speedup("cg_poisson256_f64", "cg_poisson256_mixed_f32_restart")
     # fixed work: 1,000 iterations (tolerance 0 never stops early)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
@@ -400,8 +403,8 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
                                             "iterations_per_s": round(res.iterations / dt, 1)}
     if oracle_cores:
         b_host = bd.cpu().numpy()
-        oracle_beside(["cg_poisson256_f64", "cg_poisson256_mixed_f32", "cg_poisson256_mixed_bf16"], "cg", A,
-                      b_host, 8)
+        oracle_beside(["cg_poisson256_f64", "cg_poisson256_mixed_f32", "cg_poisson256_mixed_bf16",
+                       "cg_poisson256_mixed_f32_restart"], "cg", A, b_host, 8)
         per_it = out["cg_poisson256_f64"]["oracle_ms"] / max(out["cg_poisson256_f64"]["iterations"], 1)
         out["cg_poisson256_1000_iterations"]["oracle_ms"] = round(per_it * 1000, 1)
         del b_host
@@ -422,7 +425,12 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
             run(f"{tag}_f64", solver, M, bd, n, nnz, G.PRECISION_F64)
             run(f"{tag}_mixed_f32", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32)
             out[f"{tag}_mixed_f32_speedup"] = speedup(f"{tag}_f64", f"{tag}_mixed_f32")
-            oracle_beside([f"{tag}_f64", f"{tag}_mixed_f32"], solver, A, b_host, 30 if solver == "gmres" else 12)
+            if solver == "bicgstab" and P == 1.0:  # the classic restarted refinement beside the default
+                run(f"{tag}_mixed_f32_restart", solver, M, bd, n, nnz, G.PRECISION_MIXED_F32,
+                    refine=G.REFINE_RESTART)
+                out[f"{tag}_mixed_f32_restart_speedup"] = speedup(f"{tag}_f64", f"{tag}_mixed_f32_restart")
+            oracle_beside([t for t in (f"{tag}_f64", f"{tag}_mixed_f32", f"{tag}_mixed_f32_restart") if t in out],
+                          solver, A, b_host, 30 if solver == "gmres" else 12)
         del A, M, ones, bd, b_host
     # Jacobi preconditioning on the variable-coefficient Poisson problem 128^3
     # (coefficients exp(N(0,1)) per cell, default_rng(0); b = A*1)

@@ -287,6 +287,32 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
 #define GKO_PRECISION_MIXED_F32 1  /* FP32 inner solve + FP64 refinement         */
 #define GKO_PRECISION_MIXED_BF16 2 /* BF16-valued inner SpMV + FP64 refinement   */
 
+/* How mixed precision recovers FP64 accuracy (opts->refinement).
+ * RESTART: iterative refinement; each step forms r = b - A x in FP64 and
+ *      solves A d = r from scratch with FP32 (or BF16-valued) A, FP32 vectors,
+ *      FP64 dots and scalars, then x += d in FP64 (Buttari et al. 2007).
+ * RELIABLE (CG, BiCGSTAB): one run of the Krylov recurrences on the FP32 copy
+ *      with FP32 vectors, FP64 dots and scalars, accumulating the iterate's
+ *      change d in FP32; whenever the recurrence residual meets rel_tol ||b||
+ *      or drops below reliable_delta times its largest norm since the last
+ *      update, d is added to the FP64 x, r is replaced by the FP64 residual
+ *      b - A x and the recurrences continue with their directions and
+ *      scalars (reliable updates: Sleijpen & van der Vorst, Computing 56,
+ *      1996; residual replacement without restart: van der Vorst & Ye, SIAM
+ *      J. Sci. Comput. 22, 2000).  BiCGSTAB restarts only after a half step
+ *      (||s|| small).  The solve converges when the replaced FP64 residual
+ *      meets rel_tol ||b||; outer_iterations counts the updates; inner_tol,
+ *      max_outer and inner_maxit are not used.  GMRES: GKO_NOT_SUPPORTED.
+ * AUTO (0): RELIABLE for BiCGSTAB and for CG with more than 2^18 rows;
+ *      RESTART for GMRES and for smaller CG systems (whose inner solves run
+ *      as one single-launch CG each).
+ * The FP32 (or BF16) copy of a CSR matrix with more than 2^18 rows whose
+ * rows are nearly equal in length (ELL padding at most 1.2 x nnz) is stored
+ * in ELL, which streams 4-byte values faster than the CSR kernels. */
+#define GKO_REFINE_AUTO 0
+#define GKO_REFINE_RESTART 1
+#define GKO_REFINE_RELIABLE 2
+
 /* Preconditioners (paper, Section 1 lists them beside the solvers; M =
  * diag(A), Saad, Iterative Methods for Sparse Linear Systems, Sec. 10.2).
  * JACOBI: CG becomes preconditioned CG (Saad Alg. 9.1) and BiCGSTAB is
@@ -308,6 +334,9 @@ typedef struct {
                            GMRES: 4 restart cycles per step)                    */
   int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */
   int32_t preconditioner; /* GKO_PRECOND_NONE or GKO_PRECOND_JACOBI (CG, BiCGSTAB) */
+  int32_t refinement;   /* mixed: GKO_REFINE_* (0: AUTO)                         */
+  int32_t reserved;     /* set to 0                                              */
+  double reliable_delta; /* RELIABLE: update factor in [0, 1) (0: 0.1)            */
 } gko_solve_opts;
 
 typedef struct {
@@ -337,11 +366,13 @@ typedef struct {
  *      the device; iterations count
  *      Arnoldi steps, outer_iterations restart cycles; each cycle starts
  *      from the true residual.
- * Mixed precision (opts->precision): x stays FP64; each refinement step
- *      forms r = b - A x in FP64, solves A d = r with the same method on an
+ * Mixed precision (opts->precision): x stays FP64 and the method runs on an
  *      FP32 (or BF16-valued) copy of A with FP32 vectors, FP64 dots and FP64
- *      scalars to ||r_inner|| <= inner_tol ||r||, and adds d in FP64, until
- *      ||b - A x|| <= rel_tol ||b|| or max_outer steps.
+ *      scalars, refined as opts->refinement says (GKO_REFINE_*).  RESTART:
+ *      each refinement step forms r = b - A x in FP64, solves A d = r to
+ *      ||r_inner|| <= inner_tol ||r|| and adds d in FP64, until
+ *      ||b - A x|| <= rel_tol ||b|| or max_outer steps.  Bad refinement or
+ *      reliable_delta: GKO_INVALID_ARG.
  * All scalars and convergence checks stay on the device; the host polls a
  * status word every few iterations.  *res is written before returning
  * (synchronises `stream`); opts may be NULL.  Returns res->status (GKO_OK,

@@ -44,6 +44,13 @@ struct Ctl {
   double rho, rho_new, alpha, beta, omega;
   double red[4];  // fused SpMV dots: red[0] = w.y, red[1] = y.y
   double rr;
+  // reliable updates (mixed precision): an update is due when the recurrence
+  // residual drops below delta times maxrr, its largest norm since the last
+  // update (delta = 0: only at convergence); half: the last check came from
+  // BiCGSTAB's half step
+  double maxrr, delta;
+  int half;
+  int pad2;
 };
 
 __device__ __forceinline__ double wd(double v) { return v; }
@@ -198,6 +205,8 @@ struct InitOp {
     }
     c->status = kRun;
     c->done = 0;
+    c->maxrr = sqrt(t[1]);
+    c->half = 0;
     if (kind == 0) {
       c->rho = t[2];
     } else if (kind == 1) {
@@ -285,6 +294,20 @@ __global__ void __launch_bounds__(256, 4) dot2_kernel(int64_t n, const T* __rest
   reduce_op<2>(acc, ws, Store2{out});
 }
 
+// Reliable-update test after a step with recurrence residual norm nr (mixed
+// precision only; delta = 0 disables it): nr raises maxrr, and nr below
+// delta * maxrr asks the host for an update (kCheck, as at convergence).
+__device__ __forceinline__ bool reliable_due(Ctl* c, double nr) {
+  if (!(c->delta > 0.0)) return false;
+  if (nr > c->maxrr) c->maxrr = nr;
+  if (nr < c->delta * c->maxrr) {
+    c->status = kCheck;
+    c->done = 1;
+    return true;
+  }
+  return false;
+}
+
 // ------------------------------------------------------------------- CG --
 
 // t[0] = r.r (convergence); with a preconditioner t[1] = r.z (the new rho)
@@ -301,11 +324,13 @@ struct CgUpdateOp {
     const double rho_new = t[NV - 1];
     c->iter += 1;
     c->rho_new = rho_new;
-    if (sqrt(t[0]) <= c->tol_abs) {
+    const double nr = sqrt(t[0]);
+    if (nr <= c->tol_abs) {
       c->status = c->check_true ? kCheck : kConverged;
       c->done = 1;
       return;
     }
+    if (reliable_due(c, nr)) return;
     if (c->iter >= c->maxit) {
       c->status = kNotConverged;
       c->done = 1;
@@ -489,10 +514,12 @@ struct BicgXOp {
   __device__ void operator()(const double (&t)[2]) const {
     if (c->phase) {  // half step: ||s|| small, x += alpha p was done
       c->phase = 0;
+      c->half = 1;
       c->status = c->check_true ? kCheck : kConverged;
       c->done = 1;
       return;
     }
+    c->half = 0;
     const double tt = c->red[1];
     if (tt == 0.0) {
       c->status = kBreakdown;
@@ -503,11 +530,13 @@ struct BicgXOp {
     c->omega = omega;
     c->rho = c->rho_new;
     c->rho_new = t[1];
-    if (sqrt(t[0]) <= c->tol_abs) {
+    const double nr = sqrt(t[0]);
+    if (nr <= c->tol_abs) {
       c->status = c->check_true ? kCheck : kConverged;
       c->done = 1;
       return;
     }
+    if (reliable_due(c, nr)) return;
     if (omega == 0.0 || (c->iter < c->maxit && c->rho_new == 0.0)) {
       c->status = kBreakdown;
       c->done = 1;
@@ -620,6 +649,106 @@ __global__ void __launch_bounds__(256, 4) bicg_restart_kernel(int64_t n, T* __re
   }
   reduce_op<1>(acc, ws, BicgRestartOp{c});
 }
+
+// ------------------------------------------------------ reliable updates --
+//
+// Mixed-precision CG / BiCGSTAB with reliable updates (Sleijpen & van der
+// Vorst 1996; residual replacement without restart as in van der Vorst & Ye
+// 2000): the recurrences run on the FP32 copy of A with FP32 vectors and
+// accumulate the iterate's change d; an update folds d into the FP64
+// solution and replaces the recurrence residual by the FP64 residual
+// b - A x, keeping the directions and scalars (BiCGSTAB restarts only after
+// its half step, whose s has no continuation).
+
+// x64 += d (exact widening), d = 0
+__global__ void __launch_bounds__(256, 4) fold_kernel(int64_t n, double* __restrict__ x64, float* __restrict__ d) {
+  GKO_GRID_LOOP(i, n) {
+    x64[i] += widen(d[i]);
+    d[i] = 0.0f;
+  }
+}
+
+// t[0] = ||b - A x||^2 (FP64), t[1] = rhat.r (BiCGSTAB) or r.z (CG) of the
+// replaced, rounded residual r.
+struct RelOp {
+  Ctl* c;
+  int solver;
+  int half;
+  __device__ void operator()(const double (&t)[2]) const {
+    const double rn = sqrt(t[0]);
+    c->phase = 0;
+    c->half = 0;
+    if (rn <= c->tol_abs) {
+      c->status = kConverged;
+      c->done = 1;
+      return;
+    }
+    c->maxrr = rn;
+    c->status = kRun;
+    c->done = 0;
+    if (solver == 0) {  // CG: cg_replace_kernel finishes (r = t, p = z + beta p)
+      if (c->iter >= c->maxit) {
+        c->status = kNotConverged;
+        c->done = 1;
+        return;
+      }
+      c->replace = 1;
+      c->rho_new = t[1];
+      return;
+    }
+    if (half) {  // BiCGSTAB after a half step: bicg_restart_kernel restarts
+      c->replace = 1;
+      return;
+    }
+    if (c->omega == 0.0) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    if (c->iter >= c->maxit) {
+      c->status = kNotConverged;
+      c->done = 1;
+      return;
+    }
+    c->rho_new = t[1];
+    if (t[1] == 0.0) {
+      c->status = kBreakdown;
+      c->done = 1;
+      return;
+    }
+    c->beta = (c->rho_new / c->rho) * (c->alpha / c->omega);
+  }
+};
+
+// dst = fl(b - q) with q = A64 x64; reduces ||b - q||^2 in FP64 and
+// w.dst (w = rhat for BiCGSTAB) or dst.(d dst) (CG, d the Jacobi diagonal
+// or none).
+template <typename T>
+__global__ void __launch_bounds__(256, 4) rel_replace_kernel(int64_t n, const double* __restrict__ b,
+                                                          const double* __restrict__ q, T* __restrict__ dst,
+                                                          const T* __restrict__ w, const T* __restrict__ d,
+                                                          RedWs ws, RelOp op) {
+  double acc[2] = {0.0, 0.0};
+  GKO_GRID_LOOP(i, n) {
+    const double ti = b[i] - q[i];
+    const T tr = (T)ti;
+    dst[i] = tr;
+    acc[0] = __fma_rn(ti, ti, acc[0]);
+    const double tw = wd(tr);
+    acc[1] = __fma_rn(w ? wd(w[i]) : tw, w ? tw : wd(d ? d[i] * tr : tr), acc[1]);
+  }
+  reduce_op<2>(acc, ws, op);
+}
+
+// What a reliable-update solve needs beyond the recurrences' operator.
+struct RelSpec {
+  const gko_matrix_s* A64;  // FP64 matrix for the replaced residuals
+  const double* b64;        // right-hand side
+  double* x64;              // FP64 solution (x0 on entry)
+  double* q64;              // n doubles of workspace
+  void* scratch;            // SpMV scratch of A64
+  double delta;
+};
 
 // ---------------------------------------------------------------- GMRES --
 
@@ -965,6 +1094,7 @@ struct SolveSpec {
   int check_true;
   int check_every;
   const void* minv = nullptr;  // Jacobi inverse diagonal (vector of T), or none
+  const RelSpec* rel = nullptr;  // reliable updates (FP32 recurrences only)
 };
 
 struct SolveOut {
@@ -1264,7 +1394,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_cg_kernel(SmallArgs<T, VT
 
 // Whether the single-launch CG serves this matrix (see above).
 static bool small_cg_ok(const gko_matrix_s* A, const SolveSpec& sp) {
-  if (sp.solver != 0 || A->fmt != GKO_CSR || A->plan.kind != 1 || A->n_rows <= 0 || A->n_rows > kSmallRows)
+  if (sp.solver != 0 || sp.rel || A->fmt != GKO_CSR || A->plan.kind != 1 || A->n_rows <= 0 || A->n_rows > kSmallRows)
     return false;
   int dev = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) !=
@@ -1394,6 +1524,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   Ctl init{};
   init.maxit = sp.maxit;
   init.check_true = sp.check_true;
+  init.delta = sp.rel ? sp.rel->delta : 0.0;
   GKO_TRY_CUDA(cudaMemcpyAsync(c, &init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   Ctl* hc = host_ctl();
   const int vg = vec_grid(n), rg = reduce_grid(n);
@@ -1472,7 +1603,10 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
     };
     // the first batch launches directly (it also initialises the launch
     // configuration caches); later batches replay one captured graph
-    const int graph_iters = sp.check_every > 0 ? sp.check_every : kGraphIters;
+    // reliable updates stop a batch early (its remaining kernels run gated
+    // off), so they poll every 8 iterations (BiCGSTAB on 128^3: 85 ms at 8,
+    // 89 ms at 16, 102 ms at 32)
+    const int graph_iters = sp.check_every > 0 ? sp.check_every : sp.rel ? 8 : kGraphIters;
     BatchGraph graph;
     bool first = true;
     while (!hc->done) {
@@ -1487,7 +1621,27 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           GKO_TRY(enqueue(graph_iters));
       }
       GKO_TRY(read_ctl(c, hc, s));
-      if (hc->status == kCheck) {  // verify with the true residual
+      if (hc->status == kCheck && sp.rel) {
+        if constexpr (std::is_same<T, float>::value) {
+          // reliable update: fold d into the FP64 x, replace r by b - A64 x
+          const RelSpec& rl = *sp.rel;
+          fold_kernel<<<vg, 256, 0, s>>>(n, rl.x64, x);
+          GKO_TRY_CUDA(cudaGetLastError());
+          GKO_TRY(spmv_run(rl.A64, rl.x64, rl.q64, 1.0, 0.0, s, rl.scratch, nullptr, nullptr));
+          const bool half = sp.solver == 1 && hc->half;
+          T* dst = (sp.solver == 1 && !half) ? r : q;
+          rel_replace_kernel<T><<<rg, 256, 0, s>>>(n, rl.b64, rl.q64, dst, sp.solver == 1 ? rh : nullptr,
+                                                   sp.solver == 0 ? dinv : nullptr, ws,
+                                                   RelOp{c, sp.solver, half ? 1 : 0});
+          if (sp.solver == 0)
+            cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
+          else if (half)
+            bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
+          GKO_TRY_CUDA(cudaGetLastError());
+          out->cycles += 1;
+          GKO_TRY(read_ctl(c, hc, s));
+        }
+      } else if (hc->status == kCheck) {  // verify with the true residual
         GKO_TRY(spmv(x, q, nullptr, nullptr));
         true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c}, sp.solver == 0 ? dinv : nullptr);
         if (sp.solver == 0)
@@ -1496,6 +1650,12 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
         GKO_TRY_CUDA(cudaGetLastError());
         GKO_TRY(read_ctl(c, hc, s));
+      }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (sp.rel) {  // what the recurrences moved since the last update
+        fold_kernel<<<vg, 256, 0, s>>>(n, sp.rel->x64, x);
+        GKO_TRY_CUDA(cudaGetLastError());
       }
     }
   } else {
@@ -1568,7 +1728,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   }
   out->status = hc->status;
   out->iterations = hc->iter;
-  out->cycles = hc->cycles;
+  if (sp.solver == 2) out->cycles = hc->cycles;  // CG / BiCGSTAB: reliable updates counted above
   return GKO_OK;
 }
 
@@ -1609,6 +1769,13 @@ static int map_status(int st) {
 }
 
 // Low-precision copy of A cached on the handle for mixed-precision solves.
+// A large CSR matrix whose rows are nearly equal in length (ELL padding at
+// most kInnerEllFill x nnz: stencils) gets its copy in ELL: with 4-byte values
+// the column-major ELL kernel streams the operator faster than the CSR
+// kernels (7-point 128^3 FP32 SpMV 30 us vs 41 us), while in FP64 the CSR
+// row-block kernel keeps up (CG on 7-point 256^3: 302 ms CSR, 314 ms ELL).
+// Systems small enough for the single-launch CG (CSR only) keep CSR.
+constexpr double kInnerEllFill = 1.2;
 static int lowp_copy(gko_matrix A, gko_dtype to, cudaStream_t s, gko_matrix* out) {
   std::lock_guard<std::mutex> lk(A->mu);
   auto it = A->lowp.find((int)to);
@@ -1617,7 +1784,18 @@ static int lowp_copy(gko_matrix A, gko_dtype to, cudaStream_t s, gko_matrix* out
     return GKO_OK;
   }
   gko_matrix m = nullptr;
-  GKO_TRY(gko_matrix_convert_values(A, to, s, &m));
+  if (A->fmt == GKO_CSR && A->n_rows > kSmallRows) {
+    gko_matrix e = nullptr;
+    const int rc = gko_matrix_convert_to_ell(A, kInnerEllFill, s, &e);
+    if (rc == GKO_OK) {
+      const int rc2 = gko_matrix_convert_values(e, to, s, &m);
+      gko_matrix_destroy(e);
+      GKO_TRY(rc2);
+    } else if (rc != GKO_FORMAT_UNSUITABLE) {
+      return rc;
+    }
+  }
+  if (!m) GKO_TRY(gko_matrix_convert_values(A, to, s, &m));
   A->lowp[(int)to] = m;
   *out = m;
   return GKO_OK;
@@ -1687,6 +1865,16 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   }
   if (o.precision != GKO_PRECISION_MIXED_F32 && o.precision != GKO_PRECISION_MIXED_BF16)
     return fail(GKO_INVALID_ARG, "unknown precision");
+  if (o.refinement != GKO_REFINE_AUTO && o.refinement != GKO_REFINE_RESTART && o.refinement != GKO_REFINE_RELIABLE)
+    return fail(GKO_INVALID_ARG, "unknown refinement");
+  if (o.refinement == GKO_REFINE_RELIABLE && solver == 2)
+    return fail(GKO_NOT_SUPPORTED, "GMRES refines by restarting (reliable updates are for CG and BiCGSTAB)");
+  if (!(o.reliable_delta >= 0.0 && o.reliable_delta < 1.0))
+    return fail(GKO_INVALID_ARG, "reliable_delta must lie in [0, 1)");
+  // AUTO: reliable updates for BiCGSTAB, and for CG where the single-launch
+  // small-system CG (which refines by restarting) does not apply
+  const bool reliable = o.refinement == GKO_REFINE_RELIABLE ||
+                        (o.refinement == GKO_REFINE_AUTO && (solver == 1 || (solver == 0 && n > kSmallRows)));
   gko_matrix A32 = nullptr;
   GKO_TRY(lowp_copy(A, o.precision == GKO_PRECISION_MIXED_F32 ? GKO_F32 : GKO_BF16, s, &A32));
   // mixed-precision iterative refinement: FP64 residual, FP32-stored inner solve
@@ -1720,6 +1908,34 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   int total_inner = 0, outer = 0;
   bool converged = nb == 0.0;
   if (nb == 0.0) zero_kernel<double><<<vg, 256, 0, s>>>(n, x);
+  if (reliable && !converged) {
+    // one run of the FP32 recurrences from fl32(b - A x); updates fold d into
+    // x and replace the recurrence residual until ||b - A x|| <= rel_tol ||b||
+    GKO_TRY(spmv_run(A, x, r, 1.0, 0.0, s, ss, nullptr, nullptr));
+    residual64_kernel<<<vg, 256, 0, s>>>(n, b, r);
+    GKO_TRY_CUDA(cudaGetLastError());
+    double nr = 0.0;
+    GKO_TRY(norm2_host(r, n, &nr, s));
+    if (nr <= rel_tol * nb) {
+      converged = true;
+    } else {
+      // r is read once to start the recurrences, then serves as the FP64
+      // product A x of every update
+      RelSpec rl{A, b, x, r, ss, o.reliable_delta > 0.0 ? o.reliable_delta : 0.1};
+      SolveSpec step = in;
+      step.rel = &rl;
+      step.check_true = 1;
+      step.maxit = max_iters;
+      step.rel_tol = rel_tol * nb / nr;
+      SolveOut so{};
+      GKO_TRY(krylov_core<float>(A32, r, d, true, step, s, &so));
+      res->iterations = so.iterations;
+      res->outer_iterations = so.cycles;
+      GKO_TRY(true_rel_residual(A, b, x, nb, &res->rel_residual, s));
+      res->status = map_status(so.status);
+      return res->status;
+    }
+  }
   while (!converged) {
     GKO_TRY(spmv_run(A, x, r, 1.0, 0.0, s, ss, nullptr, nullptr));
     residual64_kernel<<<vg, 256, 0, s>>>(n, b, r);

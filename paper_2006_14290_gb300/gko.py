@@ -23,6 +23,7 @@ OK, INVALID_ARG, OUT_OF_MEMORY, FORMAT_UNSUITABLE, NOT_CONVERGED, BREAKDOWN, TIM
 F64, F32, BF16 = 0, 1, 2
 CSR, ELL, COO, HYBRID, SELLP = 0, 1, 2, 3, 4
 PRECISION_F64, PRECISION_MIXED_F32, PRECISION_MIXED_BF16 = 0, 1, 2
+REFINE_AUTO, REFINE_RESTART, REFINE_RELIABLE = 0, 1, 2
 
 _lib = None
 _P = C.c_void_p
@@ -42,7 +43,8 @@ class GkoError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("precision", C.c_int32), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int32), ("inner_maxit", C.c_int32), ("check_every", C.c_int32),
-                ("preconditioner", C.c_int32)]
+                ("preconditioner", C.c_int32), ("refinement", C.c_int32), ("reserved", C.c_int32),
+                ("reliable_delta", C.c_double)]
 
 
 class SolveResult(C.Structure):
@@ -444,8 +446,9 @@ BATCH_CSR, BATCH_ELL = 0, 1
 
 
 def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0,
-         preconditioner=PRECOND_NONE):
-    return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, preconditioner)
+         preconditioner=PRECOND_NONE, refinement=REFINE_AUTO, reliable_delta=0.0):
+    return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, preconditioner,
+                     refinement, 0, reliable_delta)
 
 
 def gko_device_status(stream=None):

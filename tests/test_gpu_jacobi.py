@@ -71,11 +71,18 @@ def test_jacobi_mixed_precision_matches_oracle(gko, name):
     which = O.CG if name == "cg" else O.BICGSTAB
     xo, ro = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, inner_maxit=5000, jacobi=True, adaptive=True)
     xg, rg = solve(G, name, M, b, 1e-10, 5000, precision=G.PRECISION_MIXED_F32, inner_tol=1e-5,
-                   inner_maxit=5000, preconditioner=G.PRECOND_JACOBI)
+                   inner_maxit=5000, preconditioner=G.PRECOND_JACOBI, refinement=G.REFINE_RESTART)
     assert ro.status == 0 and rg.status == G.OK, (ro, rg)
     assert rg.rel_residual <= 1e-10
     assert np.linalg.norm(xg - np.ones(A.n_rows)) <= 1e-6 * np.sqrt(A.n_rows)
     assert abs(rg.outer_iterations - ro.outer_iterations) <= 1
+    # reliable updates (FP32 recurrences, FP64 replacements) with Jacobi
+    xr, rr = O.solve_reliable(which, A, b, tol=1e-12, maxit=5000, delta=0.1, jacobi=True)
+    xg, rg = solve(G, name, M, b, 1e-12, 5000, precision=G.PRECISION_MIXED_F32, preconditioner=G.PRECOND_JACOBI,
+                   refinement=G.REFINE_RELIABLE)
+    assert rr.status == 0 and rg.status == G.OK, (rr, rg)
+    assert np.linalg.norm(b - O.spmv_csr(A, xg)) <= 1.01e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(xg - xr) <= 1e-8 * np.linalg.norm(xr)
 
 
 @pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hybrid", "sellp"])

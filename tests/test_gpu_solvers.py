@@ -155,7 +155,8 @@ def test_mixed_precision_refinement(gko, precision, name):
     A, b = spd_problem() if name == "cg" else nonsym_problem()
     M = G.from_csr(A)
     prec = G.PRECISION_MIXED_F32 if precision == "f32" else G.PRECISION_MIXED_BF16
-    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=2000, precision=prec, inner_tol=1e-3 if precision == "bf16" else 1e-4)
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=2000, precision=prec,
+                        inner_tol=1e-3 if precision == "bf16" else 1e-4, refinement=G.REFINE_RESTART)
     assert res.status == G.OK, res
     assert res.outer_iterations >= 2
     assert res.rel_residual <= 1e-12 and true_rel_res(A, xg, b) <= 1.01e-12
@@ -168,6 +169,103 @@ def test_mixed_precision_refinement(gko, precision, name):
         inner = dict(inner_maxit=120, max_outer=30) if name == "gmres" else dict(inner_maxit=2000)
         xi, ri = O.solve_ir(SOLVERS[name], A, b, tol=1e-12, inner_tol=1e-4, adaptive=True, **inner)
         assert ri.status == 0 and abs(res.outer_iterations - ri.outer_iterations) <= 2, (res, ri)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo"])
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("name", ["cg", "bicgstab"])
+def test_reliable_updates_match_oracle(gko, name, precision, fmt):
+    """Mixed precision with reliable updates: FP32 (or BF16-valued) recurrences
+    with FP32 vectors, the partial solution folded into the FP64 x and the
+    residual replaced by the FP64 one; both sides to 1e-12, solution parity
+    with the oracle's reliable-update solve (FP32 values; BF16 rounds A
+    further, so there only the residual and the FP64 solution are judged);
+    update counts are of the same order (the GPU applies FP64 scalars to FP32
+    vectors as float pairs, the oracle in FP64 then rounds)."""
+    G = gko
+    A, b = spd_problem() if name == "cg" else nonsym_problem(10, 3.0)
+    M = G.from_csr(A)
+    if fmt == "ell":
+        M = G.gko_matrix_convert_to_ell(M)
+    elif fmt == "coo":
+        M = G.gko_matrix_convert_to_coo(M)
+    prec = G.PRECISION_MIXED_F32 if precision == "f32" else G.PRECISION_MIXED_BF16
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=5000, precision=prec, refinement=G.REFINE_RELIABLE)
+    assert res.status == G.OK, res
+    assert res.rel_residual <= 1e-12 and true_rel_res(A, xg, b) <= 1.01e-12
+    assert abs(res.rel_residual - true_rel_res(A, xg, b)) <= 1e-13
+    xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    if precision == "f32":
+        xr, rr = O.solve_reliable(SOLVERS[name], A, b, tol=1e-12, maxit=5000, delta=0.1)
+        assert rr.status == 0 and np.linalg.norm(xg - xr) <= 1e-8 * np.linalg.norm(xr)
+        assert abs(res.iterations - rr.iterations) <= max(3, 0.15 * rr.iterations), (res, rr)
+        assert abs(res.outer_iterations - rr.outer_iterations) <= max(2, 0.3 * rr.outer_iterations), (res, rr)
+
+
+@pytest.mark.parametrize("name", ["cg", "bicgstab"])
+def test_reliable_updates_large_default(gko, name):
+    """The library's default mixed-precision path above 2^18 rows: reliable
+    updates with the FP32 copy stored in ELL (rows of near-equal length),
+    against the oracle's reliable-update solve (FP32 CSR recurrences; the ELL
+    copy sums each row in the same storage order) and its FP64 solve, both
+    sides to 1e-12: n = 65^3 = 274,625."""
+    G = gko
+    if name == "cg":
+        A = I.stencil3d_7pt(65)
+        b = np.random.default_rng(12).uniform(-1, 1, A.n_rows)
+    else:
+        A = I.convdiff3d_7pt(65, 1.0)
+        b = O.spmv_csr(A, np.ones(A.n_rows))
+    assert A.n_rows > 1 << 18
+    M = G.from_csr(A)
+    G.gko_matrix_convert_to_ell(M, 1.2)  # the copy's format rule accepts this matrix
+    xg, res = gpu_solve(G, name, M, b, tol=1e-12, maxit=5000, precision=G.PRECISION_MIXED_F32)
+    assert res.status == G.OK and res.outer_iterations >= 3, res
+    assert true_rel_res(A, xg, b) <= 1.01e-12
+    assert abs(res.rel_residual - true_rel_res(A, xg, b)) <= 1e-13
+    xr, rr = O.solve_reliable(SOLVERS[name], A, b, tol=1e-12, maxit=5000, delta=0.1)
+    assert rr.status == 0 and np.linalg.norm(xg - xr) <= 1e-8 * np.linalg.norm(xr)
+    assert abs(res.iterations - rr.iterations) <= max(3, 0.15 * rr.iterations), (res, rr)
+    xo, ro = O.solve(SOLVERS[name], A, b, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_reliable_updates_options(gko):
+    """Refinement options: GMRES refuses reliable updates, bad modes and
+    factors are refused, delta = 0 updates only at convergence, x0 and b = 0
+    behave as in the other solves, and the iteration cap holds."""
+    G = gko
+    A, b = nonsym_problem(8, 3.0)
+    M = G.from_csr(A)
+    mixed = dict(precision=G.PRECISION_MIXED_F32)
+    for bad in (dict(refinement=7), dict(refinement=G.REFINE_RELIABLE, reliable_delta=1.5),
+                dict(refinement=G.REFINE_RELIABLE, reliable_delta=-0.1)):
+        with pytest.raises(G.GkoError) as e:
+            gpu_solve(G, "bicgstab", M, b, **mixed, **bad)
+        assert e.value.status == G.INVALID_ARG
+    with pytest.raises(G.GkoError) as e:
+        gpu_solve(G, "gmres", M, b, **mixed, refinement=G.REFINE_RELIABLE)
+    assert e.value.status == G.NOT_SUPPORTED
+    for name in ("cg", "bicgstab"):
+        A2, b2 = spd_problem() if name == "cg" else (A, b)
+        M2 = G.from_csr(A2)
+        x, res = gpu_solve(G, name, M2, np.zeros(A2.n_rows), x0=np.ones(A2.n_rows), **mixed,
+                           refinement=G.REFINE_RELIABLE)
+        assert res.status == G.OK and res.iterations == 0 and np.all(x == 0)
+        xs, _ = O.solve(SOLVERS[name], A2, b2, tol=1e-14, maxit=5000)
+        x, res = gpu_solve(G, name, M2, b2, x0=xs, tol=1e-10, **mixed, refinement=G.REFINE_RELIABLE)
+        assert res.status == G.OK and res.iterations == 0
+        x, res = gpu_solve(G, name, M2, b2, tol=1e-14, maxit=3, **mixed, refinement=G.REFINE_RELIABLE)
+        assert res.status == G.NOT_CONVERGED and res.iterations == 3
+        assert abs(res.rel_residual - true_rel_res(A2, x, b2)) <= 1e-12
+        x0 = np.random.default_rng(1).uniform(-1, 1, A2.n_rows)
+        x, res = gpu_solve(G, name, M2, b2, x0=x0, tol=1e-10, maxit=5000, **mixed, refinement=G.REFINE_RELIABLE,
+                           reliable_delta=0.01)
+        assert res.status == G.OK and true_rel_res(A2, x, b2) <= 1.01e-10
+        x2, res2 = gpu_solve(G, name, M2, b2, x0=x0, tol=1e-10, maxit=5000, **mixed,
+                             refinement=G.REFINE_RELIABLE, reliable_delta=0.01)
+        assert x.tobytes() == x2.tobytes() and res.iterations == res2.iterations
 
 
 def test_edge_cases(gko):
