@@ -288,6 +288,35 @@ def fma_peak(G, dev, fp64=True):
     return 8.0 * n * (hi - lo) / ((best[hi] - best[lo]) * 1e-3)
 
 
+def gather_peak(G, dev, fp64=True, log2_len=20):
+    """Random-gather rate of the GPU measured with the library's probe
+    (gko_bench_gather: 8 independent LCG index streams per thread, 8 resident
+    256-thread blocks per SM, one element per gather from an L2-resident
+    vector of 2^20 elements, the power-law matrices' x): gathers per second
+    from the difference of two loop counts."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n = sms * 8 * 256
+    dt = torch.float64 if fp64 else torch.float32
+    x = torch.rand(1 << log2_len, dtype=dt, device=dev)
+    out = torch.empty(n, dtype=dt, device=dev)
+    lo, hi = 32, 96
+    G.gko_bench_gather(x, out, lo)
+    best = {}
+    for loops in (lo, hi):
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.gko_bench_gather(x, out, loops)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        best[loops] = min(ts)
+    return 8.0 * n * (hi - lo) / ((best[hi] - best[lo]) * 1e-3)
+
+
 def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     """Krylov solves to 1e-8 relative residual, FP64 vs mixed precision:
     CG on the 7-point Poisson problem 256^3 (b = A*1) and BiCGSTAB / GMRES(30)
@@ -1036,6 +1065,7 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     fp64_fma = fma_peak(G, dev)
+    gathers = {"f64": gather_peak(G, dev, True), "f32": gather_peak(G, dev, False)}
     dom = int(np.argmax(per_case_ms))
     dom_case = cases[dom]
     achieved = dom_case["bytes"] / (per_case_ms[dom] * 1e-3) / 1e9
@@ -1061,10 +1091,17 @@ def run_ours(args):
                                            "GB_s": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9, 1),
                                            "frac": round(c["bytes"] / (per_case_ms[i] * 1e-3) / 1e9 / peak, 4)},
                                           **({"frac_fp64": round(c["nnz"] / (per_case_ms[i] * 1e-3) / fp64_fma, 4)}
-                                             if c["label"].endswith("/f64") else {}))
+                                             if c["label"].endswith("/f64") else {}),
+                                          **({"frac_gather": round(c["nnz"] / (per_case_ms[i] * 1e-3)
+                                                                   / gathers[c["label"][-3:]], 4)}
+                                             if c["label"].startswith("powerlaw") else {}))
                          for i, c in enumerate(cases)},
             "fp64_fma_peak": {"fma_per_s": round(fp64_fma, -8), "tflops": round(2 * fp64_fma / 1e12, 3),
                               "note": "per_case frac_fp64 = nnz FMAs per SpMV / time / this rate (FP64 cases)"},
+            "gather_peak": {"f64_per_s": round(gathers["f64"], -8), "f32_per_s": round(gathers["f32"], -8),
+                            "note": "random gathers from an L2-resident 2^20-element vector (gko_bench_gather); "
+                                    "per_case frac_gather = nnz gathers per SpMV / time / this rate "
+                                    "(power-law cases: uniformly random columns)"},
             "e2e": {"value": round(whole_job_gbs(world, step_bytes, e2e_ms), 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(sum(c["x"].numel() * c["x"].element_size() for c in cases)),
                     "d2h_bytes_per_step": int(sum(c["y"].numel() * c["y"].element_size() for c in cases))},

@@ -523,6 +523,20 @@ GKO_API int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype dt
  * Stream-ordered.  GKO_INVALID_ARG on bad sizes or dtype. */
 GKO_API int gko_bench_fma(gko_dtype dtype, int32_t inner_loops, void *data, int64_t n, void *stream);
 
+/* Random-gather throughput probe (no counterpart in the paper; it measures
+ * the access pattern that bounds SpMV on matrices with uniformly random
+ * columns: one element per L2 sector).  x: 2^log2_len device elements of
+ * `dtype` (F64: 8 bytes, F32: 4 bytes; log2_len 1..30), read as raw bits;
+ * out: `n` elements (n a positive multiple of 256, n * 8 < 2^32), one per
+ * thread.  Thread t keeps 8 streams with states s_c = 8 t + c; each of
+ * `inner_loops` steps sets s_c = 1664525 s_c + 1013904223 (mod 2^32) and
+ * xors element (s_c >> (32 - log2_len)) of x into its accumulator (loaded
+ * bypassing L1), which it writes to out[t].  n * 8 * inner_loops gathers
+ * per call; time two loop counts and subtract.  Stream-ordered.
+ * GKO_INVALID_ARG on bad sizes or dtype. */
+GKO_API int gko_bench_gather(gko_dtype dtype, int32_t inner_loops, const void *x, int32_t log2_len, void *out,
+                             int64_t n, void *stream);
+
 /* Failure-detection check (no counterpart in the paper): one warp waits on a
  * shared-memory barrier that nothing completes, through the bounded wait the
  * bulk-copy SpMV kernels use, for at most `cycles` clock cycles (1 .. 2^32).

@@ -39,6 +39,15 @@ __device__ __forceinline__ void dot_accum(const DotSpec& d, int64_t i, XT v, dou
   if (d.want_yy) yy = __fma_rn(yv, yv, yy);
 }
 
+// The same with w[i] loaded earlier (issued when the thread takes its rows,
+// so its latency overlaps the row's gathers instead of following them).
+template <typename XT>
+__device__ __forceinline__ void dot_accum_w(const DotSpec& d, XT w, XT v, double& wy, double& yy) {
+  const double yv = widen(v);
+  wy = __fma_rn(widen(w), yv, wy);
+  if (d.want_yy) yy = __fma_rn(yv, yv, yy);
+}
+
 // Blocks that prefetch slices of x into L2 at the start of the gather-heavy
 // kernels (COO, merge path): about the first wave of blocks.
 constexpr unsigned kXPrefetchBlocks = 512;
@@ -227,15 +236,18 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
     }
   }
   int32_t rs[R], re[R];
+  XT wv[R];  // fused dot: w of the subwarp's R rows, loaded with their bounds
   auto row_bounds = [&](int64_t b) {
     if (COO) return;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t i = b * RB + sg + (int64_t)r * G;
       rs[r] = re[r] = 0;
+      if (DOT) wv[r] = XT(0);
       if (i < a.n) {
         rs[r] = __ldg(a.rp + i);
         re[r] = __ldg(a.rp + i + 1);
+        if (DOT) wv[r] = static_cast<const XT*>(d.w)[i];
       }
     }
   };
@@ -354,7 +366,16 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
           if (i < a.n) {
             const XT v = (XT)finish_row(a.y, i, sum[j], a.alpha, a.beta, a.plain);
             a.y[i] = v;
-            if (DOT) dot_accum(d, i, v, dwy, dyy);
+            if (DOT) {
+              if (COO) {
+                dot_accum(d, i, v, dwy, dyy);
+              } else {
+                XT w = wv[0];
+#pragma unroll
+                for (int t = 1; t < R; ++t) w = (t == first + j) ? wv[t] : w;
+                dot_accum_w(d, w, v, dwy, dyy);
+              }
+            }
           }
         }
       }
@@ -783,8 +804,12 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
       step = a.C;
     }
     AT sum[RPT];
+    XT wv[RPT];  // fused dot: w of the thread's rows, loaded before the row sums
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) sum[r] = AT(0);
+    for (int r = 0; r < RPT; ++r) {
+      sum[r] = AT(0);
+      if (DOT) wv[r] = i0 + r < a.n ? static_cast<const XT*>(d.w)[i0 + r] : XT(0);
+    }
     for (int32_t k = 0; k < width; k += U) {
       int32_t c[U][RPT];
       VT v[U][RPT];
@@ -818,7 +843,7 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
       if (i < a.n) {
         const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
         a.y[i] = v;
-        if (DOT) dot_accum(d, i, v, dwy, dyy);
+        if (DOT) dot_accum_w(d, wv[r], v, dwy, dyy);
       }
     }
   }

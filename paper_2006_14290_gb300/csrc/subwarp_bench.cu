@@ -91,6 +91,33 @@ __global__ void __launch_bounds__(kBenchThreads) fma_chain_kernel(T* __restrict_
   data[i] = sum;
 }
 
+// Random-gather throughput probe: every thread keeps 8 independent index
+// streams (a 32-bit linear congruential step each, indices = the state's
+// top bits masked to the power-of-two vector length) and gathers one
+// element per stream per loop from x, folding the element's bits into an
+// integer xor so no floating-point pipe is involved; the load addresses
+// never depend on loaded data, so every gather of a loop can be in flight.
+// This is the access pattern of an SpMV whose columns are uniformly random
+// (the power-law matrices): one 8- or 4-byte element per L2 sector.
+constexpr uint32_t kLcgA = 1664525u, kLcgC = 1013904223u;
+template <typename U>
+__global__ void __launch_bounds__(kBenchThreads) gather_kernel(const U* __restrict__ x, uint32_t mask, int shift,
+                                                               U* __restrict__ out, int loops) {
+  const int64_t i = (int64_t)blockIdx.x * kBenchThreads + threadIdx.x;
+  uint32_t st[8];
+  U acc = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) st[c] = (uint32_t)i * 8u + (uint32_t)c;
+  for (int it = 0; it < loops; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      st[c] = st[c] * kLcgA + kLcgC;
+      acc ^= __ldcg(x + ((st[c] >> shift) & mask));
+    }
+  }
+  out[i] = acc;
+}
+
 // Failure-detection check of the bounded waits: one warp waits on an
 // mbarrier that nothing ever completes, through the same bounded wait the
 // bulk-copy pipelines use, but with a caller-given cycle limit.  The wait
@@ -138,6 +165,28 @@ extern "C" int gko_bench_subwarp_reduce(int32_t subwarp, int32_t impl, gko_dtype
   if (dtype == GKO_F64) return launch_typed(subwarp, impl, static_cast<double*>(data), n, inner_loops, s);
   if (dtype == GKO_F32) return launch_typed(subwarp, impl, static_cast<float*>(data), n, inner_loops, s);
   return fail(GKO_INVALID_ARG, "dtype must be F64 or F32");
+}
+
+extern "C" int gko_bench_gather(gko_dtype dtype, int32_t inner_loops, const void* x, int32_t log2_len, void* out,
+                                int64_t n, void* stream) {
+  if (!x || !out || n <= 0 || n % kBenchThreads != 0 || n / kBenchThreads > INT32_MAX || inner_loops < 0 ||
+      log2_len < 1 || log2_len > 30 || (n * 8) >> 32 != 0)
+    return fail(GKO_INVALID_ARG, "bad gather benchmark arguments (n a positive multiple of 256, log2_len 1..30)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned blocks = (unsigned)(n / kBenchThreads);
+  const uint32_t mask = (uint32_t)((1ull << log2_len) - 1);
+  const int shift = 32 - log2_len;
+  if (dtype == GKO_F64) {
+    gather_kernel<unsigned long long><<<blocks, kBenchThreads, 0, s>>>(
+        static_cast<const unsigned long long*>(x), mask, shift, static_cast<unsigned long long*>(out), inner_loops);
+  } else if (dtype == GKO_F32) {
+    gather_kernel<unsigned><<<blocks, kBenchThreads, 0, s>>>(static_cast<const unsigned*>(x), mask, shift,
+                                                             static_cast<unsigned*>(out), inner_loops);
+  } else {
+    return fail(GKO_INVALID_ARG, "dtype must be F64 or F32");
+  }
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
 }
 
 extern "C" int gko_bench_fma(gko_dtype dtype, int32_t inner_loops, void* data, int64_t n, void* stream) {

@@ -83,6 +83,7 @@ SIGNATURES = {
     "gko_spmv_host": (C.c_int, [C.POINTER(_D), _P, _P, C.POINTER(_D), _P, C.c_int, _P, _P, _P]),
     "gko_bench_subwarp_reduce": (C.c_int, [_I32, _I32, C.c_int, _I32, _P, C.c_int64, _P]),
     "gko_bench_fma": (C.c_int, [C.c_int, _I32, _P, C.c_int64, _P]),
+    "gko_bench_gather": (C.c_int, [C.c_int, _I32, _P, _I32, _P, C.c_int64, _P]),
     "gko_diag_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _P]),
     "gko_dot": (C.c_int, [_I64, _P, _P, C.POINTER(_D), _P]),
     "gko_nrm2": (C.c_int, [_I64, _P, C.POINTER(_D), _P]),
@@ -366,6 +367,22 @@ def gko_bench_fma(data, inner_loops: int, stream=None):
     dt = F64 if data.dtype == torch.float64 else F32
     _check(lib().gko_bench_fma(dt, inner_loops, _dptr(data), data.numel(), _stream(stream)), "gko_bench_fma")
     return data
+
+
+def gko_bench_gather(x, out, inner_loops: int, stream=None):
+    """Random-gather probe: x a float64/float32 CUDA tensor of 2^k elements,
+    out one element per thread of the same dtype (length a multiple of 256);
+    8 * out.numel() * inner_loops gathers."""
+    import torch
+
+    n_x = x.numel()
+    k = n_x.bit_length() - 1
+    if n_x != 1 << k or out.dtype != x.dtype:
+        raise ValueError("x needs a power-of-two length and out the same dtype")
+    dt = F64 if x.dtype == torch.float64 else F32
+    _check(lib().gko_bench_gather(dt, inner_loops, _dptr(x), k, _dptr(out), out.numel(), _stream(stream)),
+           "gko_bench_gather")
+    return out
 
 
 def gko_diag_bounded_wait(cycles: int, stream=None) -> bool:

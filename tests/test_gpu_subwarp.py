@@ -59,3 +59,28 @@ def test_fma_probe_runs_the_stated_recurrence(gko, dt):
     np.testing.assert_allclose(got, want, rtol=tol, atol=tol)
     with pytest.raises(G.GkoError):
         G.gko_bench_fma(dev(np.zeros(100)), 1)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_gather_probe_xors_the_stated_elements(gko, dt):
+    """gko_bench_gather: thread t keeps states 8t + c, steps them by the
+    stated linear congruence and xors element (s >> (32 - k)) of x into its
+    accumulator; the host replays the same integer recurrence (bit-exact)."""
+    G = gko
+    k, n, loops = 12, 512, 5
+    npt, ut = (np.float64, np.uint64) if dt == "f64" else (np.float32, np.uint32)
+    xh = np.random.default_rng(7).uniform(-1, 1, 1 << k).astype(npt)
+    x = dev(xh) if dt == "f64" else dev(xh, np.float32)
+    out = dev(np.zeros(n)) if dt == "f64" else dev(np.zeros(n), np.float32)
+    G.gko_bench_gather(x, out, loops)
+    bits = xh.view(ut)
+    st = (np.arange(n, dtype=np.uint64)[:, None] * 8 + np.arange(8, dtype=np.uint64)[None, :]) & 0xFFFFFFFF
+    acc = np.zeros(n, ut)
+    for _ in range(loops):
+        st = (st * 1664525 + 1013904223) & 0xFFFFFFFF
+        idx = (st >> (32 - k)) & ((1 << k) - 1)
+        for c in range(8):
+            acc ^= bits[idx[:, c]]
+    np.testing.assert_array_equal(host(out).view(ut), acc)
+    with pytest.raises(ValueError):
+        G.gko_bench_gather(dev(np.zeros(100)), out, 1)
