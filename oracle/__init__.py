@@ -84,6 +84,7 @@ _SIGS = {
                                  C.POINTER(_Result)]),
     "or_solve_reliable": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _I32, _P, _P, _D, _I32, _D,
                                     C.POINTER(_Result)]),
+    "or_batch_cg_reliable": (None, [_I32, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _P, _P, _P, _P]),
 }
 
 
@@ -442,3 +443,31 @@ def batch_cg(systems, bs, x0=None, tol=1e-10, maxit=10000):
     lib().or_batch_cg(count, _p(row_off), _p(nnz_off), _p(rp), _p(col), _p(val), _p(b), _p(x), tol, maxit,
                       _p(it), _p(rr), _p(st))
     return [x[row_off[i]:row_off[i + 1]] for i in range(count)], it, rr, st
+
+
+def batch_cg_reliable(systems, bs, x0=None, tol=1e-10, maxit=10000, delta=0.1, storage_f32=False):
+    """The single-system reliable-update CG on every system of a batch
+    (OpenMP over systems): recurrences on the systems' FP32 values, replaced
+    residuals with their FP64 values (storage_f32: the systems are their
+    FP32 roundings, so both use those).  Returns (x per system, iterations,
+    updates, true relative residuals, statuses)."""
+    count = len(systems)
+    rows = np.array([S.n_rows for S in systems], np.int64)
+    nnzs = np.array([int(S.row_ptr[-1]) for S in systems], np.int64)
+    row_off = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
+    nnz_off = np.concatenate([[0], np.cumsum(nnzs)]).astype(np.int64)
+    rp = np.concatenate([_i32(S.row_ptr) for S in systems])
+    col = np.concatenate([_i32(S.col) for S in systems])
+    val = np.concatenate([_f64(S.val) for S in systems])
+    val32 = val.astype(np.float32)
+    if storage_f32:
+        val = val32.astype(np.float64)
+    b = np.concatenate([_f64(v) for v in bs])
+    x = np.zeros(b.size) if x0 is None else np.concatenate([_f64(v) for v in x0])
+    it = np.zeros(count, np.int32)
+    up = np.zeros(count, np.int32)
+    rr = np.zeros(count, np.float64)
+    st = np.zeros(count, np.int32)
+    lib().or_batch_cg_reliable(count, _p(row_off), _p(nnz_off), _p(rp), _p(col), _p(val), _p(val32), _p(b), _p(x),
+                               tol, maxit, delta, _p(it), _p(up), _p(rr), _p(st))
+    return [x[row_off[i]:row_off[i + 1]] for i in range(count)], it, up, rr, st

@@ -1108,3 +1108,28 @@ int or_solve_reliable(int solver, int64_t n, const int32_t *rp, const int32_t *c
   free(m);
   return out->status;
 }
+
+/* Batched CG with reliable updates: the single-system reliable-update CG
+ * above applied to each system of a batch laid out as in or_batch_cg.  val:
+ * the systems' FP64 values (replaced residuals); val32: their FP32 values
+ * (the recurrences).  Systems spread over the OpenMP threads; each solve is
+ * sequential.  iters, updates, relres, status: per system. */
+void or_batch_cg_reliable(int32_t count, const int64_t *row_off, const int64_t *nnz_off, const int32_t *rp,
+                          const int32_t *col, const double *val, const float *val32, const double *b, double *x,
+                          double tol, int32_t maxit, double delta, int32_t *iters, int32_t *updates,
+                          double *relres, int32_t *status) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+#endif
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t r0 = row_off[i], k0 = nnz_off[i], n = row_off[i + 1] - r0;
+    or_op A64 = {n, rp + r0 + i, col + k0, val + k0, NULL};
+    or_op A32 = {n, rp + r0 + i, col + k0, NULL, val32 + k0};
+    or_ctx c = {&A32, 1, 0, NULL, 0, NULL};
+    const or_result res = reliable_core(&c, &A64, OR_SOLVER_CG, b + r0, x + r0, tol, maxit, delta);
+    iters[i] = res.iterations;
+    updates[i] = res.outer_iterations;
+    relres[i] = res.rel_residual;
+    status[i] = res.status;
+  }
+}

@@ -686,3 +686,40 @@ def test_reliable_partial_solution_is_fp32_stored(solver):
     assert r.status == O.STATUS_NOT_CONVERGED and r.outer_iterations == 0
     np.testing.assert_array_equal(x.astype(np.float32).astype(np.float64), x)
     assert np.any(x != 0)
+
+
+def test_batch_cg_reliable_is_the_single_system_solve_per_system():
+    """The batched reliable-update oracle equals the single-system
+    reliable-update CG bit for bit whatever the thread count, reaches the
+    tolerance in FP64 and agrees with dense solves; with FP32 storage the
+    systems are the FP32-rounded ones."""
+    sides = [5, 9, 3, 12, 7]
+    systems, bs = [], []
+    for i, sd in enumerate(sides):
+        A, b = I.batch_system(i, sd)
+        systems.append(A)
+        bs.append(b)
+    bs[2] = np.zeros_like(bs[2])
+    outs = []
+    for threads in (1, 4):
+        O.set_threads(threads)
+        outs.append(O.batch_cg_reliable(systems, bs, tol=1e-12, maxit=5000))
+    O.set_threads(1)
+    (x1, it1, up1, rr1, st1), (x4, it4, up4, rr4, st4) = outs
+    for i, (A, b) in enumerate(zip(systems, bs)):
+        xs, rs = O.solve_reliable(O.CG, A, b, tol=1e-12, maxit=5000, delta=0.1)
+        assert x1[i].tobytes() == xs.tobytes() == x4[i].tobytes()
+        assert it1[i] == rs.iterations == it4[i] and up1[i] == rs.outer_iterations == up4[i]
+        assert st1[i] == rs.status == 0 and rr1[i] == rs.rel_residual
+        if i != 2:
+            assert rr1[i] <= 1e-12
+            xd = np.linalg.solve(dense(A), b)
+            assert np.linalg.norm(xs - xd) <= 1e-8 * np.linalg.norm(xd)
+        else:
+            assert np.all(x1[i] == 0) and it1[i] == 0
+    x32, it32, up32, rr32, st32 = O.batch_cg_reliable(systems, bs, tol=1e-12, maxit=5000, storage_f32=True)
+    for i, (A, b) in enumerate(zip(systems, bs)):
+        if i == 2:
+            continue
+        A32 = I.Csr(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+        assert st32[i] == 0 and np.linalg.norm(b - dense(A32) @ x32[i]) <= 1.01e-12 * np.linalg.norm(b)
