@@ -509,8 +509,10 @@ def batched_suite(G, dev, stream, oracle_cores=0, fp64_fma=None):
     nnzs = np.array([S.nnz for S in systems], np.int64)
     res = {"systems": 4096, "rows": int(rows.sum()), "nnz": int(nnzs.sum())}
     peak_hbm, _ = measured_peaks()
-    for storage, tag in ((G.F64, "f64"), (G.F32, "f32_storage")):
+    for storage, tag, mixed in ((G.F64, "f64", False), (G.F32, "f32_storage", False), (G.F64, "mixed_f32", True)):
         B = G.Batch(systems, storage=storage)
+        if mixed:
+            B.set_precision(G.PRECISION_MIXED_F32)
         x0 = torch.zeros(B.total_rows, dtype=torch.float64, device=dev)
         tuned = B.tune(b, x0, 1e-10, 20000, stream=stream)
         x = torch.zeros_like(x0)
@@ -526,10 +528,18 @@ def batched_suite(G, dev, stream, oracle_cores=0, fp64_fma=None):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
-        sv = 8 if storage == G.F64 else 4
+        sv = 8 if storage == G.F64 and not mixed else 4
         itd = it.astype(np.float64)
-        nbytes = float(np.sum(itd * (nnzs * (sv + 4) + 4 * (rows + 1) + 16 * rows)))
-        fmas = float(np.sum(itd * (nnzs + 5 * rows)))
+        up = B.last_updates().astype(np.float64)
+        # mixed: FP32 values in the recurrences (x stays in global memory only
+        # at updates), two FP64 FMAs per row and iteration (the dots), and per
+        # update an FP64 product with the stored values plus its residual norm
+        nbytes = float(np.sum(itd * (nnzs * (sv + 4) + 4 * (rows + 1) + (0 if mixed else 16) * rows)))
+        if mixed:
+            nbytes += float(np.sum(up * (nnzs * 12 + 4 * (rows + 1) + 32 * rows)))
+            fmas = float(np.sum(itd * 2 * rows + up * (nnzs + 2 * rows)))
+        else:
+            fmas = float(np.sum(itd * (nnzs + 5 * rows)))
         fp64_fma = fp64_fma or fma_peak(G, dev)
         fp64_frac = fmas / (ms * 1e-3) / fp64_fma
         res[tag] = {"status": int(code), "time_ms": round(ms, 3), "systems_per_s": round(4096 / (ms * 1e-3), 1),
@@ -540,6 +550,10 @@ def batched_suite(G, dev, stream, oracle_cores=0, fp64_fma=None):
                     "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
                     "frac_fp64": round(fp64_frac, 4),
                     "fp64_peak": f"{2 * fp64_fma / 1e12:.3f} TFLOP/s measured (gko_bench_fma)"}
+        if mixed:
+            res[tag]["updates_total"] = int(up.sum())
+            res[tag]["note"] = ("reliable-update CG per system: FP32 recurrences, FP64 dots and x, "
+                                "replaced residuals with the FP64 values")
         del B
     if oracle_cores:
         import oracle as O
@@ -553,6 +567,17 @@ def batched_suite(G, dev, stream, oracle_cores=0, fp64_fma=None):
                          "sample": "the full batch: the oracle's FP64 CG per system, OpenMP over systems"}
         res["f64"]["oracle_ms"] = res["oracle"]["ms"]
         res["f32_storage"]["oracle_ms"] = res["oracle"]["ms"]
+        t0 = time.perf_counter()
+        _, oit, oup, orr, ost = O.batch_cg_reliable(systems, bs, tol=1e-10, maxit=20000)
+        dt = time.perf_counter() - t0
+        res["oracle_mixed"] = {"ms": round(dt * 1e3, 1), "systems_per_s": round(4096 / dt, 1),
+                               "threads": oracle_cores, "converged": int(np.sum(ost == 0)),
+                               "iterations_total": int(oit.sum()), "updates_total": int(oup.sum()),
+                               "sample": "the full batch: the oracle's reliable-update CG per system, "
+                                         "OpenMP over systems"}
+        res["mixed_f32"]["oracle_ms"] = res["oracle_mixed"]["ms"]
+    res["mixed_f32_speedup"] = (round(res["f64"]["time_ms"] / res["mixed_f32"]["time_ms"], 3)
+                                if res["f64"]["status"] == G.OK and res["mixed_f32"]["status"] == G.OK else None)
     return res
 
 

@@ -452,6 +452,26 @@ GKO_API int gko_batch_tune(gko_batch B, const double *b, const double *x0, doubl
 GKO_API int gko_batch_set_schedule(gko_batch B, int32_t warp_rows, int32_t threads, int32_t storage, void *stream);
 GKO_API int gko_batch_set_threshold(gko_batch B, int32_t warp_rows, void *stream);
 
+/* Precision of gko_batch_cg (and of gko_batch_tune's timings).
+ * GKO_PRECISION_F64 (the default): FP64 vectors and arithmetic on the stored
+ * values.  GKO_PRECISION_MIXED_F32: per system, CG with reliable updates
+ * (Sleijpen & van der Vorst, Computing 56, 1996; residual replacement
+ * without restart, van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000): the
+ * recurrences run on the FP32 rounding of the stored values with FP32
+ * vectors (r, p, q and the iterate's change), FP64 dots and FP64 scalars;
+ * when the recurrence residual meets rel_tol ||b_i|| or drops below
+ * reliable_delta (0: 0.1) times its largest norm since the last update, the
+ * change is added to the FP64 x and r is replaced by b - A x computed in FP64
+ * with the stored values; a system converges when that FP64 residual meets
+ * rel_tol ||b_i||.  The FP32 values are made once (FP64 storage) or are the
+ * stored ones (FP32 storage).  Bad arguments: GKO_INVALID_ARG.  Synchronises
+ * `stream`. */
+GKO_API int gko_batch_set_precision(gko_batch B, int32_t precision, double reliable_delta, void *stream);
+
+/* Reliable updates per system (`count` HOST entries) of the last
+ * gko_batch_cg call: zeros after an FP64 solve.  Synchronises `stream`. */
+GKO_API int gko_batch_last_updates(gko_batch B, int32_t *updates, void *stream);
+
 /* The batch's sizes and schedule (outputs may be NULL). */
 GKO_API int gko_batch_info(gko_batch B, int32_t *count, int64_t *total_rows, int64_t *total_nnz,
                            int32_t *warp_rows, int32_t *n_items, int32_t *threads, int32_t *storage);

@@ -44,6 +44,12 @@ struct BatchArgs {
   const int32_t* ell_k;
   const int32_t* ell_col;
   const void* ell_val;
+  // FP32 values of the recurrences of a mixed-precision solve (CSR and ELL
+  // order; the stored values themselves for FP32 storage)
+  const float* val32;
+  const float* ell_val32;
+  double delta;       // reliable-update factor
+  int32_t* updates;   // per system: reliable updates of the last mixed solve
   const double* b;
   double* x;
   double rel_tol;
@@ -84,6 +90,35 @@ __device__ __forceinline__ const double* block_sum_fin(double v, double* red, F 
   return red + THREADS;
 }
 
+// Group primitives of a solve by G threads (G = THREADS: a block; G = 32: a
+// warp): gstep sums v over the group and fin(total, out) derives up to four
+// scalars from it (once per block, in every lane of a warp); gsync orders
+// the group's shared- and global-memory accesses.
+struct Scal {
+  double o[4];
+};
+template <int G, int THREADS, typename F>
+__device__ __forceinline__ Scal gstep(double v, double* red, F fin) {
+  Scal sc;
+  if (G == kWarp) {
+    fin(subwarp_sum<32>(v, 0xffffffffu), sc.o);
+  } else {
+    const double* o = block_sum_fin<THREADS>(v, red, fin);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sc.o[j] = o[j];
+  }
+  return sc;
+}
+template <int G, int THREADS>
+__device__ __forceinline__ double gsum(double v, double* red) {
+  return gstep<G, THREADS>(v, red, [](double t, double* o) { o[0] = t; }).o[0];
+}
+template <int G>
+__device__ __forceinline__ void gsync() {
+  if (G == kWarp) __syncwarp();
+  else __syncthreads();
+}
+
 // One CG solve by a group of G threads (G = THREADS: a block; G = 32: a
 // warp).  r, p, q: the group's shared-memory vectors.  Follows the
 // single-system solver: recurrence residual test, then the true residual; a
@@ -101,29 +136,9 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   const int K = ELL ? a.ell_k[sys] : 0;
   const double* b = a.b + r0;
   double* x = a.x + r0;
-  // group sum; fin(total, out) derives the step's scalars from it (once per
-  // block for a block group, in every lane of a warp group)
-  struct Scal {
-    double o[4];
-  };
-  auto gstep = [&](double v, auto fin) -> Scal {
-    Scal sc;
-    if (G == kWarp) {
-      fin(subwarp_sum<32>(v, 0xffffffffu), sc.o);
-    } else {
-      const double* o = block_sum_fin<THREADS>(v, red, fin);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) sc.o[j] = o[j];
-    }
-    return sc;
-  };
-  auto gsum = [&](double v) -> double {
-    return gstep(v, [](double t, double* o) { o[0] = t; }).o[0];
-  };
-  auto gsync = [&]() {
-    if (G == kWarp) __syncwarp();
-    else __syncthreads();
-  };
+  auto gstep = [&](double v, auto fin) -> Scal { return gko::gstep<G, THREADS>(v, red, fin); };
+  auto gsum = [&](double v) -> double { return gko::gsum<G, THREADS>(v, red); };
+  auto gsync = [&]() { gko::gsync<G>(); };
   auto row_dot = [&](int i, const double* v) -> double {
     double s = 0.0;
     if (ELL) {
@@ -244,6 +259,217 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   gsync();
 }
 
+// One mixed-precision CG solve with reliable updates by a group of G threads
+// (Sleijpen & van der Vorst 1996; residual replacement without restart,
+// van der Vorst & Ye 2000): the recurrences run on the system's FP32 values
+// with r, p, q and the iterate's change y in FP32 shared memory, dots and
+// scalars in FP64 (FP32 values widened exactly) and each FP64 scalar applied
+// as a float pair; when the recurrence residual meets rel_tol ||b|| or drops
+// below delta times its largest norm since the last update, y is added to
+// the FP64 x, r is replaced by fl32(b - A x) computed in FP64 with the
+// system's stored values, and the recurrences go on (rho = r.r of the
+// replaced r).  Converged when that FP64 residual meets the tolerance.  Per
+// row and iteration this costs two FP64 FMAs (the dots) instead of nnz_i/n_i
+// + 5 in the FP64 solve.
+template <int G, int THREADS, typename VT, bool ELL>
+__device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, float* q, float* y, double* red,
+                             int lane) {
+  const int64_t r0 = a.row_off[sys];
+  const int n = (int)(a.row_off[sys + 1] - r0);
+  const int32_t* rp = a.rp + r0 + sys;
+  const int64_t k0 = ELL ? a.ell_off[sys] : a.nnz_off[sys];
+  const int32_t* col = (ELL ? a.ell_col : a.col) + k0;
+  const VT* val = static_cast<const VT*>(ELL ? a.ell_val : a.val) + k0;
+  const float* v32 = (ELL ? a.ell_val32 : a.val32) + k0;
+  const int K = ELL ? a.ell_k[sys] : 0;
+  const double* b = a.b + r0;
+  double* x = a.x + r0;
+  // FP64 row product with the stored values over the FP64 x (global memory)
+  auto row_dot64 = [&](int i) -> double {
+    double s = 0.0;
+    if (ELL) {
+      for (int k = 0; k < K; ++k) {
+        const int64_t o = (int64_t)k * n + i;
+        const int32_t c = col[o];
+        if (c >= 0) s = __fma_rn(ldv(val, o), x[c], s);
+      }
+    } else {
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fma_rn(ldv(val, k), x[col[k]], s);
+    }
+    return s;
+  };
+  // FP32 row product of the recurrences (FP32 accumulation)
+  auto row_dot32 = [&](int i, const float* v) -> float {
+    float s = 0.0f;
+    if (ELL) {
+      for (int k = 0; k < K; ++k) {
+        const int64_t o = (int64_t)k * n + i;
+        const int32_t c = col[o];
+        if (c >= 0) s = __fmaf_rn(v32[o], v[c], s);
+      }
+    } else {
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fmaf_rn(v32[k], v[col[k]], s);
+    }
+    return s;
+  };
+  // r = fl32(b - A x) from the FP64 x; returns ||b - A x||^2 and sets rz = r.r
+  auto replace = [&](double& rz) -> double {
+    double tt = 0.0, z = 0.0;
+    for (int i = lane; i < n; i += G) {
+      const double ti = b[i] - row_dot64(i);
+      const float tr = __double2float_rn(ti);
+      r[i] = tr;
+      tt = __fma_rn(ti, ti, tt);
+      const double tw = widen(tr);
+      z = __fma_rn(tw, tw, z);
+    }
+    rz = z;
+    return tt;
+  };
+  auto fold = [&]() {  // x += y, y = 0
+    gsync<G>();
+    for (int i = lane; i < n; i += G) {
+      x[i] += widen(y[i]);
+      y[i] = 0.0f;
+    }
+    gsync<G>();
+  };
+  double bb = 0.0;
+  for (int i = lane; i < n; i += G) bb = __fma_rn(b[i], b[i], bb);
+  double rz = 0.0;
+  const double tt0 = replace(rz);
+  for (int i = lane; i < n; i += G) {
+    p[i] = r[i];
+    y[i] = 0.0f;
+  }
+  const double nb = sqrt(gsum<G, THREADS>(bb, red));
+  const double tn0 = sqrt(gsum<G, THREADS>(tt0, red));
+  double rho = gsum<G, THREADS>(rz, red);
+  const double tol = a.rel_tol * nb;
+  double maxrr = tn0;
+  int status = kBRun, it = 0, updates = 0;
+  double res = nb > 0.0 ? tn0 / nb : 0.0;
+  if (nb == 0.0) {
+    for (int i = lane; i < n; i += G) x[i] = 0.0;
+    status = kBOk;
+  } else if (tn0 <= tol) {
+    status = kBOk;
+  }
+  gsync<G>();
+  while (status == kBRun && it < a.maxit) {
+    double pq = 0.0;
+    for (int i = lane; i < n; i += G) {
+      const float qi = row_dot32(i, p);
+      q[i] = qi;
+      pq = __fma_rn(widen(p[i]), widen(qi), pq);
+    }
+    const Scal sp = gstep<G, THREADS>(pq, red, [&](double t, double* o) {
+      const double alpha = rho / t;
+      o[0] = t > 0.0 ? 1.0 : 0.0;
+      o[1] = Lin<float>(alpha).pack();
+      o[2] = Lin<float>(-alpha).pack();
+    });
+    if (sp.o[0] == 0.0) {
+      status = kBBreak;
+      break;
+    }
+    const Lin<float> ay = Lin<float>::unpack(sp.o[1]), ar = Lin<float>::unpack(sp.o[2]);
+    double rn = 0.0;
+    for (int i = lane; i < n; i += G) {
+      y[i] = ay(p[i], y[i]);
+      const float ri = ar(q[i], r[i]);
+      r[i] = ri;
+      const double rw = widen(ri);
+      rn = __fma_rn(rw, rw, rn);
+    }
+    const Scal sr = gstep<G, THREADS>(rn, red, [&](double t, double* o) {
+      const double nr = sqrt(t);
+      const double mx = nr > maxrr ? nr : maxrr;
+      o[0] = t;
+      o[1] = (nr <= tol || nr < a.delta * mx) ? 1.0 : 0.0;
+      o[2] = Lin<float>(t / rho).pack();
+      o[3] = mx;
+    });
+    ++it;
+    double rho_new = sr.o[0];
+    Lin<float> bp = Lin<float>::unpack(sr.o[2]);
+    maxrr = sr.o[3];
+    if (sr.o[1] != 0.0) {  // reliable update
+      fold();
+      const double tt = replace(rz);
+      ++updates;
+      const Scal st = gstep<G, THREADS>(tt, red, [&](double t, double* o) {
+        o[0] = sqrt(t) / nb;
+        o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
+        o[2] = sqrt(t);
+      });
+      res = st.o[0];
+      if (st.o[1] != 0.0) {
+        status = kBOk;
+        break;
+      }
+      maxrr = st.o[2];
+      const Scal sz = gstep<G, THREADS>(rz, red, [&](double t, double* o) {
+        o[0] = t;
+        o[1] = Lin<float>(t / rho).pack();
+      });
+      rho_new = sz.o[0];
+      bp = Lin<float>::unpack(sz.o[1]);
+    }
+    rho = rho_new;
+    for (int i = lane; i < n; i += G) p[i] = bp(p[i], r[i]);
+    gsync<G>();
+  }
+  if (status == kBRun) status = kBNotConv;
+  if (status != kBOk) {  // fold what moved since the last update; report the true residual
+    fold();
+    double tt = 0.0;
+    for (int i = lane; i < n; i += G) {
+      const double ti = b[i] - row_dot64(i);
+      tt = __fma_rn(ti, ti, tt);
+    }
+    tt = gsum<G, THREADS>(tt, red);
+    res = nb > 0.0 ? sqrt(tt) / nb : 0.0;
+  }
+  if (lane == 0) {
+    a.iters[sys] = it;
+    a.relres[sys] = res;
+    a.status[sys] = status;
+    a.updates[sys] = updates;
+  }
+  gsync<G>();
+}
+
+// The mixed-precision counterpart of batch_cg_kernel: the same persistent
+// schedule, with four FP32 vectors (r, p, q, y) per system in shared memory.
+template <int THREADS, typename VT, bool ELL>
+__global__ void __launch_bounds__(THREADS) batch_cg_rel_kernel(BatchArgs a, int block_rows) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ double red[THREADS + 4];
+  __shared__ int item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= a.n_items) return;
+    const int2 it = a.items[item];
+    const int kind = it.x & 1, first = it.x >> 1;
+    if (kind == 0) {
+      float* v = smf;
+      cg_group_rel<THREADS, THREADS, VT, ELL>(a, a.order[first], v, v + block_rows, v + 2 * block_rows,
+                                              v + 3 * block_rows, red, threadIdx.x);
+    } else {
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      float* base = smf + (size_t)w * 4 * kWarpMaxRows;
+      if (w < it.y)
+        cg_group_rel<kWarp, THREADS, VT, ELL>(a, a.order[first + w], base, base + kWarpMaxRows,
+                                              base + 2 * kWarpMaxRows, base + 3 * kWarpMaxRows, red, lane);
+      __syncthreads();
+    }
+  }
+}
+
 // Persistent batched CG: blocks of THREADS threads take work items from an
 // atomic queue, largest systems first; a block item is one system solved by
 // the whole block, a warp item THREADS/32 systems, one per warp.
@@ -295,6 +521,11 @@ struct gko_batch_s {
   Buf row_off, nnz_off, rp, col, val, order, items, iters, relres, status, queue;
   Buf ell_off, ell_k, ell_col, ell_val;  // the same systems in per-system column-major ELL
   int64_t ell_slots = 0;
+  // mixed precision (reliable updates): FP32 values of the recurrences (the
+  // stored ones for FP32 storage) and per-system update counts
+  int32_t mixed = 0;
+  double delta = 0.1;
+  Buf val32, ell_val32, updates;
   std::vector<int64_t> h_rows;   // rows per system
   std::vector<int32_t> h_order;  // largest first
   int32_t threshold = 0;         // warp mode for systems with <= threshold rows
@@ -348,14 +579,16 @@ static int build_items(gko_batch B, int32_t threshold, cudaStream_t s) {
 }
 
 static size_t batch_smem(const gko_batch_s* B) {
-  const size_t blk = (size_t)3 * B->block_rows * sizeof(double);
-  const size_t wrp = B->threshold > 0 ? (size_t)(B->threads / kWarp) * 3 * kWarpMaxRows * sizeof(double) : 0;
+  // FP64: r, p, q as doubles; mixed: r, p, q, y as floats
+  const size_t per = B->mixed ? 4 * sizeof(float) : 3 * sizeof(double);
+  const size_t blk = per * B->block_rows;
+  const size_t wrp = B->threshold > 0 ? (size_t)(B->threads / kWarp) * per * kWarpMaxRows : 0;
   return std::max<size_t>(std::max(blk, wrp), 16);
 }
 
 template <int T, typename VT, bool E>
-static int batch_launch_t(const BatchArgs& a, int n_items, int block_rows, size_t smem, cudaStream_t s) {
-  auto kern = batch_cg_kernel<T, VT, E>;
+static int batch_launch_t(const BatchArgs& a, int n_items, int block_rows, size_t smem, bool mixed, cudaStream_t s) {
+  auto kern = mixed ? batch_cg_rel_kernel<T, VT, E> : batch_cg_kernel<T, VT, E>;
   GKO_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
   GKO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
@@ -387,13 +620,18 @@ static int batch_launch(gko_batch B, const double* b, double* x, double tol, int
   a.ell_k = ptr<int32_t>(B->ell_k);
   a.ell_col = ptr<int32_t>(B->ell_col);
   a.ell_val = B->ell_val ? B->ell_val->ptr : nullptr;
+  a.val32 = B->val32 ? ptr<float>(B->val32) : nullptr;
+  a.ell_val32 = B->ell_val32 ? ptr<float>(B->ell_val32) : nullptr;
+  a.delta = B->delta;
+  a.updates = ptr<int32_t>(B->updates);
   const size_t smem = batch_smem(B);
   GKO_TRY_CUDA(cudaMemsetAsync(B->queue->ptr, 0, sizeof(unsigned), s));
+  if (!B->mixed) GKO_TRY_CUDA(cudaMemsetAsync(B->updates->ptr, 0, sizeof(int32_t) * B->count, s));
   const bool f64 = B->dtype == GKO_F64;
   switch (B->threads * 4 + (f64 ? 2 : 0) + (B->ell ? 1 : 0)) {
 #define GKO_BATCH_CASE(T, VT, E) \
   case T * 4 + (std::is_same<VT, double>::value ? 2 : 0) + (E ? 1 : 0): \
-    return batch_launch_t<T, VT, E>(a, B->n_items, B->block_rows, smem, s);
+    return batch_launch_t<T, VT, E>(a, B->n_items, B->block_rows, smem, B->mixed != 0, s);
 #define GKO_BATCH_T(T) \
   GKO_BATCH_CASE(T, double, false) GKO_BATCH_CASE(T, double, true) GKO_BATCH_CASE(T, float, false) \
   GKO_BATCH_CASE(T, float, true)
@@ -545,6 +783,8 @@ int gko_batch_create(int32_t count, const int64_t* row_off, const int64_t* nnz_o
   GKO_TRY(alloc(sizeof(int32_t) * count, &B->iters));
   GKO_TRY(alloc(sizeof(double) * count, &B->relres));
   GKO_TRY(alloc(sizeof(int32_t) * count, &B->status));
+  GKO_TRY(alloc(sizeof(int32_t) * count, &B->updates));
+  GKO_TRY_CUDA(cudaMemsetAsync(B->updates->ptr, 0, sizeof(int32_t) * count, s));
   GKO_TRY(alloc(sizeof(unsigned), &B->queue));
   GKO_TRY_CUDA(cudaMemcpyAsync(B->row_off->ptr, row_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
   GKO_TRY_CUDA(cudaMemcpyAsync(B->nnz_off->ptr, nnz_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
@@ -632,6 +872,49 @@ int gko_batch_set_schedule(gko_batch B, int32_t warp_rows, int32_t threads, int3
   B->threads = threads;
   B->ell = storage == GKO_BATCH_ELL ? 1 : 0;
   return build_items(B, warp_rows, (cudaStream_t)stream);
+}
+
+int gko_batch_set_precision(gko_batch B, int32_t precision, double reliable_delta, void* stream) {
+  if (!B || (precision != GKO_PRECISION_F64 && precision != GKO_PRECISION_MIXED_F32) ||
+      !(reliable_delta >= 0.0 && reliable_delta < 1.0))
+    return fail(GKO_INVALID_ARG, "batch precision: F64 or MIXED_F32, reliable_delta in [0, 1)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == GKO_PRECISION_MIXED_F32 && !B->val32) {
+    if (B->dtype == GKO_F32) {  // the stored values are the recurrences' values
+      B->val32 = B->val;
+      B->ell_val32 = B->ell_val;
+    } else {
+      Buf v, e;
+      GKO_TRY(alloc(sizeof(float) * std::max<int64_t>(B->total_nnz, 1), &v));
+      GKO_TRY(alloc(sizeof(float) * std::max<int64_t>(B->ell_slots, 1), &e));
+      const int g = sm_count() * 16;
+      if (B->total_nnz > 0)
+        round_f32_kernel<<<(unsigned)std::min<int64_t>((B->total_nnz + 255) / 256, g), 256, 0, s>>>(
+            B->total_nnz, ptr<double>(B->val), ptr<float>(v));
+      if (B->ell_slots > 0)
+        round_f32_kernel<<<(unsigned)std::min<int64_t>((B->ell_slots + 255) / 256, g), 256, 0, s>>>(
+            B->ell_slots, ptr<double>(B->ell_val), ptr<float>(e));
+      GKO_TRY_CUDA(cudaGetLastError());
+      GKO_TRY_CUDA(cudaStreamSynchronize(s));
+      B->val32 = v;
+      B->ell_val32 = e;
+    }
+  }
+  B->mixed = precision == GKO_PRECISION_MIXED_F32 ? 1 : 0;
+  B->delta = reliable_delta > 0.0 ? reliable_delta : 0.1;
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  return GKO_OK;
+}
+
+int gko_batch_last_updates(gko_batch B, int32_t* updates, void* stream) {
+  if (!B || !updates) return fail(GKO_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  GKO_TRY_CUDA(cudaMemcpyAsync(updates, B->updates->ptr, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost, s));
+  GKO_TRY_CUDA(cudaStreamSynchronize(s));
+  return GKO_OK;
 }
 
 int gko_batch_info(gko_batch B, int32_t* count, int64_t* total_rows, int64_t* total_nnz, int32_t* warp_rows,

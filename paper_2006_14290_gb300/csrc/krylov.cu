@@ -56,31 +56,6 @@ struct Ctl {
 __device__ __forceinline__ double wd(double v) { return v; }
 __device__ __forceinline__ double wd(float v) { return widen(v); }
 
-// y + a*x stored as T for an FP64 scalar a.  FP64 vectors: one FP64 FMA.
-// FP32 vectors: a is applied as the float pair hi + lo (hi = fl32(a),
-// lo = fl32(a - hi)) in two FP32 FMAs, so the scalar keeps FP64 accuracy
-// while the arithmetic stays on GB300's FP32 pipe (its FP64 rate is about
-// 1/64 of FP32).
-template <typename T>
-struct Lin;
-template <>
-struct Lin<double> {
-  double a;
-  __device__ explicit Lin(double a_) : a(a_) {}
-  __device__ double operator()(double x, double y) const { return __fma_rn(a, x, y); }
-  __device__ double scale(double x) const { return a * x; }
-};
-template <>
-struct Lin<float> {
-  float hi, lo;
-  __device__ explicit Lin(double a) {
-    hi = __double2float_rn(a);
-    lo = __double2float_rn(a - (double)hi);
-  }
-  __device__ float operator()(float x, float y) const { return __fmaf_rn(lo, x, __fmaf_rn(hi, x, y)); }
-  __device__ float scale(float x) const { return __fmaf_rn(lo, x, hi * x); }
-};
-
 __device__ __forceinline__ double dsq(double a) { return a * a; }
 
 template <typename T>

@@ -103,6 +103,8 @@ SIGNATURES.update({
     "gko_batch_tune": (C.c_int, [_P, _P, _P, _D, _I32, _PI32, _PI32, _PI32, C.POINTER(C.c_float), _P]),
     "gko_batch_set_threshold": (C.c_int, [_P, _I32, _P]),
     "gko_batch_set_schedule": (C.c_int, [_P, _I32, _I32, _I32, _P]),
+    "gko_batch_set_precision": (C.c_int, [_P, _I32, C.c_double, _P]),
+    "gko_batch_last_updates": (C.c_int, [_P, _P, _P]),
     "gko_batch_info": (C.c_int, [_P, _PI32, _PI64, _PI64, _PI32, _PI32, _PI32, _PI32]),
     "gko_batch_destroy": (C.c_int, [_P]),
 })
@@ -546,6 +548,17 @@ class Batch:
 
     def set_threshold(self, warp_rows, stream=None):
         _check(lib().gko_batch_set_threshold(self.handle, warp_rows, _stream(stream)), "gko_batch_set_threshold")
+
+    def set_precision(self, precision, reliable_delta=0.0, stream=None):
+        """PRECISION_F64, or PRECISION_MIXED_F32 (reliable-update CG per system)."""
+        _check(lib().gko_batch_set_precision(self.handle, precision, reliable_delta, _stream(stream)),
+               "gko_batch_set_precision")
+
+    def last_updates(self, stream=None):
+        up = np.zeros(self.count, np.int32)
+        _check(lib().gko_batch_last_updates(self.handle, up.ctypes.data_as(_P), _stream(stream)),
+               "gko_batch_last_updates")
+        return up
 
     def set_schedule(self, warp_rows, threads=256, storage=None, stream=None):
         st = BATCH_CSR if storage is None else storage

@@ -172,3 +172,88 @@ def test_batch_storages_give_identical_results(gko):
             outs[(threads, st)] = (host(xd).tobytes(), it.tobytes())
     for threads in (256, 1024):
         assert outs[(threads, G.BATCH_CSR)] == outs[(threads, G.BATCH_ELL)]
+
+
+@pytest.mark.parametrize("storage", ["csr", "ell"])
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("threshold", [0, 144, 256])
+def test_batch_mixed_reliable_matches_oracle(gko, threshold, threads, storage):
+    """Mixed precision (FP32 recurrences, reliable updates) on every schedule
+    against the oracle's reliable-update CG per system: both sides to 1e-12,
+    solutions within 1e-8 of each other and of the FP64 oracle CG, the
+    reported residual the true one, iteration counts within 15% (the GPU
+    applies FP64 scalars to FP32 vectors as float pairs)."""
+    G = gko
+    systems, bs = batch_problem(120)
+    bs[5] = np.zeros_like(bs[5])
+    B = G.Batch(systems)
+    B.set_schedule(threshold, threads, G.BATCH_ELL if storage == "ell" else G.BATCH_CSR)
+    B.set_precision(G.PRECISION_MIXED_F32)
+    b = concat(bs)
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-12, 20000)
+    up = B.last_updates()
+    assert code == G.OK and np.all(st == G.OK)
+    x = host(xd)
+    off = B.row_off
+    picks = list(range(0, len(systems), 9)) + [5, len(systems) - 3, len(systems) - 2, len(systems) - 1]
+    xr, itr, upr, rrr, str_ = O.batch_cg_reliable([systems[i] for i in picks], [bs[i] for i in picks], tol=1e-12,
+                                                  maxit=20000)
+    for j, i in enumerate(picks):
+        A = systems[i]
+        xi = x[off[i]:off[i + 1]]
+        if i == 5:
+            assert it[i] == 0 and up[i] == 0 and np.all(xi == 0) and rr[i] == 0
+            continue
+        assert str_[j] == 0 and up[i] >= 1
+        assert np.linalg.norm(xi - xr[j]) <= 1e-8 * np.linalg.norm(xr[j]), i
+        xo, _ = O.cg(A, bs[i], tol=1e-12, maxit=20000)
+        assert np.linalg.norm(xi - xo) <= 1e-8 * np.linalg.norm(xo), i
+        assert abs(int(it[i]) - int(itr[j])) <= max(3, 0.15 * itr[j]), (i, it[i], itr[j])
+        true = np.linalg.norm(bs[i] - O.spmv_csr(A, xi)) / np.linalg.norm(bs[i])
+        assert true <= 1.01e-12 and abs(true - rr[i]) <= 1e-14
+
+
+def test_batch_mixed_reliable_options_storage_and_caps(gko):
+    """FP32 storage (the recurrences and the replaced residuals both use the
+    stored FP32 values), deterministic replay, x0, switching back to FP64
+    (update counts read zero), the iteration cap and bad arguments."""
+    G = gko
+    systems, bs = batch_problem(40, seed=4)
+    b = concat(bs)
+    B = G.Batch(systems, storage=G.F32)
+    B.set_precision(G.PRECISION_MIXED_F32, 0.05)
+    outs = []
+    for _ in range(2):
+        xd = dev(np.zeros(b.size))
+        code, it, rr, st = B.cg(dev(b), xd, 1e-10, 20000)
+        assert code == G.OK
+        outs.append(host(xd).tobytes())
+    assert outs[0] == outs[1]
+    x = host(xd)
+    off = B.row_off
+    for i in range(0, len(systems), 7):
+        A = systems[i]
+        A32 = I.Csr(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+        xi = x[off[i]:off[i + 1]]
+        assert np.linalg.norm(bs[i] - O.spmv_csr(A32, xi)) <= 1.01e-10 * np.linalg.norm(bs[i])
+    x0 = np.random.default_rng(9).uniform(-1, 1, B.total_rows)
+    xd = dev(x0)
+    code, it, rr, st = B.cg(dev(b), xd, 1e-10, 20000)
+    assert code == G.OK
+    xd = dev(np.zeros(b.size))
+    code, it, rr, st = B.cg(dev(b), xd, 1e-14, 3)
+    assert code == G.NOT_CONVERGED and np.all(it <= 3)
+    x = host(xd)
+    for i in range(0, len(systems), 7):
+        A32 = I.Csr(systems[i].n_rows, systems[i].n_cols, systems[i].row_ptr, systems[i].col,
+                    systems[i].val.astype(np.float32).astype(np.float64))
+        xi = x[off[i]:off[i + 1]]
+        true = np.linalg.norm(bs[i] - O.spmv_csr(A32, xi)) / np.linalg.norm(bs[i])
+        assert abs(true - rr[i]) <= 1e-12
+    B.set_precision(G.PRECISION_F64)
+    code, it, rr, st = B.cg(dev(b), dev(np.zeros(b.size)), 1e-10, 20000)
+    assert code == G.OK and np.all(B.last_updates() == 0)
+    for bad in ((G.PRECISION_MIXED_BF16, 0.1), (G.PRECISION_MIXED_F32, 1.0), (G.PRECISION_MIXED_F32, -0.5)):
+        with pytest.raises(G.GkoError):
+            B.set_precision(*bad)
