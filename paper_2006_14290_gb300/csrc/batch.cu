@@ -90,6 +90,58 @@ __device__ __forceinline__ const double* block_sum_fin(double v, double* red, F 
   return red + THREADS;
 }
 
+// Row sums of the mixed-precision batched solve: a row's entries in storage
+// order (ELL: its slots k*n + i, padding column -1 skipped), four entries'
+// column and value loads issued before their FMAs, so each entry's L2
+// latency is not exposed in turn (the FP64 solve keeps the plain loop: it is
+// FP64-pipe bound, and with FP32 storage the chunked form ran slower there,
+// 31.8 -> 40.4 ms).  A: the accumulation type (double for the replaced
+// residuals, float for the recurrences).
+__device__ __forceinline__ double ldacc(const double* v, int64_t k, double) { return v[k]; }
+__device__ __forceinline__ double ldacc(const float* v, int64_t k, double) { return widen(v[k]); }
+__device__ __forceinline__ float ldacc(const float* v, int64_t k, float) { return v[k]; }
+__device__ __forceinline__ double fmacc(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmacc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <typename A, typename VT, typename V>
+__device__ __forceinline__ A row_sum_csr(const int32_t* col, const VT* val, int32_t kb, int32_t ke, const V* v) {
+  A s = A(0);
+  for (int32_t k = kb; k < ke; k += 4) {
+    int32_t c[4];
+    A w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = k + u < ke;
+      c[u] = ok ? col[k + u] : 0;
+      w[u] = ok ? ldacc(val, k + u, A(0)) : A(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u < ke) s = fmacc(w[u], (A)v[c[u]], s);
+  }
+  return s;
+}
+
+template <typename A, typename VT, typename V>
+__device__ __forceinline__ A row_sum_ell(const int32_t* col, const VT* val, int K, int n, int i, const V* v) {
+  A s = A(0);
+  for (int k = 0; k < K; k += 4) {
+    int32_t c[4];
+    A w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t o = (int64_t)(k + u) * n + i;
+      const bool ok = k + u < K;
+      c[u] = ok ? col[o] : -1;
+      w[u] = ok ? ldacc(val, o, A(0)) : A(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c[u] >= 0) s = fmacc(w[u], (A)v[c[u]], s);
+  }
+  return s;
+}
+
 // Group primitives of a solve by G threads (G = THREADS: a block; G = 32: a
 // warp): gstep sums v over the group and fin(total, out) derives up to four
 // scalars from it (once per block, in every lane of a warp); gsync orders
@@ -286,31 +338,12 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
   double* x = a.x + r0;
   // FP64 row product with the stored values over the FP64 x (global memory)
   auto row_dot64 = [&](int i) -> double {
-    double s = 0.0;
-    if (ELL) {
-      for (int k = 0; k < K; ++k) {
-        const int64_t o = (int64_t)k * n + i;
-        const int32_t c = col[o];
-        if (c >= 0) s = __fma_rn(ldv(val, o), x[c], s);
-      }
-    } else {
-      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fma_rn(ldv(val, k), x[col[k]], s);
-    }
-    return s;
+    return ELL ? row_sum_ell<double>(col, val, K, n, i, (const double*)x)
+               : row_sum_csr<double>(col, val, rp[i], rp[i + 1], (const double*)x);
   };
   // FP32 row product of the recurrences (FP32 accumulation)
   auto row_dot32 = [&](int i, const float* v) -> float {
-    float s = 0.0f;
-    if (ELL) {
-      for (int k = 0; k < K; ++k) {
-        const int64_t o = (int64_t)k * n + i;
-        const int32_t c = col[o];
-        if (c >= 0) s = __fmaf_rn(v32[o], v[c], s);
-      }
-    } else {
-      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __fmaf_rn(v32[k], v[col[k]], s);
-    }
-    return s;
+    return ELL ? row_sum_ell<float>(col, v32, K, n, i, v) : row_sum_csr<float>(col, v32, rp[i], rp[i + 1], v);
   };
   // r = fl32(b - A x) from the FP64 x; returns ||b - A x||^2 and sets rz = r.r
   auto replace = [&](double& rz) -> double {

@@ -41,6 +41,13 @@ __device__ __forceinline__ void dot_accum(const DotSpec& d, int64_t i, XT v, dou
 
 // The same with w[i] loaded earlier (issued when the thread takes its rows,
 // so its latency overlaps the row's gathers instead of following them).
+// A caller may pass the output itself as w (w = y: the dot is ||y||^2,
+// GMRES's norm of A v); an early load would read y's old contents, so the
+// kernels pass the row's new value instead (dot_w).
+template <typename XT>
+__device__ __forceinline__ XT dot_w(const DotSpec& d, const XT* y, XT w_early, XT v) {
+  return static_cast<const XT*>(d.w) == y ? v : w_early;
+}
 template <typename XT>
 __device__ __forceinline__ void dot_accum_w(const DotSpec& d, XT w, XT v, double& wy, double& yy) {
   const double yv = widen(v);
@@ -373,7 +380,7 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
                 XT w = wv[0];
 #pragma unroll
                 for (int t = 1; t < R; ++t) w = (t == first + j) ? wv[t] : w;
-                dot_accum_w(d, w, v, dwy, dyy);
+                dot_accum_w(d, dot_w(d, a.y, w, v), v, dwy, dyy);
               }
             }
           }
@@ -843,7 +850,7 @@ __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, 
       if (i < a.n) {
         const XT v = (XT)finish_row(a.y, i, sum[r], a.alpha, a.beta, a.plain);
         a.y[i] = v;
-        if (DOT) dot_accum_w(d, wv[r], v, dwy, dyy);
+        if (DOT) dot_accum_w(d, dot_w(d, a.y, wv[r], v), v, dwy, dyy);
       }
     }
   }
