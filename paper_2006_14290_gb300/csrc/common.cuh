@@ -11,6 +11,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "gko.h"
 
@@ -291,5 +292,52 @@ struct Lin<float> {
 
 
 inline unsigned ceil_div_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may be dispatched while its predecessor
+// in the stream is still draining; it must not touch memory the predecessor
+// writes before griddepcontrol.wait returns (the predecessor has completed
+// and its writes are visible).  Every kernel that launch_k may launch this
+// way starts with pdl_begin(): that wait, then launch_dependents, which lets
+// its own successor be dispatched as soon as this grid's blocks leave.  For
+// a kernel launched without the attribute the stream has already ordered the
+// predecessor and the wait returns at once.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Whether launch_k uses programmatic serialization on this host thread (set
+// by the solvers around their iteration launches, PdlScope).
+bool& pdl_launches();
+struct PdlScope {
+  bool old;
+  explicit PdlScope(bool on) : old(pdl_launches()) { pdl_launches() = on; }
+  ~PdlScope() { pdl_launches() = old; }
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
+
+// kern<<<grid, block, smem, s>>>(args...), with programmatic stream
+// serialization when pdl_launches() is set.  Only kernels that begin with
+// pdl_begin() may be launched through it.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  if (!pdl_launches()) {
+    kern<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 }  // namespace gko

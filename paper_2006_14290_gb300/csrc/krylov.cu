@@ -259,6 +259,7 @@ struct Store2 {
 template <typename T>
 __global__ void __launch_bounds__(256, 4) dot2_kernel(int64_t n, const T* __restrict__ w, const T* __restrict__ y,
                                                    RedWs ws, double* out, const int* gate) {
+  pdl_begin();
   if (gated(gate)) return;
   double acc[2] = {0.0, 0.0};
   GKO_GRID_LOOP(i, n) {
@@ -322,6 +323,7 @@ template <typename T, bool PC>
 __global__ void __launch_bounds__(256, 4) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
                                                         const T* __restrict__ p, const T* __restrict__ q, Ctl* c,
                                                         RedWs ws, const T* __restrict__ d) {
+  pdl_begin();
   constexpr int NV = PC ? 2 : 1;
   if (gated(&c->done)) return;
   const bool ok = c->red[0] > 0.0;
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(256, 4) cg_update_kernel(int64_t n, T* __restr
 template <typename T, bool PC>
 __global__ void __launch_bounds__(256, 4) cg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p, Ctl* c,
                                                    const T* __restrict__ d) {
+  pdl_begin();
   if (gated(&c->done)) return;
   const Lin<T> bp = block_bcast<Lin<T>>([&] { return Lin<T>(c->beta); });
   const bool aligned = al16(r) && al16(p) && (!PC || al16(d));
@@ -409,6 +412,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 4) bicg_p_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
                                                      const T* __restrict__ v, Ctl* c, const T* __restrict__ d = nullptr,
                                                      T* __restrict__ ph = nullptr) {
+  pdl_begin();
   if (gated(&c->done)) return;
   const LinPair<T> L = block_bcast<LinPair<T>>([&] { return LinPair<T>{Lin<T>(c->beta), Lin<T>(-c->omega)}; });
   const Lin<T> bp = L.a, wv = L.b;
@@ -450,6 +454,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 4) bicg_s_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ v,
                                                      T* __restrict__ s, Ctl* c, RedWs ws,
                                                      const T* __restrict__ d = nullptr, T* __restrict__ sh = nullptr) {
+  pdl_begin();
   if (gated(&c->done)) return;
   const double rv = c->red[0];
   const Lin<T> av = block_bcast<Lin<T>>([&] { return Lin<T>(rv != 0.0 ? -(c->rho_new / rv) : 0.0); });
@@ -535,6 +540,7 @@ __global__ void __launch_bounds__(256, 4) bicg_x_kernel(int64_t n, T* __restrict
                                                      T* __restrict__ r, const T* __restrict__ rh, Ctl* c, RedWs ws,
                                                      const T* __restrict__ ph = nullptr,
                                                      const T* __restrict__ sh = nullptr) {
+  pdl_begin();
   if (gated(&c->done)) return;
   double acc[2] = {0.0, 0.0};
   const LinTriple<T> L = block_bcast<LinTriple<T>>([&] {
@@ -780,6 +786,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 4) gm_multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ldv,
                                                           const T* __restrict__ w, double* __restrict__ partials,
                                                           Ctl* c, int pass) {
+  pdl_begin();
   if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
   const int j = blockIdx.y;
   const T* v = V + (int64_t)j * ldv;
@@ -792,6 +799,7 @@ __global__ void __launch_bounds__(256, 4) gm_multidot_kernel(int64_t n, const T*
 __global__ void __launch_bounds__(256, 4) gm_multidot_finish_kernel(int g, const double* __restrict__ partials,
                                                                  double* __restrict__ h, int accumulate, Ctl* c,
                                                                  int pass) {
+  pdl_begin();
   if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
   const int j = blockIdx.x;
   double acc = 0.0;
@@ -840,6 +848,7 @@ template <typename T, bool NORM>
 __global__ void __launch_bounds__(256, 4) gm_axpy_kernel(int64_t n, int jcount, const double* __restrict__ h,
                                                       const T* __restrict__ V, int64_t ldv, T* __restrict__ w, Ctl* c,
                                                       RedWs ws, int pass) {
+  pdl_begin();
   __shared__ T s_hi[kMaxRestart + 1], s_lo[kMaxRestart + 1];
   if (gated(&c->phase) || (pass == 1 && *(volatile int*)&c->noreorth)) return;
   load_coefs<T>(h, jcount, -1.0, s_hi, s_lo);
@@ -862,6 +871,7 @@ __global__ void __launch_bounds__(256, 4) gm_axpy_kernel(int64_t n, int jcount, 
 __global__ void gm_givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
                                  double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                                  double* __restrict__ g, Ctl* c) {
+  pdl_begin();
   if (gated(&c->phase)) return;
   double* col = H + (int64_t)j;  // H[i*m + j]
   const bool two = !c->noreorth;
@@ -898,6 +908,7 @@ __global__ void gm_givens_kernel(int j, int m, const double* __restrict__ h1, co
 template <typename T>
 __global__ void __launch_bounds__(256, 4) gm_next_kernel(int64_t n, const T* __restrict__ w, T* __restrict__ vn,
                                                       Ctl* c) {
+  pdl_begin();
   if (gated(&c->phase)) return;
   const Lin<T> sc = block_bcast<Lin<T>>([&] { return Lin<T>(1.0 / c->rho); });
   GKO_GRID_LOOP(i, n) vn[i] = sc.scale(w[i]);
@@ -1515,10 +1526,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       return spmv_run(A, in, outv, 1.0, 0.0, s, spmv_scratch, &d, gate);
     }
     GKO_TRY(spmv_run(A, in, outv, 1.0, 0.0, s, spmv_scratch, nullptr, gate));
-    if (w) {
-      dot2_kernel<T><<<rg, 256, 0, s>>>(n, w, outv, ws, c->red, gate);
-      GKO_TRY_CUDA(cudaGetLastError());
-    }
+    if (w) GKO_TRY_CUDA(launch_k(dot2_kernel<T>, dim3(rg), dim3(256), 0, s, n, w, outv, ws, c->red, gate));
     return GKO_OK;
   };
   out->iterations = 0;
@@ -1554,25 +1562,31 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       hc->status = kNotConverged;
       hc->done = 1;
     }
+    // An iteration's kernels run back to back on s: each is launched with
+    // programmatic serialization (PdlScope), so its dispatch overlaps the
+    // drain of the one before; each waits for that one before touching memory.
+    const dim3 B256(256);
     auto enqueue = [&](int count) -> int {
+      PdlScope pdl(true);
       for (int it = 0; it < count; ++it) {
         if (sp.solver == 0) {
           GKO_TRY(spmv(p, q, p, &c->done));
           if (dinv) {
-            cg_update_kernel<T, true><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws, dinv);
-            cg_p_kernel<T, true><<<vg, 256, 0, s>>>(n, r, p, c, dinv);
+            GKO_TRY_CUDA(launch_k(cg_update_kernel<T, true>, dim3(rg), B256, 0, s, n, x, r, p, q, c, ws, dinv));
+            GKO_TRY_CUDA(launch_k(cg_p_kernel<T, true>, dim3(vg), B256, 0, s, n, r, p, c, dinv));
           } else {
-            cg_update_kernel<T, false><<<rg, 256, 0, s>>>(n, x, r, p, q, c, ws, nullptr);
-            cg_p_kernel<T, false><<<vg, 256, 0, s>>>(n, r, p, c, nullptr);
+            GKO_TRY_CUDA(launch_k(cg_update_kernel<T, false>, dim3(rg), B256, 0, s, n, x, r, p, q, c, ws,
+                                  (const T*)nullptr));
+            GKO_TRY_CUDA(launch_k(cg_p_kernel<T, false>, dim3(vg), B256, 0, s, n, r, p, c, (const T*)nullptr));
           }
         } else {
-          bicg_p_kernel<T><<<vg, 256, 0, s>>>(n, r, p, v, c, dinv, ph);
+          GKO_TRY_CUDA(launch_k(bicg_p_kernel<T>, dim3(vg), B256, 0, s, n, r, p, v, c, dinv, ph));
           GKO_TRY(spmv(dinv ? ph : p, v, rh, &c->done));
-          bicg_s_kernel<T><<<rg, 256, 0, s>>>(n, r, v, sv, c, ws, dinv, sh);
+          GKO_TRY_CUDA(launch_k(bicg_s_kernel<T>, dim3(rg), B256, 0, s, n, r, v, sv, c, ws, dinv, sh));
           GKO_TRY(spmv(dinv ? sh : sv, tv, sv, &c->phase, true));
-          bicg_x_kernel<T><<<rg, 256, 0, s>>>(n, x, p, sv, tv, r, rh, c, ws, ph, sh);
+          GKO_TRY_CUDA(launch_k(bicg_x_kernel<T>, dim3(rg), B256, 0, s, n, x, p, sv, tv, r, rh, c, ws,
+                                (const T*)ph, (const T*)sh));
         }
-        GKO_TRY_CUDA(cudaGetLastError());
       }
       return GKO_OK;
     };
@@ -1679,6 +1693,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       }
       gm_scale_kernel<T><<<vg, 256, 0, s>>>(n, V, &c->beta, c);
       for (int j = 0; j < m; ++j) {
+        PdlScope pdl(true);  // as in the CG / BiCGSTAB iterations
         T* vj = V + (int64_t)j * ld;
         // w = A v_j with ||w||^2 from the SpMV epilogue (red[0])
         GKO_TRY(spmv(vj, w, w, &c->phase));
@@ -1686,13 +1701,18 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
         // shrank ||w|| below ||w0|| / sqrt(2) (selective reorthogonalisation)
         for (int pass = 0; pass < 2; ++pass) {
           double* hp = pass == 0 ? h1 : h2;
-          gm_multidot_kernel<T><<<dim3((unsigned)mg, (unsigned)(j + 1)), 256, 0, s>>>(n, V, ld, w, mpart, c, pass);
-          gm_multidot_finish_kernel<<<j + 1, 256, 0, s>>>((int)mg, mpart, hp, 0, c, pass);
-          gm_axpy_kernel<T, true><<<rg, 256, 0, s>>>(n, j + 1, hp, V, ld, w, c, ws, pass);
+          GKO_TRY_CUDA(launch_k(gm_multidot_kernel<T>, dim3((unsigned)mg, (unsigned)(j + 1)), dim3(256), 0, s, n,
+                                (const T*)V, ld, (const T*)w, mpart, c, pass));
+          GKO_TRY_CUDA(launch_k(gm_multidot_finish_kernel, dim3(j + 1), dim3(256), 0, s, (int)mg,
+                                (const double*)mpart, hp, 0, c, pass));
+          GKO_TRY_CUDA(launch_k(gm_axpy_kernel<T, true>, dim3(rg), dim3(256), 0, s, n, j + 1, (const double*)hp,
+                                (const T*)V, ld, w, c, ws, pass));
         }
-        gm_givens_kernel<<<1, 1, 0, s>>>(j, m, h1, h2, H, cs, sn, g, c);
-        if (j + 1 <= m) gm_next_kernel<T><<<vg, 256, 0, s>>>(n, w, V + (int64_t)(j + 1) * ld, c);
-        GKO_TRY_CUDA(cudaGetLastError());
+        GKO_TRY_CUDA(launch_k(gm_givens_kernel, dim3(1), dim3(1), 0, s, j, m, (const double*)h1, (const double*)h2, H,
+                              cs, sn, g, c));
+        if (j + 1 <= m)
+          GKO_TRY_CUDA(launch_k(gm_next_kernel<T>, dim3(vg), dim3(256), 0, s, n, (const T*)w,
+                                V + (int64_t)(j + 1) * ld, c));
       }
       gm_backsolve_kernel<<<1, 1, 0, s>>>(m, H, g, ny, c);
       gm_update_x_kernel<T><<<vg, 256, 0, s>>>(n, ny, V, ld, x, c);

@@ -24,6 +24,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void clear_error() { g_err.clear(); }
 
+bool& pdl_launches() {
+  static thread_local bool on = false;
+  return on;
+}
+
 // ------------------------------------------------------------- budget ----
 
 static std::atomic<int64_t> g_budget{0};

@@ -398,6 +398,7 @@ __device__ __forceinline__ void rowblock_body(const CsrArgs<VT, XT>& a, int cap,
 template <int S, int R, typename VT, typename XT, bool DOT>
 __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
                                                                    int expected, const int* gate, int* err) {
+  pdl_begin();
   if (gated(gate)) return;
   rowblock_body<S, R, VT, XT, DOT, false>(a, cap, d, expected, err);
 }
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(kRbThreads) csr_rowblock_kernel(CsrArgs<VT, XT
 template <int S, int R, typename VT, typename XT, bool DOT>
 __global__ void __launch_bounds__(kRbThreads) coo_rowblock_kernel(CsrArgs<VT, XT> a, int cap, DotSpec d,
                                                                    int expected, const int* gate, int* err) {
+  pdl_begin();
   if (gated(gate)) return;
   rowblock_body<S, R, VT, XT, DOT, true>(a, cap, d, expected, err);
 }
@@ -796,6 +798,7 @@ template <int RPT, typename VT, typename XT, bool DOT, bool SELL>
 __global__ void __launch_bounds__(256) ell_kernel(EllArgs<VT, XT> a, DotSpec d, int expected, const int* gate) {
   using AT = acc_t<VT>;
   constexpr int U = 4;
+  pdl_begin();
   if (gated(gate)) return;
   const int64_t groups = (a.n + RPT - 1) / RPT;
   double dwy = 0.0, dyy = 0.0;
@@ -1377,7 +1380,13 @@ struct SpmvImpl {
       ca.row = ptr<int32_t>(A->coo_row);
       ca.rb_ptr = ptr<int32_t>(A->plan.coo_rb);
     }
-    kern<<<(unsigned)g, kRbThreads, smem, s>>>(ca, cap, d, (int)g + extra, gate, device_error_word());
+    const cudaError_t le =
+        launch_k(kern, dim3((unsigned)g), dim3(kRbThreads), smem, s, ca, cap, d, (int)g + extra, gate,
+                 device_error_word());
+    if (le != cudaSuccess) {
+      cuda_fail(le, "row-block kernel launch");
+      return kLaunchCudaError;
+    }
     return (int)g;
   }
 
@@ -1499,8 +1508,7 @@ struct SpmvImpl {
       while ((1 << a.cshift) < a.C) ++a.cshift;
       a.sets = ptr<int32_t>(A->sellp_sets);
     }
-    kern<<<(unsigned)g, 256, 0, s>>>(a, d, (int)g, gate);
-    GKO_TRY_CUDA(cudaGetLastError());
+    GKO_TRY_CUDA(launch_k(kern, dim3((unsigned)g), dim3(256), 0, s, a, d, (int)g, gate));
     return GKO_OK;
   }
 
