@@ -11,6 +11,7 @@
 // convergence cost one empty launch each.  Dots and norms accumulate in FP64;
 // vectors are stored as T (double, or float for the inner solve of mixed
 // precision) with every update computed in FP64 and rounded once on store.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
@@ -1396,8 +1397,8 @@ static bool small_cg_ok(const gko_matrix_s* A, const SolveSpec& sp) {
 template <typename K>
 static int small_per_sm(K kern, size_t smem) {
   int nb = 0;
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                              cudaSuccess) {
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kSmallSmemMax) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1414,8 +1415,10 @@ static int small_cg_launch(const gko_matrix_s* A, SmallArgs<T, VT>& a, int G, si
   void* args[] = {&a};
   if (staged) {
     auto kern = small_cg_kernel<T, VT, RPT, true>;
+    // always the largest request (kSmallSmemMax), so concurrent solves with
+    // different sizes never lower each other's limit
     if (smem > 48 * 1024)
-      GKO_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      GKO_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemMax));
     GKO_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)G), dim3(kSmallThreads), args, smem, s));
   } else {
     auto kern = small_cg_kernel<T, VT, RPT, false>;
@@ -1474,6 +1477,300 @@ static int small_cg(const gko_matrix_s* A, const double* b, T* x, bool x_zero, c
   return GKO_OK;
 }
 
+// ------------------------------------------------ cluster CG (tiny n) --
+//
+// The same CG as small_cg_kernel (Saad Alg. 6.18 / 9.1, true-residual check,
+// residual replacement, breakdown and iteration-cap rules) for n <= 16 x 256
+// x 4 rows, run by ONE thread-block cluster of CS <= 16 CTAs instead of a
+// cooperative grid: CTA k owns rows [k RB, (k+1) RB) (RB = 256 RPT) and keeps
+// its slice of p (and, for the true-residual check, of x) in shared memory;
+// the SpMV gathers p from the owning CTA's shared memory through distributed
+// shared memory, and every grid barrier becomes a hardware cluster barrier
+// (barrier.cluster with release/acquire semantics) instead of a round trip
+// through an L2 counter.  Reductions: each CTA publishes its block sums in
+// its shared memory, and after the barrier warp 0 of every CTA reads the CS
+// partials (lane l from CTA l) and adds them with a fixed butterfly, so all
+// CTAs hold bit-identical totals and take the same branch.  That uniformity is
+// what keeps the hardware barriers safe: no CTA leaves the loop or the kernel
+// on its own, and a last barrier keeps every CTA's shared memory alive until
+// the others have finished reading it.
+namespace cgx = cooperative_groups;
+constexpr int kClusterMax = 16;
+constexpr int64_t kClusterRows = (int64_t)kClusterMax * kSmallThreads * 4;
+constexpr size_t kClusterSmemMax = 200 * 1024;
+
+template <int NV>
+__device__ __forceinline__ void cluster_reduce(const cgx::cluster_group& cl, double (&v)[NV], double (*s_red)[4],
+                                               int site, double* s_tot) {
+  block_sum_n<kSmallThreads, NV>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_red[site][k] = v[k];
+  cl.sync();
+  if (threadIdx.x < 32) {
+    const int cs = (int)cl.num_blocks();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = (int)threadIdx.x < cs ? *cl.map_shared_rank(&s_red[site][k], threadIdx.x) : 0.0;
+      t = subwarp_sum<32>(t, 0xffffffffu);
+      if (threadIdx.x == 0) s_tot[k] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
+}
+
+template <typename T, typename VT, int RPT, bool SMEM>
+__global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, VT> a) {
+  using AT = acc_t<VT>;
+  constexpr int RB = kSmallThreads * RPT;
+  const cgx::cluster_group cl = cgx::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_p = reinterpret_cast<T*>(smem_raw);
+  T* s_x = s_p + RB;
+  int32_t* scol = reinterpret_cast<int32_t*>(smem_raw + 2 * (size_t)RB * sizeof(T));
+  VT* sval = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(scol) +
+                                   (((size_t)a.block_cap * sizeof(int32_t) + 15) & ~(size_t)15));
+  __shared__ double s_red[4][4];
+  __shared__ double s_tot[4];
+  const int64_t row0 = (int64_t)rank * RB;
+  const int64_t row1 = row0 + RB < a.n ? row0 + RB : a.n;
+  const int32_t e0 = __ldg(a.rp + row0), e1 = __ldg(a.rp + row1);
+  if (SMEM) {
+    for (int32_t k = e0 + (int32_t)threadIdx.x; k < e1; k += kSmallThreads) {
+      scol[k - e0] = __ldg(a.col + k);
+      sval[k - e0] = a.val[k];
+    }
+  }
+  int32_t ks[RPT], ke[RPT];
+  bool own[RPT];
+  double bj[RPT];
+  T xj[RPT], rj[RPT], pj[RPT], dj[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    const int64_t i = row0 + threadIdx.x + (int64_t)j * kSmallThreads;
+    own[j] = i < a.n;
+    ks[j] = own[j] ? __ldg(a.rp + i) - (SMEM ? e0 : 0) : 0;
+    ke[j] = own[j] ? __ldg(a.rp + i + 1) - (SMEM ? e0 : 0) : 0;
+    bj[j] = own[j] ? a.b[i] : 0.0;
+    xj[j] = own[j] && !a.x_zero ? a.x[i] : T(0);
+    dj[j] = own[j] && a.d ? a.d[i] : T(1);
+  }
+  const bool pc = a.d != nullptr;
+  // element c of a vector whose slices live in the CTAs' shared memory (s)
+  auto gat = [&](const T* s, int32_t c) -> T {
+    const int owner = c / RB, off = c - owner * RB;
+    return owner == rank ? s[off] : *cl.map_shared_rank(s + off, owner);
+  };
+  // row j of A v, v in the CTAs' slices s; up to 8 gathers issued before their FMAs
+  auto row_dot = [&](int j, const T* s) -> T {
+    constexpr int U = 8;
+    AT acc = AT(0);
+    for (int32_t k = ks[j]; k < ke[j]; k += U) {
+      VT w[U];
+      T g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = k + u < ke[j];
+        const int32_t c = in ? (SMEM ? scol[k + u] : __ldg(a.col + k + u)) : 0;
+        w[u] = in ? (SMEM ? sval[k + u] : a.val[k + u]) : VT(0);
+        g[u] = in ? gat(s, c) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k + u < ke[j]) acc = madd(to_acc(w[u]), to_acc(g[u]), acc);
+    }
+    return (T)acc;
+  };
+  auto publish = [&](T* dst, const T (&v)[RPT]) {
+#pragma unroll
+    for (int j = 0; j < RPT; ++j)
+      if (own[j]) dst[threadIdx.x + j * kSmallThreads] = v[j];
+  };
+  int status = kRun, it = 0;
+  // r = b - A x0 (x0 = 0: r = b), z = d r, p = z; ||b||^2, r.r, r.z
+  if (!a.x_zero) {
+    publish(s_x, xj);
+    cl.sync();
+  } else {
+    __syncthreads();  // the staged entries
+  }
+  double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    if (!own[j]) continue;
+    const T ri = a.x_zero ? (T)bj[j] : (T)(bj[j] - wd(row_dot(j, s_x)));
+    const T zi = pc ? dj[j] * ri : ri;
+    rj[j] = ri;
+    pj[j] = zi;
+    v3[0] += bj[j] * bj[j];
+    v3[1] += wd(ri) * wd(ri);
+    v3[2] += wd(ri) * wd(zi);
+  }
+  publish(s_p, pj);  // visible after the reduction's cluster barrier
+  cluster_reduce<3>(cl, v3, s_red, 0, s_tot);
+  const double nb = sqrt(v3[0]), tol_abs = a.rel_tol * nb;
+  double rho = v3[2];
+  if (v3[0] == 0.0) {  // b == 0: x = 0 after 0 iterations
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) xj[j] = T(0);
+    status = kConverged;
+  } else if (sqrt(v3[1]) <= tol_abs) {
+    status = kConverged;
+  } else if (a.maxit <= 0) {
+    status = kNotConverged;
+  }
+  while (status == kRun) {
+    T qj[RPT];
+    double v1[1] = {0.0};
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      qj[j] = own[j] ? row_dot(j, s_p) : T(0);
+      v1[0] += wd(pj[j]) * wd(qj[j]);
+    }
+    cluster_reduce<1>(cl, v1, s_red, 1, s_tot);
+    const double pq = v1[0];
+    if (!(pq > 0.0)) {
+      status = kBreakdown;
+      break;
+    }
+    const double alpha = rho / pq;
+    const Lin<T> ax(alpha), ar(-alpha);
+    double v2[2] = {0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      if (!own[j]) continue;
+      xj[j] = ax(pj[j], xj[j]);
+      rj[j] = ar(qj[j], rj[j]);
+      const double rw = wd(rj[j]);
+      v2[0] = __fma_rn(rw, rw, v2[0]);
+      v2[1] = pc ? __fma_rn(rw, wd(dj[j] * rj[j]), v2[1]) : v2[0];
+    }
+    cluster_reduce<2>(cl, v2, s_red, 2, s_tot);
+    ++it;
+    double rho_new = pc ? v2[1] : v2[0];
+    if (sqrt(v2[0]) <= tol_abs) {
+      if (!a.check_true) {
+        status = kConverged;
+        break;
+      }
+      // true residual t = b - A x: every CTA's slice of x first
+      publish(s_x, xj);
+      cl.sync();
+      T tj[RPT];
+      double vt[2] = {0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        tj[j] = own[j] ? (T)(bj[j] - wd(row_dot(j, s_x))) : T(0);
+        vt[0] += wd(tj[j]) * wd(tj[j]);
+        vt[1] += wd(tj[j]) * wd(pc ? dj[j] * tj[j] : tj[j]);
+      }
+      cluster_reduce<2>(cl, vt, s_red, 3, s_tot);
+      if (sqrt(vt[0]) <= tol_abs) {
+        status = kConverged;
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) rj[j] = tj[j];  // residual replacement (p is kept)
+      rho_new = vt[1];
+    } else if (it >= a.maxit) {
+      status = kNotConverged;
+      break;
+    }
+    const Lin<T> bp(rho_new / rho);
+    rho = rho_new;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) pj[j] = bp(pj[j], pc ? dj[j] * rj[j] : rj[j]);
+    publish(s_p, pj);
+    cl.sync();
+  }
+#pragma unroll
+  for (int j = 0; j < RPT; ++j)
+    if (own[j]) a.x[row0 + threadIdx.x + (int64_t)j * kSmallThreads] = xj[j];
+  if (rank == 0 && threadIdx.x == 0) {
+    a.c->status = status;
+    a.c->iter = it;
+    a.c->cycles = 0;
+  }
+  cl.sync();  // no CTA's shared memory goes while another may still read it
+}
+
+// Launch the cluster CG when it applies (n <= kClusterRows and a cluster of
+// the needed size fits); GKO_NOT_SUPPORTED otherwise (the caller takes the
+// cooperative-grid kernel).
+template <typename T, typename VT, int RPT>
+static int cluster_cg_launch(SmallArgs<T, VT>& a, int CS, size_t smem, bool staged, cudaStream_t s) {
+  auto kern = staged ? cluster_cg_kernel<T, VT, RPT, true> : cluster_cg_kernel<T, VT, RPT, false>;
+  // attributes set once per instantiation, to the largest request, so
+  // concurrent solves (serving threads) never undo each other's setting
+  static const bool attrs_ok = [] {
+    bool ok = true;
+    for (auto k : {cluster_cg_kernel<T, VT, RPT, true>, cluster_cg_kernel<T, VT, RPT, false>})
+      ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax) ==
+               cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+  }();
+  if (!attrs_ok || smem > kClusterSmemMax) return GKO_NOT_SUPPORTED;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)CS);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return GKO_NOT_SUPPORTED;
+  }
+  GKO_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+  return GKO_OK;
+}
+
+template <typename T, typename VT>
+static int cluster_cg(const gko_matrix_s* A, const double* b, T* x, bool x_zero, const SolveSpec& sp,
+                      cudaStream_t s, SolveOut* out) {
+  const int64_t n = A->n_rows;
+  if (n > kClusterRows) return GKO_NOT_SUPPORTED;
+  // rows per thread: the fewest (1, 2, 4) for which 16 CTAs cover n
+  int rpt = 1;
+  while (rpt < 4 && n > (int64_t)kClusterMax * kSmallThreads * rpt) rpt *= 2;
+  const int64_t RB = (int64_t)kSmallThreads * rpt;
+  const int CS = (int)((n + RB - 1) / RB);
+  const size_t cap = (size_t)RB * (size_t)std::max(1, A->plan.max_len);
+  const size_t vec = 2 * (size_t)RB * sizeof(T);
+  const size_t stage = ((cap * sizeof(int32_t) + 15) & ~(size_t)15) + cap * sizeof(VT);
+  const bool staged = vec + stage <= kClusterSmemMax;
+  const size_t smem = staged ? vec + stage : vec;
+  Scratch mem;
+  GKO_TRY(mem.get(sizeof(Ctl) + 1024, s));
+  Carve cv{static_cast<char*>(mem.data())};
+  Ctl* c = cv.take<Ctl>(1);
+  SmallArgs<T, VT> a{n,  ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col), ptr<VT>(A->val),
+                     b,  x, nullptr, static_cast<const T*>(sp.minv), sp.rel_tol, sp.maxit, sp.check_true,
+                     x_zero ? 1 : 0, (int32_t)cap, nullptr, nullptr, device_error_word(), c};
+  int rc = GKO_NOT_SUPPORTED;
+  if (rpt == 1) rc = cluster_cg_launch<T, VT, 1>(a, CS, smem, staged, s);
+  if (rpt == 2) rc = cluster_cg_launch<T, VT, 2>(a, CS, smem, staged, s);
+  if (rpt == 4) rc = cluster_cg_launch<T, VT, 4>(a, CS, smem, staged, s);
+  if (rc != GKO_OK) return rc;
+  Ctl* hc = host_ctl();
+  GKO_TRY(read_ctl(c, hc, s));
+  out->status = hc->status;
+  out->iterations = hc->iter;
+  out->cycles = 0;
+  return GKO_OK;
+}
+
 // One Krylov solve on the device.  A: matrix whose value type matches T
 // (double: F64; float: F32/BF16).  b: FP64 right-hand side; x: T vector,
 // x0 on entry (x_zero: treat x0 as zero without reading it).
@@ -1483,10 +1780,14 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   if (small_cg_ok(A, sp)) {
     int rc = GKO_NOT_SUPPORTED;
     if constexpr (std::is_same<T, double>::value) {
-      if (A->dtype == GKO_F64) rc = small_cg<double, double>(A, b, x, x_zero, sp, s, out);
+      if (A->dtype == GKO_F64) rc = cluster_cg<double, double>(A, b, x, x_zero, sp, s, out);
+      if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_F64) rc = small_cg<double, double>(A, b, x, x_zero, sp, s, out);
     } else {
-      if (A->dtype == GKO_F32) rc = small_cg<float, float>(A, b, x, x_zero, sp, s, out);
-      if (A->dtype == GKO_BF16) rc = small_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
+      if (A->dtype == GKO_F32) rc = cluster_cg<float, float>(A, b, x, x_zero, sp, s, out);
+      if (A->dtype == GKO_BF16) rc = cluster_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
+      if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_F32) rc = small_cg<float, float>(A, b, x, x_zero, sp, s, out);
+      if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_BF16)
+        rc = small_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
     }
     if (rc != GKO_NOT_SUPPORTED) return rc;
   }

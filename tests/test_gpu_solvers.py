@@ -268,6 +268,30 @@ def test_reliable_updates_options(gko):
         assert x.tobytes() == x2.tobytes() and res.iterations == res2.iterations
 
 
+@pytest.mark.parametrize("N", [128, 129])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_cg_small_system_paths_match_oracle(gko, N, precision):
+    """CG on 2D systems at the edge of the one-cluster CG (n = 128^2 = 16,384,
+    16 CTAs of 256 threads x 4 rows) and just past it (n = 129^2, the
+    cooperative-grid CG): solution parity with the oracle at 1e-12, FP64 and
+    mixed FP32 (restarted refinement, whose inner solves take the same
+    small-system kernels), with and without Jacobi."""
+    G = gko
+    A = I.varcoef2d_5pt(N, np.random.default_rng(N))
+    b = np.random.default_rng(3).uniform(-1, 1, A.n_rows)
+    M = G.from_csr(A)
+    opt = {} if precision == "f64" else {"precision": G.PRECISION_MIXED_F32, "refinement": G.REFINE_RESTART}
+    xo, ro = O.cg(A, b, tol=1e-12, maxit=20000)
+    for pc in (G.PRECOND_NONE, G.PRECOND_JACOBI):
+        xg, res = gpu_solve(G, "cg", M, b, tol=1e-12, maxit=20000, preconditioner=pc, **opt)
+        assert res.status == G.OK, res
+        assert true_rel_res(A, xg, b) <= 1.01e-12
+        assert abs(res.rel_residual - true_rel_res(A, xg, b)) <= 1e-13
+        assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+        if precision == "f64" and pc == G.PRECOND_NONE:
+            assert iters_close(res.iterations, ro.iterations), (res.iterations, ro.iterations)
+
+
 def test_edge_cases(gko):
     G = gko
     A, b = spd_problem()
