@@ -1496,6 +1496,32 @@ static int small_cg(const gko_matrix_s* A, const double* b, T* x, bool x_zero, c
 // the others have finished reading it.
 namespace cgx = cooperative_groups;
 constexpr int kClusterMax = 16;
+
+// Cluster barrier and distributed-shared-memory loads as inline PTX with
+// memory clobbers, so the compiler can move no shared-memory access across
+// the barrier and no remote load ahead of it (built on the cooperative-groups
+// calls, one instantiation read a remote reduction slot before its owner had
+// written it).  Call the barrier from control flow that is the same in every
+// thread of the cluster.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t dsmem_addr(const void* local, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double dsmem_ld(const double* local, unsigned rank) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+  return v;
+}
+__device__ __forceinline__ float dsmem_ld(const float* local, unsigned rank) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+  return v;
+}
 constexpr int64_t kClusterRows = (int64_t)kClusterMax * kSmallThreads * 4;
 constexpr size_t kClusterSmemMax = 200 * 1024;
 
@@ -1506,12 +1532,12 @@ __device__ __forceinline__ void cluster_reduce(const cgx::cluster_group& cl, dou
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < NV; ++k) s_red[site][k] = v[k];
-  cl.sync();
+  cluster_barrier();
   if (threadIdx.x < 32) {
     const int cs = (int)cl.num_blocks();
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double t = (int)threadIdx.x < cs ? *cl.map_shared_rank(&s_red[site][k], threadIdx.x) : 0.0;
+      double t = (int)threadIdx.x < cs ? dsmem_ld(&s_red[site][k], threadIdx.x) : 0.0;
       t = subwarp_sum<32>(t, 0xffffffffu);
       if (threadIdx.x == 0) s_tot[k] = t;
     }
@@ -1562,7 +1588,7 @@ __global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, 
   // element c of a vector whose slices live in the CTAs' shared memory (s)
   auto gat = [&](const T* s, int32_t c) -> T {
     const int owner = c / RB, off = c - owner * RB;
-    return owner == rank ? s[off] : *cl.map_shared_rank(s + off, owner);
+    return owner == rank ? s[off] : dsmem_ld(s + off, (unsigned)owner);
   };
   // row j of A v, v in the CTAs' slices s; up to 8 gathers issued before their FMAs
   auto row_dot = [&](int j, const T* s) -> T {
@@ -1593,7 +1619,7 @@ __global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, 
   // r = b - A x0 (x0 = 0: r = b), z = d r, p = z; ||b||^2, r.r, r.z
   if (!a.x_zero) {
     publish(s_x, xj);
-    cl.sync();
+    cluster_barrier();
   } else {
     __syncthreads();  // the staged entries
   }
@@ -1658,7 +1684,7 @@ __global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, 
       }
       // true residual t = b - A x: every CTA's slice of x first
       publish(s_x, xj);
-      cl.sync();
+      cluster_barrier();
       T tj[RPT];
       double vt[2] = {0.0, 0.0};
 #pragma unroll
@@ -1684,7 +1710,7 @@ __global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, 
 #pragma unroll
     for (int j = 0; j < RPT; ++j) pj[j] = bp(pj[j], pc ? dj[j] * rj[j] : rj[j]);
     publish(s_p, pj);
-    cl.sync();
+    cluster_barrier();
   }
 #pragma unroll
   for (int j = 0; j < RPT; ++j)
@@ -1694,7 +1720,7 @@ __global__ void __launch_bounds__(kSmallThreads) cluster_cg_kernel(SmallArgs<T, 
     a.c->iter = it;
     a.c->cycles = 0;
   }
-  cl.sync();  // no CTA's shared memory goes while another may still read it
+  cluster_barrier();  // no CTA's shared memory goes while another may still read it
 }
 
 // Launch the cluster CG when it applies (n <= kClusterRows and a cluster of
