@@ -1493,7 +1493,8 @@ static int small_cg(const gko_matrix_s* A, const double* b, T* x, bool x_zero, c
 // CTAs hold bit-identical totals and take the same branch.  That uniformity is
 // what keeps the hardware barriers safe: no CTA leaves the loop or the kernel
 // on its own, and a last barrier keeps every CTA's shared memory alive until
-// the others have finished reading it.
+// the others have finished reading it.  It serves FP64 solves; the FP32 /
+// BF16 inner solves of mixed precision keep the cooperative-grid kernel.
 namespace cgx = cooperative_groups;
 constexpr int kClusterMax = 16;
 
@@ -1809,11 +1810,10 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       if (A->dtype == GKO_F64) rc = cluster_cg<double, double>(A, b, x, x_zero, sp, s, out);
       if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_F64) rc = small_cg<double, double>(A, b, x, x_zero, sp, s, out);
     } else {
-      if (A->dtype == GKO_F32) rc = cluster_cg<float, float>(A, b, x, x_zero, sp, s, out);
-      if (A->dtype == GKO_BF16) rc = cluster_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
-      if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_F32) rc = small_cg<float, float>(A, b, x, x_zero, sp, s, out);
-      if (rc == GKO_NOT_SUPPORTED && A->dtype == GKO_BF16)
-        rc = small_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
+      // FP32 / BF16 inner solves keep the cooperative-grid kernel (see
+      // cluster_cg_kernel)
+      if (A->dtype == GKO_F32) rc = small_cg<float, float>(A, b, x, x_zero, sp, s, out);
+      if (A->dtype == GKO_BF16) rc = small_cg<float, __nv_bfloat16>(A, b, x, x_zero, sp, s, out);
     }
     if (rc != GKO_NOT_SUPPORTED) return rc;
   }

@@ -118,3 +118,26 @@ def test_jacobi_refusals(gko):
     with pytest.raises(G.GkoError) as e:
         G.gko_solve_cg(M, b, dev(np.zeros(A.n_rows)), 1e-8, 100, G.opts(preconditioner=7))
     assert e.value.status == G.INVALID_ARG
+
+
+@pytest.mark.parametrize("N", [16, 17, 20, 24])
+def test_small_mixed_jacobi_inner_solve_matches_oracle(gko, N):
+    """Mixed Jacobi-CG on variable-coefficient 3D systems of 4,096-13,824 rows
+    (the small-system single-launch inner solves): one restarted
+    refinement step to an inner tolerance of 1e-5 takes as many inner
+    iterations as the oracle's (within 15%), and the full solve to 1e-10
+    needs few refinement steps."""
+    G = gko
+    A = I.varcoef3d_7pt(N, np.random.default_rng(0))
+    b = np.random.default_rng(1).uniform(-1, 1, A.n_rows)
+    M = G.from_csr(A)
+    _, ro = O.solve_ir(O.CG, A, b, tol=1e-8, max_outer=1, inner_tol=1e-5, inner_maxit=5000, jacobi=True)
+    _, rg = solve(G, "cg", M, b, 1e-8, 5000, precision=G.PRECISION_MIXED_F32, refinement=G.REFINE_RESTART,
+                  preconditioner=G.PRECOND_JACOBI, max_outer=1, inner_tol=1e-5)
+    assert ro.outer_iterations == rg.outer_iterations == 1
+    assert abs(rg.iterations - ro.iterations) <= max(3, 0.15 * ro.iterations), (rg, ro)
+    assert abs(rg.rel_residual - ro.rel_residual) <= 0.5 * ro.rel_residual
+    xg, rg = solve(G, "cg", M, b, 1e-10, 5000, precision=G.PRECISION_MIXED_F32, refinement=G.REFINE_RESTART,
+                   preconditioner=G.PRECOND_JACOBI)
+    assert rg.status == G.OK and rg.outer_iterations <= 4, rg
+    assert np.linalg.norm(b - O.spmv_csr(A, xg)) <= 1.01e-10 * np.linalg.norm(b)

@@ -274,8 +274,8 @@ def test_cg_small_system_paths_match_oracle(gko, N, precision):
     """CG on 2D systems at the edge of the one-cluster CG (n = 128^2 = 16,384,
     16 CTAs of 256 threads x 4 rows) and just past it (n = 129^2, the
     cooperative-grid CG): solution parity with the oracle at 1e-12, FP64 and
-    mixed FP32 (restarted refinement, whose inner solves take the same
-    small-system kernels), with and without Jacobi."""
+    mixed FP32 (restarted refinement, whose FP32 inner solves take the
+    cooperative-grid kernel), with and without Jacobi."""
     G = gko
     A = I.varcoef2d_5pt(N, np.random.default_rng(N))
     b = np.random.default_rng(3).uniform(-1, 1, A.n_rows)
