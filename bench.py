@@ -960,8 +960,10 @@ def profile_solvers(args):
 
 def profile_batch(args):
     """The 4,096-system batched CG (FP64 storage, schedule 512 threads per
-    block, warp threshold 0, CSR: the autotuner's choice on this workload)
-    once untimed, then once inside the NVTX range "profile_batch", for ncu."""
+    block, warp threshold 0, CSR: the autotuner's choice on this workload;
+    with --mixed the mixed-precision solve with reliable updates, 256 threads,
+    warp threshold 64, ELL) once untimed, then once inside the NVTX range
+    "profile_batch", for ncu."""
     import torch
     from paper_2006_14290_gb300 import gko as G
     from paper_2006_14290_gb300 import inputs as I
@@ -975,7 +977,11 @@ def profile_batch(args):
         bs.append(b)
     b = torch.from_numpy(np.concatenate(bs)).cuda()
     B = G.Batch(systems, storage=G.F64)
-    B.set_schedule(0, 512, G.BATCH_CSR)
+    if args.mixed:
+        B.set_precision(G.PRECISION_MIXED_F32)
+        B.set_schedule(64, 256, G.BATCH_ELL)
+    else:
+        B.set_schedule(0, 512, G.BATCH_CSR)
     out = {}
     for rep in range(2):
         x = torch.zeros(B.total_rows, dtype=torch.float64, device="cuda")
@@ -1182,6 +1188,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="with --profile-cases: 27-point stencil at 96^3")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the batched CG once inside an NVTX range (for ncu)")
+    ap.add_argument("--mixed", action="store_true", help="with --profile-batch: the mixed-precision batched CG")
     ap.add_argument("--profile-solvers", action="store_true",
                     help="short BiCGSTAB and GMRES(30) solves at 128^3 inside an NVTX range (for ncu)")
     args = ap.parse_args()
