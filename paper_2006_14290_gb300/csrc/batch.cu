@@ -171,6 +171,24 @@ __device__ __forceinline__ void gsync() {
   else __syncthreads();
 }
 
+// a / b with a short chain of FP64 operations for the step scalars, which
+// one thread computes while its block waits: the hardware reciprocal
+// estimate of b refined by two Newton-Raphson steps (r += r (1 - b r), each
+// doubling the correct bits) and one correction of the quotient
+// (q += r (a - b q)), after Markstein (IBM J. Res. Dev. 34, 1990).  Within an
+// ulp or so of the IEEE quotient for normal operands; b must be nonzero and
+// finite (the callers divide by a positive p.q or r.r).
+__device__ __forceinline__ double quick_div(double a, double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  double e = __fma_rn(-b, r, 1.0);
+  r = __fma_rn(r, e, r);
+  e = __fma_rn(-b, r, 1.0);
+  r = __fma_rn(r, e, r);
+  const double q = a * r;
+  return __fma_rn(r, __fma_rn(-b, q, a), q);
+}
+
 // One CG solve by a group of G threads (G = THREADS: a block; G = 32: a
 // warp).  r, p, q: the group's shared-memory vectors.  Follows the
 // single-system solver: recurrence residual test, then the true residual; a
@@ -221,6 +239,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
   const double nb = sqrt(gsum(bb));
   double rho = gsum(rr);
   const double tol = a.rel_tol * nb;
+  const double tol2 = tol * tol;  // step tests on squared norms
   int status = kBRun, it = 0;
   double res = nb > 0.0 ? sqrt(rho) / nb : 0.0;
   if (nb == 0.0) {
@@ -239,7 +258,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
     }
     const Scal sp = gstep(pq, [&](double t, double* o) {
       o[0] = t > 0.0 ? 1.0 : 0.0;
-      o[1] = rho / t;
+      o[1] = t > 0.0 ? quick_div(rho, t) : 0.0;
     });
     if (sp.o[0] == 0.0) {
       status = kBBreak;
@@ -255,8 +274,8 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
     }
     const Scal sr = gstep(rn, [&](double t, double* o) {
       o[0] = t;
-      o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
-      o[2] = t / rho;
+      o[1] = t <= tol2 ? 1.0 : 0.0;
+      o[2] = quick_div(t, rho);
     });
     double rho_new = sr.o[0];
     double beta = sr.o[2];
@@ -274,9 +293,9 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
       }
       const Scal st = gstep(tt, [&](double t, double* o) {
         o[0] = sqrt(t) / nb;
-        o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
+        o[1] = t <= tol2 ? 1.0 : 0.0;
         o[2] = t;
-        o[3] = t / rho;
+        o[3] = quick_div(t, rho);
       });
       res = st.o[0];
       if (st.o[1] != 0.0) {
@@ -379,7 +398,9 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
   const double tn0 = sqrt(gsum<G, THREADS>(tt0, red));
   double rho = gsum<G, THREADS>(rz, red);
   const double tol = a.rel_tol * nb;
-  double maxrr = tn0;
+  // the step tests compare squared norms (no square root on the critical path)
+  const double tol2 = tol * tol, delta2 = a.delta * a.delta;
+  double maxrr2 = tn0 * tn0;
   int status = kBRun, it = 0, updates = 0;
   double res = nb > 0.0 ? tn0 / nb : 0.0;
   if (nb == 0.0) {
@@ -397,10 +418,10 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
       pq = __fma_rn(widen(p[i]), widen(qi), pq);
     }
     const Scal sp = gstep<G, THREADS>(pq, red, [&](double t, double* o) {
-      const double alpha = rho / t;
       o[0] = t > 0.0 ? 1.0 : 0.0;
-      o[1] = Lin<float>(alpha).pack();
-      o[2] = Lin<float>(-alpha).pack();
+      const Lin<float> la(t > 0.0 ? quick_div(rho, t) : 0.0);
+      o[1] = la.pack();
+      o[2] = la.neg().pack();
     });
     if (sp.o[0] == 0.0) {
       status = kBBreak;
@@ -416,35 +437,34 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
       rn = __fma_rn(rw, rw, rn);
     }
     const Scal sr = gstep<G, THREADS>(rn, red, [&](double t, double* o) {
-      const double nr = sqrt(t);
-      const double mx = nr > maxrr ? nr : maxrr;
+      const double mx2 = t > maxrr2 ? t : maxrr2;
       o[0] = t;
-      o[1] = (nr <= tol || nr < a.delta * mx) ? 1.0 : 0.0;
-      o[2] = Lin<float>(t / rho).pack();
-      o[3] = mx;
+      o[1] = (t <= tol2 || t < delta2 * mx2) ? 1.0 : 0.0;
+      o[2] = Lin<float>(quick_div(t, rho)).pack();
+      o[3] = mx2;
     });
     ++it;
     double rho_new = sr.o[0];
     Lin<float> bp = Lin<float>::unpack(sr.o[2]);
-    maxrr = sr.o[3];
+    maxrr2 = sr.o[3];
     if (sr.o[1] != 0.0) {  // reliable update
       fold();
       const double tt = replace(rz);
       ++updates;
       const Scal st = gstep<G, THREADS>(tt, red, [&](double t, double* o) {
         o[0] = sqrt(t) / nb;
-        o[1] = sqrt(t) <= tol ? 1.0 : 0.0;
-        o[2] = sqrt(t);
+        o[1] = t <= tol2 ? 1.0 : 0.0;
+        o[2] = t;
       });
       res = st.o[0];
       if (st.o[1] != 0.0) {
         status = kBOk;
         break;
       }
-      maxrr = st.o[2];
+      maxrr2 = st.o[2];
       const Scal sz = gstep<G, THREADS>(rz, red, [&](double t, double* o) {
         o[0] = t;
-        o[1] = Lin<float>(t / rho).pack();
+        o[1] = Lin<float>(quick_div(t, rho)).pack();
       });
       rho_new = sz.o[0];
       bp = Lin<float>::unpack(sz.o[1]);
