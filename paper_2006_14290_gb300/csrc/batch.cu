@@ -421,7 +421,7 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
       o[0] = t > 0.0 ? 1.0 : 0.0;
       const Lin<float> la(t > 0.0 ? quick_div(rho, t) : 0.0);
       o[1] = la.pack();
-      o[2] = la.neg().pack();
+      o[2] = Lin<float>(-la.hi, -la.lo).pack();  // the pair of -alpha (exact)
     });
     if (sp.o[0] == 0.0) {
       status = kBBreak;

@@ -288,7 +288,6 @@ struct Lin<float> {
   // the pair's bits in one double (for broadcasting through shared memory)
   __device__ double pack() const { return __hiloint2double(__float_as_int(hi), __float_as_int(lo)); }
   __device__ static Lin unpack(double d) { return Lin(__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))); }
-  __device__ Lin neg() const { return Lin(-hi, -lo); }  // the pair of -a (exact)
 };
 
 
