@@ -78,6 +78,8 @@ _SIGS = {
     "or_solve_ir": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32, _I32,
                               C.POINTER(_Result)]),
     "or_jacobi_inv": (None, [_I64, _P, _P, _P, _P]),
+    "or_block_jacobi_inv": (_I64, [_I64, _P, _P, _P, _I32, _P]),
+    "or_solve_bj": (C.c_int, [C.c_int, _I64, _P, _P, _P, _I32, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
     "or_batch_cg": (None, [_I32, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _P, _P, _P]),
     "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
     "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
@@ -419,6 +421,32 @@ def solve_jacobi(solver: int, A, b, x0=None, tol=1e-10, maxit=1000):
     x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     res = _Result()
     lib().or_solve_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(minv), _p(b), _p(x), tol, maxit,
+                      C.byref(res))
+    return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
+
+
+def block_jacobi_inv(A, bs: int):
+    """Inverse diagonal blocks of size bs (rows k*bs .. k*bs + nb - 1, the
+    last block possibly smaller), each by Gauss-Jordan elimination with
+    partial pivoting; a singular block becomes the identity.  Returns
+    (B, singular): B[i, j] = row i of its block's inverse at column j of the
+    block (zeros past the last block's size), singular = blocks replaced."""
+    rp, col, val = _i32(A.row_ptr), _i32(A.col), _f64(A.val)
+    B = np.empty((A.n_rows, bs))
+    singular = lib().or_block_jacobi_inv(A.n_rows, _p(rp), _p(col), _p(val), bs, _p(B))
+    if singular < 0:
+        raise ValueError("block size must lie in 1..64")
+    return B, int(singular)
+
+
+def solve_block_jacobi(solver: int, A, b, bs: int, x0=None, tol=1e-10, maxit=1000):
+    """Block-Jacobi-preconditioned FP64 CG (Saad Alg. 9.1 with M the block
+    diagonal of A) or right-preconditioned BiCGSTAB.  Returns (x, SolveResult)."""
+    rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
+    B, _ = block_jacobi_inv(A, bs)
+    x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    res = _Result()
+    lib().or_solve_bj(solver, A.n_rows, _p(rp), _p(col), _p(val), bs, _p(B), _p(b), _p(x), tol, maxit,
                       C.byref(res))
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
 

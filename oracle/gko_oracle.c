@@ -23,6 +23,10 @@
  *             Alg. 6.9/6.11), and mixed-precision iterative refinement (an
  *             FP64 outer residual loop around an inner solve whose matrix and
  *             vectors are stored in FP32; Buttari et al. 2007).
+ *   Precond.  Jacobi M = diag(A) (Saad Sec. 10.2) and block-Jacobi M = the
+ *             diagonal blocks of A, inverted by Gauss-Jordan elimination with
+ *             partial pivoting (Saad Sec. 12.2; Golub & Van Loan, Matrix
+ *             Computations, Sec. 3.4).
  *
  * The paper (Section 1) names these formats and solvers but prints no
  * algorithm for them, so the textbook definitions above are the reference.
@@ -406,12 +410,27 @@ typedef struct {
   double *hist;
   int32_t hist_len;
   const double *minv; /* Jacobi preconditioner: inverse diagonal, or NULL */
+  const double *bj;   /* block-Jacobi: inverse diagonal blocks (or_block_jacobi_inv), or NULL */
+  int32_t bs;         /* block-Jacobi block size */
 } or_ctx;
 
-/* z = M^-1 r for the Jacobi preconditioner M = diag(A) (Saad, Sec. 10.2);
- * the identity without one. */
+/* z = M^-1 r for the Jacobi preconditioner M = diag(A) (Saad, Sec. 10.2),
+ * or for block-Jacobi M = the block diagonal of A (Saad, Sec. 12.2): row i
+ * of block k (rows k*bs .. k*bs + nb - 1) takes z_i = sum_j B[i*bs + j] *
+ * r[k*bs + j], j = 0 .. nb - 1 in order; the identity without either. */
 static void precond(const or_ctx *c, const double *r, double *z) {
-  for (int64_t i = 0; i < c->A->n; ++i) z[i] = c->minv ? st(c->f32, c->minv[i] * r[i]) : r[i];
+  const int64_t n = c->A->n;
+  if (c->bj) {
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t base = i / c->bs * c->bs;
+      const int64_t nb = n - base < c->bs ? n - base : c->bs;
+      double s = 0.0;
+      for (int64_t j = 0; j < nb; ++j) s += c->bj[i * c->bs + j] * r[base + j];
+      z[i] = st(c->f32, s);
+    }
+    return;
+  }
+  for (int64_t i = 0; i < n; ++i) z[i] = c->minv ? st(c->f32, c->minv[i] * r[i]) : r[i];
 }
 
 /* Inverse diagonal of a CSR matrix: diagonal entries of a row summed in
@@ -424,6 +443,66 @@ void or_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const doubl
       if (col[k] == i) d += val[k];
     minv[i] = d != 0.0 ? 1.0 / d : 1.0;
   }
+}
+
+/* Block-Jacobi setup (Saad, Sec. 12.2): the diagonal blocks of A are rows
+ * and columns k*bs .. k*bs + nb - 1 with nb = min(bs, n - k*bs) (the last
+ * block may be smaller).  Each block is gathered densely (entries of a row
+ * summed in storage order, so duplicates add up as in the SpMV) and inverted
+ * by Gauss-Jordan elimination on [D | I] with partial pivoting (pivot: the
+ * first row of largest magnitude in the column; the pivot row divided by
+ * the pivot, then every other row r takes row_r - m_r * row_k with m_r its
+ * entry in the pivot column).  A block whose pivot column is all zero at
+ * some step is singular and is replaced by the identity (its rows are left
+ * unscaled, as a zero diagonal is for Jacobi).  Output: row i of the inverse
+ * at B[i*bs .. i*bs + nb - 1], zeros in B[i*bs + nb .. i*bs + bs - 1].
+ * Returns the number of singular blocks; bs must lie in 1..64. */
+int64_t or_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t bs,
+                            double *B) {
+  if (bs < 1 || bs > 64) return -1;
+  double *M = malloc(sizeof(double) * (size_t)bs * 2 * (size_t)bs);
+  int64_t singular = 0;
+  for (int64_t base = 0; base < n; base += bs) {
+    const int64_t nb = n - base < bs ? n - base : bs;
+    const int64_t w = 2 * nb;
+    for (int64_t r = 0; r < nb; ++r) {
+      for (int64_t c = 0; c < w; ++c) M[r * w + c] = 0.0;
+      M[r * w + nb + r] = 1.0;
+      for (int64_t k = rp[base + r]; k < rp[base + r + 1]; ++k) {
+        const int64_t c = (int64_t)col[k] - base;
+        if (c >= 0 && c < nb) M[r * w + c] += val[k];
+      }
+    }
+    int ok = 1;
+    for (int64_t k = 0; k < nb && ok; ++k) {
+      int64_t piv = k;
+      for (int64_t r = k + 1; r < nb; ++r)
+        if (fabs(M[r * w + k]) > fabs(M[piv * w + k])) piv = r;
+      if (M[piv * w + k] == 0.0) {
+        ok = 0;
+        break;
+      }
+      if (piv != k)
+        for (int64_t c = 0; c < w; ++c) {
+          const double t = M[k * w + c];
+          M[k * w + c] = M[piv * w + c];
+          M[piv * w + c] = t;
+        }
+      const double d = M[k * w + k];
+      for (int64_t c = 0; c < w; ++c) M[k * w + c] = M[k * w + c] / d;
+      for (int64_t r = 0; r < nb; ++r) {
+        if (r == k) continue;
+        const double m = M[r * w + k];
+        for (int64_t c = 0; c < w; ++c) M[r * w + c] = M[r * w + c] - m * M[k * w + c];
+      }
+    }
+    for (int64_t r = 0; r < nb; ++r)
+      for (int64_t j = 0; j < bs; ++j)
+        B[(base + r) * bs + j] = j < nb ? (ok ? M[r * w + nb + j] : (r == j ? 1.0 : 0.0)) : 0.0;
+    if (!ok) ++singular;
+  }
+  free(M);
+  return singular;
 }
 
 static void hist_put(const or_ctx *c, int32_t it, double v) {
@@ -768,6 +847,21 @@ int or_solve_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col, co
   }
   or_op A = {n, rp, col, val, NULL};
   or_ctx c = {&A, 0, 1, NULL, 0, minv};
+  *out = run_solver(&c, solver, b, x, tol, maxit, 0);
+  return out->status;
+}
+
+/* Block-Jacobi-preconditioned FP64 CG / BiCGSTAB (B, bs: the inverse
+ * diagonal blocks from or_block_jacobi_inv).  GMRES: OR_INVALID. */
+int or_solve_bj(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t bs,
+                const double *B, const double *b, double *x, double tol, int32_t maxit, or_result *out) {
+  or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+  if ((solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) || bs < 1) {
+    *out = bad;
+    return OR_INVALID;
+  }
+  or_op A = {n, rp, col, val, NULL};
+  or_ctx c = {&A, 0, 1, NULL, 0, NULL, B, bs};
   *out = run_solver(&c, solver, b, x, tol, maxit, 0);
   return out->status;
 }

@@ -567,6 +567,128 @@ def test_jacobi_gmres_refused():
     assert r.status == 1
 
 
+# -------------------------------------------------------- block-Jacobi --
+
+def csr_from_dense(D, dup=None):
+    """CSR of a dense matrix (nonzeros in ascending column order); dup =
+    (i, j, v) splits entry (i, j) into v and D[i, j] - v stored twice."""
+    rp, col, val = [0], [], []
+    for i in range(D.shape[0]):
+        for j in range(D.shape[1]):
+            if D[i, j] != 0.0:
+                if dup is not None and (i, j) == dup[:2]:
+                    col += [j, j]
+                    val += [dup[2], D[i, j] - dup[2]]
+                else:
+                    col.append(j)
+                    val.append(D[i, j])
+        rp.append(len(col))
+    return I.Csr(D.shape[0], D.shape[1], np.array(rp, np.int32), np.array(col, np.int32),
+                 np.array(val, np.float64))
+
+
+@pytest.mark.parametrize("n,bs", [(37, 8), (32, 4), (5, 8), (40, 1), (33, 32)])
+def test_block_jacobi_inverts_each_diagonal_block(n, bs):
+    """Each block of B is the inverse of the matching diagonal block of A
+    (numpy's LU-based inverse and B D = I), off-block entries play no part,
+    and the last block of n % bs rows is inverted on its own."""
+    rng = np.random.default_rng(n * 100 + bs)
+    D = rng.uniform(-1, 1, (n, n)) * (rng.uniform(0, 1, (n, n)) < 0.5)
+    D += np.diag(rng.uniform(2, 4, n) * rng.choice([-1, 1], n))  # nonsymmetric, nonsingular blocks
+    B, singular = O.block_jacobi_inv(csr_from_dense(D), bs)
+    assert singular == 0 and B.shape == (n, bs)
+    for base in range(0, n, bs):
+        nb = min(bs, n - base)
+        blk = D[base:base + nb, base:base + nb]
+        inv = B[base:base + nb, :nb]
+        np.testing.assert_allclose(inv, np.linalg.inv(blk), rtol=0, atol=1e-13 * np.linalg.cond(blk))
+        np.testing.assert_allclose(inv @ blk, np.eye(nb), rtol=0, atol=1e-13 * np.linalg.cond(blk))
+        assert np.all(B[base:base + nb, nb:] == 0.0)
+
+
+def test_block_jacobi_pivots_sums_duplicates_and_replaces_singular_blocks():
+    # block 0 = [[0, 2], [3, 1]] needs a row swap; its inverse is
+    # [[-1/6, 1/3], [1/2, 0]].  Block 1 = [[1, 2], [2, 4]] is singular and
+    # becomes the identity; block 2 is the single row 5 (stored as 1.5 + 3.5).
+    D = np.zeros((5, 5))
+    D[0, 1], D[1, 0], D[1, 1] = 2.0, 3.0, 1.0
+    D[2, 2], D[2, 3], D[3, 2], D[3, 3] = 1.0, 2.0, 2.0, 4.0
+    D[4, 4] = 5.0
+    D[0, 4], D[4, 0] = 7.0, -9.0  # outside every block
+    B, singular = O.block_jacobi_inv(csr_from_dense(D, dup=(4, 4, 1.5)), 2)
+    assert singular == 1
+    exact = [[Fraction(-1, 6), Fraction(1, 3)], [Fraction(1, 2), Fraction(0)]]
+    for i in range(2):
+        for j in range(2):
+            assert abs(B[i, j] - float(exact[i][j])) <= 2 * U64 * abs(float(exact[i][j]))
+    np.testing.assert_array_equal(B[2:4], np.eye(2))
+    np.testing.assert_array_equal(B[4], [0.2, 0.0])
+
+
+def test_block_jacobi_block_size_one_is_jacobi():
+    rng = np.random.default_rng(7)
+    A = I.varcoef3d_7pt(5, rng)
+    Z = I.Csr(A.n_rows, A.n_cols, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    diag = np.flatnonzero(Z.col == np.repeat(np.arange(Z.n_rows), np.diff(Z.row_ptr)))
+    Z.val[diag[3]] = 0.0  # a zero diagonal: Jacobi takes 1, block size 1 the identity block
+    B, singular = O.block_jacobi_inv(Z, 1)
+    assert singular == 1
+    np.testing.assert_array_equal(B[:, 0], O.jacobi_inv(Z))
+    b = rng.uniform(-1, 1, A.n_rows)
+    for solver in (O.CG, O.BICGSTAB):
+        x1, r1 = O.solve_jacobi(solver, A, b, tol=1e-10, maxit=2000)
+        x2, r2 = O.solve_block_jacobi(solver, A, b, 1, tol=1e-10, maxit=2000)
+        assert r1.iterations == r2.iterations
+        np.testing.assert_array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_block_jacobi_exact_on_block_diagonal_matrix(solver):
+    """A block diagonal with blocks of bs rows: M = A, so the preconditioned
+    operator is the identity and one iteration solves the system."""
+    rng = np.random.default_rng(11)
+    n, bs = 29, 4
+    D = np.zeros((n, n))
+    for base in range(0, n, bs):
+        nb = min(bs, n - base)
+        Q = rng.uniform(-1, 1, (nb, nb))
+        D[base:base + nb, base:base + nb] = Q @ Q.T + nb * np.eye(nb) if solver == "cg" else Q + 3 * np.eye(nb)
+    b = rng.uniform(-1, 1, n)
+    which = O.CG if solver == "cg" else O.BICGSTAB
+    x, r = O.solve_block_jacobi(which, csr_from_dense(D), b, bs, tol=1e-12, maxit=10)
+    assert r.status == 0 and r.iterations == 1
+    np.testing.assert_allclose(x, np.linalg.solve(D, b), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("solver,bs", [("cg", 4), ("cg", 8), ("bicgstab", 2), ("bicgstab", 16)])
+def test_block_jacobi_solves_badly_scaled_systems(solver, bs):
+    """Rows and columns scaled blockwise by D A D with a wide scaling: the
+    block-Jacobi solve matches a dense solve and needs fewer iterations
+    than the unpreconditioned one."""
+    rng = np.random.default_rng(13)
+    A = I.laplace2d_5pt(11) if solver == "cg" else I.convdiff3d_7pt(5, 2.0)
+    n = A.n_rows
+    sc = np.exp(rng.uniform(-3, 3, n))
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    A.val[:] = A.val * sc[rows] * sc[A.col]
+    b = rng.uniform(-1, 1, n)
+    xd = np.linalg.solve(dense(A), b)
+    which = O.CG if solver == "cg" else O.BICGSTAB
+    x0, r0 = O.solve(which, A, b, tol=1e-10, maxit=20000)
+    x1, r1 = O.solve_block_jacobi(which, A, b, bs, tol=1e-10, maxit=20000)
+    assert r1.status == 0 and r1.rel_residual <= 1e-10
+    assert np.linalg.norm(x1 - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert r1.iterations < 0.5 * r0.iterations, (r1.iterations, r0.iterations)
+
+
+def test_block_jacobi_gmres_and_bad_block_size_refused():
+    A = I.laplace2d_5pt(4)
+    x, r = O.solve_block_jacobi(O.GMRES, A, np.ones(16), 4)
+    assert r.status == 1
+    with pytest.raises(ValueError):
+        O.block_jacobi_inv(A, 0)
+
+
 def test_batch_cg_is_the_single_system_cg_per_system():
     """The batched oracle (c8: CG applied to each system on its own) equals
     the single-system CG bit for bit, whatever the thread count, and its
