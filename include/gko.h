@@ -320,9 +320,18 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
  * residual ||b - A x||.  The inverse diagonal is built per solve from the FP64
  * matrix (diagonal duplicates summed, a zero diagonal taken as 1) and, for
  * mixed precision, rounded to FP32 for the inner solve.  GMRES with a
- * preconditioner returns GKO_NOT_SUPPORTED. */
+ * preconditioner returns GKO_NOT_SUPPORTED.
+ * BLOCK_JACOBI: M = the diagonal blocks of A (Saad Sec. 12.2), blocks of
+ * opts->block_size consecutive rows (the last one n % block_size rows when
+ * the size does not divide n), each inverted once per solve by Gauss-Jordan
+ * elimination with partial pivoting (as gko_block_jacobi_inverse); CG and
+ * BiCGSTAB use it as JACOBI uses diag(A).  FP64 precision and a CSR matrix
+ * only (otherwise GKO_NOT_SUPPORTED); a block whose elimination meets an
+ * all-zero pivot column leaves its rows unscaled, as a zero diagonal does
+ * for JACOBI.  Extra device memory: n * block_size doubles. */
 #define GKO_PRECOND_NONE 0
 #define GKO_PRECOND_JACOBI 1
+#define GKO_PRECOND_BLOCK_JACOBI 2
 
 typedef struct {
   int32_t restart;      /* GMRES restart length m (<= 0: 30; at most 128)        */
@@ -333,9 +342,9 @@ typedef struct {
   int32_t inner_maxit;  /* mixed: inner iteration cap per step (<= 0: max_iters;
                            GMRES: 4 restart cycles per step)                    */
   int32_t check_every;  /* host status poll interval in iterations (<= 0: auto)  */
-  int32_t preconditioner; /* GKO_PRECOND_NONE or GKO_PRECOND_JACOBI (CG, BiCGSTAB) */
+  int32_t preconditioner; /* GKO_PRECOND_* (CG, BiCGSTAB)                        */
   int32_t refinement;   /* mixed: GKO_REFINE_* (0: AUTO)                         */
-  int32_t reserved;     /* set to 0                                              */
+  int32_t block_size;   /* BLOCK_JACOBI: rows per diagonal block, 1..32 (<= 0: 8) */
   double reliable_delta; /* RELIABLE: update factor in [0, 1) (0: 0.1)            */
 } gko_solve_opts;
 
@@ -384,6 +393,25 @@ GKO_API int gko_solve_bicgstab(gko_matrix A, const double *b, double *x, double 
                        void *stream);
 GKO_API int gko_solve_gmres(gko_matrix A, const double *b, double *x, double rel_tol, int32_t max_iters,
                     const gko_solve_opts *opts, gko_solve_result *res, void *stream);
+
+/* Block-Jacobi setup (the preconditioner of GKO_PRECOND_BLOCK_JACOBI; Saad,
+ * Iterative Methods for Sparse Linear Systems, Sec. 12.2; Golub & Van Loan,
+ * Matrix Computations, Sec. 3.4 for the elimination).  A: square FP64 CSR
+ * matrix.  The diagonal blocks are rows and columns k*block_size ..
+ * k*block_size + nb - 1, nb = min(block_size, n - k*block_size); each is
+ * gathered densely (entries of a row summed in storage order) and inverted
+ * by Gauss-Jordan elimination on [D | I] with partial pivoting (pivot: the
+ * first row of largest magnitude in the column; the pivot row divided by the
+ * pivot; every other row r becomes row_r - m_r row_k, each product and
+ * difference rounded separately).  B: device array of n * block_size
+ * doubles, written with row i of its block's inverse at B[i*block_size ..
+ * i*block_size + nb - 1] and zeros after it.  A block whose pivot column is
+ * all zero at some step gets identity rows; *singular (host, nullable)
+ * receives how many.  block_size: 1..32 (GKO_INVALID_ARG otherwise); other
+ * formats or value types: GKO_NOT_SUPPORTED.  Synchronises `stream` when
+ * singular is given. */
+GKO_API int gko_block_jacobi_inverse(gko_matrix A, int32_t block_size, double *B, int64_t *singular,
+                                     void *stream);
 
 /* ------------------------------------------------------------ batched CG -- */
 

@@ -20,6 +20,7 @@
 #include "blas1.cuh"
 #include "reduce.cuh"
 #include "spmv.cuh"
+#include "precond.cuh"
 
 namespace gko {
 
@@ -271,6 +272,64 @@ __global__ void __launch_bounds__(256, 4) dot2_kernel(int64_t n, const T* __rest
   reduce_op<2>(acc, ws, Store2{out});
 }
 
+// ------------------------------------------------------- block-Jacobi --
+
+// z = M^-1 v for block-Jacobi (M = the diagonal blocks of A, Saad Sec.
+// 12.2): z_i = sum_j B[i*bs + j] v[base + j] over the nb rows of i's block
+// (base = i - i % bs), accumulated in FP64 and stored as T; B from
+// block_jacobi_inverse.  z2 (nullable) also receives z.  With a reducing
+// Op, v.z is reduced into it.  gate: skip while its words are set (the
+// iteration kernels); need (nullable): skip unless *need is set (the
+// residual replacement after a true-residual check).  Op = NoOp: no
+// reduction.
+
+// CG start: rho = r.z
+struct BjInitOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const { c->rho = t[0]; }
+};
+
+// CG step: beta = (r.z)_new / (r.z)_old (Saad Alg. 9.1)
+struct BjStepOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const {
+    const double rho_new = t[0];
+    c->rho_new = rho_new;
+    c->beta = rho_new / c->rho;
+    c->rho = rho_new;
+  }
+};
+
+// CG residual replacement: the replaced residual's t.z
+struct BjReplaceOp {
+  Ctl* c;
+  __device__ void operator()(const double (&t)[1]) const { c->rho_new = t[0]; }
+};
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, const double* __restrict__ B,
+                                                       const T* __restrict__ v, T* __restrict__ z,
+                                                       T* __restrict__ z2, RedWs ws, Op op, const int* gate,
+                                                       const int* need) {
+  constexpr bool RED = !std::is_same<Op, NoOp>::value;
+  pdl_begin();
+  if (gated(gate)) return;
+  if (need && !*(volatile const int*)need) return;
+  double acc[1] = {0.0};
+  GKO_GRID_LOOP(i, n) {
+    const int64_t base = (int64_t)((int32_t)i / bs) * bs;
+    const int nb = (int)(n - base < bs ? n - base : bs);
+    const double* Bi = B + i * bs;
+    double sum = 0.0;
+    for (int j = 0; j < nb; ++j) sum = __fma_rn(Bi[j], wd(v[base + j]), sum);
+    const T zi = (T)sum;
+    z[i] = zi;
+    if (z2) z2[i] = zi;
+    if (RED) acc[0] = __fma_rn(wd(v[i]), wd(zi), acc[0]);
+  }
+  if constexpr (RED) reduce_op<1>(acc, ws, op);
+}
+
 // Reliable-update test after a step with recurrence residual norm nr (mixed
 // precision only; delta = 0 disables it): nr raises maxrr, and nr below
 // delta * maxrr asks the host for an update (kCheck, as at convergence).
@@ -287,8 +346,10 @@ __device__ __forceinline__ bool reliable_due(Ctl* c, double nr) {
 
 // ------------------------------------------------------------------- CG --
 
-// t[0] = r.r (convergence); with a preconditioner t[1] = r.z (the new rho)
-template <int NV>
+// t[0] = r.r (convergence); with a preconditioner t[1] = r.z (the new rho).
+// LATER (block-Jacobi): beta and rho come from the following block-Jacobi
+// kernel, which forms z = M^-1 r and r.z.
+template <int NV, bool LATER = false>
 struct CgUpdateOp {
   Ctl* c;
   __device__ void operator()(const double (&t)[NV]) const {
@@ -313,14 +374,16 @@ struct CgUpdateOp {
       c->done = 1;
       return;
     }
+    if (LATER) return;
     c->beta = rho_new / c->rho;
     c->rho = rho_new;
   }
 };
 
 // alpha = rho / (p.q); x += alpha p; r -= alpha q; reduces r.r and, with
-// the Jacobi inverse diagonal d (PC), r.z for z = d r.
-template <typename T, bool PC>
+// the Jacobi inverse diagonal d (PC), r.z for z = d r.  BJ: r.r only, the
+// step scalars left to the block-Jacobi kernel that follows.
+template <typename T, bool PC, bool BJ = false>
 __global__ void __launch_bounds__(256, 4) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
                                                         const T* __restrict__ p, const T* __restrict__ q, Ctl* c,
                                                         RedWs ws, const T* __restrict__ d) {
@@ -359,7 +422,7 @@ __global__ void __launch_bounds__(256, 4) cg_update_kernel(int64_t n, T* __restr
           if (PC) acc[NV - 1] = __fma_rn(rw, wd(d[i] * ri), acc[NV - 1]);
         });
   }
-  reduce_op<NV>(acc, ws, CgUpdateOp<NV>{c});
+  reduce_op<NV>(acc, ws, CgUpdateOp<NV, BJ>{c});
 }
 
 // p = z + beta p, z = d r with the Jacobi inverse diagonal (PC), else r
@@ -390,17 +453,19 @@ struct CgReplaceOp {
   }
 };
 
+// z (block-Jacobi, nullable): the preconditioned t, p = z + beta p
 template <typename T>
 __global__ void __launch_bounds__(256, 4) cg_replace_kernel(int64_t n, T* __restrict__ r, T* __restrict__ p,
                                                          const T* __restrict__ t, Ctl* c, RedWs ws,
-                                                         const T* __restrict__ d = nullptr) {
+                                                         const T* __restrict__ d = nullptr,
+                                                         const T* __restrict__ z = nullptr) {
   if (!*(volatile int*)&c->replace) return;
   const Lin<T> bp = block_bcast<Lin<T>>([&] { return Lin<T>(c->rho_new / c->rho); });
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
     const T ri = t[i];
     r[i] = ri;
-    p[i] = bp(p[i], d ? d[i] * ri : ri);
+    p[i] = bp(p[i], z ? z[i] : (d ? d[i] * ri : ri));
   }
   reduce_op<1>(acc, ws, CgReplaceOp{c});
 }
@@ -1082,6 +1147,8 @@ struct SolveSpec {
   int check_every;
   const void* minv = nullptr;  // Jacobi inverse diagonal (vector of T), or none
   const RelSpec* rel = nullptr;  // reliable updates (FP32 recurrences only)
+  const double* bj = nullptr;  // block-Jacobi inverse blocks (FP64, n x bs), or none
+  int bs = 0;                  // block-Jacobi block size
 };
 
 struct SolveOut {
@@ -1381,7 +1448,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_cg_kernel(SmallArgs<T, VT
 
 // Whether the single-launch CG serves this matrix (see above).
 static bool small_cg_ok(const gko_matrix_s* A, const SolveSpec& sp) {
-  if (sp.solver != 0 || sp.rel || A->fmt != GKO_CSR || A->plan.kind != 1 || A->n_rows <= 0 || A->n_rows > kSmallRows)
+  if (sp.solver != 0 || sp.rel || sp.bj || A->fmt != GKO_CSR || A->plan.kind != 1 || A->n_rows <= 0 ||
+      A->n_rows > kSmallRows)
     return false;
   int dev = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) !=
@@ -1819,8 +1887,10 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   }
   const int64_t n = A->n_rows;
   const int m = std::max(1, sp.restart);
-  const int nvec = sp.solver == 0 ? 3 : sp.solver == 1 ? 9 : (m + 2);
+  const int nvec = sp.solver == 0 ? (sp.bj ? 4 : 3) : sp.solver == 1 ? 9 : (m + 2);
   const T* dinv = static_cast<const T*>(sp.minv);
+  const double* bj = sp.bj;  // block-Jacobi (FP64 solves only)
+  const int bs = sp.bs;
   const size_t spmv_sb = spmv_scratch_bytes(A);
   const size_t bytes = 256 * 16 + sizeof(Ctl) + sizeof(double) * 3 * kDotSlots + 512 +
                        (size_t)nvec * (sizeof(T) * ((size_t)n + 64) + 320) + spmv_sb + 320 +
@@ -1864,18 +1934,24 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
     T* p = cv.take<T>(n);
     T* q = cv.take<T>(n);
     T *rh = nullptr, *v = nullptr, *sv = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
+    T* zb = (sp.solver == 0 && bj) ? cv.take<T>(n) : nullptr;  // CG with block-Jacobi: z = M^-1 r
     if (sp.solver == 1) {
       rh = cv.take<T>(n);
       v = cv.take<T>(n);
       sv = cv.take<T>(n);
       tv = cv.take<T>(n);
-      if (dinv) {
+      if (dinv || bj) {
         ph = cv.take<T>(n);
         sh = cv.take<T>(n);
       }
     }
     if (!x_zero) GKO_TRY(spmv(x, q, nullptr, nullptr));
-    if (sp.solver == 0)
+    if (sp.solver == 0 && bj) {
+      // z = M^-1 r, p = z, rho = r.z
+      init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, nullptr, nullptr, nullptr, nullptr,
+                                                 ws, InitOp{c, sp.rel_tol, 0});
+      bj_apply_kernel<T, BjInitOp><<<rg, 256, 0, s>>>(n, bs, bj, r, zb, p, ws, BjInitOp{c}, &c->done, nullptr);
+    } else if (sp.solver == 0)
       init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, p, nullptr, nullptr, nullptr, ws,
                                                  InitOp{c, sp.rel_tol, 0}, dinv);
     else
@@ -1898,7 +1974,14 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       for (int it = 0; it < count; ++it) {
         if (sp.solver == 0) {
           GKO_TRY(spmv(p, q, p, &c->done));
-          if (dinv) {
+          if (bj) {
+            GKO_TRY_CUDA(launch_k(cg_update_kernel<T, false, true>, dim3(rg), B256, 0, s, n, x, r, p, q, c, ws,
+                                  (const T*)nullptr));
+            GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, BjStepOp>, dim3(rg), B256, 0, s, n, bs, bj, (const T*)r, zb,
+                                  (T*)nullptr, ws, BjStepOp{c}, (const int*)&c->done, (const int*)nullptr));
+            GKO_TRY_CUDA(launch_k(cg_p_kernel<T, false>, dim3(vg), B256, 0, s, n, (const T*)zb, p, c,
+                                  (const T*)nullptr));
+          } else if (dinv) {
             GKO_TRY_CUDA(launch_k(cg_update_kernel<T, true>, dim3(rg), B256, 0, s, n, x, r, p, q, c, ws, dinv));
             GKO_TRY_CUDA(launch_k(cg_p_kernel<T, true>, dim3(vg), B256, 0, s, n, r, p, c, dinv));
           } else {
@@ -1906,6 +1989,20 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
                                   (const T*)nullptr));
             GKO_TRY_CUDA(launch_k(cg_p_kernel<T, false>, dim3(vg), B256, 0, s, n, r, p, c, (const T*)nullptr));
           }
+        } else if (bj) {
+          // right preconditioned: ph = M^-1 p, sh = M^-1 s
+          GKO_TRY_CUDA(launch_k(bicg_p_kernel<T>, dim3(vg), B256, 0, s, n, (const T*)r, p, (const T*)v, c,
+                                (const T*)nullptr, (T*)nullptr));
+          GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, NoOp>, dim3(vg), B256, 0, s, n, bs, bj, (const T*)p, ph,
+                                (T*)nullptr, ws, NoOp{}, (const int*)&c->done, (const int*)nullptr));
+          GKO_TRY(spmv(ph, v, rh, &c->done));
+          GKO_TRY_CUDA(launch_k(bicg_s_kernel<T>, dim3(rg), B256, 0, s, n, (const T*)r, (const T*)v, sv, c, ws,
+                                (const T*)nullptr, (T*)nullptr));
+          GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, NoOp>, dim3(vg), B256, 0, s, n, bs, bj, (const T*)sv, sh,
+                                (T*)nullptr, ws, NoOp{}, (const int*)&c->phase, (const int*)nullptr));
+          GKO_TRY(spmv(sh, tv, sv, &c->phase, true));
+          GKO_TRY_CUDA(launch_k(bicg_x_kernel<T>, dim3(rg), B256, 0, s, n, x, (const T*)p, (const T*)sv,
+                                (const T*)tv, r, (const T*)rh, c, ws, (const T*)ph, (const T*)sh));
         } else {
           GKO_TRY_CUDA(launch_k(bicg_p_kernel<T>, dim3(vg), B256, 0, s, n, r, p, v, c, dinv, ph));
           GKO_TRY(spmv(dinv ? ph : p, v, rh, &c->done));
@@ -1960,7 +2057,12 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       } else if (hc->status == kCheck) {  // verify with the true residual
         GKO_TRY(spmv(x, q, nullptr, nullptr));
         true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c}, sp.solver == 0 ? dinv : nullptr);
-        if (sp.solver == 0)
+        if (sp.solver == 0 && bj) {
+          // z = M^-1 t and rho_new = t.z for the replaced residual t
+          bj_apply_kernel<T, BjReplaceOp><<<rg, 256, 0, s>>>(n, bs, bj, q, zb, nullptr, ws, BjReplaceOp{c}, nullptr,
+                                                             &c->replace);
+          cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, nullptr, zb);
+        } else if (sp.solver == 0)
           cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
         else
           bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
@@ -2161,10 +2263,19 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   if (sp.restart > kMaxRestart) return fail(GKO_INVALID_ARG, "GMRES restart length is limited to 128");
   sp.check_true = 1;
   sp.check_every = o.check_every;
-  if (o.preconditioner != GKO_PRECOND_NONE && o.preconditioner != GKO_PRECOND_JACOBI)
+  if (o.preconditioner != GKO_PRECOND_NONE && o.preconditioner != GKO_PRECOND_JACOBI &&
+      o.preconditioner != GKO_PRECOND_BLOCK_JACOBI)
     return fail(GKO_INVALID_ARG, "unknown preconditioner");
   const bool jacobi = o.preconditioner == GKO_PRECOND_JACOBI;
-  if (jacobi && solver == 2) return fail(GKO_NOT_SUPPORTED, "GMRES takes no preconditioner");
+  const bool bjac = o.preconditioner == GKO_PRECOND_BLOCK_JACOBI;
+  if ((jacobi || bjac) && solver == 2) return fail(GKO_NOT_SUPPORTED, "GMRES takes no preconditioner");
+  const int bsize = o.block_size > 0 ? o.block_size : 8;
+  if (bjac) {
+    if (bsize > kBlockJacobiMax) return fail(GKO_INVALID_ARG, "block-Jacobi block size must lie in 1..32");
+    if (o.precision != GKO_PRECISION_F64)
+      return fail(GKO_NOT_SUPPORTED, "block-Jacobi preconditioning runs with FP64 precision");
+    if (A->fmt != GKO_CSR) return fail(GKO_NOT_SUPPORTED, "the block-Jacobi setup reads a CSR matrix");
+  }
   double nb = 0.0;
   GKO_TRY(norm2_host(b, n, &nb, s));
   Scratch pc_mem;  // Jacobi inverse diagonal: FP64, and its FP32 rounding for inner solves
@@ -2174,6 +2285,13 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
     d64 = pc_mem.as<double>();
     GKO_TRY(jacobi_inverse(A, d64, s));
     sp.minv = d64;
+  }
+  Scratch bj_mem;  // block-Jacobi: n x bs inverse-block rows (FP64)
+  if (bjac) {
+    GKO_TRY(bj_mem.get(sizeof(double) * (size_t)n * bsize + 512, s));
+    GKO_TRY(block_jacobi_inverse(A, bsize, bj_mem.as<double>(), nullptr, s));
+    sp.bj = bj_mem.as<double>();
+    sp.bs = bsize;
   }
 
   if (o.precision == GKO_PRECISION_F64) {

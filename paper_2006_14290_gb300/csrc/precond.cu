@@ -4,7 +4,7 @@
 // Sec. 10.2).  The diagonal entries of a row are summed in CSR storage order
 // (duplicates add up as in the SpMV); a zero or missing diagonal gives 1, so
 // that row is left unscaled.
-#include "spmv.cuh"
+#include "precond.cuh"
 
 namespace gko {
 namespace {
@@ -87,9 +87,104 @@ __global__ void narrow_kernel(int64_t n, const double* __restrict__ d, float* __
   GKO_ROWS(i, n) f[i] = (float)d[i];
 }
 
+// Block-Jacobi setup (M = the diagonal blocks of A, Saad Sec. 12.2): one
+// warp per block of nb = min(bs, n - base) rows, the augmented [D | I] in
+// shared memory (row stride 2 bs), Gauss-Jordan elimination with partial
+// pivoting (the first row of largest magnitude; the pivot row divided by the
+// pivot; every other row r takes row_r - m_r row_k, products and
+// differences rounded separately, never fused).  Lane L holds columns L and
+// L + 32.  A block whose pivot column is all zero at some step is left
+// unscaled (identity rows) and counted in *singular.
+__global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, double* __restrict__ B,
+                                unsigned long long* singular) {
+  extern __shared__ double bj_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wpc = blockDim.x >> 5;
+  const int ST = 2 * bs;
+  double* M = bj_smem + (size_t)(threadIdx.x >> 5) * bs * ST;
+  const int64_t blocks = (n + bs - 1) / bs;
+  for (int64_t blk = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); blk < blocks; blk += (int64_t)gridDim.x * wpc) {
+    const int64_t base = blk * bs;
+    const int nb = (int)(n - base < bs ? n - base : bs);
+    const int w = 2 * nb;
+    for (int e = lane; e < nb * ST; e += 32) M[e] = 0.0;
+    __syncwarp();
+    if (lane < nb) {
+      M[lane * ST + nb + lane] = 1.0;
+      for (int32_t k = rp[base + lane]; k < rp[base + lane + 1]; ++k) {
+        const int64_t c = (int64_t)col[k] - base;
+        if (c >= 0 && c < nb) M[lane * ST + c] += val[k];
+      }
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < nb; ++k) {
+      double a = (lane >= k && lane < nb) ? fabs(M[lane * ST + k]) : -1.0;
+      int idx = lane;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double oa = __shfl_xor_sync(0xffffffffu, a, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        if (oa > a || (oa == a && oi < idx)) {
+          a = oa;
+          idx = oi;
+        }
+      }
+      // the butterfly leaves every lane with the same pivot; lane 0's copy
+      // and a vote keep the control flow warp-uniform even for NaN input
+      a = __shfl_sync(0xffffffffu, a, 0);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      if (__any_sync(0xffffffffu, !(a > 0.0))) {
+        ok = false;
+        break;
+      }
+      if (idx != k)
+        for (int c = lane; c < w; c += 32) {
+          const double t = M[k * ST + c];
+          M[k * ST + c] = M[idx * ST + c];
+          M[idx * ST + c] = t;
+        }
+      __syncwarp();
+      const double d = M[k * ST + k];
+      __syncwarp();
+      for (int c = lane; c < w; c += 32) M[k * ST + c] = M[k * ST + c] / d;
+      __syncwarp();
+      for (int r = 0; r < nb; ++r) {
+        if (r == k) continue;
+        const double m = M[r * ST + k];
+        __syncwarp();
+        for (int c = lane; c < w; c += 32) M[r * ST + c] = __dsub_rn(M[r * ST + c], __dmul_rn(m, M[k * ST + c]));
+        __syncwarp();
+      }
+    }
+    for (int r = 0; r < nb; ++r)
+      for (int j = lane; j < bs; j += 32)
+        B[(base + r) * bs + j] = j < nb ? (ok ? M[r * ST + nb + j] : (r == j ? 1.0 : 0.0)) : 0.0;
+    if (!ok && lane == 0 && singular) atomicAdd(singular, 1ull);
+    __syncwarp();
+  }
+}
+
 #undef GKO_ROWS
 
 }  // namespace
+
+int block_jacobi_inverse(const gko_matrix_s* A, int bs, double* B, unsigned long long* singular, cudaStream_t s) {
+  if (A->dtype != GKO_F64 || A->fmt != GKO_CSR)
+    return fail(GKO_NOT_SUPPORTED, "the block-Jacobi setup reads an FP64 CSR matrix");
+  if (bs < 1 || bs > kBlockJacobiMax) return fail(GKO_INVALID_ARG, "block-Jacobi block size must lie in 1..32");
+  const int64_t n = A->n_rows;
+  if (n == 0) return GKO_OK;
+  const int wpc = bs > 16 ? 2 : 4;  // warps per block: at most 32 KB of shared memory
+  const size_t smem = sizeof(double) * (size_t)wpc * bs * 2 * bs;
+  const int64_t blocks = (n + bs - 1) / bs;
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>((blocks + wpc - 1) / wpc, (int64_t)sm_count() * 32));
+  bj_setup_kernel<<<(unsigned)g, 32 * wpc, smem, s>>>(n, bs, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col),
+                                                      ptr<double>(A->val), B, singular);
+  GKO_TRY_CUDA(cudaGetLastError());
+  return GKO_OK;
+}
 
 int jacobi_inverse(const gko_matrix_s* A, double* d, cudaStream_t s) {
   if (A->dtype != GKO_F64) return fail(GKO_INVALID_ARG, "the Jacobi setup reads the FP64 matrix");
@@ -128,3 +223,29 @@ int narrow_to_f32(const double* d, float* f, int64_t n, cudaStream_t s) {
 }
 
 }  // namespace gko
+
+extern "C" {
+
+int gko_block_jacobi_inverse(gko_matrix A, int32_t block_size, double* B, int64_t* singular, void* stream) {
+  if (!A) return gko::fail(GKO_INVALID_ARG, "null matrix");
+  if (A->n_rows != A->n_cols) return gko::fail(GKO_INVALID_ARG, "block-Jacobi needs a square matrix");
+  if (A->n_rows > 0 && !B) return gko::fail(GKO_INVALID_ARG, "null B");
+  cudaStream_t s = (cudaStream_t)stream;
+  gko::Scratch cnt;
+  unsigned long long* dc = nullptr;
+  if (singular) {
+    GKO_TRY(cnt.get(sizeof(unsigned long long), s));
+    dc = cnt.as<unsigned long long>();
+    GKO_TRY_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), s));
+  }
+  GKO_TRY(gko::block_jacobi_inverse(A, block_size, B, dc, s));
+  if (singular) {
+    unsigned long long h = 0;
+    GKO_TRY_CUDA(cudaMemcpyAsync(&h, dc, sizeof h, cudaMemcpyDeviceToHost, s));
+    GKO_TRY_CUDA(cudaStreamSynchronize(s));
+    *singular = (int64_t)h;
+  }
+  return GKO_OK;
+}
+
+}  // extern "C"

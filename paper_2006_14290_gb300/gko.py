@@ -43,7 +43,7 @@ class GkoError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("precision", C.c_int32), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int32), ("inner_maxit", C.c_int32), ("check_every", C.c_int32),
-                ("preconditioner", C.c_int32), ("refinement", C.c_int32), ("reserved", C.c_int32),
+                ("preconditioner", C.c_int32), ("refinement", C.c_int32), ("block_size", C.c_int32),
                 ("reliable_delta", C.c_double)]
 
 
@@ -94,6 +94,7 @@ SIGNATURES = {
     "gko_solve_cg": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "gko_solve_bicgstab": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "gko_solve_gmres": (C.c_int, [_P, _P, _P, _D, _I32, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "gko_block_jacobi_inverse": (C.c_int, [_P, _I32, _P, _PI64, _P]),
 }
 SIGNATURES.update({
     "gko_batch_create": (C.c_int, [_I32, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)]),
@@ -460,14 +461,25 @@ def gko_solve_gmres(A, b, x, rel_tol=1e-10, max_iters=10000, opts=None, stream=N
     return _solve("gko_solve_gmres", A, b, x, rel_tol, max_iters, opts, stream)
 
 
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_BLOCK_JACOBI = 0, 1, 2
+
+
+def gko_block_jacobi_inverse(A, block_size: int, B, stream=None) -> int:
+    """Inverse diagonal blocks of an FP64 CSR handle into the device array B
+    (n * block_size doubles, row i of its block's inverse at
+    B[i*block_size:(i+1)*block_size]); returns how many blocks were singular
+    (left as identity)."""
+    sing = C.c_int64()
+    _check(lib().gko_block_jacobi_inverse(A.handle, block_size, _dptr(B), C.byref(sing), _stream(stream)),
+           "gko_block_jacobi_inverse")
+    return int(sing.value)
 BATCH_CSR, BATCH_ELL = 0, 1
 
 
 def opts(restart=30, precision=PRECISION_F64, inner_tol=0.0, max_outer=0, inner_maxit=0, check_every=0,
-         preconditioner=PRECOND_NONE, refinement=REFINE_AUTO, reliable_delta=0.0):
+         preconditioner=PRECOND_NONE, refinement=REFINE_AUTO, reliable_delta=0.0, block_size=0):
     return SolveOpts(restart, precision, inner_tol, max_outer, inner_maxit, check_every, preconditioner,
-                     refinement, 0, reliable_delta)
+                     refinement, block_size, reliable_delta)
 
 
 def gko_device_status(stream=None):
