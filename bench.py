@@ -182,14 +182,17 @@ def traffic_record():
 
 # ----------------------------------------------------------------- solvers --
 
-def oracle_solver_sample(solver, A, b, iters, pc=False):
+def oracle_solver_sample(solver, A, b, iters, pc=False, bs=0):
     """The oracle's FP64 solve (as it stands: OpenMP over rows in its SpMV,
     vector operations sequential) run for a bounded number of iterations
-    (tolerance 0 never stops early): ms per iteration on the host cores."""
+    (tolerance 0 never stops early): ms per iteration on the host cores.
+    bs > 0: block-Jacobi with blocks of bs rows (its setup inside the time)."""
     import oracle as O
 
     t0 = time.perf_counter()
-    if pc:
+    if bs:
+        _, r = O.solve_block_jacobi(solver, A, b, bs, tol=0.0, maxit=iters)
+    elif pc:
         _, r = O.solve_jacobi(solver, A, b, tol=0.0, maxit=iters)
     else:
         _, r = O.solve(solver, A, b, tol=0.0, maxit=iters)
@@ -342,12 +345,12 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     if flush is not None:
         out["cfg1_laplace64"] = cfg1_suite(G, dev, stream, flush, oracle_cores or (os.cpu_count() or 1))
 
-    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0, refine=0):
+    def run(tag, solver, M, bd, n, nnz, prec, maxit=20000, tol=1e-8, restart=30, pc=0, refine=0, bs=0):
         fn = {"cg": G.gko_solve_cg, "bicgstab": G.gko_solve_bicgstab, "gmres": G.gko_solve_gmres}[solver]
         if solver == "bicgstab":
             maxit = 2000
         # the library's refinement defaults (GMRES: one restart cycle per step)
-        opts = G.opts(precision=prec, restart=restart, preconditioner=pc, refinement=refine)
+        opts = G.opts(precision=prec, restart=restart, preconditioner=pc, refinement=refine, block_size=bs)
         if tag == "bicgstab_convdiff128_mixed_f32":  # known not to converge: keep it short
             opts = G.opts(precision=prec, inner_maxit=500, max_outer=3)
             maxit = 500
@@ -365,7 +368,10 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
         ms = e0.elapsed_time(e1)
         sv = 8 if prec == G.PRECISION_F64 else (4 if prec == G.PRECISION_MIXED_F32 else 2)
         vb = 8 if prec == G.PRECISION_F64 else 4
-        per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver] + (2 if pc else 0)
+        # Jacobi: d and z = d r; block-Jacobi: r, z and bs FP64 block entries per row
+        bjac = pc == G.PRECOND_BLOCK_JACOBI
+        per_vec_passes = {"cg": 10, "bicgstab": 16, "gmres": 2 * 30 + 6}[solver]
+        per_vec_passes += (2 + bs) if bjac else 2 if pc else 0
         spmvs = {"cg": 1, "bicgstab": 2, "gmres": 1}[solver]
         it_bytes = spmvs * (nnz * (sv + 4) + 4 * (n + 1) + 2 * vb * n) + per_vec_passes * vb * n
         its = max(res.iterations, 1)
@@ -379,9 +385,9 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
             # p.q and r.r dots; BiCGSTAB p (2), s, x (2), r updates and five
             # dots; GMRES(30) both Gram-Schmidt passes (a dot and an axpy
             # per basis vector each, mean j + 1 = 15.5) and the norm;
-            # Jacobi: z = d r and r.z
+            # Jacobi: z = d r and r.z; block-Jacobi: bs per row for z and r.z
             fma_it = {"cg": nnz + 5 * n, "bicgstab": 2 * nnz + 12 * n, "gmres": nnz + 63 * n}[solver]
-            fma_it += 2 * n if pc else 0
+            fma_it += (bs + 1) * n if bjac else 2 * n if pc else 0
             t_fp64, t_hbm = fma_it / fp64_fma, it_bytes / (hbm_peak * 1e9)
             out[tag].update({"fp64_fmas_per_iteration": int(fma_it),
                              "frac_fp64": round(fma_it * its / (ms * 1e-3) / fp64_fma, 4),
@@ -389,17 +395,18 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
                              "frac_of_bound": round(max(t_fp64, t_hbm) * its / (ms * 1e-3), 4)})
         return ms
 
-    def oracle_beside(tags, solver, A, b, sample_iters, pc=False, fp64_tag=None):
+    def oracle_beside(tags, solver, A, b, sample_iters, pc=False, fp64_tag=None, bs=0):
         """Oracle FP64 solve of the same problem on a bounded sample; each tag
         gets oracle_ms = ms per iteration x the FP64 GPU run's iterations."""
         if not oracle_cores:
             return
         sid = {"cg": O.CG, "bicgstab": O.BICGSTAB, "gmres": O.GMRES}[solver]
-        per_it, done = oracle_solver_sample(sid, A, b, sample_iters, pc=pc)
+        per_it, done = oracle_solver_sample(sid, A, b, sample_iters, pc=pc, bs=bs)
         its = out[fp64_tag or tags[0]]["iterations"]
+        pcname = f" + block-Jacobi({bs})" if bs else " + Jacobi" if pc else ""
         for t in tags:
             out[t]["oracle_ms"] = round(per_it * its, 1)
-            out[t]["oracle_sample"] = (f"oracle FP64 {solver}{' + Jacobi' if pc else ''}: {done} iterations timed "
+            out[t]["oracle_sample"] = (f"oracle FP64 {solver}{pcname}: {done} iterations timed "
                                        f"({per_it:.2f} ms each, {oracle_cores} threads in its SpMV), "
                                        f"x {its} iterations of the GPU FP64 run")
 
@@ -484,12 +491,16 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     run("cg_varcoef128_f64", "cg", M, bd, n, nnz, G.PRECISION_F64)
     run("cg_varcoef128_jacobi_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_JACOBI)
     run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
+    # block-Jacobi: blocks of 8 consecutive rows (x-line segments of the grid)
+    run("cg_varcoef128_bjacobi8_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_BLOCK_JACOBI, bs=8)
     out["cg_varcoef128_jacobi_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_f64")
     out["cg_varcoef128_jacobi_mixed_f32_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_mixed_f32")
+    out["cg_varcoef128_bjacobi8_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_bjacobi8_f64")
     if oracle_cores:
         b_host = bd.cpu().numpy()
         oracle_beside(["cg_varcoef128_f64"], "cg", A, b_host, 12)
         oracle_beside(["cg_varcoef128_jacobi_f64", "cg_varcoef128_jacobi_mixed_f32"], "cg", A, b_host, 12, pc=True)
+        oracle_beside(["cg_varcoef128_bjacobi8_f64"], "cg", A, b_host, 12, bs=8)
         del b_host
     del A, M, ones, bd
     out["batched_cg"] = batched_suite(G, dev, stream, oracle_cores, fp64_fma)
