@@ -80,6 +80,10 @@ _SIGS = {
     "or_jacobi_inv": (None, [_I64, _P, _P, _P, _P]),
     "or_block_jacobi_inv": (_I64, [_I64, _P, _P, _P, _I32, _P]),
     "or_solve_bj": (C.c_int, [C.c_int, _I64, _P, _P, _P, _I32, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
+    "or_solve_ir_bj": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _I32, _P, _P, _P, _D, _I32, _D, _I32, _I32,
+                                 C.POINTER(_Result)]),
+    "or_solve_reliable_bj": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _I32, _P, _I32, _P, _P, _D, _I32, _D,
+                                       C.POINTER(_Result)]),
     "or_batch_cg": (None, [_I32, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _P, _P, _P]),
     "or_solve_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _D, _I32, C.POINTER(_Result)]),
     "or_solve_ir_pc": (C.c_int, [C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _I32, _I32,
@@ -367,16 +371,21 @@ def gmres(A, b, **kw):
 
 
 def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
-             inner_maxit=1000, restart=30, jacobi=False, adaptive=False):
+             inner_maxit=1000, restart=30, jacobi=False, adaptive=False, block_size=0):
     """Mixed-precision iterative refinement (FP32-stored inner solve, FP64
     outer); each inner solve reduces the residual by inner_tol (adaptive: by
     max(inner_tol, min(0.5, 0.5 tol ||b|| / ||r||)), the library's tunable);
-    jacobi: the inner CG / BiCGSTAB is Jacobi preconditioned."""
+    jacobi: the inner CG / BiCGSTAB is Jacobi preconditioned; block_size > 0:
+    block-Jacobi with blocks of that size (inverse blocks rounded to FP32)."""
     rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
     val32 = val.astype(np.float32)
     x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     res = _Result()
-    if jacobi:
+    if block_size:
+        B, _ = block_jacobi_inv(A, block_size)
+        lib().or_solve_ir_bj(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), block_size, _p(B), _p(b),
+                             _p(x), tol, max_outer, inner_tol, inner_maxit, int(adaptive), C.byref(res))
+    elif jacobi:
         minv = jacobi_inv(A)
         lib().or_solve_ir_pc(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32), _p(minv), _p(b), _p(x),
                              tol, max_outer, inner_tol, inner_maxit, int(adaptive), C.byref(res))
@@ -386,16 +395,26 @@ def solve_ir(solver: int, A, b, x0=None, tol=1e-8, max_outer=30, inner_tol=1e-4,
     return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
 
 
-def solve_reliable(solver: int, A, b, x0=None, tol=1e-8, maxit=5000, delta=0.1, f32=True, jacobi=False):
+def solve_reliable(solver: int, A, b, x0=None, tol=1e-8, maxit=5000, delta=0.1, f32=True, jacobi=False,
+                   block_size=0):
     """CG / BiCGSTAB with reliable updates: recurrences on FP32 values with
     FP32-stored vectors (f32=False: the FP64 matrix and FP64 vectors), the
     partial solution folded into the FP64 x and the recurrence residual
     replaced by the FP64 residual b - A x whenever the recurrence residual
     meets tol ||b|| or drops below delta times its largest value since the
-    last update.  outer_iterations counts the updates.  Returns (x,
+    last update.  outer_iterations counts the updates.  jacobi / block_size
+    > 0: Jacobi / block-Jacobi preconditioned recurrences.  Returns (x,
     SolveResult)."""
     rp, col, val, b = _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(b)
     val32 = val.astype(np.float32) if f32 else None
+    if block_size:
+        B, _ = block_jacobi_inv(A, block_size)
+        x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        res = _Result()
+        lib().or_solve_reliable_bj(solver, A.n_rows, _p(rp), _p(col), _p(val), _p(val32) if f32 else None,
+                                   block_size, _p(B), int(bool(f32)), _p(b), _p(x), tol, maxit, delta,
+                                   C.byref(res))
+        return x, SolveResult(res.status, res.iterations, res.outer_iterations, res.rel_residual)
     minv = jacobi_inv(A) if jacobi else None
     x = np.zeros(A.n_rows) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     res = _Result()

@@ -896,15 +896,15 @@ void or_batch_cg(int32_t count, const int64_t *row_off, const int64_t *nnz_off, 
  * 0.5 tol ||b|| / ||r||)) ||r||, the library's adaptive tunable); x += d in
  * FP64 }. */
 static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-                    const float *val32, const double *minv, const double *b, double *x, double tol,
-                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, int adaptive,
-                    or_result *out);
+                    const float *val32, const double *minv, const double *bj, int32_t bs, const double *b,
+                    double *x, double tol, int32_t max_outer, double inner_tol, int32_t inner_maxit,
+                    int32_t restart, int adaptive, or_result *out);
 
 int or_solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                 const float *val32, const double *b, double *x, double tol, int32_t max_outer,
                 double inner_tol, int32_t inner_maxit, int32_t restart, int32_t adaptive, or_result *out) {
-  return solve_ir(solver, n, rp, col, val, val32, NULL, b, x, tol, max_outer, inner_tol, inner_maxit, restart,
-                  adaptive, out);
+  return solve_ir(solver, n, rp, col, val, val32, NULL, NULL, 0, b, x, tol, max_outer, inner_tol, inner_maxit,
+                  restart, adaptive, out);
 }
 
 /* Mixed-precision refinement whose inner CG / BiCGSTAB is Jacobi
@@ -918,23 +918,43 @@ int or_solve_ir_pc(int solver, int64_t n, const int32_t *rp, const int32_t *col,
     *out = bad;
     return OR_INVALID;
   }
-  return solve_ir(solver, n, rp, col, val, val32, minv, b, x, tol, max_outer, inner_tol, inner_maxit, 0, adaptive,
-                  out);
+  return solve_ir(solver, n, rp, col, val, val32, minv, NULL, 0, b, x, tol, max_outer, inner_tol, inner_maxit, 0,
+                  adaptive, out);
+}
+
+/* Mixed-precision refinement whose inner CG / BiCGSTAB is block-Jacobi
+ * preconditioned with the FP64 inverse blocks (or_block_jacobi_inv) rounded
+ * to FP32. */
+int or_solve_ir_bj(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   const float *val32, int32_t bs, const double *B, const double *b, double *x, double tol,
+                   int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t adaptive, or_result *out) {
+  if ((solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) || bs < 1) {
+    or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+    *out = bad;
+    return OR_INVALID;
+  }
+  return solve_ir(solver, n, rp, col, val, val32, NULL, B, bs, b, x, tol, max_outer, inner_tol, inner_maxit, 0,
+                  adaptive, out);
+}
+
+/* fl32 copy of a preconditioner array (as doubles), or NULL */
+static double *round32_copy(const double *a, int64_t count) {
+  if (!a) return NULL;
+  double *m = calloc((size_t)count + 1, 8);
+  for (int64_t i = 0; i < count; ++i) m[i] = (double)(float)a[i];
+  return m;
 }
 
 static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-                    const float *val32, const double *minv, const double *b, double *x, double tol,
-                    int32_t max_outer, double inner_tol, int32_t inner_maxit, int32_t restart, int adaptive,
-                    or_result *out) {
+                    const float *val32, const double *minv, const double *bj, int32_t bs, const double *b,
+                    double *x, double tol, int32_t max_outer, double inner_tol, int32_t inner_maxit,
+                    int32_t restart, int adaptive, or_result *out) {
   or_op A64 = {n, rp, col, val, NULL};
   or_op A32 = {n, rp, col, NULL, val32};
   size_t sz = (size_t)n + 1;
-  double *minv32 = NULL;
-  if (minv) {
-    minv32 = calloc(sz, 8);
-    for (int64_t i = 0; i < n; ++i) minv32[i] = (double)(float)minv[i];
-  }
-  or_ctx inner = {&A32, 1, 0, NULL, 0, minv32};
+  double *minv32 = round32_copy(minv, n);
+  double *bj32 = round32_copy(bj, n * (int64_t)bs);
+  or_ctx inner = {&A32, 1, 0, NULL, 0, minv32, bj32, bs};
   or_result res = {OR_OK, 0, 0, 0, 0.0};
   double *r = calloc(sz, 8), *d = calloc(sz, 8), *tmp = calloc(sz, 8);
   double nb = nrm2(n, b);
@@ -979,6 +999,7 @@ static int solve_ir(int solver, int64_t n, const int32_t *rp, const int32_t *col
   free(d);
   free(tmp);
   free(minv32);
+  free(bj32);
   *out = res;
   return res.status;
 }
@@ -1198,6 +1219,25 @@ int or_solve_reliable(int solver, int64_t n, const int32_t *rp, const int32_t *c
     for (int64_t i = 0; i < n; ++i) m[i] = st(f32, minv[i]);
   }
   or_ctx c = {&Ain, f32 != 0, 0, NULL, 0, m};
+  *out = reliable_core(&c, &A64, solver, b, x, tol, maxit, delta);
+  free(m);
+  return out->status;
+}
+
+/* The same with block-Jacobi: B, bs from or_block_jacobi_inv, rounded to
+ * FP32 for the recurrences when f32 is set. */
+int or_solve_reliable_bj(int solver, int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                         const float *val32, int32_t bs, const double *B, int32_t f32, const double *b, double *x,
+                         double tol, int32_t maxit, double delta, or_result *out) {
+  if ((solver != OR_SOLVER_CG && solver != OR_SOLVER_BICGSTAB) || bs < 1) {
+    or_result bad = {OR_INVALID, 0, 0, 0, 0.0};
+    *out = bad;
+    return OR_INVALID;
+  }
+  or_op A64 = {n, rp, col, val, NULL};
+  or_op Ain = {n, rp, col, val32 ? NULL : val, val32};
+  double *m = f32 ? round32_copy(B, n * (int64_t)bs) : NULL;
+  or_ctx c = {&Ain, f32 != 0, 0, NULL, 0, NULL, f32 ? m : B, bs};
   *out = reliable_core(&c, &A64, solver, b, x, tol, maxit, delta);
   free(m);
   return out->status;

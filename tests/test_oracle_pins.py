@@ -681,6 +681,54 @@ def test_block_jacobi_solves_badly_scaled_systems(solver, bs):
     assert r1.iterations < 0.5 * r0.iterations, (r1.iterations, r0.iterations)
 
 
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_block_jacobi_mixed_size_one_is_mixed_jacobi(solver):
+    """With blocks of one row the FP32-rounded inverse blocks are the FP32
+    Jacobi inverse, so the mixed solves (restarted refinement and reliable
+    updates) repeat the Jacobi ones bit for bit."""
+    rng = np.random.default_rng(17)
+    A = I.varcoef3d_7pt(6, rng) if solver == "cg" else I.convdiff3d_7pt(6, 2.0)
+    b = rng.uniform(-1, 1, A.n_rows)
+    which = O.CG if solver == "cg" else O.BICGSTAB
+    x1, r1 = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, jacobi=True)
+    x2, r2 = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, block_size=1)
+    assert (r1.iterations, r1.outer_iterations) == (r2.iterations, r2.outer_iterations)
+    np.testing.assert_array_equal(x1, x2)
+    x1, r1 = O.solve_reliable(which, A, b, tol=1e-12, jacobi=True)
+    x2, r2 = O.solve_reliable(which, A, b, tol=1e-12, block_size=1)
+    assert (r1.iterations, r1.outer_iterations) == (r2.iterations, r2.outer_iterations)
+    np.testing.assert_array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("solver,bs", [("cg", 4), ("cg", 16), ("bicgstab", 8)])
+def test_block_jacobi_mixed_reaches_fp64_accuracy(solver, bs):
+    """FP32 recurrences preconditioned by FP32-rounded inverse blocks: the
+    FP64 refinement (restarted, and by reliable updates) still reaches FP64
+    tolerances and the dense solution; the reliable-update solve with the FP64
+    operator, FP64 storage and delta = 0 is the FP64 block-Jacobi solve."""
+    rng = np.random.default_rng(19)
+    A = scaled_copy(I.laplace2d_5pt(13) if solver == "cg" else I.convdiff3d_7pt(6, 2.0), rng)
+    b = rng.uniform(-1, 1, A.n_rows)
+    xd = np.linalg.solve(dense(A), b)
+    which = O.CG if solver == "cg" else O.BICGSTAB
+    x, r = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, inner_maxit=5000, block_size=bs)
+    assert r.status == 0 and r.rel_residual <= 1e-10 and r.outer_iterations >= 2
+    assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+    x, r = O.solve_reliable(which, A, b, tol=1e-12, maxit=5000, block_size=bs)
+    assert r.status == 0 and r.rel_residual <= 1e-12 and r.outer_iterations >= 1
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    x1, r1 = O.solve_reliable(which, A, b, tol=1e-10, maxit=5000, delta=0.0, f32=False, block_size=bs)
+    x2, r2 = O.solve_block_jacobi(which, A, b, bs, tol=1e-10, maxit=5000)
+    assert r1.iterations == r2.iterations
+    np.testing.assert_array_equal(x1, x2)
+
+
+def scaled_copy(A, rng, spread=2.0):
+    s = np.exp(rng.uniform(-spread, spread, A.n_rows))
+    rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
+    return I.Csr(A.n_rows, A.n_cols, A.row_ptr.copy(), A.col.copy(), A.val * s[rows] * s[A.col])
+
+
 def test_block_jacobi_gmres_and_bad_block_size_refused():
     A = I.laplace2d_5pt(4)
     x, r = O.solve_block_jacobi(O.GMRES, A, np.ones(16), 4)
