@@ -493,14 +493,18 @@ def solver_suite(G, dev, stream, flush=None, oracle_cores=0):
     run("cg_varcoef128_jacobi_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_JACOBI)
     # block-Jacobi: blocks of 8 consecutive rows (x-line segments of the grid)
     run("cg_varcoef128_bjacobi8_f64", "cg", M, bd, n, nnz, G.PRECISION_F64, pc=G.PRECOND_BLOCK_JACOBI, bs=8)
+    run("cg_varcoef128_bjacobi8_mixed_f32", "cg", M, bd, n, nnz, G.PRECISION_MIXED_F32, pc=G.PRECOND_BLOCK_JACOBI,
+        bs=8)
     out["cg_varcoef128_jacobi_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_f64")
     out["cg_varcoef128_jacobi_mixed_f32_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_jacobi_mixed_f32")
     out["cg_varcoef128_bjacobi8_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_bjacobi8_f64")
+    out["cg_varcoef128_bjacobi8_mixed_f32_speedup"] = speedup("cg_varcoef128_f64", "cg_varcoef128_bjacobi8_mixed_f32")
     if oracle_cores:
         b_host = bd.cpu().numpy()
         oracle_beside(["cg_varcoef128_f64"], "cg", A, b_host, 12)
         oracle_beside(["cg_varcoef128_jacobi_f64", "cg_varcoef128_jacobi_mixed_f32"], "cg", A, b_host, 12, pc=True)
-        oracle_beside(["cg_varcoef128_bjacobi8_f64"], "cg", A, b_host, 12, bs=8)
+        oracle_beside(["cg_varcoef128_bjacobi8_f64", "cg_varcoef128_bjacobi8_mixed_f32"], "cg", A, b_host, 12,
+                      bs=8)
         del b_host
     del A, M, ones, bd
     out["batched_cg"] = batched_suite(G, dev, stream, oracle_cores, fp64_fma)

@@ -325,10 +325,12 @@ GKO_API int gko_spmv_dot(gko_matrix A, const double *x, double *y, double *resul
  * opts->block_size consecutive rows (the last one n % block_size rows when
  * the size does not divide n), each inverted once per solve by Gauss-Jordan
  * elimination with partial pivoting (as gko_block_jacobi_inverse); CG and
- * BiCGSTAB use it as JACOBI uses diag(A).  FP64 precision and a CSR matrix
- * only (otherwise GKO_NOT_SUPPORTED); a block whose elimination meets an
- * all-zero pivot column leaves its rows unscaled, as a zero diagonal does
- * for JACOBI.  Extra device memory: n * block_size doubles. */
+ * BiCGSTAB use it as JACOBI uses diag(A); mixed-precision recurrences apply
+ * the inverse blocks rounded to FP32.  A CSR matrix only (otherwise
+ * GKO_NOT_SUPPORTED); a block whose elimination meets an all-zero pivot
+ * column leaves its rows unscaled, as a zero diagonal does for JACOBI.
+ * Extra device memory: n * block_size doubles (and as many floats for
+ * mixed precision). */
 #define GKO_PRECOND_NONE 0
 #define GKO_PRECOND_JACOBI 1
 #define GKO_PRECOND_BLOCK_JACOBI 2

@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(256, 4) dot2_kernel(int64_t n, const T* __rest
 
 // z = M^-1 v for block-Jacobi (M = the diagonal blocks of A, Saad Sec.
 // 12.2): z_i = sum_j B[i*bs + j] v[base + j] over the nb rows of i's block
-// (base = i - i % bs), accumulated in FP64 and stored as T; B from
-// block_jacobi_inverse.  z2 (nullable) also receives z.  With a reducing
+// (base = i - i % bs), accumulated in T (FP64 solves: the inverse blocks of
+// block_jacobi_inverse; FP32 recurrences: their FP32 rounding, FP32 FMAs).  z2 (nullable) also receives z.  With a reducing
 // Op, v.z is reduced into it.  gate: skip while its words are set (the
 // iteration kernels); need (nullable): skip unless *need is set (the
 // residual replacement after a true-residual check).  Op = NoOp: no
@@ -307,7 +307,7 @@ struct BjReplaceOp {
 };
 
 template <typename T, typename Op>
-__global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, const double* __restrict__ B,
+__global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, const T* __restrict__ B,
                                                        const T* __restrict__ v, T* __restrict__ z,
                                                        T* __restrict__ z2, RedWs ws, Op op, const int* gate,
                                                        const int* need) {
@@ -315,14 +315,29 @@ __global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, con
   pdl_begin();
   if (gated(gate)) return;
   if (need && !*(volatile const int*)need) return;
+  constexpr int VN = Vec16<T>::N;
+  // Blocks of a power-of-two size start at i & -bs; blocks whose size is a
+  // multiple of VN read their B row and the block of v with 16-byte loads
+  // (the row and the block start 16-byte aligned: B and v are 256-byte
+  // aligned allocations), the same FMAs in the same order.
+  const bool pow2 = (bs & (bs - 1)) == 0;
+  const bool vec = bs % VN == 0 && al16(B) && al16(v);
   double acc[1] = {0.0};
   GKO_GRID_LOOP(i, n) {
-    const int64_t base = (int64_t)((int32_t)i / bs) * bs;
+    const int64_t base = pow2 ? (i & ~(int64_t)(bs - 1)) : (int64_t)((int32_t)i / bs) * bs;
     const int nb = (int)(n - base < bs ? n - base : bs);
-    const double* Bi = B + i * bs;
-    double sum = 0.0;
-    for (int j = 0; j < nb; ++j) sum = __fma_rn(Bi[j], wd(v[base + j]), sum);
-    const T zi = (T)sum;
+    const T* Bi = B + i * bs;
+    T sum = T(0);
+    if (vec && nb == bs) {
+      for (int j = 0; j < bs; j += VN) {
+        const Vec16<T> bv = vload(Bi + j), xv = vload(v + base + j);
+#pragma unroll
+        for (int k = 0; k < VN; ++k) sum = madd(bv.v[k], xv.v[k], sum);
+      }
+    } else {
+      for (int j = 0; j < nb; ++j) sum = madd(Bi[j], v[base + j], sum);
+    }
+    const T zi = sum;
     z[i] = zi;
     if (z2) z2[i] = zi;
     if (RED) acc[0] = __fma_rn(wd(v[i]), wd(zi), acc[0]);
@@ -1147,7 +1162,7 @@ struct SolveSpec {
   int check_every;
   const void* minv = nullptr;  // Jacobi inverse diagonal (vector of T), or none
   const RelSpec* rel = nullptr;  // reliable updates (FP32 recurrences only)
-  const double* bj = nullptr;  // block-Jacobi inverse blocks (FP64, n x bs), or none
+  const void* bj = nullptr;  // block-Jacobi inverse blocks (n x bs, of T), or none
   int bs = 0;                  // block-Jacobi block size
 };
 
@@ -1889,7 +1904,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
   const int m = std::max(1, sp.restart);
   const int nvec = sp.solver == 0 ? (sp.bj ? 4 : 3) : sp.solver == 1 ? 9 : (m + 2);
   const T* dinv = static_cast<const T*>(sp.minv);
-  const double* bj = sp.bj;  // block-Jacobi (FP64 solves only)
+  const T* bj = static_cast<const T*>(sp.bj);  // block-Jacobi inverse blocks
   const int bs = sp.bs;
   const size_t spmv_sb = spmv_scratch_bytes(A);
   const size_t bytes = 256 * 16 + sizeof(Ctl) + sizeof(double) * 3 * kDotSlots + 512 +
@@ -2046,7 +2061,12 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           rel_replace_kernel<T><<<rg, 256, 0, s>>>(n, rl.b64, rl.q64, dst, sp.solver == 1 ? rh : nullptr,
                                                    sp.solver == 0 ? dinv : nullptr, ws,
                                                    RelOp{c, sp.solver, half ? 1 : 0});
-          if (sp.solver == 0)
+          if (sp.solver == 0 && bj) {
+            // z = M^-1 t and rho_new = t.z for the replaced residual t
+            bj_apply_kernel<T, BjReplaceOp><<<rg, 256, 0, s>>>(n, bs, bj, q, zb, nullptr, ws, BjReplaceOp{c},
+                                                               nullptr, &c->replace);
+            cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, nullptr, zb);
+          } else if (sp.solver == 0)
             cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
           else if (half)
             bicg_restart_kernel<T><<<rg, 256, 0, s>>>(n, r, rh, p, v, q, c, ws);
@@ -2272,8 +2292,6 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
   const int bsize = o.block_size > 0 ? o.block_size : 8;
   if (bjac) {
     if (bsize > kBlockJacobiMax) return fail(GKO_INVALID_ARG, "block-Jacobi block size must lie in 1..32");
-    if (o.precision != GKO_PRECISION_F64)
-      return fail(GKO_NOT_SUPPORTED, "block-Jacobi preconditioning runs with FP64 precision");
     if (A->fmt != GKO_CSR) return fail(GKO_NOT_SUPPORTED, "the block-Jacobi setup reads a CSR matrix");
   }
   double nb = 0.0;
@@ -2286,9 +2304,12 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
     GKO_TRY(jacobi_inverse(A, d64, s));
     sp.minv = d64;
   }
-  Scratch bj_mem;  // block-Jacobi: n x bs inverse-block rows (FP64)
+  Scratch bj_mem;  // block-Jacobi: n x bs inverse-block rows (FP64), and their FP32 rounding
+  const size_t bj_count = bjac ? (size_t)n * bsize : 0;
+  const size_t bj32_off = ((sizeof(double) * bj_count + 255) / 256) * 256;
   if (bjac) {
-    GKO_TRY(bj_mem.get(sizeof(double) * (size_t)n * bsize + 512, s));
+    const bool mixed = o.precision != GKO_PRECISION_F64;
+    GKO_TRY(bj_mem.get(bj32_off + (mixed ? sizeof(float) * bj_count : 0) + 512, s));
     GKO_TRY(block_jacobi_inverse(A, bsize, bj_mem.as<double>(), nullptr, s));
     sp.bj = bj_mem.as<double>();
     sp.bs = bsize;
@@ -2323,6 +2344,11 @@ static int solve_entry(int solver, gko_matrix A, const double* b, double* x, dou
     float* d32 = pc_mem.as<float>(((sizeof(double) * (size_t)n + 255) / 256) * 256);
     GKO_TRY(narrow_to_f32(d64, d32, n, s));
     in.minv = d32;
+  }
+  if (bjac) {  // the inner recurrences apply the FP32-rounded inverse blocks
+    float* b32 = bj_mem.as<float>(bj32_off);
+    GKO_TRY(narrow_to_f32(bj_mem.as<double>(), b32, (int64_t)bj_count, s));
+    in.bj = b32;
   }
   in.rel_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
   // GMRES: at most 4 restart cycles per refinement step by default.  An

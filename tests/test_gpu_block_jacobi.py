@@ -153,6 +153,36 @@ def test_block_jacobi_block_diagonal_system_one_step(gko, name):
     np.testing.assert_allclose(xg, np.linalg.solve(D, b), rtol=1e-11, atol=1e-12)
 
 
+@pytest.mark.parametrize("name,bs,refine", [("cg", 8, "restart"), ("cg", 8, "reliable"), ("cg", 32, "reliable"),
+                                            ("bicgstab", 4, "restart"), ("bicgstab", 4, "reliable")])
+def test_block_jacobi_mixed_precision_matches_oracle(gko, name, bs, refine):
+    """Mixed precision with the FP32-rounded inverse blocks in the FP32
+    recurrences: restarted refinement (the library's adaptive inner
+    tolerance) and reliable updates against the oracle's same schemes."""
+    G = gko
+    A = scaled(I.laplace2d_5pt(41) if name == "cg" else I.convdiff3d_7pt(11, 3.0), spread=2.0)
+    b = O.spmv_csr(A, np.ones(A.n_rows))
+    which = O.CG if name == "cg" else O.BICGSTAB
+    M = G.from_csr(A)
+    if refine == "restart":
+        xo, ro = O.solve_ir(which, A, b, tol=1e-10, inner_tol=1e-5, inner_maxit=5000, adaptive=True,
+                            block_size=bs)
+        xg, rg = solve(G, name, M, b, 1e-10, 5000, precision=G.PRECISION_MIXED_F32, inner_tol=1e-5,
+                       inner_maxit=5000, preconditioner=G.PRECOND_BLOCK_JACOBI, block_size=bs,
+                       refinement=G.REFINE_RESTART)
+        assert abs(rg.outer_iterations - ro.outer_iterations) <= 1, (rg, ro)
+    else:
+        xo, ro = O.solve_reliable(which, A, b, tol=1e-12, maxit=5000, delta=0.1, block_size=bs)
+        xg, rg = solve(G, name, M, b, 1e-12, 5000, precision=G.PRECISION_MIXED_F32,
+                       preconditioner=G.PRECOND_BLOCK_JACOBI, block_size=bs, refinement=G.REFINE_RELIABLE)
+        assert abs(rg.iterations - ro.iterations) <= max(3, 0.15 * ro.iterations), (rg, ro)
+    tol = 1e-10 if refine == "restart" else 1e-12
+    assert ro.status == 0 and rg.status == G.OK, (ro, rg)
+    assert rg.rel_residual <= tol
+    assert np.linalg.norm(b - O.spmv_csr(A, xg)) <= 1.01 * tol * np.linalg.norm(b)
+    assert np.linalg.norm(xg - np.ones(A.n_rows)) <= 1e-6 * np.sqrt(A.n_rows)
+
+
 def test_block_jacobi_refusals(gko):
     G = gko
     A = I.laplace2d_5pt(8)
@@ -162,7 +192,6 @@ def test_block_jacobi_refusals(gko):
     cases = [
         (G.gko_solve_gmres, M, G.opts(preconditioner=bj), G.NOT_SUPPORTED),
         (G.gko_solve_cg, M, G.opts(preconditioner=bj, block_size=33), G.INVALID_ARG),
-        (G.gko_solve_cg, M, G.opts(preconditioner=bj, precision=G.PRECISION_MIXED_F32), G.NOT_SUPPORTED),
         (G.gko_solve_bicgstab, G.gko_matrix_convert_to_ell(M), G.opts(preconditioner=bj), G.NOT_SUPPORTED),
     ]
     for fn, H, o, want in cases:
