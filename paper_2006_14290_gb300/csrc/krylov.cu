@@ -306,7 +306,10 @@ struct BjReplaceOp {
   __device__ void operator()(const double (&t)[1]) const { c->rho_new = t[0]; }
 };
 
-template <typename T, typename Op>
+// BS > 0: the block size as a compile-time constant (rows of full blocks
+// then issue all their loads before the first FMA, and each thread takes
+// two rows per trip); BS = 0: any block size.
+template <typename T, typename Op, int BS = 0>
 __global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, const T* __restrict__ B,
                                                        const T* __restrict__ v, T* __restrict__ z,
                                                        T* __restrict__ z2, RedWs ws, Op op, const int* gate,
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, con
   if (gated(gate)) return;
   if (need && !*(volatile const int*)need) return;
   constexpr int VN = Vec16<T>::N;
+  if (BS) bs = BS;
   // Blocks of a power-of-two size start at i & -bs; blocks whose size is a
   // multiple of VN read their B row and the block of v with 16-byte loads
   // (the row and the block start 16-byte aligned: B and v are 256-byte
@@ -323,26 +327,73 @@ __global__ void __launch_bounds__(256, 4) bj_apply_kernel(int64_t n, int bs, con
   const bool pow2 = (bs & (bs - 1)) == 0;
   const bool vec = bs % VN == 0 && al16(B) && al16(v);
   double acc[1] = {0.0};
-  GKO_GRID_LOOP(i, n) {
+  auto row_sum = [&](int64_t i) -> T {
     const int64_t base = pow2 ? (i & ~(int64_t)(bs - 1)) : (int64_t)((int32_t)i / bs) * bs;
     const int nb = (int)(n - base < bs ? n - base : bs);
     const T* Bi = B + i * bs;
     T sum = T(0);
     if (vec && nb == bs) {
-      for (int j = 0; j < bs; j += VN) {
-        const Vec16<T> bv = vload(Bi + j), xv = vload(v + base + j);
+      if constexpr (BS > 0 && BS % VN == 0) {
+        Vec16<T> bv[BS / VN], xv[BS / VN];
 #pragma unroll
-        for (int k = 0; k < VN; ++k) sum = madd(bv.v[k], xv.v[k], sum);
+        for (int j = 0; j < BS / VN; ++j) {
+          bv[j] = vload(Bi + j * VN);
+          xv[j] = vload(v + base + j * VN);
+        }
+#pragma unroll
+        for (int j = 0; j < BS / VN; ++j)
+#pragma unroll
+          for (int k = 0; k < VN; ++k) sum = madd(bv[j].v[k], xv[j].v[k], sum);
+      } else {
+        for (int j = 0; j < bs; j += VN) {
+          const Vec16<T> bv = vload(Bi + j), xv = vload(v + base + j);
+#pragma unroll
+          for (int k = 0; k < VN; ++k) sum = madd(bv.v[k], xv.v[k], sum);
+        }
       }
     } else {
       for (int j = 0; j < nb; ++j) sum = madd(Bi[j], v[base + j], sum);
     }
-    const T zi = sum;
+    return sum;
+  };
+  auto finish = [&](int64_t i, T zi) {
     z[i] = zi;
     if (z2) z2[i] = zi;
     if (RED) acc[0] = __fma_rn(wd(v[i]), wd(zi), acc[0]);
+  };
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if constexpr (BS > 0) {
+    for (; i + nth < n; i += 2 * nth) {  // rows in the same order as the loop below
+      const T z0 = row_sum(i), z1 = row_sum(i + nth);
+      finish(i, z0);
+      finish(i + nth, z1);
+    }
   }
+  for (; i < n; i += nth) finish(i, row_sum(i));
   if constexpr (RED) reduce_op<1>(acc, ws, op);
+}
+
+// Launch of bj_apply_kernel with the block size as a template argument
+// where it is a common one (FP64 up to 8, FP32 up to 16: the row's B and v
+// values stay in registers), else the general kernel.
+template <typename T, typename Op>
+static cudaError_t bj_launch(dim3 grid, cudaStream_t s, int64_t n, int bs, const T* B, const T* v, T* z, T* z2,
+                             RedWs ws, Op op, const int* gate, const int* need) {
+  const dim3 blk(256);
+  switch (bs) {
+    case 4:
+      return launch_k(bj_apply_kernel<T, Op, 4>, grid, blk, 0, s, n, bs, B, v, z, z2, ws, op, gate, need);
+    case 8:
+      return launch_k(bj_apply_kernel<T, Op, 8>, grid, blk, 0, s, n, bs, B, v, z, z2, ws, op, gate, need);
+    case 16:
+      if constexpr (sizeof(T) == 4)
+        return launch_k(bj_apply_kernel<T, Op, 16>, grid, blk, 0, s, n, bs, B, v, z, z2, ws, op, gate, need);
+      break;
+    default:
+      break;
+  }
+  return launch_k(bj_apply_kernel<T, Op, 0>, grid, blk, 0, s, n, bs, B, v, z, z2, ws, op, gate, need);
 }
 
 // Reliable-update test after a step with recurrence residual norm nr (mixed
@@ -1965,7 +2016,7 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
       // z = M^-1 r, p = z, rho = r.z
       init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, nullptr, nullptr, nullptr, nullptr,
                                                  ws, InitOp{c, sp.rel_tol, 0});
-      bj_apply_kernel<T, BjInitOp><<<rg, 256, 0, s>>>(n, bs, bj, r, zb, p, ws, BjInitOp{c}, &c->done, nullptr);
+      GKO_TRY_CUDA(bj_launch<T>(dim3(rg), s, n, bs, bj, (const T*)r, zb, p, ws, BjInitOp{c}, &c->done, nullptr));
     } else if (sp.solver == 0)
       init_residual_kernel<T><<<rg, 256, 0, s>>>(n, b, x_zero ? nullptr : q, r, p, nullptr, nullptr, nullptr, ws,
                                                  InitOp{c, sp.rel_tol, 0}, dinv);
@@ -1992,8 +2043,8 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           if (bj) {
             GKO_TRY_CUDA(launch_k(cg_update_kernel<T, false, true>, dim3(rg), B256, 0, s, n, x, r, p, q, c, ws,
                                   (const T*)nullptr));
-            GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, BjStepOp>, dim3(rg), B256, 0, s, n, bs, bj, (const T*)r, zb,
-                                  (T*)nullptr, ws, BjStepOp{c}, (const int*)&c->done, (const int*)nullptr));
+            GKO_TRY_CUDA(bj_launch<T>(dim3(rg), s, n, bs, bj, (const T*)r, zb, (T*)nullptr, ws, BjStepOp{c},
+                                      (const int*)&c->done, (const int*)nullptr));
             GKO_TRY_CUDA(launch_k(cg_p_kernel<T, false>, dim3(vg), B256, 0, s, n, (const T*)zb, p, c,
                                   (const T*)nullptr));
           } else if (dinv) {
@@ -2008,13 +2059,13 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
           // right preconditioned: ph = M^-1 p, sh = M^-1 s
           GKO_TRY_CUDA(launch_k(bicg_p_kernel<T>, dim3(vg), B256, 0, s, n, (const T*)r, p, (const T*)v, c,
                                 (const T*)nullptr, (T*)nullptr));
-          GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, NoOp>, dim3(vg), B256, 0, s, n, bs, bj, (const T*)p, ph,
-                                (T*)nullptr, ws, NoOp{}, (const int*)&c->done, (const int*)nullptr));
+          GKO_TRY_CUDA(bj_launch<T>(dim3(vg), s, n, bs, bj, (const T*)p, ph, (T*)nullptr, ws, NoOp{},
+                                    (const int*)&c->done, (const int*)nullptr));
           GKO_TRY(spmv(ph, v, rh, &c->done));
           GKO_TRY_CUDA(launch_k(bicg_s_kernel<T>, dim3(rg), B256, 0, s, n, (const T*)r, (const T*)v, sv, c, ws,
                                 (const T*)nullptr, (T*)nullptr));
-          GKO_TRY_CUDA(launch_k(bj_apply_kernel<T, NoOp>, dim3(vg), B256, 0, s, n, bs, bj, (const T*)sv, sh,
-                                (T*)nullptr, ws, NoOp{}, (const int*)&c->phase, (const int*)nullptr));
+          GKO_TRY_CUDA(bj_launch<T>(dim3(vg), s, n, bs, bj, (const T*)sv, sh, (T*)nullptr, ws, NoOp{},
+                                    (const int*)&c->phase, (const int*)nullptr));
           GKO_TRY(spmv(sh, tv, sv, &c->phase, true));
           GKO_TRY_CUDA(launch_k(bicg_x_kernel<T>, dim3(rg), B256, 0, s, n, x, (const T*)p, (const T*)sv,
                                 (const T*)tv, r, (const T*)rh, c, ws, (const T*)ph, (const T*)sh));
@@ -2063,8 +2114,8 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
                                                    RelOp{c, sp.solver, half ? 1 : 0});
           if (sp.solver == 0 && bj) {
             // z = M^-1 t and rho_new = t.z for the replaced residual t
-            bj_apply_kernel<T, BjReplaceOp><<<rg, 256, 0, s>>>(n, bs, bj, q, zb, nullptr, ws, BjReplaceOp{c},
-                                                               nullptr, &c->replace);
+            GKO_TRY_CUDA(bj_launch<T>(dim3(rg), s, n, bs, bj, (const T*)q, zb, (T*)nullptr, ws, BjReplaceOp{c},
+                                      (const int*)nullptr, (const int*)&c->replace));
             cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, nullptr, zb);
           } else if (sp.solver == 0)
             cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
@@ -2079,8 +2130,8 @@ static int krylov_core(const gko_matrix_s* A, const double* b, T* x, bool x_zero
         true_res_kernel<T><<<rg, 256, 0, s>>>(n, b, q, ws, TrueResOp{c}, sp.solver == 0 ? dinv : nullptr);
         if (sp.solver == 0 && bj) {
           // z = M^-1 t and rho_new = t.z for the replaced residual t
-          bj_apply_kernel<T, BjReplaceOp><<<rg, 256, 0, s>>>(n, bs, bj, q, zb, nullptr, ws, BjReplaceOp{c}, nullptr,
-                                                             &c->replace);
+          GKO_TRY_CUDA(bj_launch<T>(dim3(rg), s, n, bs, bj, (const T*)q, zb, (T*)nullptr, ws, BjReplaceOp{c},
+                                    (const int*)nullptr, (const int*)&c->replace));
           cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, nullptr, zb);
         } else if (sp.solver == 0)
           cg_replace_kernel<T><<<rg, 256, 0, s>>>(n, r, p, q, c, ws, dinv);
