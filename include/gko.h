@@ -403,9 +403,9 @@ GKO_API int gko_solve_gmres(gko_matrix A, const double *b, double *x, double rel
  * k*block_size + nb - 1, nb = min(block_size, n - k*block_size); each is
  * gathered densely (entries of a row summed in storage order) and inverted
  * by Gauss-Jordan elimination on [D | I] with partial pivoting (pivot: the
- * first row of largest magnitude in the column; the pivot row divided by the
- * pivot; every other row r becomes row_r - m_r row_k, each product and
- * difference rounded separately).  B: device array of n * block_size
+ * first row of largest magnitude in the column; the pivot row multiplied by
+ * the reciprocal of the pivot; every other row r becomes row_r - m_r row_k,
+ * each product and difference rounded separately).  B: device array of n * block_size
  * doubles, written with row i of its block's inverse at B[i*block_size ..
  * i*block_size + nb - 1] and zeros after it.  A block whose pivot column is
  * all zero at some step gets identity rows; *singular (host, nullable)

@@ -450,9 +450,10 @@ void or_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const doubl
  * block may be smaller).  Each block is gathered densely (entries of a row
  * summed in storage order, so duplicates add up as in the SpMV) and inverted
  * by Gauss-Jordan elimination on [D | I] with partial pivoting (pivot: the
- * first row of largest magnitude in the column; the pivot row divided by
- * the pivot, then every other row r takes row_r - m_r * row_k with m_r its
- * entry in the pivot column).  A block whose pivot column is all zero at
+ * first row of largest magnitude in the column; the pivot row multiplied
+ * by the reciprocal of the pivot, one division per step, as Golub & Van
+ * Loan scale it; then every other row r takes row_r - m_r * row_k with m_r
+ * its entry in the pivot column).  A block whose pivot column is all zero at
  * some step is singular and is replaced by the identity (its rows are left
  * unscaled, as a zero diagonal is for Jacobi).  Output: row i of the inverse
  * at B[i*bs .. i*bs + nb - 1], zeros in B[i*bs + nb .. i*bs + bs - 1].
@@ -488,8 +489,8 @@ int64_t or_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, co
           M[k * w + c] = M[piv * w + c];
           M[piv * w + c] = t;
         }
-      const double d = M[k * w + k];
-      for (int64_t c = 0; c < w; ++c) M[k * w + c] = M[k * w + c] / d;
+      const double inv = 1.0 / M[k * w + k];
+      for (int64_t c = 0; c < w; ++c) M[k * w + c] = M[k * w + c] * inv;
       for (int64_t r = 0; r < nb; ++r) {
         if (r == k) continue;
         const double m = M[r * w + k];

@@ -90,11 +90,16 @@ __global__ void narrow_kernel(int64_t n, const double* __restrict__ d, float* __
 // Block-Jacobi setup (M = the diagonal blocks of A, Saad Sec. 12.2): one
 // warp per block of nb = min(bs, n - base) rows, the augmented [D | I] in
 // shared memory (row stride 2 bs), Gauss-Jordan elimination with partial
-// pivoting (the first row of largest magnitude; the pivot row divided by the
-// pivot; every other row r takes row_r - m_r row_k, products and
-// differences rounded separately, never fused).  Lane L holds columns L and
-// L + 32.  A block whose pivot column is all zero at some step is left
-// unscaled (identity rows) and counted in *singular.
+// pivoting: the first row of largest magnitude in the pivot column, the
+// pivot row multiplied by the reciprocal of the pivot (one division per
+// step), then every other row r takes row_r - m_r row_k, products and
+// differences rounded separately, never fused.  The pivot search and the
+// row swap run over lanes = rows / columns; the elimination spreads all nb x
+// 2 nb entries over the 32 lanes, with the multipliers m_r (the pivot
+// column before the step) staged in shared memory first, so each entry gets
+// exactly the operations of the sequential elimination.  A block whose
+// pivot column is all zero at some step is left unscaled (identity rows)
+// and counted in *singular.
 __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, double* __restrict__ B,
                                 unsigned long long* singular) {
@@ -102,7 +107,8 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
   const int lane = threadIdx.x & 31;
   const int wpc = blockDim.x >> 5;
   const int ST = 2 * bs;
-  double* M = bj_smem + (size_t)(threadIdx.x >> 5) * bs * ST;
+  double* M = bj_smem + (size_t)(threadIdx.x >> 5) * (bs * ST + bs);
+  double* mk = M + bs * ST;  // multipliers of the current step
   const int64_t blocks = (n + bs - 1) / bs;
   for (int64_t blk = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); blk < blocks; blk += (int64_t)gridDim.x * wpc) {
     const int64_t base = blk * bs;
@@ -146,17 +152,16 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
           M[idx * ST + c] = t;
         }
       __syncwarp();
-      const double d = M[k * ST + k];
+      const double inv = 1.0 / M[k * ST + k];
       __syncwarp();
-      for (int c = lane; c < w; c += 32) M[k * ST + c] = M[k * ST + c] / d;
+      for (int c = lane; c < w; c += 32) M[k * ST + c] = __dmul_rn(M[k * ST + c], inv);
+      if (lane < nb) mk[lane] = M[lane * ST + k];
       __syncwarp();
-      for (int r = 0; r < nb; ++r) {
-        if (r == k) continue;
-        const double m = M[r * ST + k];
-        __syncwarp();
-        for (int c = lane; c < w; c += 32) M[r * ST + c] = __dsub_rn(M[r * ST + c], __dmul_rn(m, M[k * ST + c]));
-        __syncwarp();
+      for (int e = lane; e < nb * w; e += 32) {
+        const int r = e / w, c = e - r * w;
+        if (r != k) M[r * ST + c] = __dsub_rn(M[r * ST + c], __dmul_rn(mk[r], M[k * ST + c]));
       }
+      __syncwarp();
     }
     for (int r = 0; r < nb; ++r)
       for (int j = lane; j < bs; j += 32)
@@ -176,8 +181,8 @@ int block_jacobi_inverse(const gko_matrix_s* A, int bs, double* B, unsigned long
   if (bs < 1 || bs > kBlockJacobiMax) return fail(GKO_INVALID_ARG, "block-Jacobi block size must lie in 1..32");
   const int64_t n = A->n_rows;
   if (n == 0) return GKO_OK;
-  const int wpc = bs > 16 ? 2 : 4;  // warps per block: at most 32 KB of shared memory
-  const size_t smem = sizeof(double) * (size_t)wpc * bs * 2 * bs;
+  const int wpc = bs > 16 ? 2 : 4;  // warps per block: at most 33 KB of shared memory
+  const size_t smem = sizeof(double) * (size_t)wpc * (bs * 2 * bs + bs);
   const int64_t blocks = (n + bs - 1) / bs;
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>((blocks + wpc - 1) / wpc, (int64_t)sm_count() * 32));
   bj_setup_kernel<<<(unsigned)g, 32 * wpc, smem, s>>>(n, bs, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col),
