@@ -940,13 +940,41 @@ def profile_solvers(args):
     128^3, tolerance 0: BiCGSTAB FP64 (40 iterations, cell Peclet 1),
     BiCGSTAB mixed FP32 (one refinement step of 40 inner iterations, Peclet 1)
     and GMRES(30) FP64 (one restart cycle, Peclet 10); each runs once
-    untimed, then once inside the NVTX range "profile_solvers"."""
+    untimed, then once inside the NVTX range "profile_solvers".  With
+    --precond instead: CG on the variable-coefficient Poisson problem 128^3,
+    40 iterations each of Jacobi mixed FP32, block-Jacobi (blocks of 8)
+    mixed FP32 and block-Jacobi FP64."""
     import torch
     from paper_2006_14290_gb300 import gko as G
     from paper_2006_14290_gb300 import inputs as I
 
     G.load()
     out = {}
+    if args.precond:
+        A = I.varcoef3d_7pt(128, np.random.default_rng(0))
+        M = G.from_csr(A)
+        ones = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+        bd = torch.zeros_like(ones)
+        G.gko_spmv(1.0, M, ones, 0.0, bd)
+        runs = (("jacobi_mixed_f32", G.PRECOND_JACOBI, G.PRECISION_MIXED_F32),
+                ("bjacobi8_mixed_f32", G.PRECOND_BLOCK_JACOBI, G.PRECISION_MIXED_F32),
+                ("bjacobi8_f64", G.PRECOND_BLOCK_JACOBI, G.PRECISION_F64))
+        for tag, pc, prec in runs:
+            o = G.opts(precision=prec, preconditioner=pc, block_size=8)
+            for rep in range(2):
+                x = torch.zeros_like(ones)
+                torch.cuda.synchronize()
+                if rep == 1:
+                    torch.cuda.nvtx.range_push("profile_solvers")
+                t0 = time.perf_counter()
+                r = G.gko_solve_cg(M, bd, x, 0.0, 40, o)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if rep == 1:
+                    torch.cuda.nvtx.range_pop()
+            out[tag] = {"n": int(A.n_rows), "iterations": int(r.iterations), "ms": round(dt * 1e3, 3)}
+        print(json.dumps(out))
+        return
     runs = (("bicgstab", 1.0, 40, None), ("bicgstab_mixed_f32", 1.0, 40, G.PRECISION_MIXED_F32),
             ("gmres", 10.0, 30, None))
     for tag, P, iters, prec in runs:
@@ -1204,6 +1232,8 @@ def main():
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the batched CG once inside an NVTX range (for ncu)")
     ap.add_argument("--mixed", action="store_true", help="with --profile-batch: the mixed-precision batched CG")
+    ap.add_argument("--precond", action="store_true",
+                    help="with --profile-solvers: Jacobi and block-Jacobi CG on variable coefficients 128^3")
     ap.add_argument("--profile-solvers", action="store_true",
                     help="short BiCGSTAB and GMRES(30) solves at 128^3 inside an NVTX range (for ncu)")
     args = ap.parse_args()
