@@ -152,13 +152,21 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
           M[idx * ST + c] = t;
         }
       __syncwarp();
-      const double inv = 1.0 / M[k * ST + k];
-      __syncwarp();
-      for (int c = lane; c < w; c += 32) M[k * ST + c] = __dmul_rn(M[k * ST + c], inv);
+      // one division per step, by lane 0 (FP64 division is a long sequence
+      // on GB300's narrow FP64 pipe)
+      double inv = 0.0;
+      if (lane == 0) inv = 1.0 / M[k * ST + k];
+      inv = __shfl_sync(0xffffffffu, inv, 0);
+      // Columns 0..k of the left half are never read again after this step
+      // (later pivot searches and multipliers read columns above k), so only
+      // columns k+1 .. 2nb-1 are scaled and eliminated: the right half, the
+      // inverse, gets exactly the sequential elimination's operations.
+      const int c0 = k + 1, wc = w - c0;
+      for (int c = c0 + lane; c < w; c += 32) M[k * ST + c] = __dmul_rn(M[k * ST + c], inv);
       if (lane < nb) mk[lane] = M[lane * ST + k];
       __syncwarp();
-      for (int e = lane; e < nb * w; e += 32) {
-        const int r = e / w, c = e - r * w;
+      for (int e = lane; e < nb * wc; e += 32) {
+        const int r = e / wc, c = c0 + (e - r * wc);
         if (r != k) M[r * ST + c] = __dsub_rn(M[r * ST + c], __dmul_rn(mk[r], M[k * ST + c]));
       }
       __syncwarp();
