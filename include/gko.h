@@ -512,7 +512,7 @@ GKO_API int gko_batch_destroy(gko_batch B);
 /* Request loop with continuous batching over resident matrices.  `slots`
  * worker threads, each with its own CUDA stream on the current device, take
  * the oldest queued request as soon as a slot is free and its device-memory
- * estimate (b, x and solver workspace) fits in budget_bytes together with
+ * estimate (b, x, solver workspace and preconditioner) fits in budget_bytes together with
  * the resident matrices and the requests already running (budget_bytes = 0:
  * no limit).  Solves of different requests overlap on the GPU; each result
  * is the one the same call gives alone (deterministic kernels).  Mixed-

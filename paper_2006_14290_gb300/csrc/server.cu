@@ -71,13 +71,24 @@ struct gko_server_s {
 namespace {
 
 // Device bytes one request holds while it runs: b and x, the solver's
-// vectors (CG 4, BiCGSTAB 8, GMRES restart+3 of length n) and, for mixed
-// precision, the FP32 inner vectors.
+// vectors (CG 4, BiCGSTAB 8, GMRES restart+3 of length n; with a
+// preconditioner one more for CG's z and two for BiCGSTAB's preconditioned
+// directions), for mixed precision the FP32 inner vectors, and the
+// preconditioner itself (Jacobi: the inverse diagonal and its FP32
+// rounding; block-Jacobi: block_size inverse-block entries per row, FP64
+// and, for mixed precision, FP32).
 int64_t request_bytes(const Request& r, int64_t n) {
   const int restart = r.has_opts && r.opts.restart > 0 ? r.opts.restart : 30;
-  const int vecs = r.solver == 0 ? 4 : r.solver == 1 ? 8 : restart + 3;
+  const int pc = r.has_opts ? r.opts.preconditioner : GKO_PRECOND_NONE;
+  int vecs = r.solver == 0 ? 4 : r.solver == 1 ? 8 : restart + 3;
+  if (pc != GKO_PRECOND_NONE) vecs += r.solver == 0 ? 1 : 2;
   const bool mixed = r.has_opts && r.opts.precision != GKO_PRECISION_F64;
-  const int64_t per = mixed ? (int64_t)(vecs * 4 + 2 * 8 + 8) : (int64_t)(vecs * 8);
+  int64_t per = mixed ? (int64_t)(vecs * 4 + 2 * 8 + 8) : (int64_t)(vecs * 8);
+  if (pc == GKO_PRECOND_JACOBI) per += 8 + 4;
+  if (pc == GKO_PRECOND_BLOCK_JACOBI) {
+    const int bs = r.opts.block_size > 0 ? r.opts.block_size : 8;
+    per += (int64_t)bs * (mixed ? 12 : 8);
+  }
   return (per + 16) * n + (4 << 20);
 }
 
