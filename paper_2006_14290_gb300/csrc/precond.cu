@@ -89,7 +89,7 @@ __global__ void narrow_kernel(int64_t n, const double* __restrict__ d, float* __
 
 // Block-Jacobi setup (M = the diagonal blocks of A, Saad Sec. 12.2): one
 // warp per block of nb = min(bs, n - base) rows, the augmented [D | I] in
-// shared memory (row stride 2 bs), Gauss-Jordan elimination with partial
+// shared memory (row stride 2 bs + 1 doubles), Gauss-Jordan elimination with partial
 // pivoting: the first row of largest magnitude in the pivot column, the
 // pivot row multiplied by the reciprocal of the pivot (one division per
 // step), then every other row r takes row_r - m_r row_k, products and
@@ -106,7 +106,7 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
   extern __shared__ double bj_smem[];
   const int lane = threadIdx.x & 31;
   const int wpc = blockDim.x >> 5;
-  const int ST = 2 * bs;
+  const int ST = 2 * bs + 1;
   double* M = bj_smem + (size_t)(threadIdx.x >> 5) * (bs * ST + bs);
   double* mk = M + bs * ST;  // multipliers of the current step
   const int64_t blocks = (n + bs - 1) / bs;
@@ -126,11 +126,18 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
     __syncwarp();
     bool ok = true;
     for (int k = 0; k < nb; ++k) {
-      double a = (lane >= k && lane < nb) ? fabs(M[lane * ST + k]) : -1.0;
+      // Pivot search on the magnitudes' bit patterns: for non-negative
+      // doubles (not NaN) the unsigned 64-bit order is the numeric order, so
+      // the arg-max runs on the integer pipe instead of GB300's narrow FP64
+      // pipe (FP64 compares in this butterfly were most of the setup's FP64
+      // work).  Lanes outside rows k .. nb-1 offer 0.
+      constexpr unsigned long long kMag = ~(1ull << 63);
+      unsigned long long a =
+          (lane >= k && lane < nb) ? ((unsigned long long)__double_as_longlong(M[lane * ST + k]) & kMag) : 0ull;
       int idx = lane;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double oa = __shfl_xor_sync(0xffffffffu, a, off);
+        const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, off);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
         if (oa > a || (oa == a && oi < idx)) {
           a = oa;
@@ -138,10 +145,10 @@ __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ r
         }
       }
       // the butterfly leaves every lane with the same pivot; lane 0's copy
-      // and a vote keep the control flow warp-uniform even for NaN input
+      // and a vote keep the control flow warp-uniform
       a = __shfl_sync(0xffffffffu, a, 0);
       idx = __shfl_sync(0xffffffffu, idx, 0);
-      if (__any_sync(0xffffffffu, !(a > 0.0))) {
+      if (__any_sync(0xffffffffu, a == 0ull)) {
         ok = false;
         break;
       }
@@ -189,8 +196,8 @@ int block_jacobi_inverse(const gko_matrix_s* A, int bs, double* B, unsigned long
   if (bs < 1 || bs > kBlockJacobiMax) return fail(GKO_INVALID_ARG, "block-Jacobi block size must lie in 1..32");
   const int64_t n = A->n_rows;
   if (n == 0) return GKO_OK;
-  const int wpc = bs > 16 ? 2 : 4;  // warps per block: at most 33 KB of shared memory
-  const size_t smem = sizeof(double) * (size_t)wpc * (bs * 2 * bs + bs);
+  const int wpc = bs > 16 ? 2 : 4;  // warps per block: at most 34 KB of shared memory
+  const size_t smem = sizeof(double) * (size_t)wpc * (bs * (2 * bs + 1) + bs);
   const int64_t blocks = (n + bs - 1) / bs;
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>((blocks + wpc - 1) / wpc, (int64_t)sm_count() * 32));
   bj_setup_kernel<<<(unsigned)g, 32 * wpc, smem, s>>>(n, bs, ptr<int32_t>(A->row_ptr), ptr<int32_t>(A->col),
