@@ -54,6 +54,34 @@ def test_binding_matches_header():
     assert set(G.SIGNATURES) <= names
 
 
+def test_struct_layouts_match_the_binding(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's size
+    and field offsets (a renamed, reordered or retyped field would otherwise
+    pass garbage through the ABI)."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    structs = {"gko_solve_opts": G.SolveOpts, "gko_solve_result": G.SolveResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gko.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    r = subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout
+    got = dict(line.split() for line in out.splitlines() if line)
+    assert len(got) == sum(1 + len(py._fields_) for py in structs.values())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
 def test_host_only_calls_work_without_gpu(libpath):
     L = ctypes.CDLL(libpath)
     L.gko_status_string.restype = ctypes.c_char_p
