@@ -178,6 +178,11 @@ __device__ __forceinline__ void gsync() {
 // (q += r (a - b q)), after Markstein (IBM J. Res. Dev. 34, 1990).  Within an
 // ulp or so of the IEEE quotient for normal operands; b must be nonzero and
 // finite (the callers divide by a positive p.q or r.r).
+// A step flag broadcast as a double (exactly 1.0 or +0.0) tested on its bit
+// pattern: an integer compare instead of an FP64 one on the narrow FP64
+// pipe, executed by every thread of every iteration.
+__device__ __forceinline__ bool flag_on(double f) { return __double_as_longlong(f) != 0; }
+
 __device__ __forceinline__ double quick_div(double a, double b) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
@@ -260,7 +265,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
       o[0] = t > 0.0 ? 1.0 : 0.0;
       o[1] = t > 0.0 ? quick_div(rho, t) : 0.0;
     });
-    if (sp.o[0] == 0.0) {
+    if (!flag_on(sp.o[0])) {
       status = kBBreak;
       break;
     }
@@ -280,7 +285,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
     double rho_new = sr.o[0];
     double beta = sr.o[2];
     ++it;
-    if (sr.o[1] != 0.0) {
+    if (flag_on(sr.o[1])) {
       // true residual b - A x (x staged through q)
       gsync();
       for (int i = lane; i < n; i += G) q[i] = x[i];
@@ -298,7 +303,7 @@ __device__ void cg_group(const BatchArgs& a, int sys, double* r, double* p, doub
         o[3] = quick_div(t, rho);
       });
       res = st.o[0];
-      if (st.o[1] != 0.0) {
+      if (flag_on(st.o[1])) {
         status = kBOk;
         break;
       }
@@ -423,7 +428,7 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
       o[1] = la.pack();
       o[2] = Lin<float>(-la.hi, -la.lo).pack();  // the pair of -alpha (exact)
     });
-    if (sp.o[0] == 0.0) {
+    if (!flag_on(sp.o[0])) {
       status = kBBreak;
       break;
     }
@@ -447,7 +452,7 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
     double rho_new = sr.o[0];
     Lin<float> bp = Lin<float>::unpack(sr.o[2]);
     maxrr2 = sr.o[3];
-    if (sr.o[1] != 0.0) {  // reliable update
+    if (flag_on(sr.o[1])) {  // reliable update
       fold();
       const double tt = replace(rz);
       ++updates;
@@ -457,7 +462,7 @@ __device__ void cg_group_rel(const BatchArgs& a, int sys, float* r, float* p, fl
         o[2] = t;
       });
       res = st.o[0];
-      if (st.o[1] != 0.0) {
+      if (flag_on(st.o[1])) {
         status = kBOk;
         break;
       }
