@@ -94,10 +94,11 @@ __global__ void narrow_kernel(int64_t n, const double* __restrict__ d, float* __
 // pivot row multiplied by the reciprocal of the pivot (one division per
 // step), then every other row r takes row_r - m_r row_k, products and
 // differences rounded separately, never fused.  The pivot search and the
-// row swap run over lanes = rows / columns; the elimination spreads all nb x
-// 2 nb entries over the 32 lanes, with the multipliers m_r (the pivot
-// column before the step) staged in shared memory first, so each entry gets
-// exactly the operations of the sequential elimination.  A block whose
+// row swap run over lanes = rows / columns; the elimination spreads the
+// entries still read later (columns k+1 .. 2 nb - 1 of every row) over the
+// 32 lanes, with the multipliers m_r (the pivot column before the step)
+// staged in shared memory first, so each entry of the inverse gets exactly
+// the operations of the sequential elimination.  A block whose
 // pivot column is all zero at some step is left unscaled (identity rows)
 // and counted in *singular.
 __global__ void bj_setup_kernel(int64_t n, int bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
